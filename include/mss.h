@@ -1,0 +1,228 @@
+/*
+ * mss.h -- C-ABI of the multi-stage preconditioned FGMRES library for GB300
+ * (libmss.so, CUDA, sm_103a).
+ *
+ * Method: Cremon, Castelletto, White, "Multi-Stage Preconditioners for
+ * Thermal-Compositional-Reactive Flow in Porous Media" (arXiv:1912.04385).
+ * The library solves the primary (statically condensed) system A x = b of
+ * Sec. 3, Eq. reduced, by split preconditioning (Sec. 4, Eqs. splitPrec1 and
+ * splitPrec2): the left scaling N^{-1} (Eq. CPR for CPR, Eqs. CPTR31 and
+ * CPTR32 for CPTR3) is applied once, then right-preconditioned FGMRES
+ * (Sec. 5.1) applies the multi-stage operator M^{-1} of Eq. multistageprec in
+ * the form of Algorithm 1 (CPR) or Algorithm 2 (CPTR3) every iteration.
+ *
+ * Conventions shared by every entry point
+ *   - A is cell-blocked BSR: row_ptr[n_rows+1] and col_idx[nnzb] (int32,
+ *     columns strictly ascending within a row, diagonal block present,
+ *     pattern structurally symmetric as for any finite-volume cell graph),
+ *     vals[nnzb * nb * nb] (float64). Blocks are row-major unless
+ *     mss_layout.col_major_blocks is set. Vectors are cell-interleaved:
+ *     unknown k of cell i lives at i*nb + k.
+ *   - Every pointer argument named as "device" is device memory of the
+ *     current CUDA device; "host" pointers are ordinary host memory.
+ *     Caller-owned arrays are only read (inputs) or written (outputs), never
+ *     retained after the call returns unless stated.
+ *   - All device work is enqueued on the handle's stream. Calls that return
+ *     results to the host synchronise that stream.
+ *   - Every function returns an int status: MSS_OK (0) or a negative
+ *     MSS_ERR_* code; no exception crosses the ABI. mss_last_error() gives a
+ *     message for the last failing call on a handle.
+ */
+#ifndef MSS_H
+#define MSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define MSS_OK 0
+#define MSS_ERR_INVALID_ARG (-1)    /* bad size, pointer, pattern or option */
+#define MSS_ERR_SINGULAR_BLOCK (-2) /* zero pivot in a cell block (no pivoting, Sec. 3) */
+#define MSS_ERR_NOT_CONVERGED (-3)  /* maxit reached; x holds the last iterate */
+#define MSS_ERR_BREAKDOWN (-4)      /* non-finite value in the Krylov recurrence */
+#define MSS_ERR_CUDA (-5)           /* a CUDA runtime call failed */
+#define MSS_ERR_OOM (-6)            /* device allocation failed */
+#define MSS_ERR_AMG (-7)            /* AMG set-up failed (coarsest level too large, ...) */
+#define MSS_ERR_NOT_SETUP (-8)      /* handle has no set-up, or another matrix was passed */
+
+/* ---- option values ------------------------------------------------------ */
+enum { MSS_CPTR3 = 0, MSS_CPR = 1, MSS_ILU0 = 2 };   /* preconditioner scheme */
+enum { MSS_STAGE_T_FIRST = 0, MSS_STAGE_P_FIRST = 1 }; /* CPTR3 stage order */
+enum { MSS_BILU0 = 0, MSS_BLOCK_JACOBI = 1 };        /* last stage */
+enum { MSS_MULTICOLOR = 0 };                         /* block ILU(0) ordering */
+enum { MSS_JACOBI = 0, MSS_CHEBYSHEV = 1 };          /* AMG smoother */
+enum { MSS_FP64 = 0 };                               /* arithmetic */
+
+/* A BSR matrix; the arrays are device memory owned by the caller. */
+typedef struct {
+  int32_t n_rows;           /* number of cells N */
+  int32_t nnzb;             /* number of stored blocks */
+  const int32_t* row_ptr;   /* device, N + 1 entries, row_ptr[0] = 0 */
+  const int32_t* col_idx;   /* device, nnzb entries */
+  const double* vals;       /* device, nnzb * nb * nb entries */
+} mss_bsr;
+
+/* Position of pressure and temperature inside a cell block (the paper's
+ * [s, P, T] partition, Sec. 4; any order is accepted). */
+typedef struct {
+  int32_t p_idx;            /* index of the pressure unknown, 0 <= p_idx < nb */
+  int32_t t_idx;            /* index of the temperature unknown, != p_idx */
+  int32_t col_major_blocks; /* 1 if vals blocks are stored column-major */
+} mss_layout;
+
+typedef struct {
+  int32_t scheme;           /* MSS_CPTR3 (default) | MSS_CPR | MSS_ILU0 */
+  int32_t stage_order;      /* MSS_STAGE_T_FIRST (Algorithm 2, default) | P first */
+  int32_t stage3;           /* MSS_BILU0 (default) | MSS_BLOCK_JACOBI */
+  int32_t ilu_order;        /* MSS_MULTICOLOR */
+  int32_t smoother;         /* MSS_JACOBI (default) | MSS_CHEBYSHEV */
+  int32_t nu_pre, nu_post;  /* smoothing sweeps per V-cycle leg (1, 1) */
+  int32_t cheb_degree;      /* Chebyshev polynomial degree (2) */
+  int32_t amg_max_coarse;   /* direct solve at or below this size (1000, Sec. 5.1) */
+  int32_t amg_max_levels;   /* at most this many levels (25) */
+  int32_t interp_max_elems; /* interpolation row truncation, 0 = none (4) */
+  int32_t restart;          /* FGMRES restart length m (30) */
+  int32_t precision;        /* MSS_FP64 */
+  int32_t pad_;
+  double amg_theta;         /* strength threshold (0.25) */
+  double jacobi_omega;      /* Jacobi damping (2/3) */
+  double cheb_lo_ratio;     /* Chebyshev interval [bound/ratio, factor*bound] (30) */
+  double cheb_hi_factor;    /* (1.0) */
+  uint64_t seed;            /* PMIS measure and colouring priorities */
+  const void* learned_interp; /* reserved, must be NULL */
+} mss_options;
+
+typedef struct {
+  int32_t iters;            /* FGMRES inner iterations in total */
+  int32_t restarts;         /* completed restart cycles */
+  int32_t status;           /* same as the return value */
+  int32_t pad_;
+  double rel_res_implicit;  /* |g_{k+1}| / ||bbar|| from the Givens recurrence */
+  double rel_res_true;      /* ||bbar - Abar x|| / ||bbar|| at return */
+  double setup_ms;          /* wall time of the last mss_setup */
+  double solve_ms;          /* wall time of this solve */
+} mss_result;
+
+typedef struct mss_handle mss_handle;
+
+/* Device memory hooks. alloc returns device memory of at least `bytes`
+ * bytes (aligned to 256 bytes) or NULL; free releases it. Both are called
+ * only from mss_* calls on the host thread that makes them. Memory passed
+ * to free may still be in use by work already enqueued on the handle's
+ * stream, so the hooks must be stream-ordered on that stream (as a caching
+ * allocator bound to the stream is) or synchronous like cudaFree. */
+typedef void* (*mss_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*mss_free_fn)(void* ptr, void* ctx);
+
+/* Fill `opt` with the defaults listed above. Errors: INVALID_ARG if NULL. */
+int mss_options_default(mss_options* opt);
+
+/* Create a handle bound to the current CUDA device and `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream). alloc/free_fn may both be
+ * NULL, in which case cudaMalloc/cudaFree are used; the handle owns every
+ * buffer it allocates and frees it in mss_destroy. Errors: INVALID_ARG,
+ * OOM. */
+int mss_create(mss_handle** h, void* cuda_stream, mss_alloc_fn alloc, mss_free_fn free_fn,
+               void* alloc_ctx);
+
+/* Release the handle and everything it owns (NULL is ignored). */
+void mss_destroy(mss_handle* h);
+
+/* Set-up for the matrix J (Sec. 4): validates the pattern; builds the cell
+ * scaling W_i = N^{-1} restricted to cell i from the diagonal block
+ * (Eq. CPR, or Eqs. CPTR31 and CPTR32; identity for MSS_ILU0) and the scaled
+ * blocks Abar_ij = W_i J_ij (Eq. splitPrec1); extracts B_PP and C_TT
+ * (Eqs. CPR, CPTR31, CPTR32) and builds an AMG hierarchy for each
+ * (Eqs. CPRM1, CPTR3M1, CPTRM2; classical AMG, coarse size <= 1000, Sec.
+ * 5.1); and factors the last stage, block ILU(0) of Abar (Eq. CPTR3M3) in a
+ * multicolour ordering. J's arrays are copied or consumed during the call;
+ * the caller may free them afterwards, except that mss_fgmres_solve checks
+ * that it receives the same mss_bsr (pointers and sizes). `opt` may be NULL
+ * (defaults). nb in [2, 8] (CPTR3 needs nb >= 2). Errors: INVALID_ARG (bad
+ * sizes, pattern, layout or option), SINGULAR_BLOCK (a cell block needs
+ * pivoting), AMG, OOM, CUDA. */
+int mss_setup(mss_handle* h, const mss_bsr* J, int nb, mss_layout layout,
+              const mss_options* opt);
+
+/* bbar = N^{-1} b (Eq. splitPrec1), device vectors of length N*nb.
+ * Errors: NOT_SETUP, INVALID_ARG. */
+int mss_scale_rhs(mss_handle* h, const double* b, double* bbar);
+
+/* y = Abar x for the scaled matrix (the FGMRES matrix-vector product),
+ * device vectors of length N*nb. Errors: NOT_SETUP, INVALID_ARG. */
+int mss_spmv(mss_handle* h, const double* x, double* y);
+
+/* y = M^{-1} r on the scaled system: Algorithm 2 for CPTR3, Algorithm 1
+ * for CPR, the last stage alone for MSS_ILU0. r, y: device, length N*nb,
+ * distinct. Errors: NOT_SETUP, INVALID_ARG. */
+int mss_apply(mss_handle* h, const double* r, double* y);
+
+/* One stage operator alone, for testing the composition of Eq.
+ * multistageprec: which = 0 temperature AMG stage (Eq. CPTR3M1), 1 pressure
+ * AMG stage (Eq. CPTRM2 / CPRM1), 2 last stage (block ILU(0) or block
+ * Jacobi of Abar). The result is zero outside the stage's unknowns.
+ * Errors: NOT_SETUP, INVALID_ARG (stage absent in the scheme). */
+int mss_stage_apply(mss_handle* h, int which, const double* r, double* y);
+
+/* Solve A x = b: bbar = N^{-1} b, then right-preconditioned restarted
+ * FGMRES(m) on Abar from x = 0 (Sec. 5.1; restart is a reading) until the
+ * implicit residual |g|/||bbar|| <= tol and the true residual
+ * ||bbar - Abar x||/||bbar|| <= tol, or maxit inner iterations. J must be
+ * the mss_bsr passed to mss_setup. b, x: device, length N*nb; x is written
+ * with the last iterate even on NOT_CONVERGED. `out` (host, may be NULL)
+ * receives iteration counts, residuals and timings. Synchronises the
+ * stream. Errors: NOT_SETUP, INVALID_ARG, NOT_CONVERGED, BREAKDOWN, CUDA. */
+int mss_fgmres_solve(mss_handle* h, const mss_bsr* J, const double* b, double* x, double tol,
+                     int maxit, mss_result* out);
+
+/* End-to-end solve from HOST buffers: copies J (host arrays in an mss_bsr)
+ * and b to the device, runs mss_setup and mss_fgmres_solve, and copies x
+ * back to the host. Device copies are owned by the handle and released at
+ * the next call or in mss_destroy. Errors: as mss_setup and
+ * mss_fgmres_solve. */
+int mss_solve_host(mss_handle* h, const mss_bsr* J_host, int nb, mss_layout layout,
+                   const mss_options* opt, const double* b_host, double* x_host, double tol,
+                   int maxit, mss_result* out);
+
+/* ---- introspection (tests) --------------------------------------------- */
+/* Copy the scaled blocks Abar (device, nnzb*nb*nb, row-major) into `abar`
+ * (device, caller-owned). */
+int mss_get_scaled(mss_handle* h, double* abar);
+
+/* Number of AMG levels of stage `which` (0 = C_TT, 1 = B_PP); 0 if the
+ * scheme has no such stage. */
+int mss_amg_num_levels(mss_handle* h, int which);
+
+/* sizes[0] = rows, sizes[1] = nnz(A_l), sizes[2] = nnz(P_l) (0 on the
+ * coarsest level); host array of 3. */
+int mss_amg_level_sizes(mss_handle* h, int which, int level, int32_t* sizes);
+
+/* Copy level `level` of stage `which` into caller-owned device arrays sized
+ * from mss_amg_level_sizes: A_l (rp, ci, v), the C/F split (1 = C), and the
+ * interpolation P_l (rp, ci, v). cf and P are not written on the coarsest
+ * level. */
+int mss_amg_level_copy(mss_handle* h, int which, int level, int32_t* arp, int32_t* aci,
+                       double* av, int32_t* cf, int32_t* prp, int32_t* pci, double* pv);
+
+/* Number of colours of the block ILU(0) ordering (host int). */
+int mss_bilu_num_colours(mss_handle* h, int32_t* ncolours);
+
+/* Copy the cell colours and the ordering (perm[k] = cell at position k)
+ * into caller-owned device arrays of N entries. */
+int mss_bilu_ordering(mss_handle* h, int32_t* colour, int32_t* perm);
+
+/* Human-readable name of a status code (static string). */
+const char* mss_status_string(int status);
+
+/* Message for the last failing call on `h` (valid until the next call). */
+const char* mss_last_error(const mss_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSS_H */

@@ -1,0 +1,548 @@
+// amg_setup.cu -- classical AMG set-up on the device (Sec. 5.1: classical
+// AMG, coarse size <= max_coarse; coarsening read as PMIS).
+//
+// Per level: sign-aware strength of connection, PMIS C/F splitting with a
+// SplitMix64 measure, direct classical interpolation with strong-F
+// distribution and row truncation, R = P^T, and the Galerkin product
+// A_c = R (A P) by a two-pass row-wise SpGEMM.
+//
+// Compiled with -fmad=false, and every floating-point reduction runs in the
+// order the method defines it (ascending columns, ascending inner index), so
+// the strength tests -- floating point deciding an index -- take the same
+// decisions as the FP64 definition.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace mss {
+
+void coarse_inverse(Handle* h, Hierarchy& H);   // amg_cycle.cu
+
+namespace {
+
+enum { ST_F = 0, ST_C = 1, ST_U = -1 };
+
+__device__ __forceinline__ double unit53(uint64_t h) {
+  return (double)(h >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// j strong for i  <=>  -sgn(a_ii) a_ij >= theta * max_{k != i}(-sgn(a_ii) a_ik) > 0
+__global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ v, double theta,
+                           unsigned char* __restrict__ strong, int* __restrict__ scount) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  double aii = 0.0;
+  for (int k = b; k < e; ++k)
+    if (ci[k] == i) aii = v[k];
+  double sg = aii < 0.0 ? 1.0 : -1.0;
+  double mx = -INFINITY;
+  for (int k = b; k < e; ++k)
+    if (ci[k] != i) {
+      double val = sg * v[k];
+      if (val > mx) mx = val;
+    }
+  double thr = theta * mx;
+  int cnt = 0;
+  for (int k = b; k < e; ++k) {
+    unsigned char s = (ci[k] != i && mx > 0.0 && sg * v[k] >= thr) ? 1 : 0;
+    strong[k] = s;
+    cnt += s;
+  }
+  scount[i] = cnt;
+}
+
+__global__ void k_fill_strong(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const unsigned char* __restrict__ strong,
+                              const int* __restrict__ srp, int* __restrict__ sci) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int q = srp[i];
+  for (int k = rp[i]; k < rp[i + 1]; ++k)
+    if (strong[k]) sci[q++] = ci[k];
+}
+
+__global__ void k_count_cols(int nnz, const int* __restrict__ ci, int* __restrict__ cnt) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnz) atomicAdd(&cnt[ci[e]], 1);
+}
+
+// scatter of a CSR pattern (and optional values) into its transpose; the
+// order inside a transposed row is fixed afterwards by k_sort_rows
+__global__ void k_fill_transpose(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                 const double* __restrict__ v, int* __restrict__ fill,
+                                 int* __restrict__ tci, double* __restrict__ tv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    int pos = atomicAdd(&fill[ci[k]], 1);
+    tci[pos] = i;
+    if (v) tv[pos] = v[k];
+  }
+}
+
+__global__ void k_sort_rows(int n, const int* __restrict__ rp, int* __restrict__ ci,
+                            double* __restrict__ v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  for (int a = b + 1; a < e; ++a) {
+    int c = ci[a];
+    double x = v ? v[a] : 0.0;
+    int q = a - 1;
+    while (q >= b && ci[q] > c) {
+      ci[q + 1] = ci[q];
+      if (v) v[q + 1] = v[q];
+      --q;
+    }
+    ci[q + 1] = c;
+    if (v) v[q + 1] = x;
+  }
+}
+
+__global__ void k_row_lengths(int n, const int* __restrict__ rp, int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = rp[i + 1] - rp[i];
+}
+
+__global__ void k_pmis_init(int n, const int* __restrict__ tcount, uint64_t seed, int level,
+                            double* __restrict__ lam, int* __restrict__ state,
+                            int* __restrict__ undecided) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t key = ((uint64_t)(unsigned)level << 32) | (uint64_t)(unsigned)i;
+  lam[i] = (double)tcount[i] + unit53(splitmix64(seed, key));
+  int st = tcount[i] == 0 ? ST_F : ST_U;
+  state[i] = st;
+  if (st == ST_U) atomicAdd(undecided, 1);
+}
+
+__device__ __forceinline__ bool beats(const double* lam, int a, int b) {
+  double la = lam[a], lb = lam[b];
+  return la > lb || (la == lb && a > b);
+}
+
+// an undecided point becomes C when its (measure, index) beats every
+// undecided strong neighbour in either direction
+__global__ void k_pmis_select(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                              const int* __restrict__ strp, const int* __restrict__ stci,
+                              const double* __restrict__ lam, const int* __restrict__ state,
+                              int* __restrict__ newc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int pick = 0;
+  if (state[i] == ST_U) {
+    pick = 1;
+    for (int k = srp[i]; k < srp[i + 1] && pick; ++k) {
+      int j = sci[k];
+      if (state[j] == ST_U && beats(lam, j, i)) pick = 0;
+    }
+    for (int k = strp[i]; k < strp[i + 1] && pick; ++k) {
+      int j = stci[k];
+      if (state[j] == ST_U && beats(lam, j, i)) pick = 0;
+    }
+  }
+  newc[i] = pick;
+}
+
+// new C points are fixed; undecided points depending strongly on one become F
+__global__ void k_pmis_update(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                              int* __restrict__ state, const int* __restrict__ newc,
+                              int* __restrict__ undecided) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (state[i] != ST_U) return;
+  if (newc[i]) {
+    state[i] = ST_C;
+    return;
+  }
+  for (int k = srp[i]; k < srp[i + 1]; ++k)
+    if (newc[sci[k]]) {
+      state[i] = ST_F;
+      return;
+    }
+  atomicAdd(undecided, 1);
+}
+
+// F points with strong dependencies but no strong C point become C
+__global__ void k_pmis_finalize(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                                const int* __restrict__ state, int* __restrict__ cf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int st = state[i];
+  int c = st == ST_C ? 1 : 0;
+  if (st == ST_F && srp[i + 1] > srp[i]) {
+    int hasc = 0;
+    for (int k = srp[i]; k < srp[i + 1]; ++k) hasc |= state[sci[k]] == ST_C;
+    c = !hasc;
+  }
+  cf[i] = c;
+}
+
+__device__ __forceinline__ bool opposite_sign(double akk, double akm) {
+  return akk < 0.0 ? akm > 0.0 : akm < 0.0;
+}
+
+// Direct classical interpolation with distribution of strong F couplings
+// (same formula and operation order as the FP64 definition). Row i's work
+// arrays live in the scratch segment [rp[i], rp[i+1]) of A's pattern.
+__global__ void k_interp(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                         const double* __restrict__ v, const unsigned char* __restrict__ strong,
+                         const int* __restrict__ cf, const int* __restrict__ cidx, int maxel,
+                         int* __restrict__ scr_ci, double* __restrict__ scr_v,
+                         int* __restrict__ scr_k, int* __restrict__ plen) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  int* cset = scr_ci + b;
+  double* num = scr_v + b;
+  int* keep = scr_k + b;
+  if (cf[i]) {
+    cset[0] = cidx[i];
+    num[0] = 1.0;
+    plen[i] = 1;
+    return;
+  }
+  int nC = 0;
+  double aii = 0.0;
+  for (int k = b; k < e; ++k) {
+    int j = ci[k];
+    if (j == i) aii = v[k];
+    else if (strong[k] && cf[j]) { cset[nC] = j; num[nC] = v[k]; ++nC; }
+  }
+  if (nC == 0) { plen[i] = 0; return; }
+  double d = aii;
+  for (int k = b; k < e; ++k) {
+    int j = ci[k];
+    if (j == i) continue;
+    if (strong[k] && cf[j]) continue;
+    if (strong[k] && !cf[j]) {
+      double aik = v[k];
+      double akk = 0.0;
+      for (int f = rp[j]; f < rp[j + 1]; ++f)
+        if (ci[f] == j) akk = v[f];
+      double sigma = 0.0;
+      for (int f = rp[j]; f < rp[j + 1]; ++f) {
+        int m = ci[f];
+        if (m == j) continue;
+        double akm = v[f];
+        bool inC = false;
+        for (int q = 0; q < nC; ++q) if (cset[q] == m) { inC = true; break; }
+        if (inC && opposite_sign(akk, akm)) sigma = sigma + akm;
+      }
+      if (sigma == 0.0) {
+        d = d + aik;
+      } else {
+        for (int f = rp[j]; f < rp[j + 1]; ++f) {
+          int m = ci[f];
+          if (m == j) continue;
+          double akm = v[f];
+          if (!opposite_sign(akk, akm)) continue;
+          for (int q = 0; q < nC; ++q)
+            if (cset[q] == m) {
+              double tq = aik * akm;
+              tq = tq / sigma;
+              num[q] = num[q] + tq;
+              break;
+            }
+        }
+      }
+    } else {
+      d = d + v[k];
+    }
+  }
+  if (d == 0.0 || !isfinite(d)) { plen[i] = 0; return; }
+  for (int q = 0; q < nC; ++q) num[q] = -num[q] / d;
+  for (int q = 0; q < nC; ++q) keep[q] = 1;
+  if (maxel > 0 && nC > maxel) {
+    double total = 0.0;
+    for (int q = 0; q < nC; ++q) total = total + num[q];
+    for (int q = 0; q < nC; ++q) keep[q] = 0;
+    for (int r = 0; r < maxel; ++r) {
+      int best = -1;
+      for (int q = 0; q < nC; ++q) {
+        if (keep[q]) continue;
+        if (best < 0 || fabs(num[q]) > fabs(num[best])) best = q;
+      }
+      keep[best] = 1;
+    }
+    double kept = 0.0;
+    for (int q = 0; q < nC; ++q) if (keep[q]) kept = kept + num[q];
+    if (kept != 0.0) {
+      double sc = total / kept;
+      for (int q = 0; q < nC; ++q) if (keep[q]) num[q] = num[q] * sc;
+    }
+  }
+  int len = 0;
+  for (int q = 0; q < nC; ++q)
+    if (keep[q]) {
+      cset[len] = cidx[cset[q]];
+      num[len] = num[q];
+      ++len;
+    }
+  plen[i] = len;
+}
+
+__global__ void k_seg_copy(int n, const int* __restrict__ src_off, const int* __restrict__ src_ci,
+                           const double* __restrict__ src_v, const int* __restrict__ dst_rp,
+                           int* __restrict__ dst_ci, double* __restrict__ dst_v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = src_off[i], d = dst_rp[i], len = dst_rp[i + 1] - dst_rp[i];
+  for (int k = 0; k < len; ++k) {
+    dst_ci[d + k] = src_ci[s + k];
+    dst_v[d + k] = src_v[s + k];
+  }
+}
+
+// ---- SpGEMM C = X Y, row by row ---------------------------------------------
+__global__ void k_spgemm_count(int n, const int* __restrict__ xrp, const int* __restrict__ xci,
+                               const int* __restrict__ yrp, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  for (int k = xrp[i]; k < xrp[i + 1]; ++k) {
+    int r = xci[k];
+    c += yrp[r + 1] - yrp[r];
+  }
+  cnt[i] = c;
+}
+
+// contributions x_ik y_kj accumulate in ascending k, then ascending j in row
+// k; the row is kept sorted by column in its scratch segment
+__global__ void k_spgemm_accum(int n, const int* __restrict__ xrp, const int* __restrict__ xci,
+                               const double* __restrict__ xv, const int* __restrict__ yrp,
+                               const int* __restrict__ yci, const double* __restrict__ yv,
+                               const int* __restrict__ off, int* __restrict__ sc_ci,
+                               double* __restrict__ sc_v, int* __restrict__ ulen) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int* cc = sc_ci + off[i];
+  double* cv = sc_v + off[i];
+  int cnt = 0;
+  for (int k = xrp[i]; k < xrp[i + 1]; ++k) {
+    int r = xci[k];
+    double x = xv[k];
+    for (int f = yrp[r]; f < yrp[r + 1]; ++f) {
+      int j = yci[f];
+      double prod = x * yv[f];
+      int lo = 0, hi = cnt;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (cc[mid] < j) lo = mid + 1; else hi = mid;
+      }
+      if (lo < cnt && cc[lo] == j) {
+        cv[lo] = cv[lo] + prod;
+      } else {
+        for (int q = cnt; q > lo; --q) {
+          cc[q] = cc[q - 1];
+          cv[q] = cv[q - 1];
+        }
+        cc[lo] = j;
+        cv[lo] = 0.0 + prod;
+        ++cnt;
+      }
+    }
+  }
+  ulen[i] = cnt;
+}
+
+// 1 / a_ii and the Gershgorin bound max_i sum_j |a_ij| / |a_ii|
+__global__ void k_dinv_bound(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const double* __restrict__ v, double* __restrict__ dinv,
+                             unsigned long long* __restrict__ bound, int* __restrict__ bad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double aii = 0.0;
+  double s = 0.0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    if (ci[k] == i) aii = v[k];
+    s = s + fabs(v[k]);
+  }
+  if (aii == 0.0 || !isfinite(aii)) {
+    atomicMin(bad, i);
+    dinv[i] = 0.0;
+    return;
+  }
+  double di = 1.0 / aii;
+  dinv[i] = di;
+  s = s * fabs(di);
+  atomicMax(bound, (unsigned long long)__double_as_longlong(s));
+}
+
+void sparse_product(Handle* h, int n, const int* xrp, const int* xci, const double* xv,
+                    const int* yrp, const int* yci, const double* yv, DBuf<int>& crp,
+                    DBuf<int>& cci, DBuf<double>& cv, int& cnnz) {
+  DBuf<int> cnt(h, n), off(h, n + 1), ulen(h, n);
+  k_spgemm_count<<<grid_for(n, 128), 128, 0, h->stream>>>(n, xrp, xci, yrp, cnt.p);
+  MSS_LAUNCH_CK("k_spgemm_count");
+  exclusive_scan(h, cnt.p, off.p, n);
+  int tot = read_int(h, off.p + n);
+  DBuf<int> sc_ci(h, tot > 0 ? tot : 1);
+  DBuf<double> sc_v(h, tot > 0 ? tot : 1);
+  k_spgemm_accum<<<grid_for(n, 128), 128, 0, h->stream>>>(n, xrp, xci, xv, yrp, yci, yv, off.p,
+                                                          sc_ci.p, sc_v.p, ulen.p);
+  MSS_LAUNCH_CK("k_spgemm_accum");
+  crp.reset(h, n + 1);
+  exclusive_scan(h, ulen.p, crp.p, n);
+  cnnz = read_int(h, crp.p + n);
+  cci.reset(h, cnnz > 0 ? cnnz : 1);
+  cv.reset(h, cnnz > 0 ? cnnz : 1);
+  k_seg_copy<<<grid_for(n, 128), 128, 0, h->stream>>>(n, off.p, sc_ci.p, sc_v.p, crp.p, cci.p,
+                                                      cv.p);
+  MSS_LAUNCH_CK("k_seg_copy");
+}
+
+void transpose(Handle* h, int n, int m, const int* rp, const int* ci, const double* v, int nnz,
+               DBuf<int>& trp, DBuf<int>& tci, DBuf<double>* tv) {
+  DBuf<int> cnt(h, m > 0 ? m : 1), fill(h, m > 0 ? m : 1);
+  fill_int(h, cnt.p, 0, m);
+  if (nnz > 0) {
+    k_count_cols<<<grid_for(nnz, 256), 256, 0, h->stream>>>(nnz, ci, cnt.p);
+    MSS_LAUNCH_CK("k_count_cols");
+  }
+  trp.reset(h, m + 1);
+  exclusive_scan(h, cnt.p, trp.p, m);
+  copy_dev(h, fill.p, trp.p, sizeof(int) * (size_t)m);
+  tci.reset(h, nnz > 0 ? nnz : 1);
+  if (tv) tv->reset(h, nnz > 0 ? nnz : 1);
+  k_fill_transpose<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, fill.p, tci.p,
+                                                            tv ? tv->p : nullptr);
+  MSS_LAUNCH_CK("k_fill_transpose");
+  k_sort_rows<<<grid_for(m, 128), 128, 0, h->stream>>>(m, trp.p, tci.p, tv ? tv->p : nullptr);
+  MSS_LAUNCH_CK("k_sort_rows");
+}
+
+void level_prepare(Handle* h, Level& L) {
+  int n = L.n;
+  L.dinv.reset(h, n);
+  DBuf<unsigned long long> bound(h, 1);
+  DBuf<int> bad(h, 1);
+  MSS_CK(cudaMemsetAsync(bound.p, 0, sizeof(unsigned long long), h->stream));
+  fill_int(h, bad.p, 0x7fffffff, 1);
+  k_dinv_bound<<<grid_for(n, 256), 256, 0, h->stream>>>(n, L.rp.p, L.ci.p, L.v.p, L.dinv.p,
+                                                        bound.p, bad.p);
+  MSS_LAUNCH_CK("k_dinv_bound");
+  unsigned long long bits = 0;
+  MSS_CK(cudaMemcpyAsync(&bits, bound.p, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  int badrow = read_int(h, bad.p);
+  if (badrow != 0x7fffffff)
+    fail(MSS_ERR_AMG, "AMG level of size " + std::to_string(n) + ": zero diagonal in row " +
+                          std::to_string(badrow));
+  double lam;
+  std::memcpy(&lam, &bits, sizeof(lam));
+  L.lam = lam;
+  L.b.reset(h, n);
+  L.x.reset(h, n);
+  L.x2.reset(h, n);
+  L.r.reset(h, n);
+  L.d.reset(h, n);
+}
+
+}  // namespace
+
+void amg_build(Handle* h, Hierarchy& H, const double* vals0) {
+  const mss_options& o = h->opt;
+  H.lev.clear();
+  H.lev.reserve(32);
+  {
+    Level L0;
+    L0.n = h->N;
+    L0.nnz = h->nnzb;
+    L0.rp.reset(h, h->N + 1);
+    L0.ci.reset(h, h->nnzb);
+    L0.v.reset(h, h->nnzb);
+    copy_dev(h, L0.rp.p, h->rp.p, sizeof(int) * ((size_t)h->N + 1));
+    copy_dev(h, L0.ci.p, h->ci.p, sizeof(int) * (size_t)h->nnzb);
+    copy_dev(h, L0.v.p, vals0, sizeof(double) * (size_t)h->nnzb);
+    H.lev.push_back(std::move(L0));
+  }
+  const int max_levels = o.amg_max_levels < 1 ? 1 : (o.amg_max_levels > 25 ? 25 : o.amg_max_levels);
+  for (int l = 0;; ++l) {
+    level_prepare(h, H.lev[l]);
+    int n = H.lev[l].n, nnz = H.lev[l].nnz;
+    if (n <= o.amg_max_coarse || l + 1 >= max_levels) break;
+    const int* rp = H.lev[l].rp.p;
+    const int* ci = H.lev[l].ci.p;
+    const double* v = H.lev[l].v.p;
+    // strength and its transpose
+    DBuf<unsigned char> strong(h, nnz);
+    DBuf<int> scount(h, n), srp(h, n + 1);
+    k_strength<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, o.amg_theta, strong.p,
+                                                        scount.p);
+    MSS_LAUNCH_CK("k_strength");
+    exclusive_scan(h, scount.p, srp.p, n);
+    int ns = read_int(h, srp.p + n);
+    DBuf<int> sci(h, ns > 0 ? ns : 1);
+    k_fill_strong<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, strong.p, srp.p, sci.p);
+    MSS_LAUNCH_CK("k_fill_strong");
+    DBuf<int> strp, stci;
+    transpose(h, n, n, srp.p, sci.p, nullptr, ns, strp, stci, nullptr);
+    // PMIS; |S_i^T| are the row lengths of the transposed strength graph
+    DBuf<int> tcount(h, n);
+    k_row_lengths<<<grid_for(n, 256), 256, 0, h->stream>>>(n, strp.p, tcount.p);
+    MSS_LAUNCH_CK("k_row_lengths");
+    DBuf<double> lam(h, n);
+    DBuf<int> state(h, n), newc(h, n), und(h, 1);
+    fill_int(h, und.p, 0, 1);
+    k_pmis_init<<<grid_for(n, 256), 256, 0, h->stream>>>(n, tcount.p, o.seed, l, lam.p, state.p,
+                                                         und.p);
+    MSS_LAUNCH_CK("k_pmis_init");
+    int undecided = read_int(h, und.p);
+    int rounds = 0;
+    while (undecided > 0) {
+      if (++rounds > n + 1) fail(MSS_ERR_AMG, "PMIS did not terminate");
+      k_pmis_select<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, strp.p, stci.p,
+                                                             lam.p, state.p, newc.p);
+      MSS_LAUNCH_CK("k_pmis_select");
+      fill_int(h, und.p, 0, 1);
+      k_pmis_update<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, state.p, newc.p,
+                                                             und.p);
+      MSS_LAUNCH_CK("k_pmis_update");
+      undecided = read_int(h, und.p);
+    }
+    Level& L = H.lev[l];
+    L.cf.reset(h, n);
+    k_pmis_finalize<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, state.p, L.cf.p);
+    MSS_LAUNCH_CK("k_pmis_finalize");
+    DBuf<int> cidx(h, n + 1);
+    exclusive_scan(h, L.cf.p, cidx.p, n);
+    int nc = read_int(h, cidx.p + n);
+    if (nc == 0 || nc == n) {     // coarsening stalled: this level is the coarsest
+      L.cf.release();
+      break;
+    }
+    L.nc = nc;
+    // interpolation
+    DBuf<int> scr_ci(h, nnz), scr_k(h, nnz), plen(h, n);
+    DBuf<double> scr_v(h, nnz);
+    k_interp<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, strong.p, L.cf.p, cidx.p,
+                                                      o.interp_max_elems, scr_ci.p, scr_v.p,
+                                                      scr_k.p, plen.p);
+    MSS_LAUNCH_CK("k_interp");
+    L.prp.reset(h, n + 1);
+    exclusive_scan(h, plen.p, L.prp.p, n);
+    L.nnzP = read_int(h, L.prp.p + n);
+    L.pci.reset(h, L.nnzP > 0 ? L.nnzP : 1);
+    L.pv.reset(h, L.nnzP > 0 ? L.nnzP : 1);
+    k_seg_copy<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, scr_ci.p, scr_v.p, L.prp.p,
+                                                        L.pci.p, L.pv.p);
+    MSS_LAUNCH_CK("k_seg_copy");
+    transpose(h, n, nc, L.prp.p, L.pci.p, L.pv.p, L.nnzP, L.rrp, L.rci, &L.rv);
+    // Galerkin product A_c = R (A P)
+    DBuf<int> aprp, apci;
+    DBuf<double> apv;
+    int apnnz = 0;
+    sparse_product(h, n, rp, ci, v, L.prp.p, L.pci.p, L.pv.p, aprp, apci, apv, apnnz);
+    Level next;
+    next.n = nc;
+    sparse_product(h, nc, L.rrp.p, L.rci.p, L.rv.p, aprp.p, apci.p, apv.p, next.rp, next.ci,
+                   next.v, next.nnz);
+    H.lev.push_back(std::move(next));
+  }
+  coarse_inverse(h, H);
+}
+
+}  // namespace mss

@@ -1,0 +1,424 @@
+// api.cu -- the C-ABI of libmss (include/mss.h): argument checks, set-up
+// orchestration (Sec. 4 scaling, subsystem extraction, AMG, last stage) and
+// the solve entry points. Internal errors become status codes here.
+#include <chrono>
+#include <new>
+
+#include "common.cuh"
+
+struct mss_handle {
+  mss::Handle h;
+};
+
+using namespace mss;
+
+namespace {
+
+template <class F>
+int guarded(mss_handle* hh, F&& f) {
+  try {
+    f();
+    if (hh) hh->h.last_error.clear();
+    return MSS_OK;
+  } catch (const Error& e) {
+    if (hh) hh->h.last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (hh) hh->h.last_error = "host allocation failed";
+    return MSS_ERR_OOM;
+  } catch (...) {
+    if (hh) hh->h.last_error = "unexpected internal error";
+    return MSS_ERR_CUDA;
+  }
+}
+
+void check_options(const mss_options& o) {
+  auto bad = [](const char* what) { fail(MSS_ERR_INVALID_ARG, std::string("option ") + what); };
+  if (o.scheme < MSS_CPTR3 || o.scheme > MSS_ILU0) bad("scheme");
+  if (o.stage_order != MSS_STAGE_T_FIRST && o.stage_order != MSS_STAGE_P_FIRST)
+    bad("stage_order");
+  if (o.stage3 != MSS_BILU0 && o.stage3 != MSS_BLOCK_JACOBI) bad("stage3");
+  if (o.ilu_order != MSS_MULTICOLOR) bad("ilu_order (only MSS_MULTICOLOR on the device)");
+  if (o.smoother != MSS_JACOBI && o.smoother != MSS_CHEBYSHEV) bad("smoother");
+  if (o.nu_pre < 0 || o.nu_pre > 16 || o.nu_post < 0 || o.nu_post > 16) bad("nu_pre/nu_post");
+  if (o.smoother == MSS_JACOBI && o.nu_pre < 1) bad("nu_pre (Jacobi needs >= 1)");
+  if (o.cheb_degree < 1 || o.cheb_degree > 16) bad("cheb_degree");
+  if (o.amg_max_coarse < 1 || o.amg_max_coarse > 8192) bad("amg_max_coarse");
+  if (o.amg_max_levels < 1 || o.amg_max_levels > 25) bad("amg_max_levels");
+  if (o.interp_max_elems < 0) bad("interp_max_elems");
+  if (o.restart < 1 || o.restart > 120) bad("restart (1..120)");
+  if (o.precision != MSS_FP64) bad("precision");
+  if (!(o.amg_theta > 0.0 && o.amg_theta <= 1.0)) bad("amg_theta");
+  if (!(o.jacobi_omega > 0.0 && o.jacobi_omega < 2.0)) bad("jacobi_omega");
+  if (!(o.cheb_lo_ratio > 1.0) || !(o.cheb_hi_factor > 0.0)) bad("Chebyshev interval");
+  if (o.learned_interp != nullptr) bad("learned_interp (reserved)");
+}
+
+void release_setup(Handle& H) {
+  H.ready = false;
+  H.amgT = Hierarchy();
+  H.amgP = Hierarchy();
+  H.rp.release(); H.ci.release(); H.diag.release();
+  H.abar.release(); H.wrows.release(); H.apt.release(); H.atp.release();
+  H.colour.release(); H.perm.release(); H.iperm.release();
+  H.frp.release(); H.fpos.release(); H.fcell.release(); H.fdp.release();
+  H.fv.release(); H.fdinv.release(); H.fcs.release();
+  H.rT.release(); H.xT.release(); H.zP.release(); H.vP.release(); H.w.release();
+  H.cstart.clear();
+  H.ncol = 0;
+}
+
+void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_options* opt) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!J || !J->row_ptr || !J->col_idx || !J->vals) fail(MSS_ERR_INVALID_ARG, "null matrix");
+  if (J->n_rows < 1 || J->nnzb < J->n_rows) fail(MSS_ERR_INVALID_ARG, "bad matrix sizes");
+  if (nb < 2 || nb > 8) fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 8]");
+  if (layout.p_idx < 0 || layout.p_idx >= nb || layout.t_idx < 0 || layout.t_idx >= nb ||
+      layout.p_idx == layout.t_idx)
+    fail(MSS_ERR_INVALID_ARG, "p_idx and t_idx must be distinct indices in [0, nb)");
+  mss_options o;
+  if (opt) o = *opt;
+  else mss_options_default(&o);
+  check_options(o);
+  release_setup(H);
+  H.opt = o;
+  H.N = J->n_rows;
+  H.nnzb = J->nnzb;
+  H.nb = nb;
+  H.p = layout.p_idx;
+  H.t = layout.t_idx;
+  const int N = H.N, nnzb = H.nnzb;
+  Handle* h = &H;
+  H.rp.reset(h, N + 1);
+  H.ci.reset(h, nnzb);
+  H.diag.reset(h, N);
+  copy_dev(h, H.rp.p, J->row_ptr, sizeof(int) * ((size_t)N + 1));
+  copy_dev(h, H.ci.p, J->col_idx, sizeof(int) * (size_t)nnzb);
+  validate_pattern(h, H.rp.p, H.ci.p, N, nnzb, H.diag.p);
+  // left scaling (Eq. splitPrec1 with Eq. CPR or Eqs. CPTR31/CPTR32)
+  H.wrows.reset(h, (size_t)N * 2 * nb);
+  H.abar.reset(h, (size_t)nnzb * nb * nb);
+  build_scaling(h, J->vals, layout.col_major_blocks != 0);
+  // scalar subsystems and their AMG hierarchies
+  if (o.scheme != MSS_ILU0) {
+    DBuf<double> bpp(h, nnzb);
+    extract_subsystem(h, H.p, bpp.p);             // B_PP
+    amg_build(h, H.amgP, bpp.p);
+  }
+  if (o.scheme == MSS_CPTR3) {
+    DBuf<double> ctt(h, nnzb);
+    extract_subsystem(h, H.t, ctt.p);             // C_TT
+    amg_build(h, H.amgT, ctt.p);
+    H.apt.reset(h, nnzb);
+    H.atp.reset(h, nnzb);
+    extract_subsystem(h, -1, H.apt.p);
+    extract_subsystem(h, -2, H.atp.p);
+  }
+  // last stage
+  bilu_setup(h);
+  H.rT.reset(h, N);
+  H.xT.reset(h, N);
+  H.zP.reset(h, N);
+  H.vP.reset(h, N);
+  H.w.reset(h, (size_t)N * nb);
+  MSS_CK(cudaStreamSynchronize(H.stream));
+  H.J = *J;
+  H.ready = true;
+  H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                   .count();
+}
+
+void need_ready(const Handle& H) {
+  if (!H.ready) fail(MSS_ERR_NOT_SETUP, "mss_setup has not completed on this handle");
+}
+
+Hierarchy& pick(Handle& H, int which) {
+  if (which == 0 && H.amgT.present()) return H.amgT;
+  if (which == 1 && H.amgP.present()) return H.amgP;
+  fail(MSS_ERR_INVALID_ARG, "no AMG stage " + std::to_string(which) + " in this scheme");
+}
+
+int solve_impl(Handle& H, const mss_bsr* J, const double* b, double* x, double tol, int maxit,
+               mss_result* out) {
+  auto t0 = std::chrono::steady_clock::now();
+  need_ready(H);
+  if (!J || J->n_rows != H.J.n_rows || J->nnzb != H.J.nnzb || J->row_ptr != H.J.row_ptr ||
+      J->col_idx != H.J.col_idx || J->vals != H.J.vals)
+    fail(MSS_ERR_NOT_SETUP, "the matrix differs from the one passed to mss_setup");
+  if (!b || !x || b == x) fail(MSS_ERR_INVALID_ARG, "b and x must be distinct device vectors");
+  if (!(tol >= 0.0) || maxit < 0) fail(MSS_ERR_INVALID_ARG, "tol >= 0 and maxit >= 0 required");
+  mss_result r{};
+  int st = fgmres(&H, b, x, tol, maxit, &r);
+  MSS_CK(cudaStreamSynchronize(H.stream));
+  r.setup_ms = H.setup_ms;
+  r.solve_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  r.status = st;
+  if (out) *out = r;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mss_options_default(mss_options* o) {
+  if (!o) return MSS_ERR_INVALID_ARG;
+  *o = mss_options{};
+  o->scheme = MSS_CPTR3;
+  o->stage_order = MSS_STAGE_T_FIRST;
+  o->stage3 = MSS_BILU0;
+  o->ilu_order = MSS_MULTICOLOR;
+  o->smoother = MSS_JACOBI;
+  o->nu_pre = 1;
+  o->nu_post = 1;
+  o->cheb_degree = 2;
+  o->amg_max_coarse = 1000;
+  o->amg_max_levels = 25;
+  o->interp_max_elems = 4;
+  o->restart = 30;
+  o->precision = MSS_FP64;
+  o->amg_theta = 0.25;
+  o->jacobi_omega = 2.0 / 3.0;
+  o->cheb_lo_ratio = 30.0;
+  o->cheb_hi_factor = 1.0;
+  o->seed = 0x5eedULL;
+  o->learned_interp = nullptr;
+  return MSS_OK;
+}
+
+int mss_create(mss_handle** out, void* cuda_stream, mss_alloc_fn alloc, mss_free_fn free_fn,
+               void* alloc_ctx) {
+  if (!out) return MSS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((alloc == nullptr) != (free_fn == nullptr)) return MSS_ERR_INVALID_ARG;
+  mss_handle* hh = new (std::nothrow) mss_handle();
+  if (!hh) return MSS_ERR_OOM;
+  int st = guarded(hh, [&] {
+    Handle& H = hh->h;
+    H.stream = static_cast<cudaStream_t>(cuda_stream);
+    H.alloc = alloc;
+    H.free_fn = free_fn;
+    H.ctx = alloc_ctx;
+    MSS_CK(cudaGetDevice(&H.device));
+    MSS_CK(cudaDeviceGetAttribute(&H.num_sms, cudaDevAttrMultiProcessorCount, H.device));
+    mss_options_default(&H.opt);
+  });
+  if (st != MSS_OK) {
+    delete hh;
+    return st;
+  }
+  *out = hh;
+  return MSS_OK;
+}
+
+void mss_destroy(mss_handle* hh) {
+  if (!hh) return;
+  cudaStreamSynchronize(hh->h.stream);
+  delete hh;
+}
+
+int mss_setup(mss_handle* hh, const mss_bsr* J, int nb, mss_layout layout,
+              const mss_options* opt) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] { do_setup(hh->h, J, nb, layout, opt); });
+}
+
+int mss_scale_rhs(mss_handle* hh, const double* b, double* bbar) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    need_ready(hh->h);
+    if (!b || !bbar) fail(MSS_ERR_INVALID_ARG, "null vector");
+    scale_vector(&hh->h, b, bbar);
+    MSS_LAUNCH_CK("mss_scale_rhs");
+  });
+}
+
+int mss_spmv(mss_handle* hh, const double* x, double* y) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    need_ready(hh->h);
+    if (!x || !y || x == y) fail(MSS_ERR_INVALID_ARG, "x and y must be distinct");
+    bsr_spmv(&hh->h, x, y);
+  });
+}
+
+int mss_apply(mss_handle* hh, const double* r, double* y) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    need_ready(hh->h);
+    if (!r || !y || r == y) fail(MSS_ERR_INVALID_ARG, "r and y must be distinct");
+    precond_apply(&hh->h, r, y);
+  });
+}
+
+int mss_stage_apply(mss_handle* hh, int which, const double* r, double* y) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    need_ready(H);
+    if (!r || !y || r == y) fail(MSS_ERR_INVALID_ARG, "r and y must be distinct");
+    if (which == 2) {
+      last_stage_apply(&H, r, nullptr, nullptr, y);
+      return;
+    }
+    Hierarchy& A = pick(H, which);
+    int var = which == 0 ? H.t : H.p;
+    gather_var(&H, r, var, H.rT.p);
+    vcycle(&H, A, H.rT.p, H.xT.p);
+    scatter_var_zero(&H, H.xT.p, var, y);
+  });
+}
+
+int mss_fgmres_solve(mss_handle* hh, const mss_bsr* J, const double* b, double* x, double tol,
+                     int maxit, mss_result* out) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  int st = MSS_OK;
+  int g = guarded(hh, [&] { st = solve_impl(hh->h, J, b, x, tol, maxit, out); });
+  if (g != MSS_OK) {
+    if (out) out->status = g;
+    return g;
+  }
+  if (st != MSS_OK) hh->h.last_error = mss_status_string(st);
+  return st;
+}
+
+int mss_solve_host(mss_handle* hh, const mss_bsr* Jh, int nb, mss_layout layout,
+                   const mss_options* opt, const double* b_host, double* x_host, double tol,
+                   int maxit, mss_result* out) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  int st = MSS_OK;
+  int g = guarded(hh, [&] {
+    Handle& H = hh->h;
+    Handle* h = &H;
+    if (!Jh || !Jh->row_ptr || !Jh->col_idx || !Jh->vals || !b_host || !x_host)
+      fail(MSS_ERR_INVALID_ARG, "null host pointer");
+    if (Jh->n_rows < 1 || Jh->nnzb < Jh->n_rows || nb < 2 || nb > 8)
+      fail(MSS_ERR_INVALID_ARG, "bad sizes");
+    const size_t N = (size_t)Jh->n_rows, nnzb = (size_t)Jh->nnzb, nb2 = (size_t)nb * nb;
+    if (H.host_rp.n < N + 1) H.host_rp.reset(h, N + 1);
+    if (H.host_ci.n < nnzb) H.host_ci.reset(h, nnzb);
+    if (H.host_vals.n < nnzb * nb2) H.host_vals.reset(h, nnzb * nb2);
+    if (H.host_b.n < N * nb) H.host_b.reset(h, N * nb);
+    if (H.host_x.n < N * nb) H.host_x.reset(h, N * nb);
+    MSS_CK(cudaMemcpyAsync(H.host_rp.p, Jh->row_ptr, sizeof(int) * (N + 1),
+                           cudaMemcpyHostToDevice, H.stream));
+    MSS_CK(cudaMemcpyAsync(H.host_ci.p, Jh->col_idx, sizeof(int) * nnzb, cudaMemcpyHostToDevice,
+                           H.stream));
+    MSS_CK(cudaMemcpyAsync(H.host_vals.p, Jh->vals, sizeof(double) * nnzb * nb2,
+                           cudaMemcpyHostToDevice, H.stream));
+    MSS_CK(cudaMemcpyAsync(H.host_b.p, b_host, sizeof(double) * N * nb, cudaMemcpyHostToDevice,
+                           H.stream));
+    mss_bsr Jd{Jh->n_rows, Jh->nnzb, H.host_rp.p, H.host_ci.p, H.host_vals.p};
+    do_setup(H, &Jd, nb, layout, opt);
+    st = solve_impl(H, &Jd, H.host_b.p, H.host_x.p, tol, maxit, out);
+    MSS_CK(cudaMemcpyAsync(x_host, H.host_x.p, sizeof(double) * N * nb, cudaMemcpyDeviceToHost,
+                           H.stream));
+    MSS_CK(cudaStreamSynchronize(H.stream));
+  });
+  if (g != MSS_OK) {
+    if (out) out->status = g;
+    return g;
+  }
+  return st;
+}
+
+int mss_get_scaled(mss_handle* hh, double* abar) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    need_ready(H);
+    if (!abar) fail(MSS_ERR_INVALID_ARG, "null output");
+    copy_dev(&H, abar, H.abar.p, sizeof(double) * H.abar.n);
+    MSS_CK(cudaStreamSynchronize(H.stream));
+  });
+}
+
+int mss_amg_num_levels(mss_handle* hh, int which) {
+  if (!hh || !hh->h.ready) return 0;
+  if (which == 0) return (int)hh->h.amgT.lev.size();
+  if (which == 1) return (int)hh->h.amgP.lev.size();
+  return 0;
+}
+
+int mss_amg_level_sizes(mss_handle* hh, int which, int level, int32_t* sizes) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    need_ready(H);
+    Hierarchy& A = pick(H, which);
+    if (level < 0 || level >= (int)A.lev.size() || !sizes)
+      fail(MSS_ERR_INVALID_ARG, "bad level");
+    const Level& L = A.lev[level];
+    bool last = level == (int)A.lev.size() - 1;
+    sizes[0] = L.n;
+    sizes[1] = L.nnz;
+    sizes[2] = last ? 0 : L.nnzP;
+  });
+}
+
+int mss_amg_level_copy(mss_handle* hh, int which, int level, int32_t* arp, int32_t* aci,
+                       double* av, int32_t* cf, int32_t* prp, int32_t* pci, double* pv) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    need_ready(H);
+    Hierarchy& A = pick(H, which);
+    if (level < 0 || level >= (int)A.lev.size()) fail(MSS_ERR_INVALID_ARG, "bad level");
+    const Level& L = A.lev[level];
+    bool last = level == (int)A.lev.size() - 1;
+    if (!arp || !aci || !av) fail(MSS_ERR_INVALID_ARG, "null output");
+    copy_dev(&H, arp, L.rp.p, sizeof(int) * ((size_t)L.n + 1));
+    copy_dev(&H, aci, L.ci.p, sizeof(int) * (size_t)L.nnz);
+    copy_dev(&H, av, L.v.p, sizeof(double) * (size_t)L.nnz);
+    if (!last) {
+      if (!cf || !prp || !pci || !pv) fail(MSS_ERR_INVALID_ARG, "null output");
+      copy_dev(&H, cf, L.cf.p, sizeof(int) * (size_t)L.n);
+      copy_dev(&H, prp, L.prp.p, sizeof(int) * ((size_t)L.n + 1));
+      copy_dev(&H, pci, L.pci.p, sizeof(int) * (size_t)L.nnzP);
+      copy_dev(&H, pv, L.pv.p, sizeof(double) * (size_t)L.nnzP);
+    }
+    MSS_CK(cudaStreamSynchronize(H.stream));
+  });
+}
+
+int mss_bilu_num_colours(mss_handle* hh, int32_t* ncolours) {
+  if (!hh || !ncolours) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    need_ready(hh->h);
+    *ncolours = hh->h.ncol;
+  });
+}
+
+int mss_bilu_ordering(mss_handle* hh, int32_t* colour, int32_t* perm) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    need_ready(H);
+    if (colour) copy_dev(&H, colour, H.colour.p, sizeof(int) * (size_t)H.N);
+    if (perm) copy_dev(&H, perm, H.perm.p, sizeof(int) * (size_t)H.N);
+    MSS_CK(cudaStreamSynchronize(H.stream));
+  });
+}
+
+const char* mss_status_string(int s) {
+  switch (s) {
+    case MSS_OK: return "MSS_OK";
+    case MSS_ERR_INVALID_ARG: return "MSS_ERR_INVALID_ARG";
+    case MSS_ERR_SINGULAR_BLOCK: return "MSS_ERR_SINGULAR_BLOCK";
+    case MSS_ERR_NOT_CONVERGED: return "MSS_ERR_NOT_CONVERGED";
+    case MSS_ERR_BREAKDOWN: return "MSS_ERR_BREAKDOWN";
+    case MSS_ERR_CUDA: return "MSS_ERR_CUDA";
+    case MSS_ERR_OOM: return "MSS_ERR_OOM";
+    case MSS_ERR_AMG: return "MSS_ERR_AMG";
+    case MSS_ERR_NOT_SETUP: return "MSS_ERR_NOT_SETUP";
+    default: return "MSS_ERR_UNKNOWN";
+  }
+}
+
+const char* mss_last_error(const mss_handle* hh) {
+  if (!hh) return "null handle";
+  return hh->h.last_error.c_str();
+}
+
+}  // extern "C"

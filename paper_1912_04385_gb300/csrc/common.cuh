@@ -1,0 +1,203 @@
+// common.cuh -- internal declarations of libmss (handle, device buffers,
+// errors, launchers). Not part of the public ABI; see include/mss.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mss.h"
+
+namespace mss {
+
+// Internal errors travel as exceptions inside the library and become status
+// codes at the C-ABI boundary.
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define MSS_CK(call) ::mss::check_cuda((call), #call, __FILE__, __LINE__)
+#define MSS_LAUNCH_CK(what) ::mss::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__)
+
+struct Handle;
+void* dev_alloc(Handle* h, size_t bytes);
+void dev_free(Handle* h, void* p);
+
+// Owning device buffer allocated through the handle's hooks.
+template <class T>
+struct DBuf {
+  Handle* h = nullptr;
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(Handle* hh, size_t nn) { reset(hh, nn); }
+  void reset(Handle* hh, size_t nn) {
+    release();
+    h = hh;
+    n = nn;
+    p = nn ? static_cast<T*>(dev_alloc(hh, nn * sizeof(T))) : nullptr;
+  }
+  void release() {
+    if (p) dev_free(h, p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DBuf() { release(); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : h(o.h), p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      h = o.h; p = o.p; n = o.n;
+      o.p = nullptr; o.n = 0;
+    }
+    return *this;
+  }
+  T* get() const { return p; }
+};
+
+// One level of a scalar AMG hierarchy (CSR, 0-based, ascending columns).
+struct Level {
+  int n = 0, nnz = 0;
+  DBuf<int> rp, ci;
+  DBuf<double> v, dinv;
+  double lam = 0.0;           // Gershgorin bound of D^-1 A (Chebyshev)
+  // transfer to the next level (absent on the coarsest level)
+  int nc = 0, nnzP = 0;
+  DBuf<int> cf;               // 1 = C point
+  DBuf<int> prp, pci;         // P: n x nc
+  DBuf<double> pv;
+  DBuf<int> rrp, rci;         // R = P^T: nc x n
+  DBuf<double> rv;
+  // V-cycle vectors
+  DBuf<double> b, x, x2, r, d;
+};
+
+struct Hierarchy {
+  std::vector<Level> lev;
+  DBuf<double> coarse_inv;    // dense inverse of the coarsest operator, row-major
+  int nc = 0;                 // size of the coarsest level
+  bool present() const { return !lev.empty(); }
+};
+
+struct Handle {
+  // binding
+  cudaStream_t stream = nullptr;
+  mss_alloc_fn alloc = nullptr;
+  mss_free_fn free_fn = nullptr;
+  void* ctx = nullptr;
+  std::string last_error;
+  int device = 0;
+  int num_sms = 0;
+  // problem
+  bool ready = false;
+  int N = 0, nb = 0, nnzb = 0, p = 0, t = 1;
+  mss_options opt{};
+  mss_bsr J{};                 // the caller's matrix (identity check in solve)
+  double setup_ms = 0.0;
+  // scaled system
+  DBuf<int> rp, ci, diag;      // copied pattern, diagonal block index per row
+  DBuf<double> abar;           // Abar blocks, row-major
+  DBuf<double> wrows;          // W rows p and t per cell: N x 2 x nb
+  DBuf<double> apt;            // Abar[p][t] per block (z_P = r_P - Abar_Pt x_T)
+  DBuf<double> atp;            // Abar[t][p] per block (P-first stage order)
+  Hierarchy amgT, amgP;
+  // last stage: multicolour block ILU(0) in colour-major positions
+  int ncol = 0;
+  std::vector<int> cstart;     // host: first position of each colour, ncol + 1
+  DBuf<int> colour, perm, iperm;
+  DBuf<int> frp, fpos, fcell;  // factor pattern: column position and cell
+  DBuf<int> fdp;               // index of the diagonal block in each factor row
+  DBuf<double> fv;             // L (strictly lower) / U (strictly upper) blocks
+  DBuf<double> fdinv;          // inverse of U's diagonal block, per position
+  DBuf<double> fcs;            // Abar column slices [t | p] per factor block (2 nb)
+  // preconditioner work vectors
+  DBuf<double> rT, xT, zP, vP, w;
+  // Krylov workspace
+  int m = 0;
+  DBuf<double> V, Z, bbar, res, hbuf, part;
+  DBuf<double> kscal;          // device scalars of the Givens recurrence
+  DBuf<int> kflag;
+  // end-to-end host solve copies
+  DBuf<int> host_rp, host_ci;
+  DBuf<double> host_vals, host_b, host_x;
+  // scratch for reductions and flags
+  DBuf<int> iflag;
+  DBuf<double> dscr;
+};
+
+// SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator: the
+// value for counter k is the (k+1)-th output of the stream seeded with seed.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// ---- launch helpers --------------------------------------------------------
+// Dispatch a call templated on the block size NB (2..8).
+#define MSS_NB_DISPATCH(NBV, CALL)                                     \
+  switch (NBV) {                                                       \
+    case 2: { constexpr int NB = 2; CALL; } break;                     \
+    case 3: { constexpr int NB = 3; CALL; } break;                     \
+    case 4: { constexpr int NB = 4; CALL; } break;                     \
+    case 5: { constexpr int NB = 5; CALL; } break;                     \
+    case 6: { constexpr int NB = 6; CALL; } break;                     \
+    case 7: { constexpr int NB = 7; CALL; } break;                     \
+    case 8: { constexpr int NB = 8; CALL; } break;                     \
+    default: fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 8]");        \
+  }
+
+inline unsigned grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 2147483647LL) g = 2147483647LL;
+  return static_cast<unsigned>(g);
+}
+
+// util.cu
+void exclusive_scan(Handle* h, const int* in, int* out, int n);   // out has n + 1 entries
+int read_int(Handle* h, const int* dptr);                         // synchronises
+double read_double(Handle* h, const double* dptr);
+void fill_int(Handle* h, int* p, int value, long long n);
+void fill_double(Handle* h, double* p, double value, long long n);
+void copy_dev(Handle* h, void* dst, const void* src, size_t bytes);
+
+// setup_scale.cu
+void validate_pattern(Handle* h, const int* rp, const int* ci, int N, int nnzb, int* diag);
+void build_scaling(Handle* h, const double* vals, bool col_major);
+void scale_vector(Handle* h, const double* b, double* bbar);
+// var >= 0: Abar[var][var] per block; var = -1: Abar[p][t]; var = -2: Abar[t][p]
+void extract_subsystem(Handle* h, int var, double* out);
+
+// amg_setup.cu
+void amg_build(Handle* h, Hierarchy& H, const double* vals0);
+
+// amg_cycle.cu
+void vcycle(Handle* h, Hierarchy& H, const double* b, double* x);
+void gather_var(Handle* h, const double* v, int var, double* out);
+void scatter_var_zero(Handle* h, const double* s, int var, double* out);
+void csr_block_pattern_spmv_sub(Handle* h, const double* vals, const double* x,
+                                const double* r, int var, double* out);
+
+// bilu.cu
+void bilu_setup(Handle* h);
+// fused last stage: u = r - Abar[:,t] xT - Abar[:,p] vP (terms absent when the
+// pointer is NULL), y = xadd + M3 u where xadd puts xT at t and vP at p.
+void last_stage_apply(Handle* h, const double* r, const double* xT, const double* vP,
+                      double* y);
+
+// krylov.cu
+void bsr_spmv(Handle* h, const double* x, double* y);
+void precond_apply(Handle* h, const double* r, double* y);
+int fgmres(Handle* h, const double* b, double* x, double tol, int maxit, mss_result* out);
+
+}  // namespace mss

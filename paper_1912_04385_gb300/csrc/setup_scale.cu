@@ -1,0 +1,292 @@
+// setup_scale.cu -- pattern validation, left scaling N^{-1} (Sec. 4, Eqs.
+// CPR, CPTR31, CPTR32) and subsystem extraction.
+//
+// This translation unit is compiled with -fmad=false: every product and sum
+// rounds separately, in the order written, so the scaled matrix feeds the
+// AMG set-up (whose strength tests turn floating point into index decisions)
+// with values that do not depend on instruction selection.
+#include "common.cuh"
+
+namespace mss {
+namespace {
+
+// error codes written to the flag (first error wins through atomicMin)
+enum { VAL_OK = 0x7fffffff, VAL_ROWPTR = 1, VAL_COLS = 2, VAL_NODIAG = 3, VAL_ASYM = 4 };
+
+__global__ void k_validate(const int* __restrict__ rp, const int* __restrict__ ci, int N,
+                           int nnzb, int* __restrict__ diag, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int b = rp[i], e = rp[i + 1];
+  if ((i == 0 && b != 0) || (i == N - 1 && e != nnzb) || e < b || b < 0 || e > nnzb) {
+    atomicMin(flag, VAL_ROWPTR);
+    diag[i] = -1;
+    return;
+  }
+  int d = -1;
+  for (int k = b; k < e; ++k) {
+    int j = ci[k];
+    if (j < 0 || j >= N || (k > b && j <= ci[k - 1])) {
+      atomicMin(flag, VAL_COLS);
+      diag[i] = -1;
+      return;
+    }
+    if (j == i) d = k;
+  }
+  diag[i] = d;
+  if (d < 0) {
+    atomicMin(flag, VAL_NODIAG);
+    return;
+  }
+  // structural symmetry: i must appear in every neighbour's row
+  for (int k = b; k < e; ++k) {
+    int j = ci[k];
+    if (j == i) continue;
+    int lo = rp[j], hi = rp[j + 1] - 1;
+    if (lo < 0 || hi >= nnzb) {
+      atomicMin(flag, VAL_ROWPTR);
+      return;
+    }
+    bool found = false;
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1;
+      int c = ci[mid];
+      if (c == i) { found = true; break; }
+      if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    if (!found) {
+      atomicMin(flag, VAL_ASYM);
+      return;
+    }
+  }
+}
+
+// Gauss-Jordan inverse without pivoting, m <= 8, same operation order as the
+// oracle: divide the pivot row, then eliminate the column from every other
+// row. Returns false on a zero or non-finite pivot.
+__device__ bool gj_inverse(int m, double* a, double* inv) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) inv[i * m + j] = (i == j) ? 1.0 : 0.0;
+  for (int k = 0; k < m; ++k) {
+    double piv = a[k * m + k];
+    if (piv == 0.0 || !isfinite(piv)) return false;
+    for (int j = 0; j < m; ++j) {
+      a[k * m + j] = a[k * m + j] / piv;
+      inv[k * m + j] = inv[k * m + j] / piv;
+    }
+    for (int i = 0; i < m; ++i) {
+      if (i == k) continue;
+      double f = a[i * m + k];
+      for (int j = 0; j < m; ++j) {
+        a[i * m + j] = a[i * m + j] - f * a[k * m + j];
+        inv[i * m + j] = inv[i * m + j] - f * inv[k * m + j];
+      }
+    }
+  }
+  return true;
+}
+
+// One thread per cell: W = N^{-1} restricted to the cell, built from the
+// diagonal block D. Only rows p and t of W differ from the identity; they
+// are stored as wrows[i][0][:] (row p) and wrows[i][1][:] (row t).
+// scheme: 0 CPTR3 (Eq. CPTR31 then Eq. CPTR32), 1 CPR (Eq. CPR), 2 none.
+template <int NB>
+__global__ void k_build_w(const double* __restrict__ vals, const int* __restrict__ diag, int N,
+                          int p, int t, int scheme, int col_major, double* __restrict__ wrows,
+                          int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double D[NB * NB];
+  const double* src = vals + (size_t)diag[i] * NB * NB;
+  for (int r = 0; r < NB; ++r)
+    for (int c = 0; c < NB; ++c) D[r * NB + c] = col_major ? src[c * NB + r] : src[r * NB + c];
+  double wp[NB], wt[NB];
+  for (int k = 0; k < NB; ++k) {
+    wp[k] = (k == p) ? 1.0 : 0.0;
+    wt[k] = (k == t) ? 1.0 : 0.0;
+  }
+  if (scheme == 1) {
+    int h[NB];
+    int nh = 0;
+    for (int k = 0; k < NB; ++k)
+      if (k != p) h[nh++] = k;
+    double Dhh[NB * NB], inv[NB * NB];
+    for (int a = 0; a < nh; ++a)
+      for (int b = 0; b < nh; ++b) Dhh[a * nh + b] = D[h[a] * NB + h[b]];
+    if (!gj_inverse(nh, Dhh, inv)) {
+      atomicMin(flag, i);
+      return;
+    }
+    for (int b = 0; b < nh; ++b) {
+      double w = 0.0;
+      for (int a = 0; a < nh; ++a) w = w + D[p * NB + h[a]] * inv[a * nh + b];
+      wp[h[b]] = -w;
+    }
+  } else if (scheme == 0) {
+    int s[NB];
+    int ns = 0;
+    for (int k = 0; k < NB; ++k)
+      if (k != p && k != t) s[ns++] = k;
+    if (ns > 0) {
+      double Dss[NB * NB], inv[NB * NB];
+      for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b) Dss[a * ns + b] = D[s[a] * NB + s[b]];
+      if (!gj_inverse(ns, Dss, inv)) {
+        atomicMin(flag, i);
+        return;
+      }
+      for (int b = 0; b < ns; ++b) {
+        double vp = 0.0, vt = 0.0;
+        for (int a = 0; a < ns; ++a) {
+          vp = vp + D[p * NB + s[a]] * inv[a * ns + b];
+          vt = vt + D[t * NB + s[a]] * inv[a * ns + b];
+        }
+        wp[s[b]] = -vp;
+        wt[s[b]] = -vt;
+      }
+    }
+    // once-scaled entries B_PP and B_Tp of N1^{-1} D, then the N2 factor
+    double bpp = 0.0, btp = 0.0;
+    for (int k = 0; k < NB; ++k) {
+      bpp = bpp + wp[k] * D[k * NB + p];
+      btp = btp + wt[k] * D[k * NB + p];
+    }
+    if (bpp == 0.0 || !isfinite(bpp)) {
+      atomicMin(flag, i);
+      return;
+    }
+    double c = btp / bpp;
+    for (int k = 0; k < NB; ++k) wt[k] = wt[k] - c * wp[k];
+  }
+  double* out = wrows + (size_t)i * 2 * NB;
+  for (int k = 0; k < NB; ++k) {
+    out[k] = wp[k];
+    out[NB + k] = wt[k];
+  }
+}
+
+// One thread per entry (row i, r, c) looping over the blocks of row i:
+// Abar_ij[r][c] = sum_k W_i[r][k] J_ij[k][c] (ascending k) for r in {p, t},
+// a copy for the other rows (their W row is a unit vector).
+template <int NB>
+__global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict__ rp, int N,
+                          int p, int t, int scheme, int col_major,
+                          const double* __restrict__ wrows, double* __restrict__ abar) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)N * NB * NB) return;
+  int i = (int)(tid / (NB * NB));
+  int rc = (int)(tid % (NB * NB));
+  int r = rc / NB, c = rc % NB;
+  bool scaled_row = scheme != 2 && (r == p || (scheme == 0 && r == t));
+  const double* w = wrows + (size_t)i * 2 * NB + (r == p ? 0 : NB);
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const double* src = vals + (size_t)e * NB * NB;
+    double out;
+    if (!scaled_row) {
+      out = col_major ? src[c * NB + r] : src[r * NB + c];
+    } else {
+      double acc = 0.0;
+      for (int k = 0; k < NB; ++k) {
+        double a = col_major ? src[c * NB + k] : src[k * NB + c];
+        acc = acc + w[k] * a;
+      }
+      out = acc;
+    }
+    abar[(size_t)e * NB * NB + r * NB + c] = out;
+  }
+}
+
+template <int NB>
+__global__ void k_scale_vec(const double* __restrict__ b, int N, int p, int t, int scheme,
+                            const double* __restrict__ wrows, double* __restrict__ out) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)N * NB) return;
+  int i = (int)(tid / NB), r = (int)(tid % NB);
+  bool scaled_row = scheme != 2 && (r == p || (scheme == 0 && r == t));
+  if (!scaled_row) {
+    out[tid] = b[tid];
+    return;
+  }
+  const double* w = wrows + (size_t)i * 2 * NB + (r == p ? 0 : NB);
+  double acc = 0.0;
+  for (int k = 0; k < NB; ++k) acc = acc + w[k] * b[(size_t)i * NB + k];
+  out[tid] = acc;
+}
+
+__global__ void k_extract(const double* __restrict__ abar, int nnzb, int nb, int var,
+                          double* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnzb) out[e] = abar[(size_t)e * nb * nb + var * nb + var];
+}
+
+__global__ void k_extract_pt(const double* __restrict__ abar, int nnzb, int nb, int p, int t,
+                             double* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnzb) out[e] = abar[(size_t)e * nb * nb + p * nb + t];
+}
+
+template <int NB>
+void build_scaling_nb(Handle* h, const double* vals, bool col_major) {
+  int N = h->N;
+  int scheme = h->opt.scheme;
+  DBuf<int> flag(h, 1);
+  fill_int(h, flag.p, 0x7fffffff, 1);
+  k_build_w<NB><<<grid_for(N, 128), 128, 0, h->stream>>>(vals, h->diag.p, N, h->p, h->t, scheme,
+                                                         col_major, h->wrows.p, flag.p);
+  MSS_LAUNCH_CK("k_build_w");
+  int bad = read_int(h, flag.p);
+  if (bad != 0x7fffffff)
+    fail(MSS_ERR_SINGULAR_BLOCK,
+         "cell " + std::to_string(bad) + ": diagonal block needs pivoting (zero pivot)");
+  long long tot = (long long)N * NB * NB;
+  k_apply_w<NB><<<grid_for(tot, 256), 256, 0, h->stream>>>(vals, h->rp.p, N, h->p, h->t, scheme,
+                                                           col_major, h->wrows.p, h->abar.p);
+  MSS_LAUNCH_CK("k_apply_w");
+}
+
+template <int NB>
+void scale_vector_nb(Handle* h, const double* b, double* bbar) {
+  long long tot = (long long)h->N * NB;
+  k_scale_vec<NB><<<grid_for(tot, 256), 256, 0, h->stream>>>(b, h->N, h->p, h->t,
+                                                             h->opt.scheme, h->wrows.p, bbar);
+  MSS_LAUNCH_CK("k_scale_vec");
+}
+
+}  // namespace
+
+void validate_pattern(Handle* h, const int* rp, const int* ci, int N, int nnzb, int* diag) {
+  DBuf<int> flag(h, 1);
+  fill_int(h, flag.p, VAL_OK, 1);
+  k_validate<<<grid_for(N, 256), 256, 0, h->stream>>>(rp, ci, N, nnzb, diag, flag.p);
+  MSS_LAUNCH_CK("k_validate");
+  int f = read_int(h, flag.p);
+  switch (f) {
+    case VAL_OK: return;
+    case VAL_ROWPTR: fail(MSS_ERR_INVALID_ARG, "row_ptr is not a valid offset array");
+    case VAL_COLS: fail(MSS_ERR_INVALID_ARG, "col_idx out of range or not strictly ascending");
+    case VAL_NODIAG: fail(MSS_ERR_INVALID_ARG, "a row has no diagonal block");
+    default: fail(MSS_ERR_INVALID_ARG, "block pattern is not structurally symmetric");
+  }
+}
+
+void build_scaling(Handle* h, const double* vals, bool col_major) {
+  MSS_NB_DISPATCH(h->nb, build_scaling_nb<NB>(h, vals, col_major));
+}
+
+void scale_vector(Handle* h, const double* b, double* bbar) {
+  MSS_NB_DISPATCH(h->nb, scale_vector_nb<NB>(h, b, bbar));
+}
+
+void extract_subsystem(Handle* h, int var, double* out) {
+  if (var >= 0) {
+    k_extract<<<grid_for(h->nnzb, 256), 256, 0, h->stream>>>(h->abar.p, h->nnzb, h->nb, var, out);
+    MSS_LAUNCH_CK("k_extract");
+  } else {
+    int row = var == -1 ? h->p : h->t, col = var == -1 ? h->t : h->p;
+    k_extract_pt<<<grid_for(h->nnzb, 256), 256, 0, h->stream>>>(h->abar.p, h->nnzb, h->nb, row,
+                                                                col, out);
+    MSS_LAUNCH_CK("k_extract_pt");
+  }
+}
+
+}  // namespace mss

@@ -1,0 +1,188 @@
+// util.cu -- errors, device allocation through the handle's hooks, a
+// device-wide exclusive scan, fills and host read-backs.
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace mss {
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file,
+                line);
+  fail(e == cudaErrorMemoryAllocation ? MSS_ERR_OOM : MSS_ERR_CUDA, buf);
+}
+
+void* dev_alloc(Handle* h, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) return nullptr;
+  if (h->alloc) {
+    p = h->alloc(bytes, h->ctx);
+    if (!p) fail(MSS_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    if (reinterpret_cast<uintptr_t>(p) % 256 != 0)
+      fail(MSS_ERR_INVALID_ARG, "allocator returned memory not aligned to 256 bytes");
+    return p;
+  }
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(MSS_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  return p;
+}
+
+void dev_free(Handle* h, void* p) {
+  if (!p) return;
+  if (h->free_fn) h->free_fn(p, h->ctx);
+  else cudaFree(p);
+}
+
+// ---- exclusive scan (three passes over tiles of SCAN_TILE ints) ------------
+namespace {
+constexpr int SCAN_T = 512;
+constexpr int SCAN_IPT = 8;
+constexpr int SCAN_TILE = SCAN_T * SCAN_IPT;
+
+__device__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int warp_sums[SCAN_T / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < SCAN_T / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < SCAN_T / 32) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  int warp_prefix = wid > 0 ? warp_sums[wid - 1] : 0;
+  *total = warp_sums[SCAN_T / 32 - 1];
+  __syncthreads();
+  return warp_prefix + x - v;
+}
+
+__global__ void k_scan_reduce(const int* __restrict__ in, int n, int* __restrict__ bsum) {
+  long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; ++k) {
+    long long idx = base + k;
+    if (idx < n) s += in[idx];
+  }
+  int tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of the tile sums in place
+__global__ void k_scan_tiles(int* bsum, int ntiles) {
+  int carry = 0;
+  for (int base = 0; base < ntiles; base += SCAN_T) {
+    int idx = base + threadIdx.x;
+    int v = idx < ntiles ? bsum[idx] : 0;
+    int tot;
+    int ex = block_exclusive_scan(v, &tot);
+    if (idx < ntiles) bsum[idx] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n,
+                             const int* __restrict__ bsum) {
+  long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+  int vals[SCAN_IPT];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; ++k) {
+    long long idx = base + k;
+    vals[k] = idx < n ? in[idx] : 0;
+    s += vals[k];
+  }
+  int tot;
+  int ex = block_exclusive_scan(s, &tot) + bsum[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; ++k) {
+    long long idx = base + k;
+    if (idx < n) out[idx] = ex;
+    if (idx == n - 1) out[n] = ex + vals[k];
+    ex += vals[k];
+  }
+}
+
+__global__ void k_fill_int(int* p, int v, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) p[i] = v;
+}
+
+__global__ void k_fill_double(double* p, double v, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) p[i] = v;
+}
+}  // namespace
+
+void exclusive_scan(Handle* h, const int* in, int* out, int n) {
+  if (n <= 0) {
+    fill_int(h, out, 0, 1);
+    return;
+  }
+  int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  DBuf<int> bsum(h, ntiles);
+  k_scan_reduce<<<ntiles, SCAN_T, 0, h->stream>>>(in, n, bsum.p);
+  MSS_LAUNCH_CK("k_scan_reduce");
+  k_scan_tiles<<<1, SCAN_T, 0, h->stream>>>(bsum.p, ntiles);
+  MSS_LAUNCH_CK("k_scan_tiles");
+  k_scan_apply<<<ntiles, SCAN_T, 0, h->stream>>>(in, out, n, bsum.p);
+  MSS_LAUNCH_CK("k_scan_apply");
+  // bsum is released here while the kernels may still run: the allocation
+  // hooks are stream-ordered (or cudaFree, which synchronises).
+}
+
+int read_int(Handle* h, const int* dptr) {
+  int v = 0;
+  MSS_CK(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  MSS_CK(cudaStreamSynchronize(h->stream));
+  return v;
+}
+
+double read_double(Handle* h, const double* dptr) {
+  double v = 0;
+  MSS_CK(cudaMemcpyAsync(&v, dptr, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  MSS_CK(cudaStreamSynchronize(h->stream));
+  return v;
+}
+
+void fill_int(Handle* h, int* p, int value, long long n) {
+  if (n <= 0) return;
+  k_fill_int<<<grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256), 256, 0, h->stream>>>(p, value, n);
+  MSS_LAUNCH_CK("k_fill_int");
+}
+
+void fill_double(Handle* h, double* p, double value, long long n) {
+  if (n <= 0) return;
+  k_fill_double<<<grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256), 256, 0, h->stream>>>(p, value,
+                                                                                          n);
+  MSS_LAUNCH_CK("k_fill_double");
+}
+
+void copy_dev(Handle* h, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return;
+  MSS_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->stream));
+}
+
+}  // namespace mss

@@ -1,0 +1,310 @@
+"""Thin ctypes binding of libmss.so (the C-ABI in include/mss.h).
+
+Argument marshalling only: every step of the set-up and the solve runs in the
+CUDA library. PyTorch provides device memory (its caching allocator, through
+the allocation hooks) and the stream. A missing library raises; there is no
+CPU or PyTorch fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "libmss.so"
+
+OK = 0
+ERR_INVALID_ARG, ERR_SINGULAR_BLOCK, ERR_NOT_CONVERGED, ERR_BREAKDOWN = -1, -2, -3, -4
+ERR_CUDA, ERR_OOM, ERR_AMG, ERR_NOT_SETUP = -5, -6, -7, -8
+
+SCHEMES = {"cptr3": 0, "cpr": 1, "ilu0": 2}
+SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
+
+# every exported symbol declared in include/mss.h
+EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
+           "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
+           "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
+           "mss_bilu_num_colours", "mss_bilu_ordering", "mss_status_string", "mss_last_error"]
+
+
+class Options(C.Structure):
+    _fields_ = [("scheme", C.c_int32), ("stage_order", C.c_int32), ("stage3", C.c_int32),
+                ("ilu_order", C.c_int32), ("smoother", C.c_int32), ("nu_pre", C.c_int32),
+                ("nu_post", C.c_int32), ("cheb_degree", C.c_int32),
+                ("amg_max_coarse", C.c_int32), ("amg_max_levels", C.c_int32),
+                ("interp_max_elems", C.c_int32), ("restart", C.c_int32),
+                ("precision", C.c_int32), ("pad_", C.c_int32),
+                ("amg_theta", C.c_double), ("jacobi_omega", C.c_double),
+                ("cheb_lo_ratio", C.c_double), ("cheb_hi_factor", C.c_double),
+                ("seed", C.c_uint64), ("learned_interp", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32),
+                ("pad_", C.c_int32), ("rel_res_implicit", C.c_double),
+                ("rel_res_true", C.c_double), ("setup_ms", C.c_double),
+                ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class Bsr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("nnzb", C.c_int32), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("vals", C.c_void_p)]
+
+
+class Layout(C.Structure):
+    _fields_ = [("p_idx", C.c_int32), ("t_idx", C.c_int32), ("col_major_blocks", C.c_int32)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib = None
+
+
+def load(path: Path | str | None = None):
+    """Load libmss.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"{p} is missing: build it with paper_1912_04385_gb300.build.build()")
+    L = C.CDLL(str(p))
+    P = C.c_void_p
+    L.mss_options_default.argtypes = [C.POINTER(Options)]
+    L.mss_create.argtypes = [C.POINTER(P), P, ALLOC_FN, FREE_FN, P]
+    L.mss_destroy.argtypes = [P]
+    L.mss_destroy.restype = None
+    L.mss_setup.argtypes = [P, C.POINTER(Bsr), C.c_int, Layout, C.POINTER(Options)]
+    L.mss_scale_rhs.argtypes = [P, P, P]
+    L.mss_spmv.argtypes = [P, P, P]
+    L.mss_apply.argtypes = [P, P, P]
+    L.mss_stage_apply.argtypes = [P, C.c_int, P, P]
+    L.mss_fgmres_solve.argtypes = [P, C.POINTER(Bsr), P, P, C.c_double, C.c_int,
+                                   C.POINTER(Result)]
+    L.mss_solve_host.argtypes = [P, C.POINTER(Bsr), C.c_int, Layout, C.POINTER(Options), P, P,
+                                 C.c_double, C.c_int, C.POINTER(Result)]
+    L.mss_get_scaled.argtypes = [P, P]
+    L.mss_amg_num_levels.argtypes = [P, C.c_int]
+    L.mss_amg_level_sizes.argtypes = [P, C.c_int, C.c_int, P]
+    L.mss_amg_level_copy.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P, P, P]
+    L.mss_bilu_num_colours.argtypes = [P, P]
+    L.mss_bilu_ordering.argtypes = [P, P, P]
+    L.mss_status_string.restype = C.c_char_p
+    L.mss_status_string.argtypes = [C.c_int]
+    L.mss_last_error.restype = C.c_char_p
+    L.mss_last_error.argtypes = [P]
+    if path is None:
+        _lib = L
+    return L
+
+
+class MssError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+def options(**kw) -> Options:
+    """Library defaults with keyword overrides (scheme/smoother accept names)."""
+    o = Options()
+    load().mss_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "scheme" and isinstance(v, str):
+            v = SCHEMES[v]
+        if k == "smoother" and isinstance(v, str):
+            v = SMOOTHERS[v]
+        if not hasattr(o, k) or k in ("pad_", "learned_interp"):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+class Solver:
+    """One library handle on the current device and torch stream."""
+
+    def __init__(self, stream=None, torch_allocator: bool = True):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.device = torch.cuda.current_device()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        self._keep = []
+        if torch_allocator:
+            dev = self.device
+
+            def _alloc(nbytes, ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, s)
+                except Exception:   # the library reports MSS_ERR_OOM
+                    return None
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+        else:
+            a, f = ALLOC_FN(), FREE_FN()
+        self._keep += [a, f]
+        h = C.c_void_p()
+        self._check(self.lib.mss_create(C.byref(h), C.c_void_p(s.cuda_stream), a, f, None),
+                    "mss_create", handle=False)
+        self.h = h
+        self.N = self.nb = self.nnzb = 0
+        self._J = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mss_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what, handle=True):
+        if st != OK:
+            msg = self.lib.mss_status_string(st).decode()
+            if handle and getattr(self, "h", None):
+                msg += ": " + self.lib.mss_last_error(self.h).decode()
+            raise MssError(st, f"{what} -> {msg}")
+        return st
+
+    # ---- set-up ---------------------------------------------------------
+    def setup(self, row_ptr, col_idx, vals, nb: int, p_idx: int = 0, t_idx: int = 1,
+              col_major: bool = False, opts: Options | None = None, **kw):
+        """row_ptr/col_idx: int32 CUDA tensors, vals: float64 CUDA tensor of
+        nnzb*nb*nb entries. The tensors are kept alive by the solver."""
+        torch = self._torch
+        for t in (row_ptr, col_idx, vals):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("matrix arrays must be contiguous CUDA tensors")
+        if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32 or vals.dtype != torch.float64:
+            raise ValueError("row_ptr/col_idx must be int32 and vals float64")
+        o = opts if opts is not None else options(**kw)
+        self.N, self.nb, self.nnzb = row_ptr.numel() - 1, nb, col_idx.numel()
+        self._J = Bsr(self.N, self.nnzb, _ptr(row_ptr), _ptr(col_idx), _ptr(vals))
+        self._Jt = (row_ptr, col_idx, vals)
+        self.opts = o
+        self._check(self.lib.mss_setup(self.h, C.byref(self._J), nb,
+                                       Layout(p_idx, t_idx, int(col_major)), C.byref(o)),
+                    "mss_setup")
+        return self
+
+    def setup_system(self, sysm, **kw):
+        torch = self._torch
+        rp = torch.from_numpy(np.ascontiguousarray(sysm.row_ptr, np.int32)).cuda()
+        ci = torch.from_numpy(np.ascontiguousarray(sysm.col_idx, np.int32)).cuda()
+        v = torch.from_numpy(np.ascontiguousarray(sysm.vals, np.float64)).cuda()
+        return self.setup(rp, ci, v, sysm.nb, sysm.p_idx, sysm.t_idx, **kw)
+
+    # ---- operators ------------------------------------------------------
+    def _vec(self, x):
+        torch = self._torch
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+                and x.numel() == self.N * self.nb):
+            raise ValueError("expected a contiguous float64 CUDA vector of length N*nb")
+        return x
+
+    def _out(self):
+        return self._torch.empty(self.N * self.nb, dtype=self._torch.float64, device="cuda")
+
+    def scale_rhs(self, b):
+        out = self._out()
+        self._check(self.lib.mss_scale_rhs(self.h, _ptr(self._vec(b)), _ptr(out)), "mss_scale_rhs")
+        return out
+
+    def spmv(self, x):
+        out = self._out()
+        self._check(self.lib.mss_spmv(self.h, _ptr(self._vec(x)), _ptr(out)), "mss_spmv")
+        return out
+
+    def apply(self, r):
+        out = self._out()
+        self._check(self.lib.mss_apply(self.h, _ptr(self._vec(r)), _ptr(out)), "mss_apply")
+        return out
+
+    def stage(self, which: int, r):
+        out = self._out()
+        self._check(self.lib.mss_stage_apply(self.h, which, _ptr(self._vec(r)), _ptr(out)),
+                    "mss_stage_apply")
+        return out
+
+    def solve(self, b, tol: float = 1e-6, maxit: int = 1000, x=None, raise_on_fail=False):
+        """Returns (x, info); info['status'] is the library status."""
+        x = self._out() if x is None else self._vec(x)
+        res = Result()
+        st = self.lib.mss_fgmres_solve(self.h, C.byref(self._J), _ptr(self._vec(b)), _ptr(x),
+                                       tol, maxit, C.byref(res))
+        if st not in (OK, ERR_NOT_CONVERGED) or (raise_on_fail and st != OK):
+            self._check(st, "mss_fgmres_solve")
+        return x, res.as_dict()
+
+    def solve_host(self, sysm, b=None, tol=1e-6, maxit=1000, opts: Options | None = None, **kw):
+        """End-to-end solve from host (numpy) arrays through mss_solve_host."""
+        o = opts if opts is not None else options(**kw)
+        rp = np.ascontiguousarray(sysm.row_ptr, np.int32)
+        ci = np.ascontiguousarray(sysm.col_idx, np.int32)
+        v = np.ascontiguousarray(sysm.vals, np.float64)
+        bb = np.ascontiguousarray(sysm.b if b is None else b, np.float64)
+        x = np.empty_like(bb)
+        J = Bsr(rp.shape[0] - 1, ci.shape[0], rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+        res = Result()
+        st = self.lib.mss_solve_host(self.h, C.byref(J), sysm.nb,
+                                     Layout(sysm.p_idx, sysm.t_idx, 0), C.byref(o),
+                                     bb.ctypes.data, x.ctypes.data, tol, maxit, C.byref(res))
+        if st not in (OK, ERR_NOT_CONVERGED):
+            self._check(st, "mss_solve_host")
+        return x, res.as_dict()
+
+    # ---- introspection ----------------------------------------------------
+    def scaled(self):
+        torch = self._torch
+        out = torch.empty(self.nnzb * self.nb * self.nb, dtype=torch.float64, device="cuda")
+        self._check(self.lib.mss_get_scaled(self.h, _ptr(out)), "mss_get_scaled")
+        return out.view(self.nnzb, self.nb, self.nb)
+
+    def amg_levels(self, which: int):
+        torch = self._torch
+        out = []
+        nlev = self.lib.mss_amg_num_levels(self.h, which)
+        for l in range(nlev):
+            sz = np.zeros(3, np.int32)
+            self._check(self.lib.mss_amg_level_sizes(self.h, which, l, sz.ctypes.data),
+                        "mss_amg_level_sizes")
+            n, nnz, nnzp = (int(v) for v in sz)
+            last = l == nlev - 1
+            i32 = dict(dtype=torch.int32, device="cuda")
+            f64 = dict(dtype=torch.float64, device="cuda")
+            arp, aci, av = torch.empty(n + 1, **i32), torch.empty(max(nnz, 1), **i32), \
+                torch.empty(max(nnz, 1), **f64)
+            cf, prp = torch.empty(max(n, 1), **i32), torch.empty(n + 1, **i32)
+            pci, pv = torch.empty(max(nnzp, 1), **i32), torch.empty(max(nnzp, 1), **f64)
+            self._check(self.lib.mss_amg_level_copy(
+                self.h, which, l, _ptr(arp), _ptr(aci), _ptr(av),
+                None if last else _ptr(cf), None if last else _ptr(prp),
+                None if last else _ptr(pci), None if last else _ptr(pv)), "mss_amg_level_copy")
+            out.append(dict(A=(arp, aci[:nnz], av[:nnz]), cf=None if last else cf[:n],
+                            P=None if last else (prp, pci[:nnzp], pv[:nnzp])))
+        return out
+
+    def bilu_ordering(self):
+        torch = self._torch
+        nc = C.c_int32(0)
+        self._check(self.lib.mss_bilu_num_colours(self.h, C.byref(nc)), "mss_bilu_num_colours")
+        colour = torch.empty(self.N, dtype=torch.int32, device="cuda")
+        perm = torch.empty(self.N, dtype=torch.int32, device="cuda")
+        self._check(self.lib.mss_bilu_ordering(self.h, _ptr(colour), _ptr(perm)),
+                    "mss_bilu_ordering")
+        return nc.value, colour, perm

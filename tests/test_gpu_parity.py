@@ -1,0 +1,228 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Bars (FP64 everywhere):
+* index work and set-up values that feed index decisions -- the scaled
+  blocks, C/F splits, interpolation operators, Galerkin coarse operators and
+  the multicolour ordering -- must match bit for bit (both sides evaluate
+  the same definition in the same order without FMA contraction);
+* operators whose summation order differs (V-cycles with a dense coarse
+  inverse versus LU, block ILU sweeps, the full preconditioner) must agree
+  to 1e-12 relative in the max norm;
+* FGMRES: converged iteration counts within +-1, and the solutions after the
+  same number of iterations (tol = 0) within 1e-8 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_04385_gb300 import synthetic as sy
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+APPLY_TOL = 1e-12
+SOL_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def mss():
+    from paper_1912_04385_gb300 import build, mss as m
+    build.build()
+    m.load()
+    return m
+
+
+def _gpu(mss, s, **kw):
+    return mss.Solver().setup_system(s, **kw)
+
+
+def _orc(s, **kw):
+    return oracle.OracleSolver.from_system(s, **kw)
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x, np.float64)).cuda()
+
+
+def _n(t):
+    return t.detach().cpu().numpy()
+
+
+CASES = [
+    dict(nx=32, ny=32, nb=4, pe=1.0),                                  # the small case
+    dict(nx=37, ny=23, nb=6, pe=10.0, sigma=2.0, band=True, seed=3),   # ragged, heterogeneous
+    dict(nx=29, ny=31, nb=5, pe=1000.0, sigma=1.0, band=True, seed=4, p_idx=2, t_idx=4),
+    dict(nx=40, ny=1, nb=3, pe=0.1, seed=5, p_idx=1, t_idx=0),          # 1D
+]
+
+
+def _sys(c):
+    c = dict(c)
+    return sy.make_system(c.pop("nx"), c.pop("ny"), c.pop("nb"), **c)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("scheme", ["cptr3", "cpr", "ilu0"])
+def test_scaled_matrix_bit_exact(mss, case, scheme):
+    s = _sys(CASES[case])
+    g = _gpu(mss, s, scheme=scheme)
+    o = _orc(s, scheme=scheme)
+    ab_o, _ = o.scaled()
+    ab_g = _n(g.scaled())
+    assert np.array_equal(ab_g, ab_o)
+    b = s.b
+    assert np.array_equal(_n(g.scale_rhs(_t(b))), o.scale_rhs(b))
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_amg_hierarchy_bit_exact(mss, case):
+    s = _sys(CASES[case])
+    kw = dict(scheme="cptr3", amg_max_coarse=10)
+    g = _gpu(mss, s, **kw)
+    o = _orc(s, scheme="cptr3", max_coarse=10)
+    for which in (0, 1):
+        lg, lo = g.amg_levels(which), o.amg_levels(which)
+        assert len(lg) == len(lo) >= 2
+        for a, b in zip(lg, lo):
+            for k in range(3):
+                assert np.array_equal(_n(a["A"][k]), b.A[k]), (which, k)
+            if b.cf is None:
+                assert a["cf"] is None
+                continue
+            assert np.array_equal(_n(a["cf"]), b.cf)
+            for k in range(3):
+                assert np.array_equal(_n(a["P"][k]), b.P[k])
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_multicolour_ordering_bit_exact(mss, case):
+    s = _sys(CASES[case])
+    g = _gpu(mss, s)
+    o = _orc(s)
+    nc, colour, perm = g.bilu_ordering()
+    f = o.bilu()
+    assert nc == f["ncolours"]
+    assert np.array_equal(_n(colour), f["colour"])
+    assert np.array_equal(_n(perm), f["perm"])
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("scheme,stage3,smoother,order", [
+    ("cptr3", 0, "jacobi", 0), ("cptr3", 1, "jacobi", 0), ("cptr3", 0, "chebyshev", 0),
+    ("cptr3", 0, "jacobi", 1), ("cpr", 0, "jacobi", 0), ("ilu0", 0, "jacobi", 0)])
+def test_stages_and_apply(mss, case, scheme, stage3, smoother, order):
+    s = _sys(CASES[case])
+    g = _gpu(mss, s, scheme=scheme, stage3=stage3, smoother=smoother, stage_order=order,
+             amg_max_coarse=40)
+    o = _orc(s, scheme=scheme, stage3=stage3, smoother=smoother, stage_order=order,
+             max_coarse=40)
+    rng = np.random.default_rng(case)
+    r = rng.standard_normal(s.n_cells * s.nb)
+    rt = _t(r)
+    stages = [2] + ([1] if scheme != "ilu0" else []) + ([0] if scheme == "cptr3" else [])
+    for which in stages:
+        assert _rel(_n(g.stage(which, rt)), o.stage(which, r)) < APPLY_TOL, which
+    assert _rel(_n(g.apply(rt)), o.apply(r)) < APPLY_TOL
+    x = rng.standard_normal(s.n_cells * s.nb)
+    assert _rel(_n(g.spmv(_t(x))), o.spmv(x)) < 1e-14
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("scheme", ["cptr3", "cpr"])
+def test_fgmres_iterations_and_solution(mss, case, scheme):
+    s = _sys(CASES[case])
+    m = 100
+    g = _gpu(mss, s, scheme=scheme, restart=m, amg_max_coarse=40)
+    o = _orc(s, scheme=scheme, restart=m, max_coarse=40)
+    bb = o.scale_rhs(s.b)
+    xo, io = o.fgmres(bb, tol=1e-8, maxit=400, restart=m)
+    xg, ig = g.solve(_t(s.b), tol=1e-8, maxit=400)
+    assert io["status"] == 0 and ig["status"] == 0
+    assert abs(ig["iters"] - io["iters"]) <= 1, (ig["iters"], io["iters"])
+    assert ig["rel_res_true"] <= 1e-8
+    # same number of iterations, no stopping test
+    k = min(io["iters"], 45)
+    xo, io2 = o.fgmres(bb, tol=0.0, maxit=k, restart=m)
+    xg, ig2 = g.solve(_t(s.b), tol=0.0, maxit=k)
+    assert ig2["iters"] == io2["iters"] == k
+    assert np.linalg.norm(_n(xg) - xo) <= SOL_TOL * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("stage3", [0, 1])
+def test_triangular_family_one_iteration_on_gpu(mss, stage3):
+    # Upper-block-triangular scaled matrix in [s, P, T]: with exact T and P
+    # stages (a one-level hierarchy is a direct solve) the residual left for
+    # the last stage has s components only, on which block ILU(0) (any
+    # ordering) and block Jacobi are exact, so M^-1 = Abar^-1.
+    s = sy.make_system(6, 5, 5, family="triangular", pe=1.0, seed=7)
+    g = _gpu(mss, s, scheme="cptr3", stage3=stage3, amg_max_coarse=1000)
+    x, info = g.solve(_t(s.b), tol=1e-10, maxit=5)
+    assert info["iters"] == 1 and info["rel_res_true"] < 1e-10
+
+
+def test_host_solve_matches_device_solve(mss):
+    s = sy.make_system(30, 20, 6, pe=10.0, sigma=2.0, band=True, seed=9)
+    g = _gpu(mss, s)
+    xd, idv = g.solve(_t(s.b), tol=1e-8, maxit=300)
+    h = mss.Solver()
+    xh, ih = h.solve_host(s, tol=1e-8, maxit=300)
+    assert ih["iters"] == idv["iters"]
+    assert np.array_equal(xh, _n(xd))
+
+
+@pytest.mark.parametrize("nb", [2, 3, 7, 8])
+def test_block_sizes(mss, nb):
+    s = sy.make_system(19, 17, nb, pe=1.0, seed=nb)
+    g = _gpu(mss, s, amg_max_coarse=30)
+    o = _orc(s, max_coarse=30)
+    r = np.random.default_rng(nb).standard_normal(s.n_cells * nb)
+    assert _rel(_n(g.apply(_t(r))), o.apply(r)) < APPLY_TOL
+
+
+def test_single_cell_and_column_major(mss):
+    s = sy.make_system(1, 1, 4, seed=1)
+    g = _gpu(mss, s)
+    o = _orc(s)
+    r = np.random.default_rng(0).standard_normal(4)
+    assert _rel(_n(g.apply(_t(r))), o.apply(r)) < APPLY_TOL
+    s2 = sy.make_system(11, 7, 5, pe=10.0, seed=2)
+    vt = np.ascontiguousarray(np.transpose(s2.vals, (0, 2, 1)))
+    rp = torch.from_numpy(s2.row_ptr).cuda()
+    ci = torch.from_numpy(s2.col_idx).cuda()
+    gc = mss.Solver().setup(rp, ci, _t(vt.reshape(-1)), 5, 0, 1, col_major=True)
+    gr = _gpu(mss, s2)
+    assert torch.equal(gc.scaled(), gr.scaled())
+
+
+def test_error_statuses(mss):
+    s = sy.make_system(6, 6, 4, seed=0)
+    ci = s.col_idx.copy()
+    ci[[1, 2]] = ci[[2, 1]]
+    bad = sy.BlockSystem(s.row_ptr, ci, s.vals, s.b, 6, 6, 4)
+    with pytest.raises(mss.MssError) as e:
+        _gpu(mss, bad)
+    assert e.value.status == mss.ERR_INVALID_ARG
+    vals = s.vals.copy()
+    vals[:] = 0.0
+    with pytest.raises(mss.MssError) as e:
+        _gpu(mss, sy.BlockSystem(s.row_ptr, s.col_idx, vals, s.b, 6, 6, 4))
+    assert e.value.status == mss.ERR_SINGULAR_BLOCK
+    g = _gpu(mss, s)
+    x, info = g.solve(_t(s.b), tol=1e-14, maxit=3)
+    assert info["status"] == mss.ERR_NOT_CONVERGED and info["iters"] == 3
+    assert np.all(np.isfinite(_n(x)))
+    nanb = s.b.copy()
+    nanb[5] = np.nan
+    with pytest.raises(mss.MssError) as e:
+        g.solve(_t(nanb), tol=1e-8, maxit=10)
+    assert e.value.status == mss.ERR_BREAKDOWN
+    with pytest.raises(mss.MssError) as e:
+        mss.Solver().setup_system(s, restart=500)
+    assert e.value.status == mss.ERR_INVALID_ARG
