@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark: time to a 1e-6 relative residual on a 1M-cell system.
+
+Workload: 1024 x 1024 grid, nb = 6 (P, T, 4 components), lognormal
+permeability (sigma 2, correlation length 16 cells), stiff reaction band,
+seed 0, one system per Peclet number in {0.1, 10, 1000}; CPTR3 preconditioned
+FGMRES(50) to a relative residual of 1e-6. One step = mss_setup +
+mss_fgmres_solve for each of the three systems, inputs resident in HBM
+(1.5 GB of blocks per system, far above the 129 MB L2). value = mean ms per
+system.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank solves its
+own replica of the workload (no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+PES = (0.1, 10.0, 1000.0)
+METRIC = "time-to-1e-6 rel. residual (ms) at 1M cells; FGMRES iters; precond HBM GB/s"
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--restart", type=int, default=50)
+    ap.add_argument("--maxit", type=int, default=1000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"cptr3-fgmres{a.restart}-{a.n}x{a.n}-nb6", "grid": [a.n, a.n], "nb": 6,
+            "cells": a.n * a.n, "pe": list(PES), "sigma": 2.0, "corr_len": 16, "band": True,
+            "seed": 0, "tol": a.tol, "scheme": "CPTR3 (T AMG, P AMG, multicolour BILU0)",
+            "restart": a.restart,
+            "l2": "inputs 1.5 GB per system >> 129 MB L2 (no flush needed)"}
+
+
+def systems(a):
+    from paper_1912_04385_gb300 import synthetic as sy
+    return [sy.plain_at_scale(a.n, pe=pe, seed=0) for pe in PES]
+
+
+# ---- clocks -----------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, enabled, device):
+        self.p = None
+        self.device = device
+        self.path = ROOT / "gpurun_out" / f"clocks_rank{device}.csv"
+        if not enabled:
+            return
+        try:
+            self.path.parent.mkdir(exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={device}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in self.path.read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        pmax = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in load for k, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": float(np.median([r[0] for r in load])),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "samples_under_load": len(load)}
+
+
+# ---- algorithmic bytes / flops of the traced kernels --------------------------
+def algorithmic(N, nnzb, nb):
+    """Per-call algorithmic bytes and flops (FP64 values, int32 indices)."""
+    nl = (nnzb - N) // 2          # strictly lower (= upper) blocks, symmetric pattern
+    B = nb * nb * 8
+    vec = N * nb * 8
+    spmv = dict(bytes=nnzb * (B + 4) + (N + 1) * 4 + 2 * vec, flops=2 * nnzb * nb * nb)
+    # forward: L blocks, column slices [t|p], indices, r, w (write), x_T, v_P
+    fwd = dict(bytes=nl * (B + 4) + nnzb * (2 * nb * 8 + 4) + 3 * N * 4 + 2 * vec + 2 * N * 8,
+               flops=2 * (nl * nb * nb + nnzb * 2 * nb))
+    # backward: U blocks, diagonal inverses, indices, w (read + write), y, x_T, v_P
+    bwd = dict(bytes=nl * (B + 4) + N * B + 3 * N * 4 + 3 * vec + 2 * N * 8,
+               flops=2 * (nl * nb * nb + N * nb * nb))
+    return {"spmv": spmv, "bilu_fwd": fwd, "bilu_bwd": bwd}
+
+
+def load_traffic(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken from the current sources."""
+    path = ROOT / "profiles" / "dram_traffic.json"
+    if not path.exists():
+        return None
+    try:
+        from paper_1912_04385_gb300 import build
+        rec = json.loads(path.read_text()).get(kernel)
+        if rec and rec.get("source_digest") == build._digest([]):
+            return rec.get("bytes_per_launch_full_size")
+    except Exception:
+        return None
+    return None
+
+
+# ---- our arm --------------------------------------------------------------------
+def run_ours(a, rank, world, dist):
+    import torch
+    from __graft_entry__ import build
+    from paper_1912_04385_gb300 import mss
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build()
+    lib = mss.load()
+    sysl = systems(a)
+    dev = []
+    for s in sysl:
+        dev.append((torch.from_numpy(s.row_ptr).cuda(), torch.from_numpy(s.col_idx).cuda(),
+                    torch.from_numpy(s.vals.reshape(-1)).cuda(), torch.from_numpy(s.b).cuda()))
+    torch.cuda.synchronize()
+    solver = mss.Solver()
+    opts = mss.options(restart=a.restart)
+    stream = torch.cuda.current_stream()
+
+    def step(trace=False, info_out=None):
+        for k, (rp, ci, v, b) in enumerate(dev):
+            solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
+            x, info = solver.solve(b, tol=a.tol, maxit=a.maxit)
+            if info["status"] != 0:
+                raise RuntimeError(f"solve failed for Pe={PES[k]}: {info}")
+            if info_out is not None:
+                info_out.append(info)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(a.warmup):
+        step()
+    barrier()
+    clocks = Clocks(not a.no_clocks, int(os.environ.get("LOCAL_RANK", "0")))
+    solver.trace(True)
+    solver.trace_read(reset=True)
+    lib.mss_kernel_launches(1)
+    infos = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(a.steps):
+        step(info_out=infos)
+    e1.record(stream)
+    barrier()
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    launches = int(lib.mss_kernel_launches(1))
+    tr = solver.trace_read(reset=True)
+    solver.trace(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    nsys = a.steps * len(PES)
+    value = ms / (nsys * world)
+    iters = [i["iters"] for i in infos[:len(PES)]]
+
+    # roofline of the dominant single-kernel class (traced live above)
+    s0 = sysl[0]
+    N, nnzb = s0.n_cells, s0.nnzb
+    alg = algorithmic(N, nnzb, 6)
+    ncol = solver.bilu_ordering()[0]
+    cands = {"spmv": tr["spmv"], "bilu_fwd": tr["bilu_fwd"], "bilu_bwd": tr["bilu_bwd"]}
+    top = max(cands, key=lambda k: cands[k][1])
+    nl, tot = cands[top]
+    calls = nl if top == "spmv" else nl / ncol        # sweeps: ncol launches per call
+    per_call_ms = tot / max(calls, 1)
+    per_launch_ms = tot / max(nl, 1)
+    flops = alg[top]["flops"] / (per_call_ms * 1e-3) / 1e12
+    gbs = alg[top]["bytes"] / (per_call_ms * 1e-3) / 1e9
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else {"hbm_gbs": 6800.0}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    kname = {"spmv": "k_bsr_spmv", "bilu_fwd": "k_bilu_fwd", "bilu_bwd": "k_bilu_bwd"}[top]
+    roofline = {"kernel": kname, "bound": "alu", "achieved": round(flops, 4),
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(flops / FP64_PEAK_TFLOPS, 4), "traffic": load_traffic(kname),
+                "peak_source": "FP64 FMA: 2/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.193 "
+                               "TFLOP/s at 2.0 GHz)",
+                "algorithmic_bytes_per_call": alg[top]["bytes"],
+                "algorithmic_flops_per_call": alg[top]["flops"],
+                "launches_per_call": 1 if top == "spmv" else ncol,
+                "avg_launch_ms": round(per_launch_ms, 5), "avg_call_ms": round(per_call_ms, 5),
+                "hbm_achieved_gbs": round(gbs, 1), "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": round(gbs / hbm_peak, 4)}
+    # preconditioner apply: algorithmic bytes (survey accounting) over traced time
+    n_apply, apply_ms = tr["apply"]
+    out = {"metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 3),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator, see DESIGN.md)",
+           "config": {**workload_config(a), "parallelism": f"replicas x{world}"},
+           "iters": iters, "iters_mean": float(np.mean(iters)),
+           "wall_ms_per_system": round(wall_ms / (nsys * world), 3),
+           "setup_ms_mean": round(float(np.mean([i["setup_ms"] for i in infos])), 3),
+           "solve_ms_mean": round(float(np.mean([i["solve_ms"] for i in infos])), 3),
+           "apply_ms_mean": round(apply_ms / max(n_apply, 1), 4),
+           "gpu_launches": launches,
+           "roofline": roofline,
+           "trace_ms": {k: [v[0], round(v[1], 3)] for k, v in tr.items()},
+           "clocks": clk}
+    bytes_apply = apply_alg_bytes(N, nnzb, 6, solver)
+    out["precond_gbs"] = round(bytes_apply / (apply_ms / max(n_apply, 1) * 1e-3) / 1e9, 1)
+    out["precond_alg_bytes"] = bytes_apply
+
+    # end to end through the C-ABI from pinned host buffers
+    if not a.no_e2e:
+        out["e2e"] = e2e(a, sysl, solver, opts, torch)
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a, sysl[1], steps=1)
+    return out
+
+
+def apply_alg_bytes(N, nnzb, nb, solver):
+    """Algorithmic bytes of one CPTR3 application: two V-cycles over the
+    stored hierarchies (each level: A twice for smoothing, once for the
+    residual, P and R once, vectors), z_P, and both last-stage sweeps."""
+    tot = 0
+    for which in (0, 1):
+        levs = solver.amg_levels(which)
+        for l, L in enumerate(levs):
+            n = L["A"][0].numel() - 1
+            nnz = L["A"][1].numel()
+            if l == len(levs) - 1:
+                tot += n * n * 8 + 2 * n * 8
+                continue
+            nnzp = L["P"][1].numel()
+            tot += 3 * (nnz * 12 + (n + 1) * 4) + 2 * (nnzp * 12 + (n + 1) * 4) + 8 * n * 8
+    tot += nnzb * 12 + (N + 1) * 4 + 3 * N * 8                  # z_P
+    alg = algorithmic(N, nnzb, nb)
+    tot += alg["bilu_fwd"]["bytes"] + alg["bilu_bwd"]["bytes"]
+    tot += 2 * N * 8                                            # gather r_T
+    return int(tot)
+
+
+def e2e(a, sysl, solver, opts, torch):
+    pinned = []
+    for s in sysl:
+        pin = {}
+        for name, arr in (("row_ptr", s.row_ptr), ("col_idx", s.col_idx), ("vals", s.vals),
+                          ("b", s.b)):
+            t = torch.empty(arr.shape, dtype={np.int32: torch.int32, np.float64: torch.float64}[
+                arr.dtype.type], pin_memory=True)
+            t.numpy()[...] = arr
+            pin[name] = t
+        x = torch.empty(s.b.shape, dtype=torch.float64, pin_memory=True)
+        from paper_1912_04385_gb300 import synthetic as sy
+        hs = sy.BlockSystem(pin["row_ptr"].numpy(), pin["col_idx"].numpy(), pin["vals"].numpy(),
+                            pin["b"].numpy(), s.nx, s.ny, s.nb, s.p_idx, s.t_idx)
+        pinned.append((hs, x, pin))
+    h2d = sum(p[0].row_ptr.nbytes + p[0].col_idx.nbytes + p[0].vals.nbytes + p[0].b.nbytes
+              for p in pinned)
+    d2h = sum(p[1].numpy().nbytes for p in pinned)
+
+    def step():
+        for hs, x, _ in pinned:
+            _, info = solver.solve_host(hs, tol=a.tol, maxit=a.maxit, opts=opts, x_out=x.numpy())
+            if info["status"] != 0:
+                raise RuntimeError(f"host solve failed: {info}")
+
+    for _ in range(max(1, min(a.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    return {"value": round(ms / (a.steps * len(sysl)), 3), "unit": "ms",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "path": "mss_solve_host (pinned host buffers; copies, set-up, solve, copy-back)"}
+
+
+def cpu_baseline(a, s, steps=1):
+    """The oracle as it stands, single-threaded, on a bounded sample: full
+    set-up of the 1M-cell Pe = 10 system plus 3 FGMRES iterations; the time
+    to solution is extrapolated with the oracle's own converged iteration
+    count (tests/golden/bench_oracle_iterations_<n>.json, written by a script
+    that calls only the oracle)."""
+    import oracle
+    it_path = ROOT / "tests" / "golden" / f"bench_oracle_iterations_{a.n}.json"
+    iters = None
+    if it_path.exists():
+        rec = json.loads(it_path.read_text())
+        for sysrec in rec["systems"]:
+            if abs(sysrec["pe"] - s.meta["pe"]) < 1e-12:
+                iters = sysrec["iters"]
+    vals = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        o = oracle.OracleSolver.from_system(s, restart=a.restart)
+        t_setup = time.perf_counter() - t0
+        bb = o.scale_rhs(s.b)
+        t1 = time.perf_counter()
+        k = 3
+        o.fgmres(bb, tol=0.0, maxit=k, restart=a.restart)
+        t_iter = (time.perf_counter() - t1) / k
+        del o
+        vals.append((t_setup, t_iter))
+    t_setup = float(np.median([v[0] for v in vals]))
+    t_iter = float(np.median([v[1] for v in vals]))
+    n_it = iters if iters is not None else 0
+    est_ms = (t_setup + n_it * t_iter) * 1e3
+    return {"value": round(est_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"oracle set-up ({t_setup:.2f} s) + 3 FGMRES iterations "
+                      f"({t_iter:.2f} s each) on the {a.n}x{a.n} Pe=10 system, extrapolated to "
+                      f"its converged count of {n_it} iterations",
+            "iters": n_it}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return None
+    from paper_1912_04385_gb300 import synthetic as sy
+    s = sy.plain_at_scale(a.n, pe=10.0, seed=0)
+    for _ in range(min(a.warmup, 1)):
+        pass                      # the CPU oracle needs no warm-up beyond this no-op
+    vals = []
+    t0 = time.perf_counter()
+    cb = None
+    for _ in range(a.steps):
+        cb = cpu_baseline(a, s, steps=1)
+        vals.append(cb["value"])
+    total = time.perf_counter() - t0
+    value = float(np.median(vals))
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(total * 1e3 / a.steps, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator)",
+            "config": {**workload_config(a), "parallelism": "cpu oracle, 1 thread"},
+            "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1,
+                             "kind": "oracle", "sample": cb["sample"] if cb else ""},
+            "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = args_()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if a.impl == "ours" and world > 1:
+        import torch
+        import torch.distributed as dist_
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist_.init_process_group("nccl")
+        dist = dist_
+    if a.impl == "reference":
+        out = run_reference(a, rank, world)
+    else:
+        out = run_ours(a, rank, world, dist)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

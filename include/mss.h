@@ -215,6 +215,25 @@ int mss_bilu_num_colours(mss_handle* h, int32_t* ncolours);
  * into caller-owned device arrays of N entries. */
 int mss_bilu_ordering(mss_handle* h, int32_t* colour, int32_t* perm);
 
+/* ---- measurement --------------------------------------------------------- */
+/* Number of kernel launches made by this library in this process since the
+ * last call with reset != 0 (the count before the reset is returned). */
+long long mss_kernel_launches(int reset);
+
+/* Event trace of kernel classes: when enabled, CUDA events recorded on the
+ * handle's stream bracket every BSR matrix-vector product (kind 0), every
+ * forward (1) and backward (2) last-stage sweep launch, every V-cycle (3),
+ * every Arnoldi orthogonalisation step (4), the set-up phases: scaling
+ * (5), each AMG hierarchy (6), ordering and factorisation (7), and every
+ * whole preconditioner application (8). */
+int mss_trace_enable(mss_handle* h, int enable);
+
+/* Totals for one kind since the last reset: number of bracketed regions
+ * and their summed elapsed GPU time in ms (host pointers, may be NULL).
+ * Synchronises the stream. reset != 0 zeroes the kind's totals after
+ * reading. Errors: INVALID_ARG for an unknown kind. */
+int mss_trace_read(mss_handle* h, int kind, int64_t* launches, double* ms, int reset);
+
 /* Human-readable name of a status code (static string). */
 const char* mss_status_string(int status);
 

@@ -342,6 +342,7 @@ void coarse_inverse(Handle* h, Hierarchy& H) {
   void* args[] = {&nn, &Mp, &pp, &sp};
   MSS_CK(cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(blocks), dim3(threads),
                                      args, smem, h->stream));
+  count_launch();
   int st = read_int(h, status.p);
   if (st != 0) fail(MSS_ERR_AMG, "coarsest AMG operator is singular (column " +
                                      std::to_string(st - 1) + ")");
@@ -350,7 +351,10 @@ void coarse_inverse(Handle* h, Hierarchy& H) {
   MSS_LAUNCH_CK("k_gj_extract");
 }
 
-void vcycle(Handle* h, Hierarchy& H, const double* b, double* x) { vcycle_level(h, H, 0, b, x); }
+void vcycle(Handle* h, Hierarchy& H, const double* b, double* x) {
+  TraceScope ts(h, TR_VCYCLE);
+  vcycle_level(h, H, 0, b, x);
+}
 
 void gather_var(Handle* h, const double* v, int var, double* out) {
   k_gather_var<<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, v, var, out);

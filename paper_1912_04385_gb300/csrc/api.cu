@@ -92,27 +92,34 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
   H.rp.reset(h, N + 1);
   H.ci.reset(h, nnzb);
   H.diag.reset(h, N);
-  copy_dev(h, H.rp.p, J->row_ptr, sizeof(int) * ((size_t)N + 1));
-  copy_dev(h, H.ci.p, J->col_idx, sizeof(int) * (size_t)nnzb);
-  validate_pattern(h, H.rp.p, H.ci.p, N, nnzb, H.diag.p);
-  // left scaling (Eq. splitPrec1 with Eq. CPR or Eqs. CPTR31/CPTR32)
-  H.wrows.reset(h, (size_t)N * 2 * nb);
-  H.abar.reset(h, (size_t)nnzb * nb * nb);
-  build_scaling(h, J->vals, layout.col_major_blocks != 0);
+  {
+    TraceScope ts(h, TR_SETUP_SCALE);
+    copy_dev(h, H.rp.p, J->row_ptr, sizeof(int) * ((size_t)N + 1));
+    copy_dev(h, H.ci.p, J->col_idx, sizeof(int) * (size_t)nnzb);
+    validate_pattern(h, H.rp.p, H.ci.p, N, nnzb, H.diag.p);
+    // left scaling (Eq. splitPrec1 with Eq. CPR or Eqs. CPTR31/CPTR32)
+    H.wrows.reset(h, (size_t)N * 2 * nb);
+    H.abar.reset(h, (size_t)nnzb * nb * nb);
+    build_scaling(h, J->vals, layout.col_major_blocks != 0);
+    if (o.scheme == MSS_CPTR3) {
+      H.apt.reset(h, nnzb);
+      H.atp.reset(h, nnzb);
+      extract_subsystem(h, -1, H.apt.p);
+      extract_subsystem(h, -2, H.atp.p);
+    }
+  }
   // scalar subsystems and their AMG hierarchies
   if (o.scheme != MSS_ILU0) {
+    TraceScope ts(h, TR_SETUP_AMG);
     DBuf<double> bpp(h, nnzb);
     extract_subsystem(h, H.p, bpp.p);             // B_PP
     amg_build(h, H.amgP, bpp.p);
   }
   if (o.scheme == MSS_CPTR3) {
+    TraceScope ts(h, TR_SETUP_AMG);
     DBuf<double> ctt(h, nnzb);
     extract_subsystem(h, H.t, ctt.p);             // C_TT
     amg_build(h, H.amgT, ctt.p);
-    H.apt.reset(h, nnzb);
-    H.atp.reset(h, nnzb);
-    extract_subsystem(h, -1, H.apt.p);
-    extract_subsystem(h, -2, H.atp.p);
   }
   // last stage
   bilu_setup(h);
@@ -398,6 +405,31 @@ int mss_bilu_ordering(mss_handle* hh, int32_t* colour, int32_t* perm) {
     if (colour) copy_dev(&H, colour, H.colour.p, sizeof(int) * (size_t)H.N);
     if (perm) copy_dev(&H, perm, H.perm.p, sizeof(int) * (size_t)H.N);
     MSS_CK(cudaStreamSynchronize(H.stream));
+  });
+}
+
+long long mss_kernel_launches(int reset) { return launch_count(reset != 0); }
+
+int mss_trace_enable(mss_handle* hh, int enable) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    trace_drain(&H);
+    H.trace = enable != 0;
+  });
+}
+
+int mss_trace_read(mss_handle* hh, int kind, int64_t* launches, double* ms, int reset) {
+  if (!hh || kind < 0 || kind >= TR_KINDS) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    trace_drain(&H);
+    if (launches) *launches = H.trace_n[kind];
+    if (ms) *ms = H.trace_ms[kind];
+    if (reset) {
+      H.trace_n[kind] = 0;
+      H.trace_ms[kind] = 0.0;
+    }
   });
 }
 

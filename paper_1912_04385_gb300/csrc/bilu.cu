@@ -408,6 +408,7 @@ void sweeps(Handle* h, const double* r, const double* xT, const double* vP, doub
     int q0 = h->cstart[c], q1 = h->cstart[c + 1];
     if (q1 <= q0) continue;
     long long warps = (q1 - q0 + RPW - 1) / RPW;
+    TraceScope ts(h, TR_BILU_FWD);
     k_bilu_fwd<NB, MODE><<<grid_for(warps * 32, T), T, 0, h->stream>>>(
         q0, q1, h->perm.p, h->frp.p, h->fdp.p, h->fpos.p, h->fcell.p, h->fv.p, h->fcs.p, r, xT, vP,
         h->w.p, bjac ? 0 : 1);
@@ -417,6 +418,7 @@ void sweeps(Handle* h, const double* r, const double* xT, const double* vP, doub
     int q0 = h->cstart[c], q1 = h->cstart[c + 1];
     if (q1 <= q0) continue;
     long long warps = (q1 - q0 + RPW - 1) / RPW;
+    TraceScope ts(h, TR_BILU_BWD);
     k_bilu_bwd<NB, MODE><<<grid_for(warps * 32, T), T, 0, h->stream>>>(
         q0, q1, h->perm.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p, h->fdinv.p, xT, vP, h->p, h->t,
         h->w.p, y, bjac ? 0 : 1);
@@ -437,7 +439,10 @@ void last_stage_nb(Handle* h, const double* r, const double* xT, const double* v
 
 }  // namespace
 
-void bilu_setup(Handle* h) { MSS_NB_DISPATCH(h->nb, bilu_setup_nb<NB>(h)); }
+void bilu_setup(Handle* h) {
+  TraceScope ts(h, TR_SETUP_BILU);
+  MSS_NB_DISPATCH(h->nb, bilu_setup_nb<NB>(h));
+}
 
 void last_stage_apply(Handle* h, const double* r, const double* xT, const double* vP, double* y) {
   MSS_NB_DISPATCH(h->nb, last_stage_nb<NB>(h, r, xT, vP, y));

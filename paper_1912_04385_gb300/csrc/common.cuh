@@ -22,8 +22,26 @@ struct Error {
 
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+void count_launch();   // process-wide count of this library's kernel launches
+long long launch_count(bool reset);
 #define MSS_CK(call) ::mss::check_cuda((call), #call, __FILE__, __LINE__)
-#define MSS_LAUNCH_CK(what) ::mss::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__)
+// every kernel launch is followed by MSS_LAUNCH_CK (error check and count)
+#define MSS_LAUNCH_CK(what) \
+  (::mss::count_launch(), ::mss::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__))
+
+// Optional event trace of kernel classes (CUDA events on the handle's stream).
+enum TraceKind {
+  TR_SPMV = 0,      // BSR matrix-vector product
+  TR_BILU_FWD,      // forward sweeps of the last stage (fused u)
+  TR_BILU_BWD,      // backward sweeps (fused y = x + v + M3 u)
+  TR_VCYCLE,        // one whole AMG V-cycle
+  TR_ORTHO,         // CGS2 projections, updates and norms of one Arnoldi step
+  TR_SETUP_SCALE,   // validation, scaling and extraction
+  TR_SETUP_AMG,     // one AMG hierarchy set-up
+  TR_SETUP_BILU,    // colouring, ordering and factorisation
+  TR_APPLY,         // one whole preconditioner application
+  TR_KINDS
+};
 
 struct Handle;
 void* dev_alloc(Handle* h, size_t bytes);
@@ -131,7 +149,28 @@ struct Handle {
   // scratch for reductions and flags
   DBuf<int> iflag;
   DBuf<double> dscr;
+  // event trace
+  struct TraceRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool trace = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<TraceRec> ev_pending;
+  double trace_ms[TR_KINDS] = {};
+  long long trace_n[TR_KINDS] = {};
+  ~Handle();
 };
+
+// Records an event pair around its lifetime when tracing is on.
+struct TraceScope {
+  Handle* h;
+  int kind;
+  cudaEvent_t a = nullptr;
+  TraceScope(Handle* hh, int k);
+  ~TraceScope();
+};
+void trace_drain(Handle* h);   // synchronises and accumulates finished pairs
 
 // SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator: the
 // value for counter k is the (k+1)-th output of the stream seeded with seed.

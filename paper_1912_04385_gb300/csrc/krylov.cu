@@ -315,11 +315,13 @@ double device_norm(Handle* h, const double* a, long long n, double* part, double
 }  // namespace
 
 void bsr_spmv(Handle* h, const double* x, double* y) {
+  TraceScope ts(h, TR_SPMV);
   MSS_NB_DISPATCH(h->nb, spmv_nb<NB>(h, x, y));
 }
 
 // y = M^{-1} r: Algorithm 2 (CPTR3), Algorithm 1 (CPR) or the last stage only
 void precond_apply(Handle* h, const double* r, double* y) {
+  TraceScope ts(h, TR_APPLY);
   const int scheme = h->opt.scheme;
   if (scheme == MSS_ILU0) {
     last_stage_apply(h, r, nullptr, nullptr, y);
@@ -403,21 +405,30 @@ int fgmres(Handle* h, const double* b, double* x, double tol, int maxit, mss_res
       precond_apply(h, vj, zj);
       bsr_spmv(h, zj, w);
       const int nv = j + 1;
-      // CGS pass 1: h1 = V^T w and ||w0||^2
-      k_mdot<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, w, 1, part);
-      MSS_LAUNCH_CK("k_mdot");
-      k_reduce<<<nv, KT, 0, h->stream>>>(nv, rs.G, part, h1);
-      k_reduce<<<1, KT, 0, h->stream>>>(1, rs.G, part + (size_t)nv * rs.G, sq);
-      // update with h1, fused pass-2 projections h2
-      k_update<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, h1, w, 0, part);
-      MSS_LAUNCH_CK("k_update");
-      k_reduce<<<nv, KT, 0, h->stream>>>(nv, rs.G, part, h2);
-      // update with h2 and the norm
-      k_update<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, h2, w, 1, part);
-      k_reduce<<<1, KT, 0, h->stream>>>(1, rs.G, part, sq + 1);
-      k_arnoldi_finish<<<1, 32, 0, h->stream>>>(j, m, h1, h2, sq, H, cs, sn, g, bnorm, ks);
-      k_normalize<<<sgrid, 256, 0, h->stream>>>(n, w, ks);
-      MSS_LAUNCH_CK("k_arnoldi");
+      {
+        TraceScope ts(h, TR_ORTHO);
+        // CGS pass 1: h1 = V^T w and ||w0||^2
+        k_mdot<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, w, 1, part);
+        MSS_LAUNCH_CK("k_mdot");
+        k_reduce<<<nv, KT, 0, h->stream>>>(nv, rs.G, part, h1);
+        MSS_LAUNCH_CK("k_reduce");
+        k_reduce<<<1, KT, 0, h->stream>>>(1, rs.G, part + (size_t)nv * rs.G, sq);
+        MSS_LAUNCH_CK("k_reduce");
+        // update with h1, fused pass-2 projections h2
+        k_update<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, h1, w, 0, part);
+        MSS_LAUNCH_CK("k_update");
+        k_reduce<<<nv, KT, 0, h->stream>>>(nv, rs.G, part, h2);
+        MSS_LAUNCH_CK("k_reduce");
+        // update with h2 and the norm
+        k_update<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, h2, w, 1, part);
+        MSS_LAUNCH_CK("k_update");
+        k_reduce<<<1, KT, 0, h->stream>>>(1, rs.G, part, sq + 1);
+        MSS_LAUNCH_CK("k_reduce");
+        k_arnoldi_finish<<<1, 32, 0, h->stream>>>(j, m, h1, h2, sq, H, cs, sn, g, bnorm, ks);
+        MSS_LAUNCH_CK("k_arnoldi_finish");
+        k_normalize<<<sgrid, 256, 0, h->stream>>>(n, w, ks);
+        MSS_LAUNCH_CK("k_normalize");
+      }
       double hks[5];
       MSS_CK(cudaMemcpyAsync(hks, ks, sizeof(hks), cudaMemcpyDeviceToHost, h->stream));
       MSS_CK(cudaStreamSynchronize(h->stream));
@@ -435,13 +446,15 @@ int fgmres(Handle* h, const double* b, double* x, double tol, int maxit, mss_res
     }
     if (k > 0) {
       k_backsolve<<<1, 32, 0, h->stream>>>(k, m, H, g, yv);
+      MSS_LAUNCH_CK("k_backsolve");
       k_xupdate<<<sgrid, 256, 0, h->stream>>>(n, Z, ld, k, yv, x);
       MSS_LAUNCH_CK("k_xupdate");
     }
     bsr_spmv(h, x, h->res.p);
     k_resid_norm<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, h->bbar.p, h->res.p, part);
-    k_reduce<<<1, KT, 0, h->stream>>>(1, rs.G, part, ks + 6);
     MSS_LAUNCH_CK("k_resid_norm");
+    k_reduce<<<1, KT, 0, h->stream>>>(1, rs.G, part, ks + 6);
+    MSS_LAUNCH_CK("k_reduce");
     beta = std::sqrt(read_double(h, ks + 6));
     res.rel_res_true = beta / bnorm;
     res.iters = total;

@@ -1,5 +1,6 @@
 // util.cu -- errors, device allocation through the handle's hooks, a
 // device-wide exclusive scan, fills and host read-backs.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -8,6 +9,58 @@
 namespace mss {
 
 [[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count(bool reset) {
+  return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+static cudaEvent_t take_event(Handle* h) {
+  if (!h->ev_free.empty()) {
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  MSS_CK(cudaEventCreate(&e));
+  return e;
+}
+
+TraceScope::TraceScope(Handle* hh, int k) : h(hh), kind(k) {
+  if (!h->trace) return;
+  a = take_event(h);
+  MSS_CK(cudaEventRecord(a, h->stream));
+}
+
+TraceScope::~TraceScope() {
+  if (!a) return;
+  cudaEvent_t b = take_event(h);
+  cudaEventRecord(b, h->stream);
+  h->ev_pending.push_back({kind, a, b});
+}
+
+void trace_drain(Handle* h) {
+  if (h->ev_pending.empty()) return;
+  MSS_CK(cudaStreamSynchronize(h->stream));
+  for (auto& r : h->ev_pending) {
+    float ms = 0.f;
+    MSS_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    h->trace_ms[r.kind] += ms;
+    h->trace_n[r.kind] += 1;
+    h->ev_free.push_back(r.a);
+    h->ev_free.push_back(r.b);
+  }
+  h->ev_pending.clear();
+}
+
+Handle::~Handle() {
+  for (auto& r : ev_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ev_free) cudaEventDestroy(e);
+}
 
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return;

@@ -25,7 +25,11 @@ SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
 EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
            "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
            "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
-           "mss_bilu_num_colours", "mss_bilu_ordering", "mss_status_string", "mss_last_error"]
+           "mss_bilu_num_colours", "mss_bilu_ordering", "mss_kernel_launches",
+           "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error"]
+
+TRACE_KINDS = {"spmv": 0, "bilu_fwd": 1, "bilu_bwd": 2, "vcycle": 3, "ortho": 4,
+               "setup_scale": 5, "setup_amg": 6, "setup_bilu": 7, "apply": 8}
 
 
 class Options(C.Structure):
@@ -94,6 +98,10 @@ def load(path: Path | str | None = None):
     L.mss_amg_level_copy.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P, P, P]
     L.mss_bilu_num_colours.argtypes = [P, P]
     L.mss_bilu_ordering.argtypes = [P, P, P]
+    L.mss_kernel_launches.restype = C.c_longlong
+    L.mss_kernel_launches.argtypes = [C.c_int]
+    L.mss_trace_enable.argtypes = [P, C.c_int]
+    L.mss_trace_read.argtypes = [P, C.c_int, P, P, C.c_int]
     L.mss_status_string.restype = C.c_char_p
     L.mss_status_string.argtypes = [C.c_int]
     L.mss_last_error.restype = C.c_char_p
@@ -251,14 +259,17 @@ class Solver:
             self._check(st, "mss_fgmres_solve")
         return x, res.as_dict()
 
-    def solve_host(self, sysm, b=None, tol=1e-6, maxit=1000, opts: Options | None = None, **kw):
-        """End-to-end solve from host (numpy) arrays through mss_solve_host."""
+    def solve_host(self, sysm, b=None, tol=1e-6, maxit=1000, opts: Options | None = None,
+                   x_out=None, **kw):
+        """End-to-end solve from host (numpy) arrays through mss_solve_host.
+        Arrays that already are contiguous (e.g. views of pinned memory) are
+        passed without a copy; x_out receives the solution when given."""
         o = opts if opts is not None else options(**kw)
         rp = np.ascontiguousarray(sysm.row_ptr, np.int32)
         ci = np.ascontiguousarray(sysm.col_idx, np.int32)
         v = np.ascontiguousarray(sysm.vals, np.float64)
         bb = np.ascontiguousarray(sysm.b if b is None else b, np.float64)
-        x = np.empty_like(bb)
+        x = np.empty_like(bb) if x_out is None else x_out
         J = Bsr(rp.shape[0] - 1, ci.shape[0], rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
         res = Result()
         st = self.lib.mss_solve_host(self.h, C.byref(J), sysm.nb,
@@ -267,6 +278,21 @@ class Solver:
         if st not in (OK, ERR_NOT_CONVERGED):
             self._check(st, "mss_solve_host")
         return x, res.as_dict()
+
+    # ---- measurement ------------------------------------------------------
+    def trace(self, enable: bool = True):
+        self._check(self.lib.mss_trace_enable(self.h, int(enable)), "mss_trace_enable")
+
+    def trace_read(self, reset: bool = True):
+        """{kind: (regions, total ms)} for every traced kind."""
+        out = {}
+        for name, k in TRACE_KINDS.items():
+            n = C.c_int64(0)
+            ms = C.c_double(0.0)
+            self._check(self.lib.mss_trace_read(self.h, k, C.byref(n), C.byref(ms), int(reset)),
+                        "mss_trace_read")
+            out[name] = (n.value, ms.value)
+        return out
 
     # ---- introspection ----------------------------------------------------
     def scaled(self):
