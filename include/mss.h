@@ -53,9 +53,10 @@ extern "C" {
 enum { MSS_CPTR3 = 0, MSS_CPR = 1, MSS_ILU0 = 2 };   /* preconditioner scheme */
 enum { MSS_STAGE_T_FIRST = 0, MSS_STAGE_P_FIRST = 1 }; /* CPTR3 stage order */
 enum { MSS_BILU0 = 0, MSS_BLOCK_JACOBI = 1 };        /* last stage */
-enum { MSS_MULTICOLOR = 0 };                         /* block ILU(0) ordering */
+enum { MSS_MULTICOLOR = 0, MSS_STRIPS = 2 };         /* block ILU(0) ordering */
 enum { MSS_JACOBI = 0, MSS_CHEBYSHEV = 1 };          /* AMG smoother */
 enum { MSS_FP64 = 0 };                               /* arithmetic */
+enum { MSS_CGS1 = 0, MSS_CGS2 = 1 };                 /* Arnoldi orthogonalisation */
 
 /* A BSR matrix; the arrays are device memory owned by the caller. */
 typedef struct {
@@ -78,7 +79,9 @@ typedef struct {
   int32_t scheme;           /* MSS_CPTR3 (default) | MSS_CPR | MSS_ILU0 */
   int32_t stage_order;      /* MSS_STAGE_T_FIRST (Algorithm 2, default) | P first */
   int32_t stage3;           /* MSS_BILU0 (default) | MSS_BLOCK_JACOBI */
-  int32_t ilu_order;        /* MSS_MULTICOLOR */
+  int32_t ilu_order;        /* MSS_STRIPS (default): strips of ilu_strip consecutive
+                               cells, coloured, natural order inside a strip;
+                               MSS_MULTICOLOR: every cell coloured on its own */
   int32_t smoother;         /* MSS_JACOBI (default) | MSS_CHEBYSHEV */
   int32_t nu_pre, nu_post;  /* smoothing sweeps per V-cycle leg (1, 1) */
   int32_t cheb_degree;      /* Chebyshev polynomial degree (2) */
@@ -87,6 +90,8 @@ typedef struct {
   int32_t interp_max_elems; /* interpolation row truncation, 0 = none (4) */
   int32_t restart;          /* FGMRES restart length m (30) */
   int32_t precision;        /* MSS_FP64 */
+  int32_t ilu_strip;        /* strip length in cells for MSS_STRIPS (32), 1..1024 */
+  int32_t orthog;           /* Arnoldi: MSS_CGS1 (default) | MSS_CGS2 */
   int32_t pad_;
   double amg_theta;         /* strength threshold (0.25) */
   double jacobi_omega;      /* Jacobi damping (2/3) */
@@ -139,7 +144,8 @@ void mss_destroy(mss_handle* h);
  * (Eqs. CPR, CPTR31, CPTR32) and builds an AMG hierarchy for each
  * (Eqs. CPRM1, CPTR3M1, CPTRM2; classical AMG, coarse size <= 1000, Sec.
  * 5.1); and factors the last stage, block ILU(0) of Abar (Eq. CPTR3M3) in a
- * multicolour ordering. J's arrays are copied or consumed during the call;
+ * colour-major ordering of strips (or of single cells). J's arrays are
+ * copied or consumed during the call;
  * the caller may free them afterwards, except that mss_fgmres_solve checks
  * that it receives the same mss_bsr (pointers and sizes). `opt` may be NULL
  * (defaults). nb in [2, 8] (CPTR3 needs nb >= 2). Errors: INVALID_ARG (bad
@@ -169,7 +175,8 @@ int mss_apply(mss_handle* h, const double* r, double* y);
 int mss_stage_apply(mss_handle* h, int which, const double* r, double* y);
 
 /* Solve A x = b: bbar = N^{-1} b, then right-preconditioned restarted
- * FGMRES(m) on Abar from x = 0 (Sec. 5.1; restart is a reading) until the
+ * FGMRES(m) on Abar from x = 0 (Sec. 5.1; restart is a reading; classical
+ * Gram-Schmidt once or twice per step, opt.orthog) until the
  * implicit residual |g|/||bbar|| <= tol and the true residual
  * ||bbar - Abar x||/||bbar|| <= tol, or maxit inner iterations. J must be
  * the mss_bsr passed to mss_setup. b, x: device, length N*nb; x is written

@@ -53,13 +53,13 @@ typedef struct {
   int stage_order;   /* 0: T stage then P stage (Alg. 2 order); 1: P then T */
   int exact_sub;     /* 1: M_TT = C_TT^-1 and M_PP = B_PP^-1 by dense LU */
   int stage3;        /* 0: block ILU(0) of the scaled matrix, 1: block Jacobi */
-  int ilu_order;     /* 0: multicolour (Jones-Plassmann), 1: natural */
+  int ilu_order;     /* 0: multicolour (Jones-Plassmann), 1: natural, 2: strips */
   int smoother;      /* 0: damped Jacobi, 1: Chebyshev, 2: symmetric Gauss-Seidel */
   int nu_pre, nu_post;
   int cheb_degree;
   int max_coarse, max_levels, interp_max;
   int restart;
-  int pad_;
+  int ilu_strip;     /* strip length (cells) of the strip ordering */
   double theta, omega, cheb_lo_ratio, cheb_hi_factor;
   uint64_t seed;
 } or_opts;
@@ -75,7 +75,7 @@ void or_opts_default(or_opts* o) {
   o->stage_order = 0;
   o->exact_sub = 0;
   o->stage3 = 0;
-  o->ilu_order = 0;
+  o->ilu_order = 2;      /* strips of ilu_strip cells (reading) */
   o->smoother = 0;
   o->nu_pre = 1;
   o->nu_post = 1;
@@ -84,6 +84,7 @@ void or_opts_default(or_opts* o) {
   o->max_levels = 25;
   o->interp_max = 4;
   o->restart = 30;
+  o->ilu_strip = 32;
   o->theta = 0.25;
   o->omega = 2.0 / 3.0;
   o->cheb_lo_ratio = 30.0;
@@ -899,13 +900,69 @@ static void bilu_free(bilu_t* f) {
   free(f);
 }
 
-/* Block ILU(0) of P Abar P^T, P the ordering permutation (natural or
- * colour-major, cells ascending within a colour), by the row-wise IKJ
+/* Strip colouring: cells are grouped into strips of `strip` consecutive
+ * indices, and the strips are coloured by Jones-Plassmann on the strip
+ * graph (strips a != b adjacent when a block couples a cell of a to a cell
+ * of b), with SplitMix64 priorities (key 0xFFFE<<32 | strip): per
+ * synchronous round every uncoloured strip whose (priority, index) beats all
+ * uncoloured adjacent strips takes the smallest colour unused by its
+ * coloured adjacent strips. A cell takes its strip's colour; with the
+ * colour-major order below each strip keeps its natural order. */
+static int strip_colour(int n, const int* rp, const int* ci, int strip, uint64_t seed,
+                        int* colour, int* ncol_out) {
+  if (strip < 1) return OR_ERR_ARG;
+  int ns = (n + strip - 1) / strip, ncol = 0;
+  int* sc = (int*)malloc(sizeof(int) * (size_t)(ns > 0 ? ns : 1));
+  int* pick = (int*)malloc(sizeof(int) * (size_t)(ns > 0 ? ns : 1));
+  uint64_t* pr = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(ns > 0 ? ns : 1));
+  if (!sc || !pick || !pr) return OR_ERR_MEM;
+  for (int a = 0; a < ns; ++a) {
+    sc[a] = -1;
+    pr[a] = or_splitmix(seed, (0xFFFEULL << 32) | (uint64_t)(unsigned)a);
+  }
+  int left = ns;
+  while (left > 0) {
+    for (int a = 0; a < ns; ++a) {
+      pick[a] = -1;
+      if (sc[a] >= 0) continue;
+      int lo = a * strip, hi = lo + strip < n ? lo + strip : n, best = 1;
+      for (int i = lo; i < hi && best; ++i)
+        for (int e = rp[i]; e < rp[i + 1] && best; ++e) {
+          int b = ci[e] / strip;
+          if (b == a || sc[b] >= 0) continue;
+          if (pr[b] > pr[a] || (pr[b] == pr[a] && b > a)) best = 0;
+        }
+      if (!best) continue;
+      for (int c = 0;; ++c) {
+        int used = 0;
+        for (int i = lo; i < hi && !used; ++i)
+          for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            int b = ci[e] / strip;
+            if (b != a && sc[b] == c) { used = 1; break; }
+          }
+        if (!used) { pick[a] = c; break; }
+      }
+    }
+    for (int a = 0; a < ns; ++a)
+      if (pick[a] >= 0) {
+        sc[a] = pick[a];
+        if (pick[a] + 1 > ncol) ncol = pick[a] + 1;
+        --left;
+      }
+  }
+  for (int i = 0; i < n; ++i) colour[i] = sc[i / strip];
+  *ncol_out = ncol;
+  free(sc); free(pick); free(pr);
+  return OR_OK;
+}
+
+/* Block ILU(0) of P Abar P^T, P the ordering permutation (natural, or
+ * colour-major with cells ascending within a colour), by the row-wise IKJ
  * elimination restricted to the block pattern, without pivoting.
  * Parity: pinned (exact on block-tridiagonal 1D systems in natural order,
  * L U reproduces the matrix on the pattern). */
 static int bilu_factor(int n, int nb, const int* rp, const int* ci, const double* v, int order,
-                       uint64_t seed, bilu_t** out) {
+                       int strip, uint64_t seed, bilu_t** out) {
   int nb2 = nb * nb;
   bilu_t* f = (bilu_t*)calloc(1, sizeof(bilu_t));
   if (!f) return OR_ERR_MEM;
@@ -924,14 +981,16 @@ static int bilu_factor(int n, int nb, const int* rp, const int* ci, const double
   int st;
   if (order == 0) {
     if ((st = jp_colour(n, rp, ci, seed, f->colour, &f->ncol)) != OR_OK) { bilu_free(f); return st; }
+  } else if (order == 2) {
+    if ((st = strip_colour(n, rp, ci, strip, seed, f->colour, &f->ncol)) != OR_OK) { bilu_free(f); return st; }
   } else {
     f->ncol = n > 0 ? 1 : 0;
   }
   /* colour-major, ascending cell index within a colour */
   int k = 0;
-  for (int c = 0; c < (order == 0 ? f->ncol : 1); ++c)
+  for (int c = 0; c < (order != 1 ? f->ncol : 1); ++c)
     for (int i = 0; i < n; ++i)
-      if (order != 0 || f->colour[i] == c) f->perm[k++] = i;
+      if (order == 1 || f->colour[i] == c) f->perm[k++] = i;
   for (int q = 0; q < n; ++q) f->iperm[f->perm[q]] = q;
   /* permuted pattern with ascending position columns */
   f->rp[0] = 0;
@@ -1168,7 +1227,7 @@ or_solver* or_setup(int N, int nb, const int* rp, const int* ci, const double* v
     }
   }
   if (o->stage3 == 0) {
-    if ((st = bilu_factor(N, nb, rp, ci, s->Abar, o->ilu_order, o->seed, &s->ilu)) != OR_OK)
+    if ((st = bilu_factor(N, nb, rp, ci, s->Abar, o->ilu_order, o->ilu_strip, o->seed, &s->ilu)) != OR_OK)
       goto fail;
   } else {
     for (int i = 0; i < N; ++i) {   /* block Jacobi: only check invertibility */

@@ -24,7 +24,7 @@ class OrOpts(C.Structure):
                 ("stage3", C.c_int), ("ilu_order", C.c_int), ("smoother", C.c_int),
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("cheb_degree", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("interp_max", C.c_int),
-                ("restart", C.c_int), ("pad_", C.c_int),
+                ("restart", C.c_int), ("ilu_strip", C.c_int),
                 ("theta", C.c_double), ("omega", C.c_double), ("cheb_lo_ratio", C.c_double),
                 ("cheb_hi_factor", C.c_double), ("seed", C.c_uint64)]
 

@@ -38,7 +38,9 @@ void check_options(const mss_options& o) {
   if (o.stage_order != MSS_STAGE_T_FIRST && o.stage_order != MSS_STAGE_P_FIRST)
     bad("stage_order");
   if (o.stage3 != MSS_BILU0 && o.stage3 != MSS_BLOCK_JACOBI) bad("stage3");
-  if (o.ilu_order != MSS_MULTICOLOR) bad("ilu_order (only MSS_MULTICOLOR on the device)");
+  if (o.ilu_order != MSS_MULTICOLOR && o.ilu_order != MSS_STRIPS) bad("ilu_order");
+  if (o.ilu_strip < 1 || o.ilu_strip > 1024) bad("ilu_strip (1..1024)");
+  if (o.orthog != MSS_CGS1 && o.orthog != MSS_CGS2) bad("orthog");
   if (o.smoother != MSS_JACOBI && o.smoother != MSS_CHEBYSHEV) bad("smoother");
   if (o.nu_pre < 0 || o.nu_pre > 16 || o.nu_post < 0 || o.nu_post > 16) bad("nu_pre/nu_post");
   if (o.smoother == MSS_JACOBI && o.nu_pre < 1) bad("nu_pre (Jacobi needs >= 1)");
@@ -61,7 +63,8 @@ void release_setup(Handle& H) {
   H.rp.release(); H.ci.release(); H.diag.release();
   H.abar.release(); H.wrows.release(); H.apt.release(); H.atp.release();
   H.colour.release(); H.perm.release(); H.iperm.release();
-  H.frp.release(); H.fpos.release(); H.fcell.release(); H.fdp.release();
+  H.frp.release(); H.fpos.release(); H.fcell.release(); H.fdp.release(); H.fsrc.release();
+  H.st_first.release(); H.st_len.release(); H.sc_start.clear();
   H.fv.release(); H.fdinv.release(); H.fcs.release();
   H.rT.release(); H.xT.release(); H.zP.release(); H.vP.release(); H.w.release();
   H.cstart.clear();
@@ -175,7 +178,9 @@ int mss_options_default(mss_options* o) {
   o->scheme = MSS_CPTR3;
   o->stage_order = MSS_STAGE_T_FIRST;
   o->stage3 = MSS_BILU0;
-  o->ilu_order = MSS_MULTICOLOR;
+  o->ilu_order = MSS_STRIPS;
+  o->ilu_strip = 32;
+  o->orthog = MSS_CGS1;
   o->smoother = MSS_JACOBI;
   o->nu_pre = 1;
   o->nu_post = 1;

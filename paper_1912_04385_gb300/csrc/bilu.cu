@@ -1,21 +1,24 @@
 // bilu.cu -- last stage of the multi-stage preconditioner: block ILU(0) of
-// the scaled matrix (Eq. CPTR3M3; the CPR second stage) in a multicolour
-// ordering, or block Jacobi, plus the fused stage arithmetic around it.
+// the scaled matrix (Eq. CPTR3M3; the CPR second stage), or block Jacobi,
+// plus the fused stage arithmetic around it.
 //
-// Ordering: Jones-Plassmann colouring with SplitMix64 priorities; cells are
-// renumbered colour-major (ascending cell index inside a colour), so that
-// every colour is a contiguous range of "positions" and the factor blocks
-// of a colour are contiguous in memory. The factorisation and both
-// triangular sweeps then run one launch per colour; cells of one colour are
-// never adjacent, so each launch is fully parallel.
+// Ordering. Cells are grouped into strips of `ilu_strip` consecutive cells
+// (or single cells for the point-multicolour order) and the strips are
+// coloured by Jones-Plassmann with SplitMix64 priorities. Cells are then
+// renumbered colour-major with ascending cell index inside a colour, so a
+// colour is a contiguous range of positions made of whole strips, and each
+// strip keeps its natural order. Strips of one colour are never coupled, so
+// they are factored and swept in parallel; inside a strip the rows are
+// processed in order. Natural order inside strips keeps the upwind chains of
+// the advection operators that a point colouring cuts at every cell.
 //
 // Apply (Algorithm 2, fused): the forward sweep forms
 //   u = r - Abar[:,t] x_T - Abar[:,p] v_P
 // on the fly from per-block column slices, and the backward sweep writes
 //   y = x + v + M3 u
-// directly, so u, z and the intermediate stage vectors are never stored.
-// Sweeps use NB lanes per cell row (lane c owns component c), so a row's
-// nb x nb blocks are read as contiguous rows by adjacent lanes.
+// directly. A strip is swept by NB lanes (lane c owns component c), so a
+// row's nb x nb blocks are read as contiguous rows by adjacent lanes; the
+// factorisation gives each strip a whole warp.
 #include <algorithm>
 
 #include "common.cuh"
@@ -23,46 +26,58 @@
 namespace mss {
 namespace {
 
-// ---- colouring ------------------------------------------------------------
-__global__ void k_jp_pick(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                          uint64_t seed, const int* __restrict__ colour, int* __restrict__ pick) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+constexpr uint64_t KEY_CELL = 0xFFFFULL << 32;    // priorities of single cells
+constexpr uint64_t KEY_STRIP = 0xFFFEULL << 32;   // priorities of strips
+
+// ---- Jones-Plassmann colouring of strips of S consecutive cells -----------
+// (S = 1 with the cell key is the point-multicolour order)
+__global__ void k_jp_pick(int ns, int S, int n, const int* __restrict__ rp,
+                          const int* __restrict__ ci, uint64_t seed, uint64_t key,
+                          const int* __restrict__ scol, int* __restrict__ pick) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= ns) return;
   int chosen = -1;
-  if (colour[i] < 0) {
-    uint64_t pi = splitmix64(seed, (0xFFFFULL << 32) | (uint64_t)(unsigned)i);
+  if (scol[a] < 0) {
+    const int lo = a * S, hi = min(lo + S, n);
+    const uint64_t pa = splitmix64(seed, key | (uint64_t)(unsigned)a);
     bool best = true;
-    for (int k = rp[i]; k < rp[i + 1] && best; ++k) {
-      int j = ci[k];
-      if (j == i || colour[j] >= 0) continue;
-      uint64_t pj = splitmix64(seed, (0xFFFFULL << 32) | (uint64_t)(unsigned)j);
-      if (pj > pi || (pj == pi && j > i)) best = false;
-    }
-    if (best) {
-      int c = 0;
-      for (;;) {
-        bool used = false;
-        for (int k = rp[i]; k < rp[i + 1]; ++k)
-          if (ci[k] != i && colour[ci[k]] == c) { used = true; break; }
-        if (!used) break;
-        ++c;
+    for (int i = lo; i < hi && best; ++i)
+      for (int k = rp[i]; k < rp[i + 1] && best; ++k) {
+        int b = ci[k] / S;
+        if (b == a || scol[b] >= 0) continue;
+        uint64_t pb = splitmix64(seed, key | (uint64_t)(unsigned)b);
+        if (pb > pa || (pb == pa && b > a)) best = false;
       }
-      chosen = c;
+    if (best) {
+      for (int c = 0;; ++c) {
+        bool used = false;
+        for (int i = lo; i < hi && !used; ++i)
+          for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            int b = ci[k] / S;
+            if (b != a && scol[b] == c) { used = true; break; }
+          }
+        if (!used) { chosen = c; break; }
+      }
     }
   }
-  pick[i] = chosen;
+  pick[a] = chosen;
 }
 
-__global__ void k_jp_commit(int n, const int* __restrict__ pick, int* __restrict__ colour,
+__global__ void k_jp_commit(int ns, const int* __restrict__ pick, int* __restrict__ scol,
                             int* __restrict__ left, int* __restrict__ maxcol) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (pick[i] >= 0) {
-    colour[i] = pick[i];
-    atomicMax(maxcol, pick[i]);
-  } else if (colour[i] < 0) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= ns) return;
+  if (pick[a] >= 0) {
+    scol[a] = pick[a];
+    atomicMax(maxcol, pick[a]);
+  } else if (scol[a] < 0) {
     atomicAdd(left, 1);
   }
+}
+
+__global__ void k_cell_colour(int n, int S, const int* __restrict__ scol, int* __restrict__ col) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) col[i] = scol[i / S];
 }
 
 __global__ void k_flag_colour(int n, const int* __restrict__ colour, int c, int* __restrict__ f) {
@@ -80,159 +95,177 @@ __global__ void k_place_colour(int n, const int* __restrict__ colour, int c, int
   perm[q] = i;
 }
 
+__global__ void k_place_strips(int ns, int S, int n, const int* __restrict__ scol, int c,
+                               int base, const int* __restrict__ rank,
+                               const int* __restrict__ iperm, int* __restrict__ st_first,
+                               int* __restrict__ st_len) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= ns || scol[a] != c) return;
+  int k = base + rank[a];
+  st_first[k] = iperm[a * S];
+  st_len[k] = min(S, n - a * S);
+}
+
 __global__ void k_perm_rowlen(int n, const int* __restrict__ perm, const int* __restrict__ rp,
                               int* __restrict__ len) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n) len[q] = rp[perm[q] + 1] - rp[perm[q]];
 }
 
-// factor pattern of row q (cell perm[q]) sorted by column position; copies
-// the scaled blocks and the column slices [Abar[:, t] | Abar[:, p]]
-template <int NB>
-__global__ void k_fill_factor(int n, const int* __restrict__ perm, const int* __restrict__ iperm,
-                              const int* __restrict__ rp, const int* __restrict__ ci,
-                              const double* __restrict__ abar, int p, int t,
-                              const int* __restrict__ frp, int* __restrict__ fpos,
-                              int* __restrict__ fcell, int* __restrict__ fdp,
-                              double* __restrict__ fv, double* __restrict__ fcs) {
-  constexpr int B2 = NB * NB;
+// factor pattern of row q (cell perm[q]) sorted by column position
+__global__ void k_factor_pattern(int n, const int* __restrict__ perm,
+                                 const int* __restrict__ iperm, const int* __restrict__ rp,
+                                 const int* __restrict__ ci, const int* __restrict__ frp,
+                                 int* __restrict__ fpos, int* __restrict__ fcell,
+                                 int* __restrict__ fsrc, int* __restrict__ fdp) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  int i = perm[q];
-  int b = rp[i], len = rp[i + 1] - b, base = frp[q];
-  // insertion sort of (position, source block) pairs
+  const int i = perm[q];
+  const int b = rp[i], len = rp[i + 1] - b, base = frp[q];
+  int d = -1;
   for (int a = 0; a < len; ++a) {
-    int e = b + a;
-    int pc = iperm[ci[e]];
+    const int e = b + a;
+    const int pc = iperm[ci[e]];
     int k = a - 1;
     while (k >= 0 && fpos[base + k] > pc) {
       fpos[base + k + 1] = fpos[base + k];
       fcell[base + k + 1] = fcell[base + k];
+      fsrc[base + k + 1] = fsrc[base + k];
       --k;
     }
     fpos[base + k + 1] = pc;
     fcell[base + k + 1] = ci[e];
+    fsrc[base + k + 1] = e;
   }
-  int d = -1;
-  for (int a = 0; a < len; ++a) {
-    int f = base + a;
-    int j = fcell[f];
-    if (j == i) d = f;
-    // source block: binary search of column j in row i
-    int lo = b, hi = b + len - 1, e = -1;
-    while (lo <= hi) {
-      int mid = (lo + hi) >> 1;
-      if (ci[mid] == j) { e = mid; break; }
-      if (ci[mid] < j) lo = mid + 1; else hi = mid - 1;
-    }
-    const double* src = abar + (size_t)e * B2;
-    double* dst = fv + (size_t)f * B2;
-    for (int k = 0; k < B2; ++k) dst[k] = src[k];
-    double* cs = fcs + (size_t)f * 2 * NB;
-    for (int r = 0; r < NB; ++r) {
-      cs[r] = src[r * NB + t];
-      cs[NB + r] = src[r * NB + p];
-    }
-  }
+  for (int a = 0; a < len; ++a)
+    if (fpos[base + a] == q) d = base + a;
   fdp[q] = d;
 }
 
+// factor blocks (copies of Abar) and column slices [Abar[:, t] | Abar[:, p]]
 template <int NB>
-__device__ bool gj_inverse_nb(const double* a_in, double* inv) {
-  double a[NB * NB];
-#pragma unroll
-  for (int k = 0; k < NB * NB; ++k) a[k] = a_in[k];
-#pragma unroll
-  for (int i = 0; i < NB; ++i)
-#pragma unroll
-    for (int j = 0; j < NB; ++j) inv[i * NB + j] = (i == j) ? 1.0 : 0.0;
-#pragma unroll
-  for (int k = 0; k < NB; ++k) {
-    double piv = a[k * NB + k];
-    if (piv == 0.0 || !isfinite(piv)) return false;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      a[k * NB + j] = a[k * NB + j] / piv;
-      inv[k * NB + j] = inv[k * NB + j] / piv;
-    }
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      if (i == k) continue;
-      double f = a[i * NB + k];
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        a[i * NB + j] = a[i * NB + j] - f * a[k * NB + j];
-        inv[i * NB + j] = inv[i * NB + j] - f * inv[k * NB + j];
-      }
-    }
+__global__ void k_factor_values(long long nnzb, const int* __restrict__ fsrc,
+                                const double* __restrict__ abar, int p, int t,
+                                double* __restrict__ fv, double* __restrict__ fcs) {
+  constexpr int B2 = NB * NB;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (; idx < nnzb * B2; idx += stride) {
+    long long f = idx / B2;
+    int k = (int)(idx - f * B2);
+    fv[idx] = abar[(size_t)fsrc[f] * B2 + k];
   }
-  return true;
+  idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; idx < nnzb * 2 * NB; idx += stride) {
+    long long f = idx / (2 * NB);
+    int k = (int)(idx - f * 2 * NB);
+    int r = k < NB ? k : k - NB;
+    int col = k < NB ? t : p;
+    fcs[idx] = abar[(size_t)fsrc[f] * B2 + r * NB + col];
+  }
 }
 
-// IKJ block ILU(0) for the rows of one colour. Lower neighbours of a row
-// belong to earlier colours and are final; their U^{-1} diagonal blocks are
-// in fdinv. diag_only: block Jacobi (invert the diagonal block only).
+// IKJ block ILU(0), one warp per strip, the strip's rows in order. Lower
+// neighbours belong to earlier colours or to earlier rows of the same strip
+// and are final; their U^{-1} diagonal blocks are in fdinv. The nb x nb block
+// products and the Gauss-Jordan inverse of the pivot block (no pivoting) are
+// spread over the lanes. diag_only: block Jacobi.
 template <int NB>
-__global__ void k_bilu_factor(int q0, int q1, const int* __restrict__ frp,
-                              const int* __restrict__ fdp, const int* __restrict__ fpos,
-                              double* __restrict__ fv, double* __restrict__ fdinv, int diag_only,
-                              int* __restrict__ bad) {
+__global__ void __launch_bounds__(256)
+k_bilu_factor(int s0, int s1, const int* __restrict__ st_first, const int* __restrict__ st_len,
+              const int* __restrict__ frp, const int* __restrict__ fdp,
+              const int* __restrict__ fpos, double* __restrict__ fv,
+              double* __restrict__ fdinv, int diag_only, int* __restrict__ bad) {
   constexpr int B2 = NB * NB;
-  int q = q0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= q1) return;
-  const int b = frp[q], e = frp[q + 1], d = fdp[q];
-  if (!diag_only) {
-    for (int f = b; f < d; ++f) {
-      const int kk = fpos[f];
-      double L[B2];
-      const double* W = fv + (size_t)f * B2;
-      const double* Ui = fdinv + (size_t)kk * B2;
-#pragma unroll
-      for (int r = 0; r < NB; ++r)
-#pragma unroll
-        for (int c = 0; c < NB; ++c) {
+  constexpr int W2 = 2 * NB;
+  __shared__ double smem[8][3 * B2];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long k = s0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (k >= s1) return;                       // uniform per warp
+  double* L = smem[wib];
+  double* aug = L + B2;                      // NB x 2NB augmented matrix
+  const int first = st_first[k], len = st_len[k];
+  for (int q = first; q < first + len; ++q) {
+    const int b = frp[q], e = frp[q + 1], d = fdp[q];
+    if (!diag_only) {
+      for (int f = b; f < d; ++f) {
+        const int kk = fpos[f];
+        const double* W = fv + (size_t)f * B2;
+        const double* Ui = fdinv + (size_t)kk * B2;
+        for (int idx = lane; idx < B2; idx += 32) {
+          const int r = idx / NB, c = idx - r * NB;
           double s = 0.0;
 #pragma unroll
-          for (int k = 0; k < NB; ++k) s += W[r * NB + k] * Ui[k * NB + c];
-          L[r * NB + c] = s;
+          for (int m = 0; m < NB; ++m) s += W[r * NB + m] * Ui[m * NB + c];
+          L[idx] = s;
         }
-      double* Wf = fv + (size_t)f * B2;
-#pragma unroll
-      for (int k = 0; k < B2; ++k) Wf[k] = L[k];
-      for (int g = fdp[kk] + 1; g < frp[kk + 1]; ++g) {
-        const int j = fpos[g];
-        int hit = -1;
-        for (int h2 = b; h2 < e; ++h2)
-          if (fpos[h2] == j) { hit = h2; break; }
-        if (hit < 0) continue;
-        double* Wq = fv + (size_t)hit * B2;
-        const double* U = fv + (size_t)g * B2;
-#pragma unroll
-        for (int r = 0; r < NB; ++r)
-#pragma unroll
-          for (int c = 0; c < NB; ++c) {
+        __syncwarp();
+        for (int idx = lane; idx < B2; idx += 32) fv[(size_t)f * B2 + idx] = L[idx];
+        for (int g = fdp[kk] + 1; g < frp[kk + 1]; ++g) {
+          const int j = fpos[g];
+          int hit = -1;
+          for (int h2 = b; h2 < e; ++h2)
+            if (fpos[h2] == j) { hit = h2; break; }
+          if (hit < 0) continue;
+          double* Wq = fv + (size_t)hit * B2;
+          const double* U = fv + (size_t)g * B2;
+          for (int idx = lane; idx < B2; idx += 32) {
+            const int r = idx / NB, c = idx - r * NB;
             double s = 0.0;
 #pragma unroll
-            for (int k = 0; k < NB; ++k) s += L[r * NB + k] * U[k * NB + c];
-            Wq[r * NB + c] -= s;
+            for (int m = 0; m < NB; ++m) s += L[r * NB + m] * U[m * NB + c];
+            Wq[idx] -= s;
           }
+        }
+        __syncwarp();
       }
     }
+    // Gauss-Jordan inverse of the pivot block, no pivoting
+    for (int idx = lane; idx < NB * W2; idx += 32) {
+      const int r = idx / W2, c = idx - r * W2;
+      aug[idx] = c < NB ? fv[(size_t)d * B2 + r * NB + c] : (c - NB == r ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int ks = 0; ks < NB; ++ks) {
+      const double piv = aug[ks * W2 + ks];
+      if (piv == 0.0 || !isfinite(piv)) { ok = false; break; }   // same value in all lanes
+      __syncwarp();
+      if (lane < W2) aug[ks * W2 + lane] = aug[ks * W2 + lane] / piv;
+      __syncwarp();
+      double fr[(NB * W2 + 31) / 32];
+      int tt = 0;
+      for (int idx = lane; idx < NB * W2; idx += 32, ++tt) fr[tt] = aug[(idx / W2) * W2 + ks];
+      __syncwarp();
+      tt = 0;
+      for (int idx = lane; idx < NB * W2; idx += 32, ++tt) {
+        const int i = idx / W2, j = idx - i * W2;
+        if (i != ks) aug[idx] = aug[idx] - fr[tt] * aug[ks * W2 + j];
+      }
+      __syncwarp();
+    }
+    if (!ok) {
+      if (lane == 0) atomicMin(bad, q);
+      return;
+    }
+    for (int idx = lane; idx < B2; idx += 32) {
+      const int r = idx / NB, c = idx - r * NB;
+      fdinv[(size_t)q * B2 + idx] = aug[r * W2 + NB + c];
+    }
+    __syncwarp();
   }
-  double inv[B2];
-  if (!gj_inverse_nb<NB>(fv + (size_t)d * B2, inv)) {
-    atomicMin(bad, q);
-    return;
-  }
-  double* out = fdinv + (size_t)q * B2;
-#pragma unroll
-  for (int k = 0; k < B2; ++k) out[k] = inv[k];
 }
 
-// ---- sweeps (NB lanes per row) -------------------------------------------
+__device__ __forceinline__ int warp_max(int v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---- sweeps: NB lanes per strip, the strip's rows in order ------------------
 // MODE bit 1: subtract Abar[:, t] x_T; bit 2: subtract Abar[:, p] v_P
 template <int NB, int MODE>
-__global__ void k_bilu_fwd(int q0, int q1, const int* __restrict__ perm,
+__global__ void k_bilu_fwd(int s0, int s1, const int* __restrict__ st_first,
+                           const int* __restrict__ st_len, const int* __restrict__ perm,
                            const int* __restrict__ frp, const int* __restrict__ fdp,
                            const int* __restrict__ fpos, const int* __restrict__ fcell,
                            const double* __restrict__ fv, const double* __restrict__ fcs,
@@ -243,36 +276,46 @@ __global__ void k_bilu_fwd(int q0, int q1, const int* __restrict__ perm,
   const int lane = threadIdx.x & 31;
   const int sub = lane / NB, comp = lane - sub * NB;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long qq = q0 + warp * RPW + sub;
-  if (sub >= RPW || qq >= q1) return;
-  const int q = (int)qq;
-  const int cell = perm[q];
-  double acc = r[(size_t)cell * NB + comp];
-  const int b = frp[q], e = frp[q + 1];
-  if (MODE) {
-    for (int f = b; f < e; ++f) {
-      const int j = fcell[f];
-      const double* cs = fcs + (size_t)f * 2 * NB;
-      if (MODE & 1) acc -= cs[comp] * xT[j];
-      if (MODE & 2) acc -= cs[NB + comp] * vP[j];
-    }
-  }
-  if (lower) {
-    const int d = fdp[q];
-    for (int f = b; f < d; ++f) {
-      const double* Lr = fv + (size_t)f * B2 + comp * NB;
-      const double* wk = w + (size_t)fpos[f] * NB;
+  const long long kk = s0 + warp * RPW + sub;
+  const bool active = sub < RPW && kk < s1;
+  const int first = active ? st_first[kk] : 0;
+  const int len = active ? st_len[kk] : 0;
+  const int maxlen = warp_max(len);
+  for (int it = 0; it < maxlen; ++it) {
+    if (it < len) {
+      const int q = first + it;
+      const int cell = perm[q];
+      double acc = r[(size_t)cell * NB + comp];
+      const int b = frp[q], e = frp[q + 1];
+      if (MODE) {
+        for (int f = b; f < e; ++f) {
+          const int j = fcell[f];
+          const double* cs = fcs + (size_t)f * 2 * NB;
+          if (MODE & 1) acc -= cs[comp] * xT[j];
+          if (MODE & 2) acc -= cs[NB + comp] * vP[j];
+        }
+      }
+      if (lower) {
+        const int d = fdp[q];
+        for (int f = b; f < d; ++f) {
+          const double* Lr = fv + (size_t)f * B2 + comp * NB;
+          const double* wk = w + (size_t)fpos[f] * NB;
 #pragma unroll
-      for (int c = 0; c < NB; ++c) acc -= Lr[c] * wk[c];
+          for (int c = 0; c < NB; ++c) acc -= Lr[c] * wk[c];
+        }
+      }
+      w[(size_t)q * NB + comp] = acc;
     }
+    __syncwarp();
   }
-  w[(size_t)q * NB + comp] = acc;
 }
 
-// backward sweep: x_q = U_qq^{-1} (w_q - sum_{upper} U_qj x_j); writes x_q
-// back into w (read by earlier colours) and y = x + stage corrections
+// backward: x_q = U_qq^{-1} (w_q - sum_{upper} U_qj x_j), rows of a strip in
+// reverse order; x_q goes back into w (read by earlier rows and colours) and
+// y = x + stage corrections
 template <int NB, int MODE>
-__global__ void k_bilu_bwd(int q0, int q1, const int* __restrict__ perm,
+__global__ void k_bilu_bwd(int s0, int s1, const int* __restrict__ st_first,
+                           const int* __restrict__ st_len, const int* __restrict__ perm,
                            const int* __restrict__ frp, const int* __restrict__ fdp,
                            const int* __restrict__ fpos, const double* __restrict__ fv,
                            const double* __restrict__ fdinv, const double* __restrict__ xT,
@@ -283,37 +326,45 @@ __global__ void k_bilu_bwd(int q0, int q1, const int* __restrict__ perm,
   const int lane = threadIdx.x & 31;
   const int sub = lane / NB, comp = lane - sub * NB;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long qq = q0 + warp * RPW + sub;
-  const bool active = sub < RPW && qq < q1;
-  const int q = active ? (int)qq : 0;
-  double tv = 0.0;
-  if (active) {
-    tv = w[(size_t)q * NB + comp];
-    if (upper) {
-      const int d = fdp[q], e = frp[q + 1];
-      for (int g = d + 1; g < e; ++g) {
-        const double* Ur = fv + (size_t)g * B2 + comp * NB;
-        const double* xj = w + (size_t)fpos[g] * NB;
+  const long long kk = s0 + warp * RPW + sub;
+  const bool active = sub < RPW && kk < s1;
+  const int first = active ? st_first[kk] : 0;
+  const int len = active ? st_len[kk] : 0;
+  const int maxlen = warp_max(len);
+  const int base = sub * NB;
+  for (int it = 0; it < maxlen; ++it) {
+    const bool on = it < len;
+    const int q = on ? first + len - 1 - it : 0;
+    double tv = 0.0;
+    if (on) {
+      tv = w[(size_t)q * NB + comp];
+      if (upper) {
+        const int d = fdp[q], e = frp[q + 1];
+        for (int g = d + 1; g < e; ++g) {
+          const double* Ur = fv + (size_t)g * B2 + comp * NB;
+          const double* xj = w + (size_t)fpos[g] * NB;
 #pragma unroll
-        for (int c = 0; c < NB; ++c) tv -= Ur[c] * xj[c];
+          for (int c = 0; c < NB; ++c) tv -= Ur[c] * xj[c];
+        }
       }
     }
-  }
-  const int base = sub * NB;
-  const double* Ui = fdinv + (size_t)q * B2 + comp * NB;
-  double x = 0.0;
+    const double* Ui = fdinv + (size_t)q * B2 + comp * NB;
+    double x = 0.0;
 #pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    double tc = __shfl_sync(0xffffffffu, tv, (base + c) & 31);
-    if (active) x += Ui[c] * tc;
+    for (int c = 0; c < NB; ++c) {
+      double tc = __shfl_sync(0xffffffffu, tv, (base + c) & 31);
+      if (on) x += Ui[c] * tc;
+    }
+    if (on) {
+      w[(size_t)q * NB + comp] = x;
+      const int cell = perm[q];
+      double out = x;
+      if ((MODE & 1) && comp == t) out += xT[cell];
+      if ((MODE & 2) && comp == p) out += vP[cell];
+      y[(size_t)cell * NB + comp] = out;
+    }
+    __syncwarp();
   }
-  if (!active) return;
-  w[(size_t)q * NB + comp] = x;
-  const int cell = perm[q];
-  double out = x;
-  if ((MODE & 1) && comp == t) out += xT[cell];
-  if ((MODE & 2) && comp == p) out += vP[cell];
-  y[(size_t)cell * NB + comp] = out;
 }
 
 template <int NB>
@@ -321,49 +372,70 @@ void bilu_setup_nb(Handle* h) {
   const int N = h->N;
   const int nnzb = h->nnzb;
   const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
+  const bool strips = !bjac && h->opt.ilu_order == MSS_STRIPS;
+  const int S = strips ? h->opt.ilu_strip : 1;
+  const int ns = (N + S - 1) / S;
+  DBuf<int> scol(h, ns);
   h->colour.reset(h, N);
   h->perm.reset(h, N);
   h->iperm.reset(h, N);
-  // ---- colouring (block Jacobi needs no order: a single colour)
+  // ---- colouring of strips (block Jacobi needs no order: one colour)
   if (bjac) {
-    fill_int(h, h->colour.p, 0, N);
+    fill_int(h, scol.p, 0, ns);
     h->ncol = 1;
   } else {
-    fill_int(h, h->colour.p, -1, N);
-    DBuf<int> pick(h, N), left(h, 1), maxcol(h, 1);
+    fill_int(h, scol.p, -1, ns);
+    DBuf<int> pick(h, ns), left(h, 1), maxcol(h, 1);
     fill_int(h, maxcol.p, -1, 1);
-    int remaining = N, rounds = 0;
+    const uint64_t key = strips ? KEY_STRIP : KEY_CELL;
+    int remaining = ns, rounds = 0;
     while (remaining > 0) {
-      if (++rounds > N + 1) fail(MSS_ERR_CUDA, "colouring did not terminate");
-      k_jp_pick<<<grid_for(N, 256), 256, 0, h->stream>>>(N, h->rp.p, h->ci.p, h->opt.seed,
-                                                         h->colour.p, pick.p);
+      if (++rounds > ns + 1) fail(MSS_ERR_CUDA, "colouring did not terminate");
+      k_jp_pick<<<grid_for(ns, 128), 128, 0, h->stream>>>(ns, S, N, h->rp.p, h->ci.p,
+                                                          h->opt.seed, key, scol.p, pick.p);
       MSS_LAUNCH_CK("k_jp_pick");
       fill_int(h, left.p, 0, 1);
-      k_jp_commit<<<grid_for(N, 256), 256, 0, h->stream>>>(N, pick.p, h->colour.p, left.p,
-                                                           maxcol.p);
+      k_jp_commit<<<grid_for(ns, 256), 256, 0, h->stream>>>(ns, pick.p, scol.p, left.p,
+                                                            maxcol.p);
       MSS_LAUNCH_CK("k_jp_commit");
       remaining = read_int(h, left.p);
     }
     h->ncol = read_int(h, maxcol.p) + 1;
   }
-  // ---- colour-major positions
+  k_cell_colour<<<grid_for(N, 256), 256, 0, h->stream>>>(N, S, scol.p, h->colour.p);
+  MSS_LAUNCH_CK("k_cell_colour");
+  // ---- colour-major positions and the strip list
   h->cstart.assign(h->ncol + 1, 0);
+  h->sc_start.assign(h->ncol + 1, 0);
+  h->st_first.reset(h, ns);
+  h->st_len.reset(h, ns);
   {
-    DBuf<int> flag(h, N), rank(h, N + 1);
-    int base = 0;
+    DBuf<int> flag(h, std::max(N, ns)), rank(h, std::max(N, ns) + 1);
+    int base = 0, sbase = 0;
     for (int c = 0; c < h->ncol; ++c) {
       k_flag_colour<<<grid_for(N, 256), 256, 0, h->stream>>>(N, h->colour.p, c, flag.p);
       MSS_LAUNCH_CK("k_flag_colour");
       exclusive_scan(h, flag.p, rank.p, N);
-      int cnt = read_int(h, rank.p + N);
+      const int cnt = read_int(h, rank.p + N);
       k_place_colour<<<grid_for(N, 256), 256, 0, h->stream>>>(N, h->colour.p, c, base, rank.p,
                                                               h->iperm.p, h->perm.p);
       MSS_LAUNCH_CK("k_place_colour");
       h->cstart[c] = base;
       base += cnt;
+      k_flag_colour<<<grid_for(ns, 256), 256, 0, h->stream>>>(ns, scol.p, c, flag.p);
+      MSS_LAUNCH_CK("k_flag_colour");
+      exclusive_scan(h, flag.p, rank.p, ns);
+      const int scnt = read_int(h, rank.p + ns);
+      k_place_strips<<<grid_for(ns, 256), 256, 0, h->stream>>>(ns, S, N, scol.p, c, sbase,
+                                                               rank.p, h->iperm.p,
+                                                               h->st_first.p, h->st_len.p);
+      MSS_LAUNCH_CK("k_place_strips");
+      h->sc_start[c] = sbase;
+      sbase += scnt;
     }
     h->cstart[h->ncol] = base;
-    if (base != N) fail(MSS_ERR_CUDA, "colour classes do not cover every cell");
+    h->sc_start[h->ncol] = sbase;
+    if (base != N || sbase != ns) fail(MSS_ERR_CUDA, "colour classes do not cover every cell");
   }
   // ---- factor pattern and values
   {
@@ -375,25 +447,35 @@ void bilu_setup_nb(Handle* h) {
   }
   h->fpos.reset(h, nnzb);
   h->fcell.reset(h, nnzb);
+  h->fsrc.reset(h, nnzb);
   h->fdp.reset(h, N);
   h->fv.reset(h, (size_t)nnzb * NB * NB);
   h->fcs.reset(h, (size_t)nnzb * 2 * NB);
   h->fdinv.reset(h, (size_t)N * NB * NB);
-  k_fill_factor<NB><<<grid_for(N, 128), 128, 0, h->stream>>>(
-      N, h->perm.p, h->iperm.p, h->rp.p, h->ci.p, h->abar.p, h->p, h->t, h->frp.p, h->fpos.p,
-      h->fcell.p, h->fdp.p, h->fv.p, h->fcs.p);
-  MSS_LAUNCH_CK("k_fill_factor");
-  // ---- factorisation, colour by colour
+  k_factor_pattern<<<grid_for(N, 128), 128, 0, h->stream>>>(
+      N, h->perm.p, h->iperm.p, h->rp.p, h->ci.p, h->frp.p, h->fpos.p, h->fcell.p, h->fsrc.p,
+      h->fdp.p);
+  MSS_LAUNCH_CK("k_factor_pattern");
+  {
+    long long tot = (long long)nnzb * NB * NB;
+    unsigned g = grid_for(tot, 256);
+    if (g > 8u * h->num_sms * 8) g = 8u * h->num_sms * 8;
+    k_factor_values<NB><<<g, 256, 0, h->stream>>>(nnzb, h->fsrc.p, h->abar.p, h->p, h->t,
+                                                  h->fv.p, h->fcs.p);
+    MSS_LAUNCH_CK("k_factor_values");
+  }
+  // ---- factorisation, colour by colour (one warp per strip)
   DBuf<int> bad(h, 1);
   fill_int(h, bad.p, 0x7fffffff, 1);
   for (int c = 0; c < h->ncol; ++c) {
-    int q0 = h->cstart[c], q1 = h->cstart[c + 1];
-    if (q1 <= q0) continue;
-    k_bilu_factor<NB><<<grid_for(q1 - q0, 128), 128, 0, h->stream>>>(
-        q0, q1, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p, h->fdinv.p, bjac ? 1 : 0, bad.p);
+    const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
+    if (s1 <= s0) continue;
+    k_bilu_factor<NB><<<grid_for((long long)(s1 - s0) * 32, 256), 256, 0, h->stream>>>(
+        s0, s1, h->st_first.p, h->st_len.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p, h->fdinv.p,
+        bjac ? 1 : 0, bad.p);
     MSS_LAUNCH_CK("k_bilu_factor");
   }
-  int badq = read_int(h, bad.p);
+  const int badq = read_int(h, bad.p);
   if (badq != 0x7fffffff)
     fail(MSS_ERR_SINGULAR_BLOCK, "block ILU(0): zero pivot in the diagonal block at position " +
                                      std::to_string(badq));
@@ -405,30 +487,30 @@ void sweeps(Handle* h, const double* r, const double* xT, const double* vP, doub
   const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
   const int T = 256;
   for (int c = 0; c < h->ncol; ++c) {
-    int q0 = h->cstart[c], q1 = h->cstart[c + 1];
-    if (q1 <= q0) continue;
-    long long warps = (q1 - q0 + RPW - 1) / RPW;
+    const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
+    if (s1 <= s0) continue;
+    const long long warps = (s1 - s0 + RPW - 1) / RPW;
     TraceScope ts(h, TR_BILU_FWD);
     k_bilu_fwd<NB, MODE><<<grid_for(warps * 32, T), T, 0, h->stream>>>(
-        q0, q1, h->perm.p, h->frp.p, h->fdp.p, h->fpos.p, h->fcell.p, h->fv.p, h->fcs.p, r, xT, vP,
-        h->w.p, bjac ? 0 : 1);
+        s0, s1, h->st_first.p, h->st_len.p, h->perm.p, h->frp.p, h->fdp.p, h->fpos.p,
+        h->fcell.p, h->fv.p, h->fcs.p, r, xT, vP, h->w.p, bjac ? 0 : 1);
     MSS_LAUNCH_CK("k_bilu_fwd");
   }
   for (int c = h->ncol - 1; c >= 0; --c) {
-    int q0 = h->cstart[c], q1 = h->cstart[c + 1];
-    if (q1 <= q0) continue;
-    long long warps = (q1 - q0 + RPW - 1) / RPW;
+    const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
+    if (s1 <= s0) continue;
+    const long long warps = (s1 - s0 + RPW - 1) / RPW;
     TraceScope ts(h, TR_BILU_BWD);
     k_bilu_bwd<NB, MODE><<<grid_for(warps * 32, T), T, 0, h->stream>>>(
-        q0, q1, h->perm.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p, h->fdinv.p, xT, vP, h->p, h->t,
-        h->w.p, y, bjac ? 0 : 1);
+        s0, s1, h->st_first.p, h->st_len.p, h->perm.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p,
+        h->fdinv.p, xT, vP, h->p, h->t, h->w.p, y, bjac ? 0 : 1);
     MSS_LAUNCH_CK("k_bilu_bwd");
   }
 }
 
 template <int NB>
 void last_stage_nb(Handle* h, const double* r, const double* xT, const double* vP, double* y) {
-  int mode = (xT ? 1 : 0) | (vP ? 2 : 0);
+  const int mode = (xT ? 1 : 0) | (vP ? 2 : 0);
   switch (mode) {
     case 0: sweeps<NB, 0>(h, r, xT, vP, y); break;
     case 1: sweeps<NB, 1>(h, r, xT, vP, y); break;

@@ -133,6 +133,9 @@ struct Handle {
   DBuf<int> colour, perm, iperm;
   DBuf<int> frp, fpos, fcell;  // factor pattern: column position and cell
   DBuf<int> fdp;               // index of the diagonal block in each factor row
+  DBuf<int> fsrc;              // source block (index into Abar) of each factor block
+  DBuf<int> st_first, st_len;  // strips in colour-major order: first position, length
+  std::vector<int> sc_start;   // host: first strip of each colour, ncol + 1
   DBuf<double> fv;             // L (strictly lower) / U (strictly upper) blocks
   DBuf<double> fdinv;          // inverse of U's diagonal block, per position
   DBuf<double> fcs;            // Abar column slices [t | p] per factor block (2 nb)

@@ -1,9 +1,11 @@
 // krylov.cu -- BSR matrix-vector product, preconditioner orchestration
 // (Algorithms 1 and 2) and right-preconditioned restarted FGMRES (Sec. 5.1).
 //
-// Arnoldi uses classical Gram-Schmidt applied twice (CGS2): every pass is one
-// streaming sweep over the basis that computes all projections at once, with
-// the second pass's projections fused into the first pass's update. All
+// Arnoldi uses classical Gram-Schmidt, once (CGS1, default) or twice (CGS2):
+// every pass is one streaming sweep over the basis that computes all
+// projections at once; CGS2 fuses its second projections into the first
+// update, and the last update carries the norm. The FP64 work per element is
+// 2(j+1) FMAs for CGS1 and 4(j+1) for CGS2. All
 // reductions are two-stage with a fixed block count and a fixed summation
 // order, so results are identical from run to run.
 #include <cmath>
@@ -179,7 +181,7 @@ __global__ void k_arnoldi_finish(int j, int m, const double* __restrict__ h1,
   // sq[0] = ||w0||^2 (before projection), sq[1] = ||w||^2 after CGS2
   double w0 = sqrt(sq[0]);
   double hn = sqrt(sq[1]);
-  for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
+  for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h2 ? h1[i] + h2[i] : h1[i];
   H[(size_t)(j + 1) * m + j] = hn;
   int happy = hn <= 1e-14 * w0;
   for (int i = 0; i < j; ++i) {
@@ -206,17 +208,17 @@ __global__ void k_arnoldi_finish(int j, int m, const double* __restrict__ h1,
 
 __global__ void k_normalize(long long n, double* __restrict__ w, const double* __restrict__ ks) {
   if (ks[KS_HAPPY] != 0.0) return;
-  const double hn = ks[KS_HN];
+  const double inv = 1.0 / ks[KS_HN];
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long stride = (long long)gridDim.x * blockDim.x;
-  for (; e < n; e += stride) w[e] = w[e] / hn;
+  for (; e < n; e += stride) w[e] = w[e] * inv;
 }
 
-__global__ void k_scale_div(long long n, const double* __restrict__ src, double beta,
-                            double* __restrict__ dst) {
+__global__ void k_scale(long long n, const double* __restrict__ src, double s,
+                        double* __restrict__ dst) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long stride = (long long)gridDim.x * blockDim.x;
-  for (; e < n; e += stride) dst[e] = src[e] / beta;
+  for (; e < n; e += stride) dst[e] = src[e] * s;
 }
 
 __global__ void k_init_g(int m, double beta, double* __restrict__ g) {
@@ -391,8 +393,8 @@ int fgmres(Handle* h, const double* b, double* x, double tol, int maxit, mss_res
   int total = 0;
   const unsigned sgrid = grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256);
   for (;;) {
-    k_scale_div<<<sgrid, 256, 0, h->stream>>>(n, h->res.p, beta, V);
-    MSS_LAUNCH_CK("k_scale_div");
+    k_scale<<<sgrid, 256, 0, h->stream>>>(n, h->res.p, 1.0 / beta, V);
+    MSS_LAUNCH_CK("k_scale");
     k_init_g<<<1, 128, 0, h->stream>>>(m, beta, g);   // restart <= 120
     MSS_LAUNCH_CK("k_init_g");
     int k = 0;
@@ -414,17 +416,21 @@ int fgmres(Handle* h, const double* b, double* x, double tol, int maxit, mss_res
         MSS_LAUNCH_CK("k_reduce");
         k_reduce<<<1, KT, 0, h->stream>>>(1, rs.G, part + (size_t)nv * rs.G, sq);
         MSS_LAUNCH_CK("k_reduce");
-        // update with h1, fused pass-2 projections h2
-        k_update<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, h1, w, 0, part);
-        MSS_LAUNCH_CK("k_update");
-        k_reduce<<<nv, KT, 0, h->stream>>>(nv, rs.G, part, h2);
-        MSS_LAUNCH_CK("k_reduce");
-        // update with h2 and the norm
-        k_update<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, h2, w, 1, part);
+        const bool cgs2 = h->opt.orthog == MSS_CGS2;
+        if (cgs2) {
+          // update with h1, fused pass-2 projections h2
+          k_update<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, h1, w, 0, part);
+          MSS_LAUNCH_CK("k_update");
+          k_reduce<<<nv, KT, 0, h->stream>>>(nv, rs.G, part, h2);
+          MSS_LAUNCH_CK("k_reduce");
+        }
+        // update (with h2 after CGS2, with h1 after CGS1) and the norm
+        k_update<<<rs.G, KT, 0, h->stream>>>(n, rs.chunk, V, ld, nv, cgs2 ? h2 : h1, w, 1, part);
         MSS_LAUNCH_CK("k_update");
         k_reduce<<<1, KT, 0, h->stream>>>(1, rs.G, part, sq + 1);
         MSS_LAUNCH_CK("k_reduce");
-        k_arnoldi_finish<<<1, 32, 0, h->stream>>>(j, m, h1, h2, sq, H, cs, sn, g, bnorm, ks);
+        k_arnoldi_finish<<<1, 32, 0, h->stream>>>(j, m, h1, cgs2 ? h2 : nullptr, sq, H, cs, sn,
+                                                  g, bnorm, ks);
         MSS_LAUNCH_CK("k_arnoldi_finish");
         k_normalize<<<sgrid, 256, 0, h->stream>>>(n, w, ks);
         MSS_LAUNCH_CK("k_normalize");

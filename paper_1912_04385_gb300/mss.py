@@ -38,7 +38,8 @@ class Options(C.Structure):
                 ("nu_post", C.c_int32), ("cheb_degree", C.c_int32),
                 ("amg_max_coarse", C.c_int32), ("amg_max_levels", C.c_int32),
                 ("interp_max_elems", C.c_int32), ("restart", C.c_int32),
-                ("precision", C.c_int32), ("pad_", C.c_int32),
+                ("precision", C.c_int32), ("ilu_strip", C.c_int32),
+                ("orthog", C.c_int32), ("pad_", C.c_int32),
                 ("amg_theta", C.c_double), ("jacobi_omega", C.c_double),
                 ("cheb_lo_ratio", C.c_double), ("cheb_hi_factor", C.c_double),
                 ("seed", C.c_uint64), ("learned_interp", C.c_void_p)]

@@ -102,10 +102,11 @@ def test_amg_hierarchy_bit_exact(mss, case):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_multicolour_ordering_bit_exact(mss, case):
+@pytest.mark.parametrize("order,strip", [(2, 32), (2, 5), (0, 1)])
+def test_ordering_bit_exact(mss, case, order, strip):
     s = _sys(CASES[case])
-    g = _gpu(mss, s)
-    o = _orc(s)
+    g = _gpu(mss, s, ilu_order=order, ilu_strip=strip)
+    o = _orc(s, ilu_order=order, ilu_strip=strip)
     nc, colour, perm = g.bilu_ordering()
     f = o.bilu()
     assert nc == f["ncolours"]
@@ -114,15 +115,16 @@ def test_multicolour_ordering_bit_exact(mss, case):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("scheme,stage3,smoother,order", [
-    ("cptr3", 0, "jacobi", 0), ("cptr3", 1, "jacobi", 0), ("cptr3", 0, "chebyshev", 0),
-    ("cptr3", 0, "jacobi", 1), ("cpr", 0, "jacobi", 0), ("ilu0", 0, "jacobi", 0)])
-def test_stages_and_apply(mss, case, scheme, stage3, smoother, order):
+@pytest.mark.parametrize("scheme,stage3,smoother,order,ilu", [
+    ("cptr3", 0, "jacobi", 0, 2), ("cptr3", 0, "jacobi", 0, 0), ("cptr3", 1, "jacobi", 0, 2),
+    ("cptr3", 0, "chebyshev", 0, 2), ("cptr3", 0, "jacobi", 1, 2), ("cpr", 0, "jacobi", 0, 2),
+    ("ilu0", 0, "jacobi", 0, 2), ("ilu0", 0, "jacobi", 0, 0)])
+def test_stages_and_apply(mss, case, scheme, stage3, smoother, order, ilu):
     s = _sys(CASES[case])
     g = _gpu(mss, s, scheme=scheme, stage3=stage3, smoother=smoother, stage_order=order,
-             amg_max_coarse=40)
+             amg_max_coarse=40, ilu_order=ilu)
     o = _orc(s, scheme=scheme, stage3=stage3, smoother=smoother, stage_order=order,
-             max_coarse=40)
+             max_coarse=40, ilu_order=ilu)
     rng = np.random.default_rng(case)
     r = rng.standard_normal(s.n_cells * s.nb)
     rt = _t(r)
@@ -135,11 +137,11 @@ def test_stages_and_apply(mss, case, scheme, stage3, smoother, order):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("scheme", ["cptr3", "cpr"])
-def test_fgmres_iterations_and_solution(mss, case, scheme):
+@pytest.mark.parametrize("scheme,orthog", [("cptr3", 0), ("cptr3", 1), ("cpr", 0), ("ilu0", 0)])
+def test_fgmres_iterations_and_solution(mss, case, scheme, orthog):
     s = _sys(CASES[case])
     m = 100
-    g = _gpu(mss, s, scheme=scheme, restart=m, amg_max_coarse=40)
+    g = _gpu(mss, s, scheme=scheme, restart=m, amg_max_coarse=40, orthog=orthog)
     o = _orc(s, scheme=scheme, restart=m, max_coarse=40)
     bb = o.scale_rhs(s.b)
     xo, io = o.fgmres(bb, tol=1e-8, maxit=400, restart=m)

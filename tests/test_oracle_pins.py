@@ -198,11 +198,11 @@ def test_bilu_exact_on_block_diagonal():
     assert np.allclose(M, np.linalg.inv(A), rtol=1e-12, atol=1e-14)
 
 
-@pytest.mark.parametrize("order", [0, 1])
-def test_bilu_reproduces_matrix_on_pattern(order):
+@pytest.mark.parametrize("order,strip", [(0, 1), (1, 1), (2, 4), (2, 7)])
+def test_bilu_reproduces_matrix_on_pattern(order, strip):
     nb = 4
     s = sy.make_system(6, 5, nb, pe=1.0, seed=12, couple_neighbors=True)
-    o = oracle.OracleSolver.from_system(s, scheme="cptr3", ilu_order=order)
+    o = oracle.OracleSolver.from_system(s, scheme="cptr3", ilu_order=order, ilu_strip=strip)
     abar, _ = o.scaled()
     f = o.bilu()
     N = s.n_cells
@@ -226,10 +226,44 @@ def test_bilu_reproduces_matrix_on_pattern(order):
             d = LU[q * nb:(q + 1) * nb, c * nb:(c + 1) * nb] - A[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb]
             err = max(err, np.abs(d).max())
     assert err < 1e-12 * np.abs(A).max()
-    if order == 0:
+    if order != 1:
         # colour-major order: cells ascend within each colour
         col = f["colour"]
         assert np.all(np.diff(col[perm]) >= 0)
+        same = col[perm][1:] == col[perm][:-1]
+        assert np.all(perm[1:][same] > perm[:-1][same])
+
+
+@pytest.mark.parametrize("strip", [3, 8, 32])
+def test_strip_colouring_is_proper_and_keeps_strips_natural(strip):
+    s = sy.make_system(23, 19, 4, pe=10.0, seed=21)
+    o = oracle.OracleSolver.from_system(s, ilu_order=2, ilu_strip=strip)
+    f = o.bilu()
+    col, perm = f["colour"], f["perm"]
+    # a strip has one colour, coupled strips differ
+    for a in range(0, s.n_cells, strip):
+        assert len(set(col[a:a + strip])) == 1
+    for i in range(s.n_cells):
+        for e in range(s.row_ptr[i], s.row_ptr[i + 1]):
+            j = s.col_idx[e]
+            if j // strip != i // strip:
+                assert col[i] != col[j]
+    # each strip occupies consecutive positions in natural order
+    iperm = np.empty_like(perm)
+    iperm[perm] = np.arange(s.n_cells)
+    for a in range(0, s.n_cells, strip):
+        pos = iperm[a:min(a + strip, s.n_cells)]
+        assert np.all(np.diff(pos) == 1)
+
+
+def test_single_strip_is_the_natural_order():
+    s = sy.make_system(9, 7, 4, pe=10.0, seed=22)
+    a = oracle.OracleSolver.from_system(s, ilu_order=2, ilu_strip=1024)
+    b = oracle.OracleSolver.from_system(s, ilu_order=1)
+    fa, fb = a.bilu(), b.bilu()
+    assert fa["ncolours"] == 1
+    assert np.array_equal(fa["perm"], fb["perm"])
+    assert np.array_equal(fa["vals"], fb["vals"])
 
 
 def test_colouring_is_proper_and_deterministic():
