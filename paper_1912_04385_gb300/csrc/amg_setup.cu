@@ -354,22 +354,29 @@ __global__ void k_dinv_bound(int n, const int* __restrict__ rp, const int* __res
                              const double* __restrict__ v, double* __restrict__ dinv,
                              unsigned long long* __restrict__ bound, int* __restrict__ bad) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double aii = 0.0;
-  double s = 0.0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) {
-    if (ci[k] == i) aii = v[k];
-    s = s + fabs(v[k]);
+  double s = 0.0;   // non-negative, so its bit pattern orders like the value
+  if (i < n) {
+    double aii = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] == i) aii = v[k];
+      s = s + fabs(v[k]);
+    }
+    if (aii == 0.0 || !isfinite(aii)) {
+      atomicMin(bad, i);
+      dinv[i] = 0.0;
+      s = 0.0;
+    } else {
+      double di = 1.0 / aii;
+      dinv[i] = di;
+      s = s * fabs(di);
+    }
   }
-  if (aii == 0.0 || !isfinite(aii)) {
-    atomicMin(bad, i);
-    dinv[i] = 0.0;
-    return;
+  unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
   }
-  double di = 1.0 / aii;
-  dinv[i] = di;
-  s = s * fabs(di);
-  atomicMax(bound, (unsigned long long)__double_as_longlong(s));
+  if ((threadIdx.x & 31) == 0 && bits != 0ULL) atomicMax(bound, bits);
 }
 
 void sparse_product(Handle* h, int n, const int* xrp, const int* xci, const double* xv,

@@ -65,6 +65,7 @@ void release_setup(Handle& H) {
   H.colour.release(); H.perm.release(); H.iperm.release();
   H.frp.release(); H.fpos.release(); H.fcell.release(); H.fdp.release(); H.fsrc.release();
   H.st_first.release(); H.st_len.release(); H.sc_start.clear();
+  H.fslo.release(); H.fshi.release(); H.cL.release(); H.cG.release(); H.cflag.release();
   H.fv.release(); H.fdinv.release(); H.fcs.release();
   H.rT.release(); H.xT.release(); H.zP.release(); H.vP.release(); H.w.release();
   H.cstart.clear();

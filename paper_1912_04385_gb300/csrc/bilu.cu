@@ -112,12 +112,29 @@ __global__ void k_perm_rowlen(int n, const int* __restrict__ perm, const int* __
   if (q < n) len[q] = rp[perm[q] + 1] - rp[perm[q]];
 }
 
-// factor pattern of row q (cell perm[q]) sorted by column position
+// position range [qlo, qhi) of the strip that holds each position
+__global__ void k_strip_ranges(int ns, const int* __restrict__ st_first,
+                               const int* __restrict__ st_len, int* __restrict__ qlo,
+                               int* __restrict__ qhi) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ns) return;
+  const int f = st_first[k], e = f + st_len[k];
+  for (int q = f; q < e; ++q) {
+    qlo[q] = f;
+    qhi[q] = e;
+  }
+}
+
+// factor pattern of row q (cell perm[q]) sorted by column position, and the
+// split of the row into other-strip lower | in-strip lower | diagonal |
+// in-strip upper | other-strip upper entries
 __global__ void k_factor_pattern(int n, const int* __restrict__ perm,
                                  const int* __restrict__ iperm, const int* __restrict__ rp,
                                  const int* __restrict__ ci, const int* __restrict__ frp,
+                                 const int* __restrict__ qlo, const int* __restrict__ qhi,
                                  int* __restrict__ fpos, int* __restrict__ fcell,
-                                 int* __restrict__ fsrc, int* __restrict__ fdp) {
+                                 int* __restrict__ fsrc, int* __restrict__ fdp,
+                                 int* __restrict__ fslo, int* __restrict__ fshi) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const int i = perm[q];
@@ -137,9 +154,17 @@ __global__ void k_factor_pattern(int n, const int* __restrict__ perm,
     fcell[base + k + 1] = ci[e];
     fsrc[base + k + 1] = e;
   }
-  for (int a = 0; a < len; ++a)
-    if (fpos[base + a] == q) d = base + a;
+  const int lo = qlo[q], hi = qhi[q];
+  int slo = base + len, shi = base;
+  for (int a = 0; a < len; ++a) {
+    const int pc = fpos[base + a];
+    if (pc == q) d = base + a;
+    if (pc >= lo && pc < q && base + a < slo) slo = base + a;
+    if (pc > q && pc < hi) shi = base + a + 1;
+  }
   fdp[q] = d;
+  fslo[q] = slo < d ? slo : d;
+  fshi[q] = shi > d + 1 ? shi : d + 1;
 }
 
 // factor blocks (copies of Abar) and column slices [Abar[:, t] | Abar[:, p]]
@@ -230,8 +255,9 @@ k_bilu_factor(int s0, int s1, const int* __restrict__ st_first, const int* __res
     for (int ks = 0; ks < NB; ++ks) {
       const double piv = aug[ks * W2 + ks];
       if (piv == 0.0 || !isfinite(piv)) { ok = false; break; }   // same value in all lanes
+      const double rpiv = 1.0 / piv;          // one division per pivot
       __syncwarp();
-      if (lane < W2) aug[ks * W2 + lane] = aug[ks * W2 + lane] / piv;
+      if (lane < W2) aug[ks * W2 + lane] = aug[ks * W2 + lane] * rpiv;
       __syncwarp();
       double fr[(NB * W2 + 31) / 32];
       int tt = 0;
@@ -261,66 +287,64 @@ __device__ __forceinline__ int warp_max(int v) {
   return v;
 }
 
-// ---- sweeps: NB lanes per strip, the strip's rows in order ------------------
-// MODE bit 1: subtract Abar[:, t] x_T; bit 2: subtract Abar[:, p] v_P
+// ---- sweeps ----------------------------------------------------------------
+// Each sweep of one colour is split in two launches: a fully parallel pass
+// (NB lanes per row) that does all the work coupling the row to other strips
+// (earlier colours in the forward sweep, later colours in the backward
+// sweep), and a chain pass (NB lanes per strip, rows in order) that adds the
+// couplings inside the strip; the value of the neighbouring row in the strip
+// is forwarded in registers.
+//
+// forward, parallel: w_q = u_q - sum_{other-strip lower} L_qk w_k, with
+// u = r - Abar[:,t] x_T - Abar[:,p] v_P (MODE bit 1: x_T term, bit 2: v_P)
 template <int NB, int MODE>
-__global__ void k_bilu_fwd(int s0, int s1, const int* __restrict__ st_first,
-                           const int* __restrict__ st_len, const int* __restrict__ perm,
-                           const int* __restrict__ frp, const int* __restrict__ fdp,
-                           const int* __restrict__ fpos, const int* __restrict__ fcell,
-                           const double* __restrict__ fv, const double* __restrict__ fcs,
-                           const double* __restrict__ r, const double* __restrict__ xT,
-                           const double* __restrict__ vP, double* __restrict__ w, int lower) {
+__global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
+                               const int* __restrict__ frp, const int* __restrict__ fslo,
+                               const int* __restrict__ fpos, const int* __restrict__ fcell,
+                               const double* __restrict__ fv, const double* __restrict__ fcs,
+                               const double* __restrict__ r, const double* __restrict__ xT,
+                               const double* __restrict__ vP, double* __restrict__ w, int lower) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
   const int sub = lane / NB, comp = lane - sub * NB;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long kk = s0 + warp * RPW + sub;
-  const bool active = sub < RPW && kk < s1;
-  const int first = active ? st_first[kk] : 0;
-  const int len = active ? st_len[kk] : 0;
-  const int maxlen = warp_max(len);
-  for (int it = 0; it < maxlen; ++it) {
-    if (it < len) {
-      const int q = first + it;
-      const int cell = perm[q];
-      double acc = r[(size_t)cell * NB + comp];
-      const int b = frp[q], e = frp[q + 1];
-      if (MODE) {
-        for (int f = b; f < e; ++f) {
-          const int j = fcell[f];
-          const double* cs = fcs + (size_t)f * 2 * NB;
-          if (MODE & 1) acc -= cs[comp] * xT[j];
-          if (MODE & 2) acc -= cs[NB + comp] * vP[j];
-        }
-      }
-      if (lower) {
-        const int d = fdp[q];
-        for (int f = b; f < d; ++f) {
-          const double* Lr = fv + (size_t)f * B2 + comp * NB;
-          const double* wk = w + (size_t)fpos[f] * NB;
-#pragma unroll
-          for (int c = 0; c < NB; ++c) acc -= Lr[c] * wk[c];
-        }
-      }
-      w[(size_t)q * NB + comp] = acc;
+  const long long qq = q0 + warp * RPW + sub;
+  if (sub >= RPW || qq >= q1) return;
+  const int q = (int)qq;
+  const int cell = perm[q];
+  double acc = r[(size_t)cell * NB + comp];
+  const int b = frp[q], e = frp[q + 1];
+  if (MODE) {
+    for (int f = b; f < e; ++f) {
+      const int j = fcell[f];
+      const double* cs = fcs + (size_t)f * 2 * NB;
+      if (MODE & 1) acc -= cs[comp] * xT[j];
+      if (MODE & 2) acc -= cs[NB + comp] * vP[j];
     }
-    __syncwarp();
   }
+  if (lower) {
+    const int d = fslo[q];
+    for (int f = b; f < d; ++f) {
+      const double* Lr = fv + (size_t)f * B2 + comp * NB;
+      const double* wk = w + (size_t)fpos[f] * NB;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc -= Lr[c] * wk[c];
+    }
+  }
+  w[(size_t)q * NB + comp] = acc;
 }
 
-// backward: x_q = U_qq^{-1} (w_q - sum_{upper} U_qj x_j), rows of a strip in
-// reverse order; x_q goes back into w (read by earlier rows and colours) and
-// y = x + stage corrections
-template <int NB, int MODE>
-__global__ void k_bilu_bwd(int s0, int s1, const int* __restrict__ st_first,
-                           const int* __restrict__ st_len, const int* __restrict__ perm,
-                           const int* __restrict__ frp, const int* __restrict__ fdp,
-                           const int* __restrict__ fpos, const double* __restrict__ fv,
-                           const double* __restrict__ fdinv, const double* __restrict__ xT,
-                           const double* __restrict__ vP, int p, int t, double* __restrict__ w,
-                           double* __restrict__ y, int upper) {
+// forward, chain: w_q -= sum_{in-strip lower} L_qk w_k, rows in order. The
+// coupling to the previous row comes from the dense per-position copy cL and
+// the previous row's values held in the lanes' registers; rows are fetched
+// two steps ahead (their addresses depend only on the position).
+template <int NB>
+__global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_first,
+                                 const int* __restrict__ st_len, const int* __restrict__ fslo,
+                                 const int* __restrict__ fdp, const int* __restrict__ fpos,
+                                 const double* __restrict__ fv, const double* __restrict__ cL,
+                                 const int* __restrict__ cflag, double* __restrict__ w) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
@@ -332,31 +356,233 @@ __global__ void k_bilu_bwd(int s0, int s1, const int* __restrict__ st_first,
   const int len = active ? st_len[kk] : 0;
   const int maxlen = warp_max(len);
   const int base = sub * NB;
+  double t0 = 0.0, t1 = 0.0, L0[NB], L1[NB];
+  int f0 = 0, f1 = 0;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) L0[c] = L1[c] = 0.0;
+  auto fetch = [&](int it2, double& t, double* Lr, int& fl) {
+    if (it2 >= len) return;
+    const size_t q2 = (size_t)first + it2;
+    t = w[q2 * NB + comp];
+    fl = cflag[q2];
+    const double* src = cL + q2 * B2 + comp * NB;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) Lr[c] = src[c];
+  };
+  fetch(0, t0, L0, f0);
+  fetch(1, t1, L1, f1);
+  double prev = 0.0;                        // component comp of w_{q-1}
+  for (int it = 0; it < maxlen; ++it) {
+    const bool on = it < len;
+    const int q = first + it;
+    double acc = t0;
+    double Lc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) Lc[c] = L0[c];
+    const int fl = f0;
+    // rotate the prefetch ring and fetch two rows ahead
+    t0 = t1;
+    f0 = f1;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) L0[c] = L1[c];
+    fetch(it + 2, t1, L1, f1);
+    double pc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) pc[c] = __shfl_sync(0xffffffffu, prev, (base + c) & 31);
+    if (on) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc -= Lc[c] * pc[c];
+      if (fl & 1) {                          // other in-strip couplings, from memory
+        for (int f = fslo[q]; f < fdp[q]; ++f) {
+          const double* Lr = fv + (size_t)f * B2 + comp * NB;
+          const double* wk = w + (size_t)fpos[f] * NB;
+#pragma unroll
+          for (int c = 0; c < NB; ++c) acc -= Lr[c] * wk[c];
+        }
+      }
+      w[(size_t)q * NB + comp] = acc;
+      prev = acc;
+    }
+    __syncwarp();
+  }
+}
+
+// After the factorisation, every in-strip upper block U_qj becomes
+// G_qj = U_qq^{-1} U_qj, so that the backward chain reads
+//   x_q = s_q - sum_{in-strip upper} G_qj x_j,  s_q = U_qq^{-1} t_q,
+// with s_q formed in the parallel pass (the same operator, written as a
+// product of the already inverted pivot block).
+template <int NB>
+__global__ void k_strip_upper_scale(int n, const int* __restrict__ fdp,
+                                    const int* __restrict__ fshi,
+                                    const double* __restrict__ fdinv, double* __restrict__ fv) {
+  constexpr int B2 = NB * NB;
+  const int lane = threadIdx.x & 31;
+  const long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= n) return;
+  const double* Ui = fdinv + (size_t)q * B2;
+  for (int g = fdp[q] + 1; g < fshi[q]; ++g) {
+    double* U = fv + (size_t)g * B2;
+    double out[(B2 + 31) / 32];
+    int tt = 0;
+    for (int idx = lane; idx < B2; idx += 32, ++tt) {
+      const int r = idx / NB, c = idx - r * NB;
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < NB; ++m) s += Ui[r * NB + m] * U[m * NB + c];
+      out[tt] = s;
+    }
+    __syncwarp();
+    tt = 0;
+    for (int idx = lane; idx < B2; idx += 32, ++tt) U[idx] = out[tt];
+    __syncwarp();
+  }
+}
+
+// Dense per-position copies of the chain couplings: cL[q] = L_{q,q-1} when
+// the only in-strip lower neighbour of q is q-1, cG[q] = G_{q,q+1} when the
+// only in-strip upper neighbour is q+1, zero blocks when there is none; any
+// other in-strip coupling sets cflag (bit 0 lower, bit 1 upper) and is then
+// taken from the factor rows instead.
+template <int NB>
+__global__ void k_chain_blocks(long long N, const int* __restrict__ fslo,
+                               const int* __restrict__ fdp, const int* __restrict__ fshi,
+                               const int* __restrict__ fpos, const double* __restrict__ fv,
+                               double* __restrict__ cL, double* __restrict__ cG,
+                               int* __restrict__ cflag) {
+  constexpr int B2 = NB * NB;
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= N * B2) return;
+  const int q = (int)(tid / B2);
+  const int k = (int)(tid - (long long)q * B2);
+  const int lo = fslo[q], d = fdp[q], hi = fshi[q];
+  const bool one_lo = d - lo == 1 && fpos[lo] == q - 1;
+  const bool one_hi = hi - d == 2 && fpos[d + 1] == q + 1;
+  cL[tid] = one_lo ? fv[(size_t)lo * B2 + k] : 0.0;
+  cG[tid] = one_hi ? fv[(size_t)(d + 1) * B2 + k] : 0.0;
+  if (k == 0) cflag[q] = ((d > lo && !one_lo) ? 1 : 0) | ((hi > d + 1 && !one_hi) ? 2 : 0);
+}
+
+// backward, parallel: s_q = U_qq^{-1} (w_q - sum_{other-strip upper} U_qj x_j)
+// (later colours, final); stored back into w
+template <int NB>
+__global__ void k_bilu_bwd_par(int q0, int q1, const int* __restrict__ frp,
+                               const int* __restrict__ fshi, const int* __restrict__ fpos,
+                               const double* __restrict__ fv, const double* __restrict__ fdinv,
+                               double* __restrict__ w) {
+  constexpr int RPW = 32 / NB;
+  constexpr int B2 = NB * NB;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / NB, comp = lane - sub * NB;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long qq = q0 + warp * RPW + sub;
+  const bool on = sub < RPW && qq < q1;
+  const int q = on ? (int)qq : q0;
+  double acc = 0.0;
+  if (on) {
+    acc = w[(size_t)q * NB + comp];
+    for (int g = fshi[q]; g < frp[q + 1]; ++g) {
+      const double* Ur = fv + (size_t)g * B2 + comp * NB;
+      const double* xj = w + (size_t)fpos[g] * NB;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc -= Ur[c] * xj[c];
+    }
+  }
+  const int base = sub * NB;
+  const double* Ui = fdinv + (size_t)q * B2 + comp * NB;
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    double tc = __shfl_sync(0xffffffffu, acc, (base + c) & 31);
+    if (on) s += Ui[c] * tc;
+  }
+  if (on) w[(size_t)q * NB + comp] = s;
+}
+
+// backward, chain: x_q = s_q - sum_{in-strip upper} G_qj x_j, rows of a
+// strip in reverse order (cG and the next row's values in registers, rows
+// fetched two steps ahead); x_q goes back into w (read by earlier rows and
+// colours) and y = x + stage corrections (MODE as forward). Block Jacobi
+// (upper = 0): x_q = D_qq^{-1} u_q.
+template <int NB, int MODE>
+__global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_first,
+                                 const int* __restrict__ st_len, const int* __restrict__ perm,
+                                 const int* __restrict__ fdp, const int* __restrict__ fshi,
+                                 const int* __restrict__ fpos, const double* __restrict__ fv,
+                                 const double* __restrict__ fdinv, const double* __restrict__ cG,
+                                 const int* __restrict__ cflag, const double* __restrict__ xT,
+                                 const double* __restrict__ vP, int p, int t,
+                                 double* __restrict__ w, double* __restrict__ y, int upper) {
+  constexpr int RPW = 32 / NB;
+  constexpr int B2 = NB * NB;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / NB, comp = lane - sub * NB;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long kk = s0 + warp * RPW + sub;
+  const bool active = sub < RPW && kk < s1;
+  const int first = active ? st_first[kk] : 0;
+  const int len = active ? st_len[kk] : 0;
+  const int maxlen = warp_max(len);
+  const int base = sub * NB;
+  double s0v = 0.0, s1v = 0.0, G0[NB], G1[NB];
+  int f0 = 0, f1 = 0;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) G0[c] = G1[c] = 0.0;
+  auto fetch = [&](int it2, double& s, double* Gr, int& fl) {
+    if (it2 >= len) return;
+    const size_t q2 = (size_t)first + len - 1 - it2;
+    s = w[q2 * NB + comp];
+    if (!upper) return;
+    fl = cflag[q2];
+    const double* src = cG + q2 * B2 + comp * NB;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) Gr[c] = src[c];
+  };
+  fetch(0, s0v, G0, f0);
+  fetch(1, s1v, G1, f1);
+  double nxt = 0.0;                         // component comp of x_{q+1}
   for (int it = 0; it < maxlen; ++it) {
     const bool on = it < len;
     const int q = on ? first + len - 1 - it : 0;
-    double tv = 0.0;
-    if (on) {
-      tv = w[(size_t)q * NB + comp];
-      if (upper) {
-        const int d = fdp[q], e = frp[q + 1];
-        for (int g = d + 1; g < e; ++g) {
-          const double* Ur = fv + (size_t)g * B2 + comp * NB;
-          const double* xj = w + (size_t)fpos[g] * NB;
+    const double sv = s0v;
+    double Gc[NB];
 #pragma unroll
-          for (int c = 0; c < NB; ++c) tv -= Ur[c] * xj[c];
+    for (int c = 0; c < NB; ++c) Gc[c] = G0[c];
+    const int fl = f0;
+    s0v = s1v;
+    f0 = f1;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) G0[c] = G1[c];
+    fetch(it + 2, s1v, G1, f1);
+    double x = 0.0;
+    if (upper) {
+      double nc[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) nc[c] = __shfl_sync(0xffffffffu, nxt, (base + c) & 31);
+      x = sv;
+      if (on) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) x -= Gc[c] * nc[c];
+        if (fl & 2) {                        // other in-strip couplings, from memory
+          for (int g = fdp[q] + 1; g < fshi[q]; ++g) {
+            const double* Gr = fv + (size_t)g * B2 + comp * NB;
+            const double* xj = w + (size_t)fpos[g] * NB;
+#pragma unroll
+            for (int c = 0; c < NB; ++c) x -= Gr[c] * xj[c];
+          }
         }
       }
-    }
-    const double* Ui = fdinv + (size_t)q * B2 + comp * NB;
-    double x = 0.0;
+    } else {
+      const double* Ui = fdinv + (size_t)q * B2 + comp * NB;
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      double tc = __shfl_sync(0xffffffffu, tv, (base + c) & 31);
-      if (on) x += Ui[c] * tc;
+      for (int c = 0; c < NB; ++c) {
+        double tc = __shfl_sync(0xffffffffu, sv, (base + c) & 31);
+        if (on) x += Ui[c] * tc;
+      }
     }
     if (on) {
       w[(size_t)q * NB + comp] = x;
+      nxt = x;
       const int cell = perm[q];
       double out = x;
       if ((MODE & 1) && comp == t) out += xT[cell];
@@ -449,13 +675,21 @@ void bilu_setup_nb(Handle* h) {
   h->fcell.reset(h, nnzb);
   h->fsrc.reset(h, nnzb);
   h->fdp.reset(h, N);
+  h->fslo.reset(h, N);
+  h->fshi.reset(h, N);
   h->fv.reset(h, (size_t)nnzb * NB * NB);
   h->fcs.reset(h, (size_t)nnzb * 2 * NB);
   h->fdinv.reset(h, (size_t)N * NB * NB);
-  k_factor_pattern<<<grid_for(N, 128), 128, 0, h->stream>>>(
-      N, h->perm.p, h->iperm.p, h->rp.p, h->ci.p, h->frp.p, h->fpos.p, h->fcell.p, h->fsrc.p,
-      h->fdp.p);
-  MSS_LAUNCH_CK("k_factor_pattern");
+  {
+    DBuf<int> qlo(h, N), qhi(h, N);
+    k_strip_ranges<<<grid_for(ns, 256), 256, 0, h->stream>>>(ns, h->st_first.p, h->st_len.p,
+                                                             qlo.p, qhi.p);
+    MSS_LAUNCH_CK("k_strip_ranges");
+    k_factor_pattern<<<grid_for(N, 128), 128, 0, h->stream>>>(
+        N, h->perm.p, h->iperm.p, h->rp.p, h->ci.p, h->frp.p, qlo.p, qhi.p, h->fpos.p,
+        h->fcell.p, h->fsrc.p, h->fdp.p, h->fslo.p, h->fshi.p);
+    MSS_LAUNCH_CK("k_factor_pattern");
+  }
   {
     long long tot = (long long)nnzb * NB * NB;
     unsigned g = grid_for(tot, 256);
@@ -479,32 +713,63 @@ void bilu_setup_nb(Handle* h) {
   if (badq != 0x7fffffff)
     fail(MSS_ERR_SINGULAR_BLOCK, "block ILU(0): zero pivot in the diagonal block at position " +
                                      std::to_string(badq));
+  if (!bjac) {
+    if (strips && S > 1) {
+      k_strip_upper_scale<NB><<<grid_for((long long)N * 32, 256), 256, 0, h->stream>>>(
+          N, h->fdp.p, h->fshi.p, h->fdinv.p, h->fv.p);
+      MSS_LAUNCH_CK("k_strip_upper_scale");
+    }
+    // chain blocks (zero blocks and no flags when strips are single cells)
+    h->cL.reset(h, (size_t)N * NB * NB);
+    h->cG.reset(h, (size_t)N * NB * NB);
+    h->cflag.reset(h, N);
+    k_chain_blocks<NB><<<grid_for((long long)N * NB * NB, 256), 256, 0, h->stream>>>(
+        N, h->fslo.p, h->fdp.p, h->fshi.p, h->fpos.p, h->fv.p, h->cL.p, h->cG.p, h->cflag.p);
+    MSS_LAUNCH_CK("k_chain_blocks");
+  }
 }
 
 template <int NB, int MODE>
 void sweeps(Handle* h, const double* r, const double* xT, const double* vP, double* y) {
   constexpr int RPW = 32 / NB;
   const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
+  // strips longer than one cell carry in-strip couplings (chain passes)
+  const bool chains = !bjac && h->opt.ilu_order == MSS_STRIPS && h->opt.ilu_strip > 1;
   const int T = 256;
   for (int c = 0; c < h->ncol; ++c) {
+    const int q0 = h->cstart[c], q1 = h->cstart[c + 1];
     const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
-    if (s1 <= s0) continue;
-    const long long warps = (s1 - s0 + RPW - 1) / RPW;
+    if (q1 <= q0) continue;
     TraceScope ts(h, TR_BILU_FWD);
-    k_bilu_fwd<NB, MODE><<<grid_for(warps * 32, T), T, 0, h->stream>>>(
-        s0, s1, h->st_first.p, h->st_len.p, h->perm.p, h->frp.p, h->fdp.p, h->fpos.p,
-        h->fcell.p, h->fv.p, h->fcs.p, r, xT, vP, h->w.p, bjac ? 0 : 1);
-    MSS_LAUNCH_CK("k_bilu_fwd");
+    const long long rw = (q1 - q0 + RPW - 1) / RPW;
+    k_bilu_fwd_par<NB, MODE><<<grid_for(rw * 32, T), T, 0, h->stream>>>(
+        q0, q1, h->perm.p, h->frp.p, h->fslo.p, h->fpos.p, h->fcell.p, h->fv.p, h->fcs.p, r, xT,
+        vP, h->w.p, bjac ? 0 : 1);
+    MSS_LAUNCH_CK("k_bilu_fwd_par");
+    if (chains) {
+      const long long sw = (s1 - s0 + RPW - 1) / RPW;
+      k_bilu_fwd_chain<NB><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
+          s0, s1, h->st_first.p, h->st_len.p, h->fslo.p, h->fdp.p, h->fpos.p, h->fv.p, h->cL.p,
+          h->cflag.p, h->w.p);
+      MSS_LAUNCH_CK("k_bilu_fwd_chain");
+    }
   }
   for (int c = h->ncol - 1; c >= 0; --c) {
+    const int q0 = h->cstart[c], q1 = h->cstart[c + 1];
     const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
-    if (s1 <= s0) continue;
-    const long long warps = (s1 - s0 + RPW - 1) / RPW;
+    if (q1 <= q0) continue;
     TraceScope ts(h, TR_BILU_BWD);
-    k_bilu_bwd<NB, MODE><<<grid_for(warps * 32, T), T, 0, h->stream>>>(
-        s0, s1, h->st_first.p, h->st_len.p, h->perm.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p,
-        h->fdinv.p, xT, vP, h->p, h->t, h->w.p, y, bjac ? 0 : 1);
-    MSS_LAUNCH_CK("k_bilu_bwd");
+    if (!bjac) {
+      const long long rw = (q1 - q0 + RPW - 1) / RPW;
+      k_bilu_bwd_par<NB><<<grid_for(rw * 32, T), T, 0, h->stream>>>(
+          q0, q1, h->frp.p, h->fshi.p, h->fpos.p, h->fv.p, h->fdinv.p, h->w.p);
+      MSS_LAUNCH_CK("k_bilu_bwd_par");
+    }
+    const long long sw = (s1 - s0 + RPW - 1) / RPW;
+    k_bilu_bwd_chain<NB, MODE><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
+        s0, s1, h->st_first.p, h->st_len.p, h->perm.p, h->fdp.p, h->fshi.p, h->fpos.p, h->fv.p,
+        h->fdinv.p, h->cG.p, h->cflag.p, xT, vP, h->p, h->t, h->w.p, y, bjac ? 0 : 1);
+    MSS_LAUNCH_CK("k_bilu_bwd_chain");
   }
 }
 

@@ -134,6 +134,9 @@ struct Handle {
   DBuf<int> frp, fpos, fcell;  // factor pattern: column position and cell
   DBuf<int> fdp;               // index of the diagonal block in each factor row
   DBuf<int> fsrc;              // source block (index into Abar) of each factor block
+  DBuf<int> fslo, fshi;        // per row: first in-strip lower entry, end of in-strip upper
+  DBuf<double> cL, cG;         // per position: L_{q,q-1} and G_{q,q+1} (zero if absent)
+  DBuf<int> cflag;             // per position: bit 0 / bit 1 = other in-strip lower / upper
   DBuf<int> st_first, st_len;  // strips in colour-major order: first position, length
   std::vector<int> sc_start;   // host: first strip of each colour, ncol + 1
   DBuf<double> fv;             // L (strictly lower) / U (strictly upper) blocks

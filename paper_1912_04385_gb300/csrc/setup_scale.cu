@@ -165,35 +165,41 @@ __global__ void k_build_w(const double* __restrict__ vals, const int* __restrict
   }
 }
 
-// One thread per entry (row i, r, c) looping over the blocks of row i:
-// Abar_ij[r][c] = sum_k W_i[r][k] J_ij[k][c] (ascending k) for r in {p, t},
-// a copy for the other rows (their W row is a unit vector).
+// block -> block row map
+__global__ void k_block_rows(int N, const int* __restrict__ rp, int* __restrict__ brow) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) brow[e] = i;
+}
+
+// One thread per output entry (block e, r, c), consecutive threads on
+// consecutive entries: Abar_ij[r][c] = sum_k W_i[r][k] J_ij[k][c] (ascending
+// k) for r in {p, t}, a copy for the other rows (their W row is a unit vector).
 template <int NB>
-__global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict__ rp, int N,
-                          int p, int t, int scheme, int col_major,
+__global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict__ brow,
+                          long long nnzb, int p, int t, int scheme, int col_major,
                           const double* __restrict__ wrows, double* __restrict__ abar) {
+  constexpr int B2 = NB * NB;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (long long)N * NB * NB) return;
-  int i = (int)(tid / (NB * NB));
-  int rc = (int)(tid % (NB * NB));
-  int r = rc / NB, c = rc % NB;
-  bool scaled_row = scheme != 2 && (r == p || (scheme == 0 && r == t));
-  const double* w = wrows + (size_t)i * 2 * NB + (r == p ? 0 : NB);
-  for (int e = rp[i]; e < rp[i + 1]; ++e) {
-    const double* src = vals + (size_t)e * NB * NB;
-    double out;
-    if (!scaled_row) {
-      out = col_major ? src[c * NB + r] : src[r * NB + c];
-    } else {
-      double acc = 0.0;
-      for (int k = 0; k < NB; ++k) {
-        double a = col_major ? src[c * NB + k] : src[k * NB + c];
-        acc = acc + w[k] * a;
-      }
-      out = acc;
+  if (tid >= nnzb * B2) return;
+  const long long e = tid / B2;
+  const int rc = (int)(tid - e * B2);
+  const int r = rc / NB, c = rc - r * NB;
+  const double* src = vals + (size_t)e * B2;
+  const bool scaled_row = scheme != 2 && (r == p || (scheme == 0 && r == t));
+  double out;
+  if (!scaled_row) {
+    out = col_major ? src[c * NB + r] : src[r * NB + c];
+  } else {
+    const double* w = wrows + (size_t)brow[e] * 2 * NB + (r == p ? 0 : NB);
+    double acc = 0.0;
+    for (int k = 0; k < NB; ++k) {
+      double a = col_major ? src[c * NB + k] : src[k * NB + c];
+      acc = acc + w[k] * a;
     }
-    abar[(size_t)e * NB * NB + r * NB + c] = out;
+    out = acc;
   }
+  abar[tid] = out;
 }
 
 template <int NB>
@@ -238,9 +244,13 @@ void build_scaling_nb(Handle* h, const double* vals, bool col_major) {
   if (bad != 0x7fffffff)
     fail(MSS_ERR_SINGULAR_BLOCK,
          "cell " + std::to_string(bad) + ": diagonal block needs pivoting (zero pivot)");
-  long long tot = (long long)N * NB * NB;
-  k_apply_w<NB><<<grid_for(tot, 256), 256, 0, h->stream>>>(vals, h->rp.p, N, h->p, h->t, scheme,
-                                                           col_major, h->wrows.p, h->abar.p);
+  DBuf<int> brow(h, h->nnzb);
+  k_block_rows<<<grid_for(N, 256), 256, 0, h->stream>>>(N, h->rp.p, brow.p);
+  MSS_LAUNCH_CK("k_block_rows");
+  long long tot = (long long)h->nnzb * NB * NB;
+  k_apply_w<NB><<<grid_for(tot, 256), 256, 0, h->stream>>>(vals, brow.p, h->nnzb, h->p, h->t,
+                                                           scheme, col_major, h->wrows.p,
+                                                           h->abar.p);
   MSS_LAUNCH_CK("k_apply_w");
 }
 
