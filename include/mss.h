@@ -195,6 +195,18 @@ int mss_solve_host(mss_handle* h, const mss_bsr* J_host, int nb, mss_layout layo
                    const mss_options* opt, const double* b_host, double* x_host, double tol,
                    int maxit, mss_result* out);
 
+/* Residual check of the unscaled system for a given x: norms[0] =
+ * ||b - J x||_2, norms[1] = ||b||_2 (Eq. reduced; the solver itself stops on
+ * the scaled residual, Sec. 5.1). Any BSR matrix with row-major blocks; no
+ * set-up is needed, the handle supplies the stream and the allocation hooks.
+ * J, b, x: device, as in mss_setup; norms: device, 2 doubles, written in
+ * stream order (the call does not synchronise). Scratch of 2 * n_rows
+ * doubles is allocated through the handle's hooks for the call. The sums run
+ * in a fixed order, so the result does not depend on the launch shape.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int mss_residual_norm(mss_handle* h, const mss_bsr* J, int nb, const double* b, const double* x,
+                      double* norms);
+
 /* ---- introspection (tests) --------------------------------------------- */
 /* Copy the scaled blocks Abar (device, nnzb*nb*nb, row-major) into `abar`
  * (device, caller-owned). */

@@ -240,6 +240,14 @@ void bilu_setup(Handle* h);
 void last_stage_apply(Handle* h, const double* r, const double* xT, const double* vP,
                       double* y);
 
+// residual.cu
+void check_residual_args(const mss_bsr* J, int nb, const double* b, const double* x,
+                         const double* norms);
+void residual_norms(cudaStream_t s, const mss_bsr* J, int nb, const double* b, const double* x,
+                    double* scratch, double* norms);   // scratch: 2 n_rows doubles
+void residual_norm(Handle* h, const mss_bsr* J, int nb, const double* b, const double* x,
+                   double* norms);
+
 // krylov.cu
 void bsr_spmv(Handle* h, const double* x, double* y);
 void precond_apply(Handle* h, const double* r, double* y);

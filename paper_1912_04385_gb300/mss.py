@@ -24,7 +24,7 @@ SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
 # every exported symbol declared in include/mss.h
 EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
            "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
-           "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
+           "mss_residual_norm", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
            "mss_bilu_num_colours", "mss_bilu_ordering", "mss_kernel_launches",
            "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error"]
 
@@ -93,6 +93,7 @@ def load(path: Path | str | None = None):
                                    C.POINTER(Result)]
     L.mss_solve_host.argtypes = [P, C.POINTER(Bsr), C.c_int, Layout, C.POINTER(Options), P, P,
                                  C.c_double, C.c_int, C.POINTER(Result)]
+    L.mss_residual_norm.argtypes = [P, C.POINTER(Bsr), C.c_int, P, P, P]
     L.mss_get_scaled.argtypes = [P, P]
     L.mss_amg_num_levels.argtypes = [P, C.c_int]
     L.mss_amg_level_sizes.argtypes = [P, C.c_int, C.c_int, P]
@@ -294,6 +295,16 @@ class Solver:
                         "mss_trace_read")
             out[name] = (n.value, ms.value)
         return out
+
+    def residual_norm(self, row_ptr, col_idx, vals, nb, b, x):
+        """(||b - J x||, ||b||) for device tensors through mss_residual_norm."""
+        torch = self._torch
+        J = Bsr(row_ptr.numel() - 1, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), _ptr(vals))
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+        self._check(self.lib.mss_residual_norm(self.h, C.byref(J), nb, _ptr(b), _ptr(x),
+                                               _ptr(out)), "mss_residual_norm")
+        r = out.cpu()
+        return float(r[0]), float(r[1])
 
     # ---- introspection ----------------------------------------------------
     def scaled(self):

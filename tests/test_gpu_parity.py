@@ -228,3 +228,23 @@ def test_error_statuses(mss):
     with pytest.raises(mss.MssError) as e:
         mss.Solver().setup_system(s, restart=500)
     assert e.value.status == mss.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("nb", [4, 6])
+def test_residual_norm_entry_point(mss, nb):
+    from tests.helpers import bsr_dense
+    s = sy.make_system(23, 17, nb, pe=10.0, seed=31)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(s.n_cells * nb)
+    A = bsr_dense(s.row_ptr, s.col_idx, s.vals)
+    ref_r = np.linalg.norm(s.b - A @ x)
+    ref_b = np.linalg.norm(s.b)
+    g = mss.Solver()
+    rp = torch.from_numpy(s.row_ptr).cuda()
+    ci = torch.from_numpy(s.col_idx).cuda()
+    v = _t(s.vals.reshape(-1))
+    r, bn = g.residual_norm(rp, ci, v, nb, _t(s.b), _t(x))
+    assert abs(r - ref_r) <= 1e-12 * ref_r
+    assert abs(bn - ref_b) <= 1e-12 * ref_b
+    r2, bn2 = g.residual_norm(rp, ci, v, nb, _t(s.b), _t(x))
+    assert r2 == r and bn2 == bn
