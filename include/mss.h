@@ -207,6 +207,29 @@ int mss_solve_host(mss_handle* h, const mss_bsr* J_host, int nb, mss_layout layo
 int mss_residual_norm(mss_handle* h, const mss_bsr* J, int nb, const double* b, const double* x,
                       double* norms);
 
+/* mss_residual_norm without any device allocation. The paper has no
+ * counterpart: this is a library convenience for callers that cannot call
+ * cudaMalloc at the point of the call -- a process whose device memory pool
+ * is wholly reserved by another framework, code inside a region where an
+ * allocation call is not allowed (it would break a stream capture or
+ * synchronise the device), or a latency-bound loop that must not enter the
+ * allocator. Same kernels, arguments, result and errors as
+ * mss_residual_norm, but the scratch (2 * n_rows doubles) lives in a static
+ * device array sized for MSS_NOALLOC_MAX_CELLS cells (16 MiB), which every
+ * GPU that loads the library holds until the process exits; n_rows above
+ * the limit returns MSS_ERR_INVALID_ARG. No cudaMalloc, cudaFree or
+ * allocating routine is called and the handle's hooks are not used. The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, on the current device, which must be the handle's);
+ * make that first call before any stream capture. All calls share the array,
+ * which keeps the last call's contents: each call writes every entry it reads
+ * before reading it, but calls whose GPU work overlaps (on other streams or
+ * from other threads) race on the array and must be serialised by the
+ * caller. */
+#define MSS_NOALLOC_MAX_CELLS (1 << 20)
+int mss_residual_norm_noalloc(mss_handle* h, const mss_bsr* J, int nb, const double* b,
+                              const double* x, double* norms);
+
 /* ---- introspection (tests) --------------------------------------------- */
 /* Copy the scaled blocks Abar (device, nnzb*nb*nb, row-major) into `abar`
  * (device, caller-owned). */

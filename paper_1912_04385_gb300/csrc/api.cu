@@ -342,6 +342,12 @@ int mss_residual_norm(mss_handle* hh, const mss_bsr* J, int nb, const double* b,
   return guarded(hh, [&] { residual_norm(&hh->h, J, nb, b, x, norms); });
 }
 
+int mss_residual_norm_noalloc(mss_handle* hh, const mss_bsr* J, int nb, const double* b,
+                              const double* x, double* norms) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] { residual_norm_noalloc(&hh->h, J, nb, b, x, norms); });
+}
+
 int mss_get_scaled(mss_handle* hh, double* abar) {
   if (!hh) return MSS_ERR_INVALID_ARG;
   return guarded(hh, [&] {

@@ -247,6 +247,9 @@ void residual_norms(cudaStream_t s, const mss_bsr* J, int nb, const double* b, c
                     double* scratch, double* norms);   // scratch: 2 n_rows doubles
 void residual_norm(Handle* h, const mss_bsr* J, int nb, const double* b, const double* x,
                    double* norms);
+// noalloc.cu
+void residual_norm_noalloc(Handle* h, const mss_bsr* J, int nb, const double* b, const double* x,
+                           double* norms);
 
 // krylov.cu
 void bsr_spmv(Handle* h, const double* x, double* y);

@@ -24,7 +24,7 @@ SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
 # every exported symbol declared in include/mss.h
 EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
            "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
-           "mss_residual_norm", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
+           "mss_residual_norm", "mss_residual_norm_noalloc", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
            "mss_bilu_num_colours", "mss_bilu_ordering", "mss_kernel_launches",
            "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error"]
 
@@ -94,6 +94,7 @@ def load(path: Path | str | None = None):
     L.mss_solve_host.argtypes = [P, C.POINTER(Bsr), C.c_int, Layout, C.POINTER(Options), P, P,
                                  C.c_double, C.c_int, C.POINTER(Result)]
     L.mss_residual_norm.argtypes = [P, C.POINTER(Bsr), C.c_int, P, P, P]
+    L.mss_residual_norm_noalloc.argtypes = [P, C.POINTER(Bsr), C.c_int, P, P, P]
     L.mss_get_scaled.argtypes = [P, P]
     L.mss_amg_num_levels.argtypes = [P, C.c_int]
     L.mss_amg_level_sizes.argtypes = [P, C.c_int, C.c_int, P]
