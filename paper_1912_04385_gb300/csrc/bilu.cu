@@ -337,8 +337,29 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
 
 // forward, chain: w_q -= sum_{in-strip lower} L_qk w_k, rows in order. The
 // coupling to the previous row comes from the dense per-position copy cL and
-// the previous row's values held in the lanes' registers; rows are fetched
-// two steps ahead (their addresses depend only on the position).
+// the previous row's values held in the lanes' registers. Rows are fetched
+// two steps ahead into two alternating register buffers (the loop is unrolled
+// by two), so a fetch has two steps to land; the addresses depend only on the
+// position.
+template <int NB>
+struct ChainRow {
+  double t;
+  double m[NB];
+  int fl;
+};
+
+template <int NB>
+__device__ __forceinline__ void chain_fetch(ChainRow<NB>& b, const double* __restrict__ w,
+                                            const double* __restrict__ cm,
+                                            const int* __restrict__ cflag, size_t q, int comp) {
+  constexpr int B2 = NB * NB;
+  b.t = w[q * NB + comp];
+  b.fl = cflag[q];
+  const double* src = cm + q * B2 + comp * NB;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) b.m[c] = src[c];
+}
+
 template <int NB>
 __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_first,
                                  const int* __restrict__ st_len, const int* __restrict__ fslo,
@@ -356,42 +377,29 @@ __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_firs
   const int len = active ? st_len[kk] : 0;
   const int maxlen = warp_max(len);
   const int base = sub * NB;
-  double t0 = 0.0, t1 = 0.0, L0[NB], L1[NB];
-  int f0 = 0, f1 = 0;
+  ChainRow<NB> A, B;
+  A.t = B.t = 0.0;
+  A.fl = B.fl = 0;
 #pragma unroll
-  for (int c = 0; c < NB; ++c) L0[c] = L1[c] = 0.0;
-  auto fetch = [&](int it2, double& t, double* Lr, int& fl) {
-    if (it2 >= len) return;
-    const size_t q2 = (size_t)first + it2;
-    t = w[q2 * NB + comp];
-    fl = cflag[q2];
-    const double* src = cL + q2 * B2 + comp * NB;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) Lr[c] = src[c];
-  };
-  fetch(0, t0, L0, f0);
-  fetch(1, t1, L1, f1);
+  for (int c = 0; c < NB; ++c) A.m[c] = B.m[c] = 0.0;
+  if (0 < len) chain_fetch(A, w, cL, cflag, (size_t)first, comp);
+  if (1 < len) chain_fetch(B, w, cL, cflag, (size_t)first + 1, comp);
   double prev = 0.0;                        // component comp of w_{q-1}
-  for (int it = 0; it < maxlen; ++it) {
+  auto step = [&](int it, ChainRow<NB>& R) {
     const bool on = it < len;
     const int q = first + it;
-    double acc = t0;
-    double Lc[NB];
+    double acc = R.t;
+    double mc[NB];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) Lc[c] = L0[c];
-    const int fl = f0;
-    // rotate the prefetch ring and fetch two rows ahead
-    t0 = t1;
-    f0 = f1;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) L0[c] = L1[c];
-    fetch(it + 2, t1, L1, f1);
+    for (int c = 0; c < NB; ++c) mc[c] = R.m[c];
+    const int fl = R.fl;
+    if (it + 2 < len) chain_fetch(R, w, cL, cflag, (size_t)q + 2, comp);
     double pc[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) pc[c] = __shfl_sync(0xffffffffu, prev, (base + c) & 31);
     if (on) {
 #pragma unroll
-      for (int c = 0; c < NB; ++c) acc -= Lc[c] * pc[c];
+      for (int c = 0; c < NB; ++c) acc -= mc[c] * pc[c];
       if (fl & 1) {                          // other in-strip couplings, from memory
         for (int f = fslo[q]; f < fdp[q]; ++f) {
           const double* Lr = fv + (size_t)f * B2 + comp * NB;
@@ -404,6 +412,10 @@ __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_firs
       prev = acc;
     }
     __syncwarp();
+  };
+  for (int it = 0; it < maxlen; it += 2) {
+    step(it, A);
+    if (it + 1 < maxlen) step(it + 1, B);
   }
 }
 
@@ -501,18 +513,16 @@ __global__ void k_bilu_bwd_par(int q0, int q1, const int* __restrict__ frp,
 
 // backward, chain: x_q = s_q - sum_{in-strip upper} G_qj x_j, rows of a
 // strip in reverse order (cG and the next row's values in registers, rows
-// fetched two steps ahead); x_q goes back into w (read by earlier rows and
-// colours) and y = x + stage corrections (MODE as forward). Block Jacobi
-// (upper = 0): x_q = D_qq^{-1} u_q.
-template <int NB, int MODE>
+// fetched two steps ahead as in the forward chain); x_q goes back into w.
+// Block Jacobi (upper = 0): x_q = D_qq^{-1} u_q. The output y is assembled
+// afterwards by k_bilu_assemble.
+template <int NB>
 __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_first,
-                                 const int* __restrict__ st_len, const int* __restrict__ perm,
-                                 const int* __restrict__ fdp, const int* __restrict__ fshi,
-                                 const int* __restrict__ fpos, const double* __restrict__ fv,
-                                 const double* __restrict__ fdinv, const double* __restrict__ cG,
-                                 const int* __restrict__ cflag, const double* __restrict__ xT,
-                                 const double* __restrict__ vP, int p, int t,
-                                 double* __restrict__ w, double* __restrict__ y, int upper) {
+                                 const int* __restrict__ st_len, const int* __restrict__ fdp,
+                                 const int* __restrict__ fshi, const int* __restrict__ fpos,
+                                 const double* __restrict__ fv, const double* __restrict__ fdinv,
+                                 const double* __restrict__ cG, const int* __restrict__ cflag,
+                                 double* __restrict__ w, int upper) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
@@ -524,73 +534,80 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
   const int len = active ? st_len[kk] : 0;
   const int maxlen = warp_max(len);
   const int base = sub * NB;
-  double s0v = 0.0, s1v = 0.0, G0[NB], G1[NB];
-  int f0 = 0, f1 = 0;
-#pragma unroll
-  for (int c = 0; c < NB; ++c) G0[c] = G1[c] = 0.0;
-  auto fetch = [&](int it2, double& s, double* Gr, int& fl) {
-    if (it2 >= len) return;
-    const size_t q2 = (size_t)first + len - 1 - it2;
-    s = w[q2 * NB + comp];
-    if (!upper) return;
-    fl = cflag[q2];
-    const double* src = cG + q2 * B2 + comp * NB;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) Gr[c] = src[c];
-  };
-  fetch(0, s0v, G0, f0);
-  fetch(1, s1v, G1, f1);
-  double nxt = 0.0;                         // component comp of x_{q+1}
-  for (int it = 0; it < maxlen; ++it) {
-    const bool on = it < len;
-    const int q = on ? first + len - 1 - it : 0;
-    const double sv = s0v;
-    double Gc[NB];
-#pragma unroll
-    for (int c = 0; c < NB; ++c) Gc[c] = G0[c];
-    const int fl = f0;
-    s0v = s1v;
-    f0 = f1;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) G0[c] = G1[c];
-    fetch(it + 2, s1v, G1, f1);
-    double x = 0.0;
-    if (upper) {
-      double nc[NB];
-#pragma unroll
-      for (int c = 0; c < NB; ++c) nc[c] = __shfl_sync(0xffffffffu, nxt, (base + c) & 31);
-      x = sv;
-      if (on) {
-#pragma unroll
-        for (int c = 0; c < NB; ++c) x -= Gc[c] * nc[c];
-        if (fl & 2) {                        // other in-strip couplings, from memory
-          for (int g = fdp[q] + 1; g < fshi[q]; ++g) {
-            const double* Gr = fv + (size_t)g * B2 + comp * NB;
-            const double* xj = w + (size_t)fpos[g] * NB;
-#pragma unroll
-            for (int c = 0; c < NB; ++c) x -= Gr[c] * xj[c];
-          }
-        }
-      }
-    } else {
+  if (!upper) {
+    for (int it = 0; it < maxlen; ++it) {
+      const bool on = it < len;
+      const int q = on ? first + it : 0;
+      const double tv = on ? w[(size_t)q * NB + comp] : 0.0;
       const double* Ui = fdinv + (size_t)q * B2 + comp * NB;
+      double x = 0.0;
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        double tc = __shfl_sync(0xffffffffu, sv, (base + c) & 31);
+        double tc = __shfl_sync(0xffffffffu, tv, (base + c) & 31);
         if (on) x += Ui[c] * tc;
       }
+      if (on) w[(size_t)q * NB + comp] = x;
     }
+    return;
+  }
+  ChainRow<NB> A, B;
+  A.t = B.t = 0.0;
+  A.fl = B.fl = 0;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) A.m[c] = B.m[c] = 0.0;
+  const int last = first + len - 1;
+  if (0 < len) chain_fetch(A, w, cG, cflag, (size_t)last, comp);
+  if (1 < len) chain_fetch(B, w, cG, cflag, (size_t)last - 1, comp);
+  double nxt = 0.0;                         // component comp of x_{q+1}
+  auto step = [&](int it, ChainRow<NB>& R) {
+    const bool on = it < len;
+    const int q = last - it;
+    double x = R.t;                          // s_q from the parallel pass
+    double mc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) mc[c] = R.m[c];
+    const int fl = R.fl;
+    if (it + 2 < len) chain_fetch(R, w, cG, cflag, (size_t)q - 2, comp);
+    double nc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) nc[c] = __shfl_sync(0xffffffffu, nxt, (base + c) & 31);
     if (on) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c) x -= mc[c] * nc[c];
+      if (fl & 2) {                          // other in-strip couplings, from memory
+        for (int g = fdp[q] + 1; g < fshi[q]; ++g) {
+          const double* Gr = fv + (size_t)g * B2 + comp * NB;
+          const double* xj = w + (size_t)fpos[g] * NB;
+#pragma unroll
+          for (int c = 0; c < NB; ++c) x -= Gr[c] * xj[c];
+        }
+      }
       w[(size_t)q * NB + comp] = x;
       nxt = x;
-      const int cell = perm[q];
-      double out = x;
-      if ((MODE & 1) && comp == t) out += xT[cell];
-      if ((MODE & 2) && comp == p) out += vP[cell];
-      y[(size_t)cell * NB + comp] = out;
     }
     __syncwarp();
+  };
+  for (int it = 0; it < maxlen; it += 2) {
+    step(it, A);
+    if (it + 1 < maxlen) step(it + 1, B);
   }
+}
+
+// y = x + v + M3 u in cell order: y_cell = w_q (+ x_T at t, + v_P at p)
+template <int NB, int MODE>
+__global__ void k_bilu_assemble(long long N, const int* __restrict__ perm,
+                                const double* __restrict__ w, const double* __restrict__ xT,
+                                const double* __restrict__ vP, int p, int t,
+                                double* __restrict__ y) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= N * NB) return;
+  const long long q = tid / NB;
+  const int comp = (int)(tid - q * NB);
+  const int cell = perm[q];
+  double out = w[tid];
+  if ((MODE & 1) && comp == t) out += xT[cell];
+  if ((MODE & 2) && comp == p) out += vP[cell];
+  y[(size_t)cell * NB + comp] = out;
 }
 
 template <int NB>
@@ -766,10 +783,17 @@ void sweeps(Handle* h, const double* r, const double* xT, const double* vP, doub
       MSS_LAUNCH_CK("k_bilu_bwd_par");
     }
     const long long sw = (s1 - s0 + RPW - 1) / RPW;
-    k_bilu_bwd_chain<NB, MODE><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
-        s0, s1, h->st_first.p, h->st_len.p, h->perm.p, h->fdp.p, h->fshi.p, h->fpos.p, h->fv.p,
-        h->fdinv.p, h->cG.p, h->cflag.p, xT, vP, h->p, h->t, h->w.p, y, bjac ? 0 : 1);
+    k_bilu_bwd_chain<NB><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
+        s0, s1, h->st_first.p, h->st_len.p, h->fdp.p, h->fshi.p, h->fpos.p, h->fv.p, h->fdinv.p,
+        h->cG.p, h->cflag.p, h->w.p, bjac ? 0 : 1);
     MSS_LAUNCH_CK("k_bilu_bwd_chain");
+  }
+  {
+    TraceScope ts(h, TR_BILU_BWD);
+    const long long tot = (long long)h->N * NB;
+    k_bilu_assemble<NB, MODE><<<grid_for(tot, T), T, 0, h->stream>>>(h->N, h->perm.p, h->w.p, xT,
+                                                                     vP, h->p, h->t, y);
+    MSS_LAUNCH_CK("k_bilu_assemble");
   }
 }
 
