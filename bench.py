@@ -46,6 +46,9 @@ def args_():
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-n", type=int, default=2048,
+                    help="grid of the mixed-precision comparison (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     return ap.parse_args()
@@ -54,7 +57,7 @@ def args_():
 def workload_config(a):
     return {"workload": f"cptr3-fgmres{a.restart}-{a.n}x{a.n}-nb6", "grid": [a.n, a.n], "nb": 6,
             "cells": a.n * a.n, "pe": list(PES), "sigma": 2.0, "corr_len": 16, "band": True,
-            "seed": 0, "tol": a.tol, "scheme": "CPTR3 (T AMG, P AMG, multicolour BILU0)",
+            "seed": 0, "tol": a.tol, "scheme": "CPTR3 (T AMG, P AMG, strip-coloured BILU0, strips of 32)",
             "restart": a.restart,
             "l2": "inputs 1.5 GB per system >> 129 MB L2 (no flush needed)"}
 
@@ -264,6 +267,11 @@ def run_ours(a, rank, world, dist):
     out["precond_gbs"] = round(bytes_apply / (apply_ms / max(n_apply, 1) * 1e-3) / 1e9, 1)
     out["precond_alg_bytes"] = bytes_apply
 
+    # the same workload with the mixed-precision preconditioner
+    if not a.no_mixed:
+        out["mixed"] = mixed_leg(a, dev, solver, torch, stream)
+        if a.mixed_n > 0:
+            out["mixed_config"] = mixed_config_leg(a, solver, torch, stream)
     # end to end through the C-ABI from pinned host buffers
     if not a.no_e2e:
         out["e2e"] = e2e(a, sysl, solver, opts, torch)
@@ -271,6 +279,112 @@ def run_ours(a, rank, world, dist):
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, sysl[1], steps=1)
     return out
+
+
+def mixed_leg(a, dev, solver, torch, stream):
+    """Mixed precision (BF16 storage, FP32 sweeps in M^-1; FP64 FGMRES) on the
+    same three systems and tolerance: time per system, iterations, and the
+    unscaled FP64 residual ||b - A x|| / ||b|| the solve reached."""
+    from paper_1912_04385_gb300 import mss
+    opts = mss.options(restart=a.restart, precision="mixed")
+    infos, rels = [], []
+
+    def step(keep):
+        for rp, ci, v, b in dev:
+            solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
+            x, info = solver.solve(b, tol=a.tol, maxit=a.maxit)
+            if info["status"] != 0:
+                raise RuntimeError(f"mixed solve failed: {info}")
+            if keep:
+                infos.append(info)
+                r, bn = solver.residual_norm(rp, ci, v, 6, b, x)
+                rels.append(r / bn)
+
+    for _ in range(max(1, a.warmup)):
+        step(False)
+    torch.cuda.synchronize()
+    solver.trace(True)
+    solver.trace_read(reset=True)
+    ms = 0.0
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for rp, ci, v, b in dev:
+            solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
+            x, info = solver.solve(b, tol=a.tol, maxit=a.maxit)
+            if info["status"] != 0:
+                raise RuntimeError(f"mixed solve failed: {info}")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    tr = solver.trace_read(reset=True)
+    solver.trace(False)
+    step(True)
+    n_apply, apply_ms = tr["apply"]
+    return {"ms_per_system": round(ms / (a.steps * len(dev)), 3),
+            "iters": [i["iters"] for i in infos],
+            "setup_ms_mean": round(float(np.mean([i["setup_ms"] for i in infos])), 3),
+            "solve_ms_mean": round(float(np.mean([i["solve_ms"] for i in infos])), 3),
+            "apply_ms_mean": round(apply_ms / max(n_apply, 1), 4),
+            "rel_res_unscaled": [float(f"{v:.3e}") for v in rels],
+            "storage": "bf16 blocks, fp32 vectors and sweeps, fp64 Krylov"}
+
+
+def mixed_config_leg(a, solver, torch, stream):
+    """The mixed-precision workload: one n x n, nb = 6 system (sigma = 3,
+    Pe = 10), FGMRES to the bench tolerance with the FP64 and with the mixed
+    preconditioner, each timed over the steps; both solutions are compared
+    with an FP64 solve converged to 1e-10 (equal final accuracy check)."""
+    from paper_1912_04385_gb300 import mss, synthetic as sy
+    n = a.mixed_n
+    s = sy.plain_at_scale(n, pe=10.0, seed=0, sigma=3.0)
+    rp = torch.from_numpy(s.row_ptr).cuda()
+    ci = torch.from_numpy(s.col_idx).cuda()
+    v = torch.from_numpy(s.vals.reshape(-1)).cuda()
+    b = torch.from_numpy(s.b).cuda()
+    del s
+    res = {"workload": f"cptr3-fgmres{a.restart}-{n}x{n}-nb6-sigma3-pe10", "cells": n * n}
+    xs = {}
+    for prec in ("fp64", "mixed"):
+        opts = mss.options(restart=a.restart, precision=prec)
+        for _ in range(max(1, min(a.warmup, 2))):
+            solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
+            solver.solve(b, tol=a.tol, maxit=a.maxit)
+        torch.cuda.synchronize()
+        solver.trace(True)
+        solver.trace_read(reset=True)
+        ms, infos = 0.0, []
+        for _ in range(a.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
+            x, info = solver.solve(b, tol=a.tol, maxit=a.maxit)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if info["status"] != 0:
+                raise RuntimeError(f"{prec} solve failed at {n}x{n}: {info}")
+            ms += e0.elapsed_time(e1)
+            infos.append(info)
+        tr = solver.trace_read(reset=True)
+        solver.trace(False)
+        r, bn = solver.residual_norm(rp, ci, v, 6, b, x)
+        n_apply, apply_ms = tr["apply"]
+        xs[prec] = x.clone()
+        res[prec] = {"ms": round(ms / a.steps, 3), "iters": infos[-1]["iters"],
+                     "setup_ms": round(infos[-1]["setup_ms"], 3),
+                     "solve_ms": round(infos[-1]["solve_ms"], 3),
+                     "apply_ms_mean": round(apply_ms / max(n_apply, 1), 4),
+                     "rel_res_unscaled": float(f"{r / bn:.3e}")}
+    # reference solution: FP64 preconditioner, converged to 1e-10
+    solver.setup(rp, ci, v, 6, 0, 1, opts=mss.options(restart=a.restart))
+    xr, ir = solver.solve(b, tol=1e-10, maxit=4 * a.maxit)
+    nr = float(torch.linalg.vector_norm(xr))
+    for prec in ("fp64", "mixed"):
+        res[prec]["rel_err_vs_fp64_1e-10"] = float(
+            f"{float(torch.linalg.vector_norm(xs[prec] - xr)) / nr:.3e}")
+    res["speedup_mixed_over_fp64"] = round(res["fp64"]["ms"] / res["mixed"]["ms"], 3)
+    res["reference_iters"] = ir["iters"]
+    return res
 
 
 def apply_alg_bytes(N, nnzb, nb, solver):

@@ -55,7 +55,7 @@ enum { MSS_STAGE_T_FIRST = 0, MSS_STAGE_P_FIRST = 1 }; /* CPTR3 stage order */
 enum { MSS_BILU0 = 0, MSS_BLOCK_JACOBI = 1 };        /* last stage */
 enum { MSS_MULTICOLOR = 0, MSS_STRIPS = 2 };         /* block ILU(0) ordering */
 enum { MSS_JACOBI = 0, MSS_CHEBYSHEV = 1 };          /* AMG smoother */
-enum { MSS_FP64 = 0 };                               /* arithmetic */
+enum { MSS_FP64 = 0, MSS_MIXED = 1 };                /* preconditioner arithmetic */
 enum { MSS_CGS1 = 0, MSS_CGS2 = 1 };                 /* Arnoldi orthogonalisation */
 
 /* A BSR matrix; the arrays are device memory owned by the caller. */
@@ -89,7 +89,18 @@ typedef struct {
   int32_t amg_max_levels;   /* at most this many levels (25) */
   int32_t interp_max_elems; /* interpolation row truncation, 0 = none (4) */
   int32_t restart;          /* FGMRES restart length m (30) */
-  int32_t precision;        /* MSS_FP64 */
+  int32_t precision;        /* MSS_FP64 (default): every stage in float64.
+                               MSS_MIXED: the preconditioner M^{-1} (Algorithms
+                               1/2) keeps BF16 copies of the AMG operators,
+                               interpolation/restriction and the block ILU(0)
+                               factors, and FP32 copies of the scaled coupling
+                               blocks; its sweeps run in FP32. The scaling, the
+                               outer matvec, Arnoldi, Givens rotations and the
+                               true residual stay float64, so FGMRES (Sec. 5.1,
+                               flexible in the preconditioner) still converges
+                               to the float64 tolerance; the iteration count
+                               may differ from the float64 run. Not in the
+                               paper, which computes in float64 throughout. */
   int32_t ilu_strip;        /* strip length in cells for MSS_STRIPS (32), 1..1024 */
   int32_t orthog;           /* Arnoldi: MSS_CGS1 (default) | MSS_CGS2 */
   int32_t pad_;
@@ -170,7 +181,8 @@ int mss_apply(mss_handle* h, const double* r, double* y);
 /* One stage operator alone, for testing the composition of Eq.
  * multistageprec: which = 0 temperature AMG stage (Eq. CPTR3M1), 1 pressure
  * AMG stage (Eq. CPTRM2 / CPRM1), 2 last stage (block ILU(0) or block
- * Jacobi of Abar). The result is zero outside the stage's unknowns.
+ * Jacobi of Abar). The result is zero outside the stage's unknowns. Always
+ * float64, whatever mss_options.precision (mss_apply follows precision).
  * Errors: NOT_SETUP, INVALID_ARG (stage absent in the scheme). */
 int mss_stage_apply(mss_handle* h, int which, const double* r, double* y);
 

@@ -4,6 +4,10 @@
 // V(nu_pre, nu_post) with damped Jacobi or Chebyshev smoothing from a zero
 // initial guess, restriction R = P^T, prolongation P, and the direct coarse
 // solve applied as a dense matrix-vector product with the explicit inverse.
+// The kernels are templates on the storage type V of the operator values and
+// the compute type C of the vectors: FP64 / FP64 for the plain method, BF16 /
+// FP32 for the mixed-precision form (the set-up always runs in FP64; the
+// BF16 and FP32 copies are packed from it).
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -99,96 +103,103 @@ __global__ void k_dense_from_csr(int n, const int* __restrict__ rp, const int* _
 
 // ---- V-cycle kernels ----------------------------------------------------
 // x = omega D^-1 b (one Jacobi sweep from zero) and r = b - A x
+template <class V, class C>
 __global__ void k_jacobi0_residual(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                   const double* __restrict__ v, const double* __restrict__ dinv,
-                                   const double* __restrict__ b, double omega,
-                                   double* __restrict__ x, double* __restrict__ r) {
+                                   const V* __restrict__ v, const C* __restrict__ dinv,
+                                   const C* __restrict__ b, C omega, C* __restrict__ x,
+                                   C* __restrict__ r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
+  C s = 0;
   for (int k = rp[i]; k < rp[i + 1]; ++k) {
     int j = ci[k];
-    s += v[k] * (omega * dinv[j] * b[j]);
+    s += cvt<C>(v[k]) * (omega * dinv[j] * b[j]);
   }
   x[i] = omega * dinv[i] * b[i];
   r[i] = b[i] - s;
 }
 
 // x_out = x_in + omega D^-1 (b - A x_in)
+template <class V, class C>
 __global__ void k_jacobi(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                         const double* __restrict__ v, const double* __restrict__ dinv,
-                         const double* __restrict__ b, double omega,
-                         const double* __restrict__ xin, double* __restrict__ xout) {
+                         const V* __restrict__ v, const C* __restrict__ dinv,
+                         const C* __restrict__ b, C omega, const C* __restrict__ xin,
+                         C* __restrict__ xout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * xin[ci[k]];
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * xin[ci[k]];
   xout[i] = xin[i] + omega * (dinv[i] * (b[i] - s));
 }
 
 // Chebyshev step: r = b - A x_in; d = c1 d + c2 D^-1 r; x_out = x_in + d
+template <class V, class C>
 __global__ void k_cheb(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                       const double* __restrict__ v, const double* __restrict__ dinv,
-                       const double* __restrict__ b, double c1, double c2,
-                       const double* __restrict__ xin, double* __restrict__ d,
-                       double* __restrict__ xout) {
+                       const V* __restrict__ v, const C* __restrict__ dinv,
+                       const C* __restrict__ b, C c1, C c2, const C* __restrict__ xin,
+                       C* __restrict__ d, C* __restrict__ xout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * xin[ci[k]];
-  double di = c1 * d[i] + c2 * (dinv[i] * (b[i] - s));
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * xin[ci[k]];
+  C di = c1 * d[i] + c2 * (dinv[i] * (b[i] - s));
   d[i] = di;
   xout[i] = xin[i] + di;
 }
 
+template <class V, class C>
 __global__ void k_residual(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                           const double* __restrict__ v, const double* __restrict__ b,
-                           const double* __restrict__ x, double* __restrict__ r) {
+                           const V* __restrict__ v, const C* __restrict__ b,
+                           const C* __restrict__ x, C* __restrict__ r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * x[ci[k]];
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * x[ci[k]];
   r[i] = b[i] - s;
 }
 
+template <class V, class C>
 __global__ void k_csr_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                           const double* __restrict__ v, const double* __restrict__ x,
-                           double* __restrict__ y) {
+                           const V* __restrict__ v, const C* __restrict__ x,
+                           C* __restrict__ y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * x[ci[k]];
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * x[ci[k]];
   y[i] = s;
 }
 
 // xout = x + P xc
+template <class V, class C>
 __global__ void k_prolong(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                          const double* __restrict__ v, const double* __restrict__ xc,
-                          const double* __restrict__ x, double* __restrict__ xout) {
+                          const V* __restrict__ v, const C* __restrict__ xc,
+                          const C* __restrict__ x, C* __restrict__ xout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * xc[ci[k]];
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * xc[ci[k]];
   xout[i] = x[i] + s;
 }
 
 // x = Ainv b, one warp per row
-__global__ void k_dense_gemv(int n, const double* __restrict__ A, const double* __restrict__ b,
-                             double* __restrict__ x) {
+template <class C>
+__global__ void k_dense_gemv(int n, const C* __restrict__ A, const C* __restrict__ b,
+                             C* __restrict__ x) {
   int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (row >= n) return;
-  const double* a = A + (size_t)row * n;
-  double s = 0.0;
+  const C* a = A + (size_t)row * n;
+  C s = 0;
   for (int j = lane; j < n; j += 32) s += a[j] * b[j];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = s;
 }
 
+template <class C>
 __global__ void k_gather_var(int N, int nb, const double* __restrict__ v, int var,
-                             double* __restrict__ out) {
+                             C* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) out[i] = v[(size_t)i * nb + var];
+  if (i < N) out[i] = (C)v[(size_t)i * nb + var];
 }
 
 __global__ void k_scatter_var_zero(int N, int nb, const double* __restrict__ s, int var,
@@ -200,38 +211,80 @@ __global__ void k_scatter_var_zero(int N, int nb, const double* __restrict__ s, 
 }
 
 // out_i = r[i*nb + var] - sum_j vals_ij x_j over the block pattern
+template <class C>
 __global__ void k_pattern_sub(int N, int nb, const int* __restrict__ rp,
-                              const int* __restrict__ ci, const double* __restrict__ vals,
-                              const double* __restrict__ x, const double* __restrict__ r, int var,
-                              double* __restrict__ out) {
+                              const int* __restrict__ ci, const C* __restrict__ vals,
+                              const C* __restrict__ x, const double* __restrict__ r, int var,
+                              C* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double s = 0.0;
+  C s = 0;
   for (int k = rp[i]; k < rp[i + 1]; ++k) s += vals[k] * x[ci[k]];
-  out[i] = r[(size_t)i * nb + var] - s;
+  out[i] = (C)r[(size_t)i * nb + var] - s;
+}
+
+__global__ void k_to_float(long long n, const double* __restrict__ in, float* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) out[i] = (float)in[i];
+}
+
+// round to nearest FP32, then to nearest BF16
+__global__ void k_to_bf16(long long n, const double* __restrict__ in,
+                          __nv_bfloat16* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) out[i] = __float2bfloat16_rn((float)in[i]);
 }
 
 constexpr int VT = 256;
 
+// pointers of one level for one precision
+template <class V, class C>
+struct LV {
+  int n, nc;
+  const int *rp, *ci, *prp, *pci, *rrp, *rci;
+  const V *v, *pv, *rv;
+  const C* dinv;
+  C *x2, *r, *d;
+  double lam;
+};
+
+LV<double, double> view(Level& L, double*) {
+  return {L.n, L.nc, L.rp.p, L.ci.p, L.prp.p, L.pci.p, L.rrp.p, L.rci.p,
+          L.v.p, L.pv.p, L.rv.p, L.dinv.p, L.x2.p, L.r.p, L.d.p, L.lam};
+}
+LV<__nv_bfloat16, float> view(Level& L, float*) {
+  return {L.n, L.nc, L.rp.p, L.ci.p, L.prp.p, L.pci.p, L.rrp.p, L.rci.p,
+          L.vh.p, L.pvh.p, L.rvh.p, L.dinvf.p, L.x2f.p, L.rf.p, L.df.p, L.lam};
+}
+double* level_b(Level& L, double*) { return L.b.p; }
+float* level_b(Level& L, float*) { return L.bf.p; }
+double* level_x(Level& L, double*) { return L.x.p; }
+float* level_x(Level& L, float*) { return L.xf.p; }
+const double* coarse_inv(Hierarchy& H, double*) { return H.coarse_inv.p; }
+const float* coarse_inv(Hierarchy& H, float*) { return H.coarse_invf.p; }
+
+template <class V, class C>
 struct Sweeper {
   Handle* h;
-  Level& L;
+  const LV<V, C>& L;
   const mss_options& o;
   // one smoothing application on (b, x): writes the result to xout; xin and
   // xout must differ
-  void jacobi(const double* b, const double* xin, double* xout) {
-    k_jacobi<<<grid_for(L.n, VT), VT, 0, h->stream>>>(L.n, L.rp.p, L.ci.p, L.v.p, L.dinv.p, b,
-                                                      o.jacobi_omega, xin, xout);
+  void jacobi(const C* b, const C* xin, C* xout) {
+    k_jacobi<V, C><<<grid_for(L.n, VT), VT, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.dinv, b,
+                                                            (C)o.jacobi_omega, xin, xout);
     MSS_LAUNCH_CK("k_jacobi");
   }
   // Chebyshev polynomial of degree o.cheb_degree; ping-pongs between x and
   // alt, returns the buffer holding the result
-  double* cheb(const double* b, double* x, double* alt) {
+  C* cheb(const C* b, C* x, C* alt) {
     double hi = o.cheb_hi_factor * L.lam, lo = L.lam / o.cheb_lo_ratio;
     double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
     double sigma = theta / delta, rho = 1.0 / sigma;
-    double* cur = x;
-    double* nxt = alt;
+    C* cur = x;
+    C* nxt = alt;
     for (int k = 1; k <= o.cheb_degree; ++k) {
       double c1, c2;
       if (k == 1) {
@@ -243,10 +296,10 @@ struct Sweeper {
         c2 = 2.0 * rn / delta;
         rho = rn;
       }
-      k_cheb<<<grid_for(L.n, VT), VT, 0, h->stream>>>(L.n, L.rp.p, L.ci.p, L.v.p, L.dinv.p, b, c1,
-                                                      c2, cur, L.d.p, nxt);
+      k_cheb<V, C><<<grid_for(L.n, VT), VT, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.dinv, b,
+                                                            (C)c1, (C)c2, cur, L.d, nxt);
       MSS_LAUNCH_CK("k_cheb");
-      double* t = cur;
+      C* t = cur;
       cur = nxt;
       nxt = t;
     }
@@ -254,48 +307,51 @@ struct Sweeper {
   }
 };
 
-void vcycle_level(Handle* h, Hierarchy& H, int l, const double* b, double* out) {
-  Level& L = H.lev[l];
+template <class V, class C>
+void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out) {
+  Level& Lev = H.lev[l];
+  const LV<V, C> L = view(Lev, (C*)nullptr);
   const mss_options& o = h->opt;
   const int n = L.n;
   if (l == (int)H.lev.size() - 1) {
-    k_dense_gemv<<<grid_for((long long)n * 32, 256), 256, 0, h->stream>>>(n, H.coarse_inv.p, b,
-                                                                          out);
+    k_dense_gemv<C><<<grid_for((long long)n * 32, 256), 256, 0, h->stream>>>(
+        n, coarse_inv(H, (C*)nullptr), b, out);
     MSS_LAUNCH_CK("k_dense_gemv");
     return;
   }
-  Sweeper sw{h, L, o};
-  Level& C = H.lev[l + 1];
+  Sweeper<V, C> sw{h, L, o};
+  Level& Cl = H.lev[l + 1];
+  C* cb = level_b(Cl, (C*)nullptr);
+  C* cx = level_x(Cl, (C*)nullptr);
   // ---- pre-smoothing from zero, then the residual
-  double* cur = out;
-  double* alt = L.x2.p;
+  C* cur = out;
+  C* alt = L.x2;
   if (o.smoother == MSS_JACOBI && o.nu_pre >= 1) {
-    k_jacobi0_residual<<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.rp.p, L.ci.p, L.v.p, L.dinv.p,
-                                                              b, o.jacobi_omega, out, L.r.p);
+    k_jacobi0_residual<V, C><<<grid_for(n, VT), VT, 0, h->stream>>>(
+        n, L.rp, L.ci, L.v, L.dinv, b, (C)o.jacobi_omega, out, L.r);
     MSS_LAUNCH_CK("k_jacobi0_residual");
     for (int s = 1; s < o.nu_pre; ++s) {
       sw.jacobi(b, cur, alt);
       std::swap(cur, alt);
     }
     if (o.nu_pre > 1) {
-      k_residual<<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.rp.p, L.ci.p, L.v.p, b, cur, L.r.p);
+      k_residual<V, C><<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
       MSS_LAUNCH_CK("k_residual");
     }
   } else {
-    fill_double(h, cur, 0.0, n);
+    MSS_CK(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)n, h->stream));
     for (int s = 0; s < o.nu_pre; ++s) {
-      double* res = sw.cheb(b, cur, alt);
+      C* res = sw.cheb(b, cur, alt);
       if (res != cur) std::swap(cur, alt);
     }
-    k_residual<<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.rp.p, L.ci.p, L.v.p, b, cur, L.r.p);
+    k_residual<V, C><<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
     MSS_LAUNCH_CK("k_residual");
   }
   // ---- restriction and the coarse correction
-  k_csr_spmv<<<grid_for(L.nc, VT), VT, 0, h->stream>>>(L.nc, L.rrp.p, L.rci.p, L.rv.p, L.r.p,
-                                                       C.b.p);
+  k_csr_spmv<V, C><<<grid_for(L.nc, VT), VT, 0, h->stream>>>(L.nc, L.rrp, L.rci, L.rv, L.r, cb);
   MSS_LAUNCH_CK("k_csr_spmv(R)");
-  vcycle_level(h, H, l + 1, C.b.p, C.x.p);
-  k_prolong<<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.prp.p, L.pci.p, L.pv.p, C.x.p, cur, alt);
+  vcycle_level<V, C>(h, H, l + 1, cb, cx);
+  k_prolong<V, C><<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.prp, L.pci, L.pv, cx, cur, alt);
   MSS_LAUNCH_CK("k_prolong");
   std::swap(cur, alt);
   // ---- post-smoothing
@@ -304,11 +360,16 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const double* b, double* out) 
       sw.jacobi(b, cur, alt);
       std::swap(cur, alt);
     } else {
-      double* res = sw.cheb(b, cur, alt);
+      C* res = sw.cheb(b, cur, alt);
       if (res != cur) std::swap(cur, alt);
     }
   }
-  if (cur != out) copy_dev(h, out, cur, sizeof(double) * (size_t)n);
+  if (cur != out) copy_dev(h, out, cur, sizeof(C) * (size_t)n);
+}
+
+unsigned stride_grid(long long n) {
+  unsigned g = grid_for(n, 256);
+  return g > 8192u ? 8192u : g;
 }
 
 }  // namespace
@@ -351,13 +412,60 @@ void coarse_inverse(Handle* h, Hierarchy& H) {
   MSS_LAUNCH_CK("k_gj_extract");
 }
 
+void to_float(Handle* h, const double* in, float* out, long long n) {
+  if (n <= 0) return;
+  k_to_float<<<stride_grid(n), 256, 0, h->stream>>>(n, in, out);
+  MSS_LAUNCH_CK("k_to_float");
+}
+
+void to_bf16(Handle* h, const double* in, __nv_bfloat16* out, long long n) {
+  if (n <= 0) return;
+  k_to_bf16<<<stride_grid(n), 256, 0, h->stream>>>(n, in, out);
+  MSS_LAUNCH_CK("k_to_bf16");
+}
+
+// BF16 copies of A, P, R values, FP32 D^-1, FP32 vectors, FP32 coarse inverse
+void pack_hierarchy_mixed(Handle* h, Hierarchy& H) {
+  for (size_t l = 0; l < H.lev.size(); ++l) {
+    Level& L = H.lev[l];
+    const bool last = l + 1 == H.lev.size();
+    L.vh.reset(h, L.nnz);
+    to_bf16(h, L.v.p, L.vh.p, L.nnz);
+    L.dinvf.reset(h, L.n);
+    to_float(h, L.dinv.p, L.dinvf.p, L.n);
+    if (!last) {
+      L.pvh.reset(h, L.nnzP);
+      to_bf16(h, L.pv.p, L.pvh.p, L.nnzP);
+      L.rvh.reset(h, L.nnzP);
+      to_bf16(h, L.rv.p, L.rvh.p, L.nnzP);
+    }
+    L.bf.reset(h, L.n);
+    L.xf.reset(h, L.n);
+    L.x2f.reset(h, L.n);
+    L.rf.reset(h, L.n);
+    L.df.reset(h, L.n);
+  }
+  H.coarse_invf.reset(h, (size_t)H.nc * H.nc);
+  to_float(h, H.coarse_inv.p, H.coarse_invf.p, (long long)H.nc * H.nc);
+}
+
 void vcycle(Handle* h, Hierarchy& H, const double* b, double* x) {
   TraceScope ts(h, TR_VCYCLE);
-  vcycle_level(h, H, 0, b, x);
+  vcycle_level<double, double>(h, H, 0, b, x);
+}
+
+void vcycle_mixed(Handle* h, Hierarchy& H, const float* b, float* x) {
+  TraceScope ts(h, TR_VCYCLE);
+  vcycle_level<__nv_bfloat16, float>(h, H, 0, b, x);
 }
 
 void gather_var(Handle* h, const double* v, int var, double* out) {
-  k_gather_var<<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, v, var, out);
+  k_gather_var<double><<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, v, var, out);
+  MSS_LAUNCH_CK("k_gather_var");
+}
+
+void gather_var(Handle* h, const double* v, int var, float* out) {
+  k_gather_var<float><<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, v, var, out);
   MSS_LAUNCH_CK("k_gather_var");
 }
 
@@ -369,8 +477,15 @@ void scatter_var_zero(Handle* h, const double* s, int var, double* out) {
 
 void csr_block_pattern_spmv_sub(Handle* h, const double* vals, const double* x, const double* r,
                                 int var, double* out) {
-  k_pattern_sub<<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, h->rp.p, h->ci.p, vals,
-                                                            x, r, var, out);
+  k_pattern_sub<double><<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, h->rp.p,
+                                                                    h->ci.p, vals, x, r, var, out);
+  MSS_LAUNCH_CK("k_pattern_sub");
+}
+
+void csr_block_pattern_spmv_sub(Handle* h, const float* vals, const float* x, const double* r,
+                                int var, float* out) {
+  k_pattern_sub<float><<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, h->rp.p, h->ci.p,
+                                                                   vals, x, r, var, out);
   MSS_LAUNCH_CK("k_pattern_sub");
 }
 

@@ -49,7 +49,7 @@ void check_options(const mss_options& o) {
   if (o.amg_max_levels < 1 || o.amg_max_levels > 25) bad("amg_max_levels");
   if (o.interp_max_elems < 0) bad("interp_max_elems");
   if (o.restart < 1 || o.restart > 120) bad("restart (1..120)");
-  if (o.precision != MSS_FP64) bad("precision");
+  if (o.precision != MSS_FP64 && o.precision != MSS_MIXED) bad("precision");
   if (!(o.amg_theta > 0.0 && o.amg_theta <= 1.0)) bad("amg_theta");
   if (!(o.jacobi_omega > 0.0 && o.jacobi_omega < 2.0)) bad("jacobi_omega");
   if (!(o.cheb_lo_ratio > 1.0) || !(o.cheb_hi_factor > 0.0)) bad("Chebyshev interval");
@@ -68,6 +68,9 @@ void release_setup(Handle& H) {
   H.fslo.release(); H.fshi.release(); H.cL.release(); H.cG.release(); H.cflag.release();
   H.fv.release(); H.fdinv.release(); H.fcs.release();
   H.rT.release(); H.xT.release(); H.zP.release(); H.vP.release(); H.w.release();
+  H.fvh.release(); H.fdinvh.release(); H.cLh.release(); H.cGh.release();
+  H.fcsf.release(); H.aptf.release(); H.atpf.release();
+  H.rTf.release(); H.xTf.release(); H.zPf.release(); H.vPf.release(); H.wf.release();
   H.cstart.clear();
   H.ncol = 0;
 }
@@ -132,6 +135,23 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
   H.zP.reset(h, N);
   H.vP.reset(h, N);
   H.w.reset(h, (size_t)N * nb);
+  if (o.precision == MSS_MIXED) {
+    // reduced-precision copies of everything the preconditioner reads
+    TraceScope ts(h, TR_SETUP_BILU);
+    if (H.amgP.present()) pack_hierarchy_mixed(h, H.amgP);
+    if (H.amgT.present()) pack_hierarchy_mixed(h, H.amgT);
+    if (o.scheme == MSS_CPTR3) {
+      H.aptf.reset(h, nnzb);
+      to_float(h, H.apt.p, H.aptf.p, nnzb);
+      H.atpf.reset(h, nnzb);
+      to_float(h, H.atp.p, H.atpf.p, nnzb);
+    }
+    pack_last_stage_mixed(h);
+    H.rTf.reset(h, N);
+    H.xTf.reset(h, N);
+    H.zPf.reset(h, N);
+    H.vPf.reset(h, N);
+  }
   MSS_CK(cudaStreamSynchronize(H.stream));
   H.J = *J;
   H.ready = true;
@@ -272,7 +292,7 @@ int mss_stage_apply(mss_handle* hh, int which, const double* r, double* y) {
     need_ready(H);
     if (!r || !y || r == y) fail(MSS_ERR_INVALID_ARG, "r and y must be distinct");
     if (which == 2) {
-      last_stage_apply(&H, r, nullptr, nullptr, y);
+      last_stage_apply(&H, r, (const double*)nullptr, (const double*)nullptr, y);
       return;
     }
     Hierarchy& A = pick(H, which);

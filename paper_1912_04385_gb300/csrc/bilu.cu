@@ -297,13 +297,13 @@ __device__ __forceinline__ int warp_max(int v) {
 //
 // forward, parallel: w_q = u_q - sum_{other-strip lower} L_qk w_k, with
 // u = r - Abar[:,t] x_T - Abar[:,p] v_P (MODE bit 1: x_T term, bit 2: v_P)
-template <int NB, int MODE>
+template <int NB, int MODE, class V, class C>
 __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
                                const int* __restrict__ frp, const int* __restrict__ fslo,
                                const int* __restrict__ fpos, const int* __restrict__ fcell,
-                               const double* __restrict__ fv, const double* __restrict__ fcs,
-                               const double* __restrict__ r, const double* __restrict__ xT,
-                               const double* __restrict__ vP, double* __restrict__ w, int lower) {
+                               const V* __restrict__ fv, const C* __restrict__ fcs,
+                               const double* __restrict__ r, const C* __restrict__ xT,
+                               const C* __restrict__ vP, C* __restrict__ w, int lower) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
@@ -313,12 +313,12 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
   if (sub >= RPW || qq >= q1) return;
   const int q = (int)qq;
   const int cell = perm[q];
-  double acc = r[(size_t)cell * NB + comp];
+  C acc = (C)r[(size_t)cell * NB + comp];
   const int b = frp[q], e = frp[q + 1];
   if (MODE) {
     for (int f = b; f < e; ++f) {
       const int j = fcell[f];
-      const double* cs = fcs + (size_t)f * 2 * NB;
+      const C* cs = fcs + (size_t)f * 2 * NB;
       if (MODE & 1) acc -= cs[comp] * xT[j];
       if (MODE & 2) acc -= cs[NB + comp] * vP[j];
     }
@@ -326,10 +326,10 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
   if (lower) {
     const int d = fslo[q];
     for (int f = b; f < d; ++f) {
-      const double* Lr = fv + (size_t)f * B2 + comp * NB;
-      const double* wk = w + (size_t)fpos[f] * NB;
+      const V* Lr = fv + (size_t)f * B2 + comp * NB;
+      const C* wk = w + (size_t)fpos[f] * NB;
 #pragma unroll
-      for (int c = 0; c < NB; ++c) acc -= Lr[c] * wk[c];
+      for (int c = 0; c < NB; ++c) acc -= cvt<C>(Lr[c]) * wk[c];
     }
   }
   w[(size_t)q * NB + comp] = acc;
@@ -341,31 +341,31 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
 // two steps ahead into two alternating register buffers (the loop is unrolled
 // by two), so a fetch has two steps to land; the addresses depend only on the
 // position.
-template <int NB>
+template <int NB, class C>
 struct ChainRow {
-  double t;
-  double m[NB];
+  C t;
+  C m[NB];
   int fl;
 };
 
-template <int NB>
-__device__ __forceinline__ void chain_fetch(ChainRow<NB>& b, const double* __restrict__ w,
-                                            const double* __restrict__ cm,
+template <int NB, class V, class C>
+__device__ __forceinline__ void chain_fetch(ChainRow<NB, C>& b, const C* __restrict__ w,
+                                            const V* __restrict__ cm,
                                             const int* __restrict__ cflag, size_t q, int comp) {
   constexpr int B2 = NB * NB;
   b.t = w[q * NB + comp];
   b.fl = cflag[q];
-  const double* src = cm + q * B2 + comp * NB;
+  const V* src = cm + q * B2 + comp * NB;
 #pragma unroll
-  for (int c = 0; c < NB; ++c) b.m[c] = src[c];
+  for (int c = 0; c < NB; ++c) b.m[c] = cvt<C>(src[c]);
 }
 
-template <int NB>
+template <int NB, class V, class C>
 __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_first,
                                  const int* __restrict__ st_len, const int* __restrict__ fslo,
                                  const int* __restrict__ fdp, const int* __restrict__ fpos,
-                                 const double* __restrict__ fv, const double* __restrict__ cL,
-                                 const int* __restrict__ cflag, double* __restrict__ w) {
+                                 const V* __restrict__ fv, const V* __restrict__ cL,
+                                 const int* __restrict__ cflag, C* __restrict__ w) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
@@ -377,24 +377,24 @@ __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_firs
   const int len = active ? st_len[kk] : 0;
   const int maxlen = warp_max(len);
   const int base = sub * NB;
-  ChainRow<NB> A, B;
-  A.t = B.t = 0.0;
+  ChainRow<NB, C> A, B;
+  A.t = B.t = 0;
   A.fl = B.fl = 0;
 #pragma unroll
-  for (int c = 0; c < NB; ++c) A.m[c] = B.m[c] = 0.0;
+  for (int c = 0; c < NB; ++c) A.m[c] = B.m[c] = 0;
   if (0 < len) chain_fetch(A, w, cL, cflag, (size_t)first, comp);
   if (1 < len) chain_fetch(B, w, cL, cflag, (size_t)first + 1, comp);
-  double prev = 0.0;                        // component comp of w_{q-1}
-  auto step = [&](int it, ChainRow<NB>& R) {
+  C prev = 0;                               // component comp of w_{q-1}
+  auto step = [&](int it, ChainRow<NB, C>& R) {
     const bool on = it < len;
     const int q = first + it;
-    double acc = R.t;
-    double mc[NB];
+    C acc = R.t;
+    C mc[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) mc[c] = R.m[c];
     const int fl = R.fl;
     if (it + 2 < len) chain_fetch(R, w, cL, cflag, (size_t)q + 2, comp);
-    double pc[NB];
+    C pc[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) pc[c] = __shfl_sync(0xffffffffu, prev, (base + c) & 31);
     if (on) {
@@ -402,10 +402,10 @@ __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_firs
       for (int c = 0; c < NB; ++c) acc -= mc[c] * pc[c];
       if (fl & 1) {                          // other in-strip couplings, from memory
         for (int f = fslo[q]; f < fdp[q]; ++f) {
-          const double* Lr = fv + (size_t)f * B2 + comp * NB;
-          const double* wk = w + (size_t)fpos[f] * NB;
+          const V* Lr = fv + (size_t)f * B2 + comp * NB;
+          const C* wk = w + (size_t)fpos[f] * NB;
 #pragma unroll
-          for (int c = 0; c < NB; ++c) acc -= Lr[c] * wk[c];
+          for (int c = 0; c < NB; ++c) acc -= cvt<C>(Lr[c]) * wk[c];
         }
       }
       w[(size_t)q * NB + comp] = acc;
@@ -477,11 +477,11 @@ __global__ void k_chain_blocks(long long N, const int* __restrict__ fslo,
 
 // backward, parallel: s_q = U_qq^{-1} (w_q - sum_{other-strip upper} U_qj x_j)
 // (later colours, final); stored back into w
-template <int NB>
+template <int NB, class V, class C>
 __global__ void k_bilu_bwd_par(int q0, int q1, const int* __restrict__ frp,
                                const int* __restrict__ fshi, const int* __restrict__ fpos,
-                               const double* __restrict__ fv, const double* __restrict__ fdinv,
-                               double* __restrict__ w) {
+                               const V* __restrict__ fv, const V* __restrict__ fdinv,
+                               C* __restrict__ w) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
@@ -490,23 +490,23 @@ __global__ void k_bilu_bwd_par(int q0, int q1, const int* __restrict__ frp,
   const long long qq = q0 + warp * RPW + sub;
   const bool on = sub < RPW && qq < q1;
   const int q = on ? (int)qq : q0;
-  double acc = 0.0;
+  C acc = 0;
   if (on) {
     acc = w[(size_t)q * NB + comp];
     for (int g = fshi[q]; g < frp[q + 1]; ++g) {
-      const double* Ur = fv + (size_t)g * B2 + comp * NB;
-      const double* xj = w + (size_t)fpos[g] * NB;
+      const V* Ur = fv + (size_t)g * B2 + comp * NB;
+      const C* xj = w + (size_t)fpos[g] * NB;
 #pragma unroll
-      for (int c = 0; c < NB; ++c) acc -= Ur[c] * xj[c];
+      for (int c = 0; c < NB; ++c) acc -= cvt<C>(Ur[c]) * xj[c];
     }
   }
   const int base = sub * NB;
-  const double* Ui = fdinv + (size_t)q * B2 + comp * NB;
-  double s = 0.0;
+  const V* Ui = fdinv + (size_t)q * B2 + comp * NB;
+  C s = 0;
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
-    double tc = __shfl_sync(0xffffffffu, acc, (base + c) & 31);
-    if (on) s += Ui[c] * tc;
+    C tc = __shfl_sync(0xffffffffu, acc, (base + c) & 31);
+    if (on) s += cvt<C>(Ui[c]) * tc;
   }
   if (on) w[(size_t)q * NB + comp] = s;
 }
@@ -516,13 +516,13 @@ __global__ void k_bilu_bwd_par(int q0, int q1, const int* __restrict__ frp,
 // fetched two steps ahead as in the forward chain); x_q goes back into w.
 // Block Jacobi (upper = 0): x_q = D_qq^{-1} u_q. The output y is assembled
 // afterwards by k_bilu_assemble.
-template <int NB>
+template <int NB, class V, class C>
 __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_first,
                                  const int* __restrict__ st_len, const int* __restrict__ fdp,
                                  const int* __restrict__ fshi, const int* __restrict__ fpos,
-                                 const double* __restrict__ fv, const double* __restrict__ fdinv,
-                                 const double* __restrict__ cG, const int* __restrict__ cflag,
-                                 double* __restrict__ w, int upper) {
+                                 const V* __restrict__ fv, const V* __restrict__ fdinv,
+                                 const V* __restrict__ cG, const int* __restrict__ cflag,
+                                 C* __restrict__ w, int upper) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
@@ -538,37 +538,37 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
     for (int it = 0; it < maxlen; ++it) {
       const bool on = it < len;
       const int q = on ? first + it : 0;
-      const double tv = on ? w[(size_t)q * NB + comp] : 0.0;
-      const double* Ui = fdinv + (size_t)q * B2 + comp * NB;
-      double x = 0.0;
+      const C tv = on ? w[(size_t)q * NB + comp] : (C)0;
+      const V* Ui = fdinv + (size_t)q * B2 + comp * NB;
+      C x = 0;
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        double tc = __shfl_sync(0xffffffffu, tv, (base + c) & 31);
-        if (on) x += Ui[c] * tc;
+        C tc = __shfl_sync(0xffffffffu, tv, (base + c) & 31);
+        if (on) x += cvt<C>(Ui[c]) * tc;
       }
       if (on) w[(size_t)q * NB + comp] = x;
     }
     return;
   }
-  ChainRow<NB> A, B;
-  A.t = B.t = 0.0;
+  ChainRow<NB, C> A, B;
+  A.t = B.t = 0;
   A.fl = B.fl = 0;
 #pragma unroll
-  for (int c = 0; c < NB; ++c) A.m[c] = B.m[c] = 0.0;
+  for (int c = 0; c < NB; ++c) A.m[c] = B.m[c] = 0;
   const int last = first + len - 1;
   if (0 < len) chain_fetch(A, w, cG, cflag, (size_t)last, comp);
   if (1 < len) chain_fetch(B, w, cG, cflag, (size_t)last - 1, comp);
-  double nxt = 0.0;                         // component comp of x_{q+1}
-  auto step = [&](int it, ChainRow<NB>& R) {
+  C nxt = 0;                                // component comp of x_{q+1}
+  auto step = [&](int it, ChainRow<NB, C>& R) {
     const bool on = it < len;
     const int q = last - it;
-    double x = R.t;                          // s_q from the parallel pass
-    double mc[NB];
+    C x = R.t;                               // s_q from the parallel pass
+    C mc[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) mc[c] = R.m[c];
     const int fl = R.fl;
     if (it + 2 < len) chain_fetch(R, w, cG, cflag, (size_t)q - 2, comp);
-    double nc[NB];
+    C nc[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) nc[c] = __shfl_sync(0xffffffffu, nxt, (base + c) & 31);
     if (on) {
@@ -576,10 +576,10 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
       for (int c = 0; c < NB; ++c) x -= mc[c] * nc[c];
       if (fl & 2) {                          // other in-strip couplings, from memory
         for (int g = fdp[q] + 1; g < fshi[q]; ++g) {
-          const double* Gr = fv + (size_t)g * B2 + comp * NB;
-          const double* xj = w + (size_t)fpos[g] * NB;
+          const V* Gr = fv + (size_t)g * B2 + comp * NB;
+          const C* xj = w + (size_t)fpos[g] * NB;
 #pragma unroll
-          for (int c = 0; c < NB; ++c) x -= Gr[c] * xj[c];
+          for (int c = 0; c < NB; ++c) x -= cvt<C>(Gr[c]) * xj[c];
         }
       }
       w[(size_t)q * NB + comp] = x;
@@ -594,20 +594,20 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
 }
 
 // y = x + v + M3 u in cell order: y_cell = w_q (+ x_T at t, + v_P at p)
-template <int NB, int MODE>
+template <int NB, int MODE, class C>
 __global__ void k_bilu_assemble(long long N, const int* __restrict__ perm,
-                                const double* __restrict__ w, const double* __restrict__ xT,
-                                const double* __restrict__ vP, int p, int t,
+                                const C* __restrict__ w, const C* __restrict__ xT,
+                                const C* __restrict__ vP, int p, int t,
                                 double* __restrict__ y) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= N * NB) return;
   const long long q = tid / NB;
   const int comp = (int)(tid - q * NB);
   const int cell = perm[q];
-  double out = w[tid];
+  C out = w[tid];
   if ((MODE & 1) && comp == t) out += xT[cell];
   if ((MODE & 2) && comp == p) out += vP[cell];
-  y[(size_t)cell * NB + comp] = out;
+  y[(size_t)cell * NB + comp] = (double)out;
 }
 
 template <int NB>
@@ -746,8 +746,25 @@ void bilu_setup_nb(Handle* h) {
   }
 }
 
-template <int NB, int MODE>
-void sweeps(Handle* h, const double* r, const double* xT, const double* vP, double* y) {
+// Factor data in one storage type V with vectors in compute type C: FP64 / FP64,
+// or BF16 blocks with FP32 vectors in the mixed form.
+template <class V, class C>
+struct Factors {
+  const V *fv, *fdinv, *cL, *cG;
+  const C* fcs;
+  C* w;
+};
+
+Factors<double, double> factors(Handle* h, const double*) {
+  return {h->fv.p, h->fdinv.p, h->cL.p, h->cG.p, h->fcs.p, h->w.p};
+}
+Factors<__nv_bfloat16, float> factors(Handle* h, const float*) {
+  return {h->fvh.p, h->fdinvh.p, h->cLh.p, h->cGh.p, h->fcsf.p, h->wf.p};
+}
+
+template <int NB, int MODE, class V, class C>
+void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, const C* vP,
+            double* y) {
   constexpr int RPW = 32 / NB;
   const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
   // strips longer than one cell carry in-strip couplings (chain passes)
@@ -759,15 +776,15 @@ void sweeps(Handle* h, const double* r, const double* xT, const double* vP, doub
     if (q1 <= q0) continue;
     TraceScope ts(h, TR_BILU_FWD);
     const long long rw = (q1 - q0 + RPW - 1) / RPW;
-    k_bilu_fwd_par<NB, MODE><<<grid_for(rw * 32, T), T, 0, h->stream>>>(
-        q0, q1, h->perm.p, h->frp.p, h->fslo.p, h->fpos.p, h->fcell.p, h->fv.p, h->fcs.p, r, xT,
-        vP, h->w.p, bjac ? 0 : 1);
+    k_bilu_fwd_par<NB, MODE, V, C><<<grid_for(rw * 32, T), T, 0, h->stream>>>(
+        q0, q1, h->perm.p, h->frp.p, h->fslo.p, h->fpos.p, h->fcell.p, F.fv, F.fcs, r, xT, vP,
+        F.w, bjac ? 0 : 1);
     MSS_LAUNCH_CK("k_bilu_fwd_par");
     if (chains) {
       const long long sw = (s1 - s0 + RPW - 1) / RPW;
-      k_bilu_fwd_chain<NB><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
-          s0, s1, h->st_first.p, h->st_len.p, h->fslo.p, h->fdp.p, h->fpos.p, h->fv.p, h->cL.p,
-          h->cflag.p, h->w.p);
+      k_bilu_fwd_chain<NB, V, C><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
+          s0, s1, h->st_first.p, h->st_len.p, h->fslo.p, h->fdp.p, h->fpos.p, F.fv, F.cL,
+          h->cflag.p, F.w);
       MSS_LAUNCH_CK("k_bilu_fwd_chain");
     }
   }
@@ -778,33 +795,34 @@ void sweeps(Handle* h, const double* r, const double* xT, const double* vP, doub
     TraceScope ts(h, TR_BILU_BWD);
     if (!bjac) {
       const long long rw = (q1 - q0 + RPW - 1) / RPW;
-      k_bilu_bwd_par<NB><<<grid_for(rw * 32, T), T, 0, h->stream>>>(
-          q0, q1, h->frp.p, h->fshi.p, h->fpos.p, h->fv.p, h->fdinv.p, h->w.p);
+      k_bilu_bwd_par<NB, V, C><<<grid_for(rw * 32, T), T, 0, h->stream>>>(
+          q0, q1, h->frp.p, h->fshi.p, h->fpos.p, F.fv, F.fdinv, F.w);
       MSS_LAUNCH_CK("k_bilu_bwd_par");
     }
     const long long sw = (s1 - s0 + RPW - 1) / RPW;
-    k_bilu_bwd_chain<NB><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
-        s0, s1, h->st_first.p, h->st_len.p, h->fdp.p, h->fshi.p, h->fpos.p, h->fv.p, h->fdinv.p,
-        h->cG.p, h->cflag.p, h->w.p, bjac ? 0 : 1);
+    k_bilu_bwd_chain<NB, V, C><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
+        s0, s1, h->st_first.p, h->st_len.p, h->fdp.p, h->fshi.p, h->fpos.p, F.fv, F.fdinv, F.cG,
+        h->cflag.p, F.w, bjac ? 0 : 1);
     MSS_LAUNCH_CK("k_bilu_bwd_chain");
   }
   {
     TraceScope ts(h, TR_BILU_BWD);
     const long long tot = (long long)h->N * NB;
-    k_bilu_assemble<NB, MODE><<<grid_for(tot, T), T, 0, h->stream>>>(h->N, h->perm.p, h->w.p, xT,
-                                                                     vP, h->p, h->t, y);
+    k_bilu_assemble<NB, MODE, C><<<grid_for(tot, T), T, 0, h->stream>>>(h->N, h->perm.p, F.w,
+                                                                        xT, vP, h->p, h->t, y);
     MSS_LAUNCH_CK("k_bilu_assemble");
   }
 }
 
-template <int NB>
-void last_stage_nb(Handle* h, const double* r, const double* xT, const double* vP, double* y) {
+template <int NB, class C>
+void last_stage_nb(Handle* h, const double* r, const C* xT, const C* vP, double* y) {
+  const auto F = factors(h, (const C*)nullptr);
   const int mode = (xT ? 1 : 0) | (vP ? 2 : 0);
   switch (mode) {
-    case 0: sweeps<NB, 0>(h, r, xT, vP, y); break;
-    case 1: sweeps<NB, 1>(h, r, xT, vP, y); break;
-    case 2: sweeps<NB, 2>(h, r, xT, vP, y); break;
-    default: sweeps<NB, 3>(h, r, xT, vP, y); break;
+    case 0: sweeps<NB, 0>(h, F, r, xT, vP, y); break;
+    case 1: sweeps<NB, 1>(h, F, r, xT, vP, y); break;
+    case 2: sweeps<NB, 2>(h, F, r, xT, vP, y); break;
+    default: sweeps<NB, 3>(h, F, r, xT, vP, y); break;
   }
 }
 
@@ -816,7 +834,27 @@ void bilu_setup(Handle* h) {
 }
 
 void last_stage_apply(Handle* h, const double* r, const double* xT, const double* vP, double* y) {
-  MSS_NB_DISPATCH(h->nb, last_stage_nb<NB>(h, r, xT, vP, y));
+  MSS_NB_DISPATCH(h->nb, (last_stage_nb<NB, double>(h, r, xT, vP, y)));
+}
+
+void last_stage_apply(Handle* h, const double* r, const float* xT, const float* vP, double* y) {
+  MSS_NB_DISPATCH(h->nb, (last_stage_nb<NB, float>(h, r, xT, vP, y)));
+}
+
+// BF16 copies of the factor blocks, the in-strip chain blocks and D^-1 blocks,
+// FP32 copies of the coupling column slices, and the FP32 work vector.
+void pack_last_stage_mixed(Handle* h) {
+  h->fvh.reset(h, h->fv.n);
+  to_bf16(h, h->fv.p, h->fvh.p, (long long)h->fv.n);
+  h->fdinvh.reset(h, h->fdinv.n);
+  to_bf16(h, h->fdinv.p, h->fdinvh.p, (long long)h->fdinv.n);
+  h->cLh.reset(h, h->cL.n);
+  to_bf16(h, h->cL.p, h->cLh.p, (long long)h->cL.n);
+  h->cGh.reset(h, h->cG.n);
+  to_bf16(h, h->cG.p, h->cGh.p, (long long)h->cG.n);
+  h->fcsf.reset(h, h->fcs.n);
+  to_float(h, h->fcs.p, h->fcsf.p, (long long)h->fcs.n);
+  h->wf.reset(h, (size_t)h->N * h->nb);
 }
 
 }  // namespace mss

@@ -2,6 +2,7 @@
 // errors, launchers). Not part of the public ABI; see include/mss.h.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -96,11 +97,15 @@ struct Level {
   DBuf<double> rv;
   // V-cycle vectors
   DBuf<double> b, x, x2, r, d;
+  // mixed precision: BF16 copies of A, P, R values, FP32 D^-1 and vectors
+  DBuf<__nv_bfloat16> vh, pvh, rvh;
+  DBuf<float> dinvf, bf, xf, x2f, rf, df;
 };
 
 struct Hierarchy {
   std::vector<Level> lev;
   DBuf<double> coarse_inv;    // dense inverse of the coarsest operator, row-major
+  DBuf<float> coarse_invf;    // its FP32 copy (mixed precision)
   int nc = 0;                 // size of the coarsest level
   bool present() const { return !lev.empty(); }
 };
@@ -137,6 +142,10 @@ struct Handle {
   DBuf<int> fslo, fshi;        // per row: first in-strip lower entry, end of in-strip upper
   DBuf<double> cL, cG;         // per position: L_{q,q-1} and G_{q,q+1} (zero if absent)
   DBuf<int> cflag;             // per position: bit 0 / bit 1 = other in-strip lower / upper
+  // mixed precision: BF16 factor blocks, FP32 column slices and work vectors
+  DBuf<__nv_bfloat16> fvh, fdinvh, cLh, cGh;
+  DBuf<float> fcsf, aptf, atpf;
+  DBuf<float> rTf, xTf, zPf, vPf, wf;
   DBuf<int> st_first, st_len;  // strips in colour-major order: first position, length
   std::vector<int> sc_start;   // host: first strip of each colour, ncol + 1
   DBuf<double> fv;             // L (strictly lower) / U (strictly upper) blocks
@@ -187,6 +196,14 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t 
   return z ^ (z >> 31);
 }
 
+// Load-and-convert to the compute type C (FP64, FP32, BF16 storage).
+template <class C>
+__device__ __forceinline__ C cvt(double x) { return (C)x; }
+template <class C>
+__device__ __forceinline__ C cvt(float x) { return (C)x; }
+template <class C>
+__device__ __forceinline__ C cvt(__nv_bfloat16 x) { return (C)__bfloat162float(x); }
+
 // ---- launch helpers --------------------------------------------------------
 // Dispatch a call templated on the block size NB (2..8).
 #define MSS_NB_DISPATCH(NBV, CALL)                                     \
@@ -228,10 +245,17 @@ void amg_build(Handle* h, Hierarchy& H, const double* vals0);
 
 // amg_cycle.cu
 void vcycle(Handle* h, Hierarchy& H, const double* b, double* x);
+void vcycle_mixed(Handle* h, Hierarchy& H, const float* b, float* x);   // BF16 / FP32
+void pack_hierarchy_mixed(Handle* h, Hierarchy& H);
 void gather_var(Handle* h, const double* v, int var, double* out);
+void gather_var(Handle* h, const double* v, int var, float* out);
 void scatter_var_zero(Handle* h, const double* s, int var, double* out);
 void csr_block_pattern_spmv_sub(Handle* h, const double* vals, const double* x,
                                 const double* r, int var, double* out);
+void csr_block_pattern_spmv_sub(Handle* h, const float* vals, const float* x, const double* r,
+                                int var, float* out);
+void to_float(Handle* h, const double* in, float* out, long long n);
+void to_bf16(Handle* h, const double* in, __nv_bfloat16* out, long long n);
 
 // bilu.cu
 void bilu_setup(Handle* h);
@@ -239,6 +263,9 @@ void bilu_setup(Handle* h);
 // pointer is NULL), y = xadd + M3 u where xadd puts xT at t and vP at p.
 void last_stage_apply(Handle* h, const double* r, const double* xT, const double* vP,
                       double* y);
+// mixed form: BF16 factor blocks, FP32 sweeps, FP64 r and y
+void last_stage_apply(Handle* h, const double* r, const float* xT, const float* vP, double* y);
+void pack_last_stage_mixed(Handle* h);
 
 // residual.cu
 void check_residual_args(const mss_bsr* J, int nb, const double* b, const double* x,

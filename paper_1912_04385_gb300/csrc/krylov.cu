@@ -322,17 +322,49 @@ void bsr_spmv(Handle* h, const double* x, double* y) {
 }
 
 // y = M^{-1} r: Algorithm 2 (CPTR3), Algorithm 1 (CPR) or the last stage only
-void precond_apply(Handle* h, const double* r, double* y) {
-  TraceScope ts(h, TR_APPLY);
+// Mixed form of the same stages: BF16 operator blocks and factors, FP32
+// vectors and arithmetic; r and y stay FP64 (the Krylov vectors).
+static void precond_apply_mixed(Handle* h, const double* r, double* y) {
   const int scheme = h->opt.scheme;
   if (scheme == MSS_ILU0) {
-    last_stage_apply(h, r, nullptr, nullptr, y);
+    last_stage_apply(h, r, (const float*)nullptr, (const float*)nullptr, y);
+    return;
+  }
+  if (scheme == MSS_CPR) {
+    gather_var(h, r, h->p, h->rTf.p);
+    vcycle_mixed(h, h->amgP, h->rTf.p, h->vPf.p);
+    last_stage_apply(h, r, (const float*)nullptr, h->vPf.p, y);
+    return;
+  }
+  if (h->opt.stage_order == MSS_STAGE_T_FIRST) {
+    gather_var(h, r, h->t, h->rTf.p);
+    vcycle_mixed(h, h->amgT, h->rTf.p, h->xTf.p);
+    csr_block_pattern_spmv_sub(h, h->aptf.p, h->xTf.p, r, h->p, h->zPf.p);
+    vcycle_mixed(h, h->amgP, h->zPf.p, h->vPf.p);
+  } else {
+    gather_var(h, r, h->p, h->rTf.p);
+    vcycle_mixed(h, h->amgP, h->rTf.p, h->vPf.p);
+    csr_block_pattern_spmv_sub(h, h->atpf.p, h->vPf.p, r, h->t, h->zPf.p);
+    vcycle_mixed(h, h->amgT, h->zPf.p, h->xTf.p);
+  }
+  last_stage_apply(h, r, h->xTf.p, h->vPf.p, y);
+}
+
+void precond_apply(Handle* h, const double* r, double* y) {
+  TraceScope ts(h, TR_APPLY);
+  if (h->opt.precision == MSS_MIXED) {
+    precond_apply_mixed(h, r, y);
+    return;
+  }
+  const int scheme = h->opt.scheme;
+  if (scheme == MSS_ILU0) {
+    last_stage_apply(h, r, (const double*)nullptr, (const double*)nullptr, y);
     return;
   }
   if (scheme == MSS_CPR) {
     gather_var(h, r, h->p, h->rT.p);
     vcycle(h, h->amgP, h->rT.p, h->vP.p);                  // x = M1 r (pressure)
-    last_stage_apply(h, r, nullptr, h->vP.p, y);           // y = x + M2 (r - Abar x)
+    last_stage_apply(h, r, (const double*)nullptr, h->vP.p, y);          // y = x + M2 (r - Abar x)
     return;
   }
   if (h->opt.stage_order == MSS_STAGE_T_FIRST) {

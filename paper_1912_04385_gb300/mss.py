@@ -20,6 +20,7 @@ ERR_CUDA, ERR_OOM, ERR_AMG, ERR_NOT_SETUP = -5, -6, -7, -8
 
 SCHEMES = {"cptr3": 0, "cpr": 1, "ilu0": 2}
 SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
 
 # every exported symbol declared in include/mss.h
 EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
@@ -121,7 +122,8 @@ class MssError(RuntimeError):
 
 
 def options(**kw) -> Options:
-    """Library defaults with keyword overrides (scheme/smoother accept names)."""
+    """Library defaults with keyword overrides (scheme, smoother and precision
+    accept names)."""
     o = Options()
     load().mss_options_default(C.byref(o))
     for k, v in kw.items():
@@ -129,6 +131,8 @@ def options(**kw) -> Options:
             v = SCHEMES[v]
         if k == "smoother" and isinstance(v, str):
             v = SMOOTHERS[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
         if not hasattr(o, k) or k in ("pad_", "learned_interp"):
             raise KeyError(k)
         setattr(o, k, v)
