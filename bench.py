@@ -49,6 +49,9 @@ def args_():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--mixed-n", type=int, default=2048,
                     help="grid of the mixed-precision comparison (0: skip)")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="systems in the batched-solve comparison (0: skip)")
+    ap.add_argument("--batch-lanes", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     return ap.parse_args()
@@ -272,6 +275,8 @@ def run_ours(a, rank, world, dist):
         out["mixed"] = mixed_leg(a, dev, solver, torch, stream)
         if a.mixed_n > 0:
             out["mixed_config"] = mixed_config_leg(a, solver, torch, stream)
+    if a.batch > 0:
+        out["batch"] = batch_leg(a, torch)
     # end to end through the C-ABI from pinned host buffers
     if not a.no_e2e:
         out["e2e"] = e2e(a, sysl, solver, opts, torch)
@@ -327,6 +332,7 @@ def mixed_leg(a, dev, solver, torch, stream):
             "solve_ms_mean": round(float(np.mean([i["solve_ms"] for i in infos])), 3),
             "apply_ms_mean": round(apply_ms / max(n_apply, 1), 4),
             "rel_res_unscaled": [float(f"{v:.3e}") for v in rels],
+            "trace_ms": {k: [v[0], round(v[1], 3)] for k, v in tr.items()},
             "storage": "bf16 blocks, fp32 vectors and sweeps, fp64 Krylov"}
 
 
@@ -374,7 +380,8 @@ def mixed_config_leg(a, solver, torch, stream):
                      "setup_ms": round(infos[-1]["setup_ms"], 3),
                      "solve_ms": round(infos[-1]["solve_ms"], 3),
                      "apply_ms_mean": round(apply_ms / max(n_apply, 1), 4),
-                     "rel_res_unscaled": float(f"{r / bn:.3e}")}
+                     "rel_res_unscaled": float(f"{r / bn:.3e}"),
+                     "trace_ms": {k: [v[0], round(v[1], 3)] for k, v in tr.items()}}
     # reference solution: FP64 preconditioner, converged to 1e-10
     solver.setup(rp, ci, v, 6, 0, 1, opts=mss.options(restart=a.restart))
     xr, ir = solver.solve(b, tol=1e-10, maxit=4 * a.maxit)
@@ -385,6 +392,89 @@ def mixed_config_leg(a, solver, torch, stream):
     res["speedup_mixed_over_fp64"] = round(res["fp64"]["ms"] / res["mixed"]["ms"], 3)
     res["reference_iters"] = ir["iters"]
     return res
+
+
+def batch_systems(a):
+    """The batched workload: grid sides uniform on [64, 512], nb in {4, 6},
+    lognormal permeability (sigma 2, correlation 16), stiff band, Pe
+    log-uniform on [0.1, 1000]; seeded."""
+    from paper_1912_04385_gb300 import synthetic as sy
+    rng = np.random.default_rng(1)
+    out = []
+    for k in range(a.batch):
+        n = int(rng.integers(64, 513))
+        nb = int(rng.choice([4, 6]))
+        pe = float(10.0 ** rng.uniform(-1.0, 3.0))
+        out.append(sy.make_system(n, n, nb, pe=pe, sigma=2.0, corr_len=16.0, band=True,
+                                  seed=1000 + k))
+    return out
+
+
+def batch_leg(a, torch):
+    """Aggregate solves/s and per-system latency of the batch API against the
+    same systems solved one after another by one handle (host driver)."""
+    from paper_1912_04385_gb300 import mss
+    sysl = batch_systems(a)
+    dev = [dict(row_ptr=torch.from_numpy(s.row_ptr).cuda(),
+                col_idx=torch.from_numpy(s.col_idx).cuda(),
+                vals=torch.from_numpy(np.ascontiguousarray(s.vals).reshape(-1)).cuda(),
+                b=torch.from_numpy(s.b).cuda(), nb=s.nb, p_idx=0, t_idx=1) for s in sysl]
+    cells = int(sum(s.n_cells for s in sysl))
+    del sysl
+    torch.cuda.synchronize()
+    # one after another, one handle
+    solver = mss.Solver()
+    opts = mss.options(restart=a.restart)
+
+    def sequential():
+        lat, its = [], []
+        for d in dev:
+            t0 = time.perf_counter()
+            solver.setup(d["row_ptr"], d["col_idx"], d["vals"], d["nb"], 0, 1, opts=opts)
+            x, info = solver.solve(d["b"], tol=a.tol, maxit=a.maxit)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - t0) * 1e3)
+            its.append(info["iters"])
+            if info["status"] != 0:
+                raise RuntimeError(f"sequential solve failed: {info}")
+        return lat, its
+
+    sequential()
+    t0 = time.perf_counter()
+    lat_s, its_s = sequential()
+    wall_s = (time.perf_counter() - t0) * 1e3
+    del solver
+    # batched: lanes with their own streams; autotuned on the warm-up run
+    B = mss.Batch(lanes=a.batch_lanes, autotune=True)
+    B.solve(dev, tol=a.tol, maxit=a.maxit, restart=a.restart)
+    walls, lat_b, its_b = [], [], []
+    for _ in range(max(1, a.steps)):
+        t0 = time.perf_counter()
+        xs, res, inf = B.solve(dev, tol=a.tol, maxit=a.maxit, restart=a.restart)
+        walls.append((time.perf_counter() - t0) * 1e3)
+        if any(r["status"] != 0 for r in res):
+            raise RuntimeError("batched solve failed")
+        lat_b = [f["latency_ms"] for f in inf]
+        its_b = [r["iters"] for r in res]
+    wall_b = float(np.median(walls))
+    assert its_b == its_s, "batched and sequential iteration counts differ"
+    n = len(dev)
+    return {"workload": f"{n} systems, sides U[64,512], nb in {{4,6}}, Pe log-U[0.1,1000], "
+                        f"sigma 2, fgmres{a.restart} to {a.tol:g}",
+            "systems": n, "cells_total": cells, "lanes": a.batch_lanes,
+            "solves_per_s": round(n / (wall_b * 1e-3), 2),
+            "wall_ms": round(wall_b, 2),
+            "latency_p50_ms": round(float(np.percentile(lat_b, 50)), 3),
+            "latency_p99_ms": round(float(np.percentile(lat_b, 99)), 3),
+            "sequential": {"solves_per_s": round(n / (wall_s * 1e-3), 2),
+                           "wall_ms": round(wall_s, 2),
+                           "latency_p50_ms": round(float(np.percentile(lat_s, 50)), 3),
+                           "latency_p99_ms": round(float(np.percentile(lat_s, 99)), 3)},
+            "speedup_solves_per_s": round(wall_s / wall_b, 3),
+            "iters_total": int(sum(its_b)),
+            "tuned": [list(t) for t in B.tuned()],
+            "timing": "host clock around each call (every solution complete on return); "
+                      "batch wall = median over the timed runs after one tuning run"}
 
 
 def apply_alg_bytes(N, nnzb, nb, solver):

@@ -57,6 +57,7 @@ enum { MSS_MULTICOLOR = 0, MSS_STRIPS = 2 };         /* block ILU(0) ordering */
 enum { MSS_JACOBI = 0, MSS_CHEBYSHEV = 1 };          /* AMG smoother */
 enum { MSS_FP64 = 0, MSS_MIXED = 1 };                /* preconditioner arithmetic */
 enum { MSS_CGS1 = 0, MSS_CGS2 = 1 };                 /* Arnoldi orthogonalisation */
+enum { MSS_DRIVER_HOST = 0, MSS_DRIVER_GRAPH = 1 };  /* who runs the FGMRES loop */
 
 /* A BSR matrix; the arrays are device memory owned by the caller. */
 typedef struct {
@@ -103,7 +104,13 @@ typedef struct {
                                paper, which computes in float64 throughout. */
   int32_t ilu_strip;        /* strip length in cells for MSS_STRIPS (32), 1..1024 */
   int32_t orthog;           /* Arnoldi: MSS_CGS1 (default) | MSS_CGS2 */
-  int32_t pad_;
+  int32_t driver;           /* MSS_DRIVER_HOST: the host reads the solve state back
+                               after every Arnoldi step and decides;
+                               MSS_DRIVER_GRAPH: the whole restarted solve is one
+                               CUDA graph (two nested while-loop conditional
+                               nodes, the decisions taken by device kernels),
+                               launched once per solve and read back once. Same
+                               kernels, same order, same results. */
   double amg_theta;         /* strength threshold (0.25) */
   double jacobi_omega;      /* Jacobi damping (2/3) */
   double cheb_lo_ratio;     /* Chebyshev interval [bound/ratio, factor*bound] (30) */
@@ -278,8 +285,10 @@ long long mss_kernel_launches(int reset);
  * handle's stream bracket every BSR matrix-vector product (kind 0), every
  * forward (1) and backward (2) last-stage sweep launch, every V-cycle (3),
  * every Arnoldi orthogonalisation step (4), the set-up phases: scaling
- * (5), each AMG hierarchy (6), ordering and factorisation (7), and every
- * whole preconditioner application (8). */
+ * (5), the span in which the two AMG hierarchies are built on worker streams
+ * while the last stage is ordered and factorised (6), that ordering and
+ * factorisation alone (7), and every whole preconditioner application (8).
+ * Solves run with MSS_DRIVER_GRAPH record no events (a graph holds none). */
 int mss_trace_enable(mss_handle* h, int enable);
 
 /* Totals for one kind since the last reset: number of bracketed regions
@@ -287,6 +296,62 @@ int mss_trace_enable(mss_handle* h, int enable);
  * Synchronises the stream. reset != 0 zeroes the kind's totals after
  * reading. Errors: INVALID_ARG for an unknown kind. */
 int mss_trace_read(mss_handle* h, int kind, int64_t* launches, double* ms, int reset);
+
+/* ---- batched solves (not in the paper) ------------------------------------
+ * Many independent systems of different sizes, set up and solved
+ * concurrently: a pool of `lanes` host worker threads, each driving its own
+ * handle on its own CUDA stream (memory from the library's stream-ordered
+ * device pool), takes the systems largest first. Every system is set up and
+ * solved exactly as by mss_setup + mss_fgmres_solve with the given options,
+ * so its solution is the one a single handle gives, bit for bit.
+ *
+ * Autotuner (autotune != 0): the first system of each size bucket
+ * (floor(log2 N), nb) is used to time the preconditioner application and the
+ * matrix-vector product at 64, 128, 256 and 512 threads per CTA (the result
+ * does not depend on it) and one solve with each driver (host loop, or the
+ * CUDA graph including its capture); the fastest choice is cached in the
+ * batch object for later systems of the bucket. With autotune == 0 every
+ * system uses 256 threads and the driver in the options. */
+typedef struct {
+  mss_bsr J;                /* device arrays, as for mss_setup */
+  int32_t nb;
+  mss_layout layout;
+  const double* b;          /* device, n_rows * nb */
+  double* x;                /* device, n_rows * nb: the solution (x0 = 0) */
+} mss_system;
+
+typedef struct {
+  int32_t bucket;           /* floor(log2(n_rows)) */
+  int32_t threads;          /* threads per CTA used */
+  int32_t driver;           /* MSS_DRIVER_* used */
+  int32_t lane;             /* worker that solved it */
+  double latency_ms;        /* host clock: start of its set-up to end of its solve */
+  double finish_ms;         /* host clock: start of the batch call to end of its solve */
+} mss_batch_info;
+
+typedef struct mss_batch mss_batch;
+
+/* lanes: worker threads, 1..64. Handles are created on the current device.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+int mss_batch_create(mss_batch** b, int lanes, int autotune);
+void mss_batch_destroy(mss_batch* b);
+
+/* Sets up and solves the n systems (tol, maxit as for mss_fgmres_solve; opt
+ * NULL = defaults). The device is synchronised first, so inputs written on
+ * any stream are complete; every solution is complete on return.
+ * results[i] (host, n entries) is system i's outcome (status per system: one
+ * failing system does not stop the others); info (host, n entries, may be
+ * NULL) its schedule. Returns MSS_OK when every system converged, else the
+ * first non-OK system status; INVALID_ARG for bad arguments. */
+int mss_batch_solve(mss_batch* b, int n, const mss_system* sys, const mss_options* opt,
+                    double tol, int maxit, mss_result* results, mss_batch_info* info);
+
+/* The autotuner's cache: up to cap entries of 4 int32 each (bucket, nb,
+ * threads, driver) written to out (host); returns the number of entries. */
+int mss_batch_tuned(mss_batch* b, int cap, int32_t* out);
+
+/* Message for the last failing call on `b`. */
+const char* mss_batch_last_error(const mss_batch* b);
 
 /* Human-readable name of a status code (static string). */
 const char* mss_status_string(int status);

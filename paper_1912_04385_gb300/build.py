@@ -25,8 +25,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
           "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 NO_FMA = {"setup_scale.cu", "amg_setup.cu"}
-SOURCES = ["util.cu", "setup_scale.cu", "amg_setup.cu", "amg_cycle.cu", "bilu.cu", "krylov.cu",
-           "residual.cu", "noalloc.cu", "api.cu"]
+SOURCES = ["util.cu", "setup_scale.cu", "amg_setup.cu", "amg_cycle.cu", "bilu.cu", "spmv.cu", "krylov.cu",
+           "residual.cu", "noalloc.cu", "api.cu", "batch.cu"]
 
 
 def _nvcc() -> str:

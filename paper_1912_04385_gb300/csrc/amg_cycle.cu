@@ -13,6 +13,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -237,7 +239,6 @@ __global__ void k_to_bf16(long long n, const double* __restrict__ in,
   for (; i < n; i += stride) out[i] = __float2bfloat16_rn((float)in[i]);
 }
 
-constexpr int VT = 256;
 
 // pointers of one level for one precision
 template <class V, class C>
@@ -273,7 +274,7 @@ struct Sweeper {
   // one smoothing application on (b, x): writes the result to xout; xin and
   // xout must differ
   void jacobi(const C* b, const C* xin, C* xout) {
-    k_jacobi<V, C><<<grid_for(L.n, VT), VT, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.dinv, b,
+    k_jacobi<V, C><<<grid_for(L.n, h->tb), h->tb, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.dinv, b,
                                                             (C)o.jacobi_omega, xin, xout);
     MSS_LAUNCH_CK("k_jacobi");
   }
@@ -296,7 +297,7 @@ struct Sweeper {
         c2 = 2.0 * rn / delta;
         rho = rn;
       }
-      k_cheb<V, C><<<grid_for(L.n, VT), VT, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.dinv, b,
+      k_cheb<V, C><<<grid_for(L.n, h->tb), h->tb, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.dinv, b,
                                                             (C)c1, (C)c2, cur, L.d, nxt);
       MSS_LAUNCH_CK("k_cheb");
       C* t = cur;
@@ -327,7 +328,7 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out) {
   C* cur = out;
   C* alt = L.x2;
   if (o.smoother == MSS_JACOBI && o.nu_pre >= 1) {
-    k_jacobi0_residual<V, C><<<grid_for(n, VT), VT, 0, h->stream>>>(
+    k_jacobi0_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(
         n, L.rp, L.ci, L.v, L.dinv, b, (C)o.jacobi_omega, out, L.r);
     MSS_LAUNCH_CK("k_jacobi0_residual");
     for (int s = 1; s < o.nu_pre; ++s) {
@@ -335,7 +336,7 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out) {
       std::swap(cur, alt);
     }
     if (o.nu_pre > 1) {
-      k_residual<V, C><<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
+      k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
       MSS_LAUNCH_CK("k_residual");
     }
   } else {
@@ -344,14 +345,14 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out) {
       C* res = sw.cheb(b, cur, alt);
       if (res != cur) std::swap(cur, alt);
     }
-    k_residual<V, C><<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
+    k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
     MSS_LAUNCH_CK("k_residual");
   }
   // ---- restriction and the coarse correction
-  k_csr_spmv<V, C><<<grid_for(L.nc, VT), VT, 0, h->stream>>>(L.nc, L.rrp, L.rci, L.rv, L.r, cb);
+  k_csr_spmv<V, C><<<grid_for(L.nc, h->tb), h->tb, 0, h->stream>>>(L.nc, L.rrp, L.rci, L.rv, L.r, cb);
   MSS_LAUNCH_CK("k_csr_spmv(R)");
   vcycle_level<V, C>(h, H, l + 1, cb, cx);
-  k_prolong<V, C><<<grid_for(n, VT), VT, 0, h->stream>>>(n, L.prp, L.pci, L.pv, cx, cur, alt);
+  k_prolong<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.prp, L.pci, L.pv, cx, cur, alt);
   MSS_LAUNCH_CK("k_prolong");
   std::swap(cur, alt);
   // ---- post-smoothing
@@ -373,6 +374,8 @@ unsigned stride_grid(long long n) {
 }
 
 }  // namespace
+
+static std::mutex g_coop_mu;
 
 void coarse_inverse(Handle* h, Hierarchy& H) {
   Level& C = H.lev.back();
@@ -401,10 +404,17 @@ void coarse_inverse(Handle* h, Hierarchy& H) {
   int* pp = piv.p;
   int* sp = status.p;
   void* args[] = {&nn, &Mp, &pp, &sp};
-  MSS_CK(cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(blocks), dim3(threads),
-                                     args, smem, h->stream));
-  count_launch();
-  int st = read_int(h, status.p);
+  int st;
+  {
+    // one cooperative grid at a time in the process: the set-up builds two
+    // hierarchies on concurrent streams, and two device-filling cooperative
+    // grids must not wait on each other's residency
+    std::lock_guard<std::mutex> lk(g_coop_mu);
+    MSS_CK(cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(blocks),
+                                       dim3(threads), args, smem, h->stream));
+    count_launch();
+    st = read_int(h, status.p);   // synchronises: the grid has finished
+  }
   if (st != 0) fail(MSS_ERR_AMG, "coarsest AMG operator is singular (column " +
                                      std::to_string(st - 1) + ")");
   k_gj_extract<<<grid_for((long long)n * n, 256), 256, 0, h->stream>>>(n, M.p, piv.p,
@@ -460,31 +470,31 @@ void vcycle_mixed(Handle* h, Hierarchy& H, const float* b, float* x) {
 }
 
 void gather_var(Handle* h, const double* v, int var, double* out) {
-  k_gather_var<double><<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, v, var, out);
+  k_gather_var<double><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, v, var, out);
   MSS_LAUNCH_CK("k_gather_var");
 }
 
 void gather_var(Handle* h, const double* v, int var, float* out) {
-  k_gather_var<float><<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, v, var, out);
+  k_gather_var<float><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, v, var, out);
   MSS_LAUNCH_CK("k_gather_var");
 }
 
 void scatter_var_zero(Handle* h, const double* s, int var, double* out) {
   long long tot = (long long)h->N * h->nb;
-  k_scatter_var_zero<<<grid_for(tot, 256), 256, 0, h->stream>>>(h->N, h->nb, s, var, out);
+  k_scatter_var_zero<<<grid_for(tot, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, s, var, out);
   MSS_LAUNCH_CK("k_scatter_var_zero");
 }
 
 void csr_block_pattern_spmv_sub(Handle* h, const double* vals, const double* x, const double* r,
                                 int var, double* out) {
-  k_pattern_sub<double><<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, h->rp.p,
+  k_pattern_sub<double><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, h->rp.p,
                                                                     h->ci.p, vals, x, r, var, out);
   MSS_LAUNCH_CK("k_pattern_sub");
 }
 
 void csr_block_pattern_spmv_sub(Handle* h, const float* vals, const float* x, const double* r,
                                 int var, float* out) {
-  k_pattern_sub<float><<<grid_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->nb, h->rp.p, h->ci.p,
+  k_pattern_sub<float><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, h->rp.p, h->ci.p,
                                                                    vals, x, r, var, out);
   MSS_LAUNCH_CK("k_pattern_sub");
 }

@@ -450,20 +450,21 @@ void level_prepare(Handle* h, Level& L) {
 
 }  // namespace
 
-void amg_build(Handle* h, Hierarchy& H, const double* vals0) {
+void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const int* ci0,
+               const double* vals0) {
   const mss_options& o = h->opt;
   H.lev.clear();
   H.lev.reserve(32);
   {
     Level L0;
-    L0.n = h->N;
-    L0.nnz = h->nnzb;
-    L0.rp.reset(h, h->N + 1);
-    L0.ci.reset(h, h->nnzb);
-    L0.v.reset(h, h->nnzb);
-    copy_dev(h, L0.rp.p, h->rp.p, sizeof(int) * ((size_t)h->N + 1));
-    copy_dev(h, L0.ci.p, h->ci.p, sizeof(int) * (size_t)h->nnzb);
-    copy_dev(h, L0.v.p, vals0, sizeof(double) * (size_t)h->nnzb);
+    L0.n = n0;
+    L0.nnz = nnz0;
+    L0.rp.reset(h, n0 + 1);
+    L0.ci.reset(h, nnz0);
+    L0.v.reset(h, nnz0);
+    copy_dev(h, L0.rp.p, rp0, sizeof(int) * ((size_t)n0 + 1));
+    copy_dev(h, L0.ci.p, ci0, sizeof(int) * (size_t)nnz0);
+    copy_dev(h, L0.v.p, vals0, sizeof(double) * (size_t)nnz0);
     H.lev.push_back(std::move(L0));
   }
   const int max_levels = o.amg_max_levels < 1 ? 1 : (o.amg_max_levels > 25 ? 25 : o.amg_max_levels);

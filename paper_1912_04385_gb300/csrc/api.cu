@@ -4,6 +4,9 @@
 #include <chrono>
 #include <new>
 
+#include <thread>
+#include <exception>
+#include <memory>
 #include "common.cuh"
 
 struct mss_handle {
@@ -50,14 +53,91 @@ void check_options(const mss_options& o) {
   if (o.interp_max_elems < 0) bad("interp_max_elems");
   if (o.restart < 1 || o.restart > 120) bad("restart (1..120)");
   if (o.precision != MSS_FP64 && o.precision != MSS_MIXED) bad("precision");
+  if (o.driver != MSS_DRIVER_HOST && o.driver != MSS_DRIVER_GRAPH) bad("driver");
   if (!(o.amg_theta > 0.0 && o.amg_theta <= 1.0)) bad("amg_theta");
   if (!(o.jacobi_omega > 0.0 && o.jacobi_omega < 2.0)) bad("jacobi_omega");
   if (!(o.cheb_lo_ratio > 1.0) || !(o.cheb_hi_factor > 0.0)) bad("Chebyshev interval");
   if (o.learned_interp != nullptr) bad("learned_interp (reserved)");
 }
 
+// Worker handle i: its own non-blocking stream, allocations from the device
+// pool, the main handle's sizes and options.
+Handle* worker(Handle& H, int i) {
+  if (!H.aux[i]) {
+    std::unique_ptr<Handle> a(new Handle());
+    a->device = H.device;
+    a->num_sms = H.num_sms;
+    MSS_CK(cudaStreamCreateWithFlags(&a->owned.s, cudaStreamNonBlocking));
+    a->stream = a->owned.s;
+    H.aux[i] = std::move(a);
+  }
+  Handle* a = H.aux[i].get();
+  a->opt = H.opt;
+  a->N = H.N;
+  a->nnzb = H.nnzb;
+  a->nb = H.nb;
+  a->p = H.p;
+  a->t = H.t;
+  return a;
+}
+
+// Makes stream `later` wait for the work queued so far on stream `first`.
+void order_streams(cudaStream_t first, cudaStream_t later) {
+  cudaEvent_t e;
+  MSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  MSS_CK(cudaEventRecord(e, first));
+  MSS_CK(cudaStreamWaitEvent(later, e, 0));
+  MSS_CK(cudaEventDestroy(e));
+}
+
+// Runs set-up tasks on worker handles in threads; join() waits for them,
+// orders the main stream after their streams and rethrows the first error.
+struct Fork {
+  Handle& H;
+  std::thread th[2];
+  std::exception_ptr err[2];
+  bool used[2] = {false, false};
+  explicit Fork(Handle& h) : H(h) {}
+  template <class F>
+  void run(int i, F fn) {
+    Handle* a = worker(H, i);
+    order_streams(H.stream, a->stream);   // the worker reads what H's stream wrote
+    used[i] = true;
+    MSS_CK(cudaGetDevice(&a->device));
+    const int dev = a->device;
+    th[i] = std::thread([this, i, a, dev, fn] {
+      try {
+        MSS_CK(cudaSetDevice(dev));
+        fn(a);
+      } catch (...) {
+        err[i] = std::current_exception();
+      }
+    });
+  }
+  void join() {
+    for (int i = 0; i < 2; ++i)
+      if (th[i].joinable()) th[i].join();
+    for (int i = 0; i < 2; ++i)
+      if (used[i]) order_streams(H.aux[i]->stream, H.stream);
+    for (int i = 0; i < 2; ++i)
+      if (err[i]) std::rethrow_exception(err[i]);
+  }
+  ~Fork() {
+    for (int i = 0; i < 2; ++i)
+      if (th[i].joinable()) th[i].join();
+  }
+};
+
 void release_setup(Handle& H) {
   H.ready = false;
+  // hierarchy memory came from the workers' streams: free it there only
+  // after everything queued on the handle's stream
+  for (auto& a : H.aux)
+    if (a) order_streams(H.stream, a->stream);
+  if (H.sgraph) {   // the solve graph holds pointers into the set-up
+    cudaGraphExecDestroy(H.sgraph);
+    H.sgraph = nullptr;
+  }
   H.amgT = Hierarchy();
   H.amgP = Hierarchy();
   H.rp.release(); H.ci.release(); H.diag.release();
@@ -115,21 +195,34 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
       extract_subsystem(h, -2, H.atp.p);
     }
   }
-  // scalar subsystems and their AMG hierarchies
-  if (o.scheme != MSS_ILU0) {
+  // The scalar subsystems' AMG hierarchies and the last-stage factorisation
+  // depend only on Abar: the hierarchies are built by worker threads on
+  // their own streams while this thread factorises on the handle's stream.
+  {
     TraceScope ts(h, TR_SETUP_AMG);
-    DBuf<double> bpp(h, nnzb);
-    extract_subsystem(h, H.p, bpp.p);             // B_PP
-    amg_build(h, H.amgP, bpp.p);
+    DBuf<double> bpp, ctt;
+    if (o.scheme != MSS_ILU0) {
+      bpp.reset(h, nnzb);
+      extract_subsystem(h, H.p, bpp.p);           // B_PP
+    }
+    if (o.scheme == MSS_CPTR3) {
+      ctt.reset(h, nnzb);
+      extract_subsystem(h, H.t, ctt.p);           // C_TT
+    }
+    Fork fork(H);
+    if (o.scheme != MSS_ILU0)
+      fork.run(0, [&](Handle* a) { amg_build(a, H.amgP, N, nnzb, H.rp.p, H.ci.p, bpp.p); });
+    if (o.scheme == MSS_CPTR3)
+      fork.run(1, [&](Handle* a) { amg_build(a, H.amgT, N, nnzb, H.rp.p, H.ci.p, ctt.p); });
+    std::exception_ptr mine;
+    try {
+      bilu_setup(h);                              // last stage
+    } catch (...) {
+      mine = std::current_exception();
+    }
+    fork.join();                                  // rethrows a worker's error
+    if (mine) std::rethrow_exception(mine);
   }
-  if (o.scheme == MSS_CPTR3) {
-    TraceScope ts(h, TR_SETUP_AMG);
-    DBuf<double> ctt(h, nnzb);
-    extract_subsystem(h, H.t, ctt.p);             // C_TT
-    amg_build(h, H.amgT, ctt.p);
-  }
-  // last stage
-  bilu_setup(h);
   H.rT.reset(h, N);
   H.xT.reset(h, N);
   H.zP.reset(h, N);
@@ -191,6 +284,17 @@ int solve_impl(Handle& H, const mss_bsr* J, const double* b, double* x, double t
 
 }  // namespace
 
+namespace mss {
+void setup_handle(Handle& H, const mss_bsr* J, int nb, mss_layout layout,
+                  const mss_options* opt) {
+  do_setup(H, J, nb, layout, opt);
+}
+int solve_handle(Handle& H, const mss_bsr* J, const double* b, double* x, double tol, int maxit,
+                 mss_result* out) {
+  return solve_impl(H, J, b, x, tol, maxit, out);
+}
+}  // namespace mss
+
 extern "C" {
 
 int mss_options_default(mss_options* o) {
@@ -211,6 +315,7 @@ int mss_options_default(mss_options* o) {
   o->interp_max_elems = 4;
   o->restart = 30;
   o->precision = MSS_FP64;
+  o->driver = MSS_DRIVER_HOST;
   o->amg_theta = 0.25;
   o->jacobi_omega = 2.0 / 3.0;
   o->cheb_lo_ratio = 30.0;
@@ -249,6 +354,7 @@ void mss_destroy(mss_handle* hh) {
   if (!hh) return;
   cudaStreamSynchronize(hh->h.stream);
   delete hh;
+  trim_pools();
 }
 
 int mss_setup(mss_handle* hh, const mss_bsr* J, int nb, mss_layout layout,

@@ -1,0 +1,289 @@
+// batch.cu -- batched solves of independent systems (not in the paper).
+//
+// A pool of host worker threads ("lanes"), each owning a handle on its own
+// non-blocking stream with memory from the device pool, takes the systems
+// largest first (longest-processing-time order) and runs, for each, the same
+// set-up and solve as mss_setup + mss_fgmres_solve. Small systems leave most
+// of the 152 SMs idle; several lanes keep them busy, and every lane's host
+// synchronisations (set-up sizes, Krylov scalars) overlap with the others'
+// GPU work.
+//
+// Autotuner: per size bucket (floor(log2 N), nb) the first system times the
+// preconditioner application and the matrix-vector product at 64..512
+// threads per CTA, then one solve per driver (host loop; CUDA graph with its
+// capture), and caches the fastest. None of these choices changes a result.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace mss;
+
+namespace {
+
+struct Choice {
+  int threads = 256;
+  int driver = MSS_DRIVER_HOST;
+  bool ready = false;   // false while the tuning system is still running
+};
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+int bucket_of(int n) {
+  int b = 0;
+  while ((2LL << b) <= n) ++b;
+  return b;
+}
+
+// mean GPU time of `reps` runs of fn on the handle's stream, after one warm-up
+template <class F>
+float time_on_stream(Handle& H, int reps, F fn) {
+  cudaEvent_t a, b;
+  MSS_CK(cudaEventCreate(&a));
+  MSS_CK(cudaEventCreate(&b));
+  fn();
+  MSS_CK(cudaEventRecord(a, H.stream));
+  for (int r = 0; r < reps; ++r) fn();
+  MSS_CK(cudaEventRecord(b, H.stream));
+  MSS_CK(cudaEventSynchronize(b));
+  float ms = 0.f;
+  MSS_CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+}  // namespace
+
+struct mss_batch {
+  int device = 0;
+  int lanes = 1;
+  int autotune = 1;
+  std::vector<std::unique_ptr<Handle>> lane;
+  std::mutex mu;
+  std::map<long long, Choice> cache;   // key: bucket * 16 + nb
+  std::string last_error;
+};
+
+namespace {
+
+Handle* make_lane(int device) {
+  std::unique_ptr<Handle> h(new Handle());
+  h->device = device;
+  MSS_CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device));
+  MSS_CK(cudaStreamCreateWithFlags(&h->owned.s, cudaStreamNonBlocking));
+  h->stream = h->owned.s;
+  mss_options_default(&h->opt);
+  return h.release();
+}
+
+// Times the candidates on the set-up system in H and returns the choice;
+// also leaves the system solved in sys.x (res filled).
+Choice tune(Handle& H, const mss_system& s, double tol, int maxit, mss_result* res) {
+  Choice c;
+  const long long n = (long long)s.J.n_rows * s.nb;
+  DBuf<double> r(&H, (size_t)n), y(&H, (size_t)n);
+  scale_vector(&H, s.b, r.p);
+  float best = 1e30f;
+  for (int tb : {64, 128, 256, 512}) {
+    H.tb = tb;
+    const float t = time_on_stream(H, 3, [&] {
+      precond_apply(&H, r.p, y.p);
+      bsr_spmv(&H, y.p, r.p);
+    });
+    if (t < best) {
+      best = t;
+      c.threads = tb;
+    }
+  }
+  H.tb = c.threads;
+  double tdrv[2];
+  for (int d : {MSS_DRIVER_HOST, MSS_DRIVER_GRAPH}) {
+    H.opt.driver = d;
+    if (H.sgraph) {   // time the graph's capture too: graphs are not shared
+      cudaGraphExecDestroy(H.sgraph);
+      H.sgraph = nullptr;
+    }
+    const auto t0 = Clock::now();
+    solve_handle(H, &s.J, s.b, s.x, tol, maxit, res);
+    tdrv[d] = ms_since(t0);
+  }
+  c.driver = tdrv[MSS_DRIVER_GRAPH] < tdrv[MSS_DRIVER_HOST] ? MSS_DRIVER_GRAPH : MSS_DRIVER_HOST;
+  c.ready = true;
+  return c;
+}
+
+void run_one(mss_batch* B, Handle& H, int lane, const mss_system& s, const mss_options& base,
+             double tol, int maxit, mss_result* res, mss_batch_info* inf,
+             Clock::time_point tbatch) {
+  const auto t0 = Clock::now();
+  mss_options o = base;
+  const int bucket = bucket_of(s.J.n_rows);
+  const long long key = (long long)bucket * 16 + s.nb;
+  Choice c;
+  bool tuner = false;
+  if (B->autotune) {
+    std::lock_guard<std::mutex> lk(B->mu);
+    auto it = B->cache.find(key);
+    if (it == B->cache.end()) {
+      B->cache[key] = Choice();   // placeholder: this lane tunes the bucket
+      tuner = true;
+    } else if (it->second.ready) {
+      c = it->second;
+    }
+  } else {
+    c.driver = base.driver;
+  }
+  o.driver = c.driver;
+  H.tb = c.threads;
+  try {
+    setup_handle(H, &s.J, s.nb, s.layout, &o);
+    if (tuner) {
+      c = tune(H, s, tol, maxit, res);
+      std::lock_guard<std::mutex> lk(B->mu);
+      B->cache[key] = c;
+    } else {
+      solve_handle(H, &s.J, s.b, s.x, tol, maxit, res);
+    }
+  } catch (...) {
+    int code = MSS_ERR_CUDA;
+    try {
+      throw;
+    } catch (const Error& e) {
+      code = e.code;
+    } catch (const std::bad_alloc&) {
+      code = MSS_ERR_OOM;
+    } catch (...) {
+    }
+    if (tuner) {   // let the next system of the bucket tune it
+      std::lock_guard<std::mutex> lk(B->mu);
+      B->cache.erase(key);
+    }
+    *res = mss_result{};
+    res->status = code;
+  }
+  if (inf) {
+    inf->bucket = bucket;
+    inf->threads = c.threads;
+    inf->driver = c.driver;
+    inf->lane = lane;
+    inf->latency_ms = ms_since(t0);
+    inf->finish_ms = ms_since(tbatch);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mss_batch_create(mss_batch** out, int lanes, int autotune) {
+  if (!out || lanes < 1 || lanes > 64) return MSS_ERR_INVALID_ARG;
+  *out = nullptr;
+  mss_batch* B = new (std::nothrow) mss_batch();
+  if (!B) return MSS_ERR_OOM;
+  try {
+    MSS_CK(cudaGetDevice(&B->device));
+    B->lanes = lanes;
+    B->autotune = autotune != 0;
+    for (int i = 0; i < lanes; ++i) B->lane.emplace_back(make_lane(B->device));
+  } catch (const Error& e) {
+    delete B;
+    return e.code;
+  } catch (...) {
+    delete B;
+    return MSS_ERR_OOM;
+  }
+  *out = B;
+  return MSS_OK;
+}
+
+void mss_batch_destroy(mss_batch* B) {
+  if (!B) return;
+  for (auto& h : B->lane)
+    if (h) cudaStreamSynchronize(h->stream);
+  delete B;
+  trim_pools();
+}
+
+int mss_batch_solve(mss_batch* B, int n, const mss_system* sys, const mss_options* opt,
+                    double tol, int maxit, mss_result* results, mss_batch_info* info) {
+  if (!B) return MSS_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!sys || !results)) || !(tol >= 0.0) || maxit < 0) {
+    B->last_error = "bad batch arguments";
+    return MSS_ERR_INVALID_ARG;
+  }
+  if (n == 0) return MSS_OK;
+  mss_options base;
+  if (opt) base = *opt;
+  else mss_options_default(&base);
+  if (cudaSetDevice(B->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    B->last_error = "device synchronisation failed";
+    return MSS_ERR_CUDA;
+  }
+  // largest first: block-row work nnzb * nb^2
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const double wa = (double)sys[a].J.nnzb * sys[a].nb * sys[a].nb;
+    const double wb = (double)sys[b].J.nnzb * sys[b].nb * sys[b].nb;
+    return wa > wb;
+  });
+  std::atomic<int> next{0};
+  const auto tbatch = Clock::now();
+  auto work = [&](int l) {
+    cudaSetDevice(B->device);
+    Handle& H = *B->lane[l];
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n) break;
+      const int i = order[k];
+      run_one(B, H, l, sys[i], base, tol, maxit, &results[i], info ? &info[i] : nullptr,
+              tbatch);
+    }
+  };
+  const int nl = std::min(B->lanes, n);
+  std::vector<std::thread> th;
+  for (int l = 1; l < nl; ++l) th.emplace_back(work, l);
+  work(0);
+  for (auto& t : th) t.join();
+  int st = MSS_OK;
+  for (int i = 0; i < n && st == MSS_OK; ++i) st = results[i].status;
+  B->last_error = st == MSS_OK ? "" : "a system did not converge or failed; see its result";
+  return st;
+}
+
+int mss_batch_tuned(mss_batch* B, int cap, int32_t* out) {
+  if (!B || cap < 0 || (cap > 0 && !out)) return MSS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(B->mu);
+  int k = 0;
+  for (auto& kv : B->cache) {
+    if (!kv.second.ready) continue;
+    if (k < cap) {
+      out[4 * k + 0] = (int32_t)(kv.first / 16);
+      out[4 * k + 1] = (int32_t)(kv.first % 16);
+      out[4 * k + 2] = kv.second.threads;
+      out[4 * k + 3] = kv.second.driver;
+    }
+    ++k;
+  }
+  return k;
+}
+
+const char* mss_batch_last_error(const mss_batch* B) {
+  return B ? B->last_error.c_str() : "null batch";
+}
+
+}  // extern "C"

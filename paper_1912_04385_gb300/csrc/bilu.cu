@@ -769,7 +769,7 @@ void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, con
   const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
   // strips longer than one cell carry in-strip couplings (chain passes)
   const bool chains = !bjac && h->opt.ilu_order == MSS_STRIPS && h->opt.ilu_strip > 1;
-  const int T = 256;
+  const int T = h->tb;   // any multiple of 32: results do not depend on it
   for (int c = 0; c < h->ncol; ++c) {
     const int q0 = h->cstart[c], q1 = h->cstart[c + 1];
     const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];

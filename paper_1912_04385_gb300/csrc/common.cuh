@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <string>
 #include <utility>
+#include <memory>
 #include <vector>
 
 #include "mss.h"
@@ -25,6 +26,10 @@ struct Error {
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 void count_launch();   // process-wide count of this library's kernel launches
 long long launch_count(bool reset);
+void add_launches(long long n);          // launches replayed by a CUDA graph
+// While a stream capture runs on this thread, launches are counted into *c
+// (the captured graph's size) instead of the process-wide count.
+void capture_count(long long* c);
 #define MSS_CK(call) ::mss::check_cuda((call), #call, __FILE__, __LINE__)
 // every kernel launch is followed by MSS_LAUNCH_CK (error check and count)
 #define MSS_LAUNCH_CK(what) \
@@ -45,8 +50,10 @@ enum TraceKind {
 };
 
 struct Handle;
-void* dev_alloc(Handle* h, size_t bytes);
+void* dev_alloc(Handle* h, size_t bytes);   // the handle's hooks, else the device pool
 void dev_free(Handle* h, void* p);
+cudaMemPool_t device_pool(int device);      // library-owned stream-ordered pool
+void trim_pools();                          // return unused pool memory
 
 // Owning device buffer allocated through the handle's hooks.
 template <class T>
@@ -110,9 +117,23 @@ struct Hierarchy {
   bool present() const { return !lev.empty(); }
 };
 
+// A stream the library created; destroyed with its owner (declared first in
+// Handle, so destroyed after every member whose frees are queued on it).
+struct OwnedStream {
+  cudaStream_t s = nullptr;
+  ~OwnedStream() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
 struct Handle {
+  OwnedStream owned;
   // binding
   cudaStream_t stream = nullptr;
+  // Worker handles of the concurrent set-up (T and P hierarchies built on
+  // their own streams and threads, allocating from the device pool). Declared
+  // before the hierarchies they allocate, so they are destroyed after them.
+  std::unique_ptr<Handle> aux[2];
   mss_alloc_fn alloc = nullptr;
   mss_free_fn free_fn = nullptr;
   void* ctx = nullptr;
@@ -123,6 +144,8 @@ struct Handle {
   bool ready = false;
   int N = 0, nb = 0, nnzb = 0, p = 0, t = 1;
   mss_options opt{};
+  int tb = 256;                // threads per CTA of the apply-path kernels (a multiple
+                               // of 32; no result depends on it); set by the autotuner
   mss_bsr J{};                 // the caller's matrix (identity check in solve)
   double setup_ms = 0.0;
   // scaled system
@@ -157,6 +180,16 @@ struct Handle {
   int m = 0;
   DBuf<double> V, Z, bbar, res, hbuf, part;
   DBuf<double> kscal;          // device scalars of the Givens recurrence
+  DBuf<double> gst;            // device solve state (step, counts, status, norms)
+  DBuf<double> rfix, zfix, wfix;   // fixed-address Arnoldi vectors (v_j, z_j, w)
+  // device-driven solve: the whole restarted FGMRES as one CUDA graph with
+  // two nested while-loop conditional nodes, built on first use
+  bool capturing = false;
+  cudaGraphExec_t sgraph = nullptr;
+  int sg_m = 0;
+  long long sg_n = 0;
+  long long sg_launch[4] = {};  // kernels in: init, cycle head, Arnoldi step, cycle tail
+  DBuf<double> gb, gx;          // the graph's own copies of b and x
   DBuf<int> kflag;
   // end-to-end host solve copies
   DBuf<int> host_rp, host_ci;
@@ -174,6 +207,9 @@ struct Handle {
   std::vector<TraceRec> ev_pending;
   double trace_ms[TR_KINDS] = {};
   long long trace_n[TR_KINDS] = {};
+  Handle() = default;
+  Handle(const Handle&) = delete;
+  Handle& operator=(const Handle&) = delete;
   ~Handle();
 };
 
@@ -241,7 +277,9 @@ void scale_vector(Handle* h, const double* b, double* bbar);
 void extract_subsystem(Handle* h, int var, double* out);
 
 // amg_setup.cu
-void amg_build(Handle* h, Hierarchy& H, const double* vals0);
+// level 0: the n0-row CSR (rp0, ci0, vals0), read on h's stream
+void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const int* ci0,
+               const double* vals0);
 
 // amg_cycle.cu
 void vcycle(Handle* h, Hierarchy& H, const double* b, double* x);
@@ -281,6 +319,11 @@ void residual_norm_noalloc(Handle* h, const mss_bsr* J, int nb, const double* b,
 // krylov.cu
 void bsr_spmv(Handle* h, const double* x, double* y);
 void precond_apply(Handle* h, const double* r, double* y);
+// api.cu: the set-up and solve behind mss_setup / mss_fgmres_solve (throw Error)
+void setup_handle(Handle& H, const mss_bsr* J, int nb, mss_layout layout,
+                  const mss_options* opt);
+int solve_handle(Handle& H, const mss_bsr* J, const double* b, double* x, double tol, int maxit,
+                 mss_result* out);
 int fgmres(Handle* h, const double* b, double* x, double tol, int maxit, mss_result* out);
 
 }  // namespace mss

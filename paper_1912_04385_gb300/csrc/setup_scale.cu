@@ -172,34 +172,38 @@ __global__ void k_block_rows(int N, const int* __restrict__ rp, int* __restrict_
   for (int e = rp[i]; e < rp[i + 1]; ++e) brow[e] = i;
 }
 
-// One thread per output entry (block e, r, c), consecutive threads on
-// consecutive entries: Abar_ij[r][c] = sum_k W_i[r][k] J_ij[k][c] (ascending
-// k) for r in {p, t}, a copy for the other rows (their W row is a unit vector).
+// One thread per block column (block e, column c): the rows of W that are
+// not unit vectors (p, and t for CPTR3) give Abar_ij[r][c] = sum_k W_i[r][k]
+// J_ij[k][c] (ascending k); the other rows are copied. Every lane of a warp
+// does the same FP64 work (FP64 issue is the bound of this kernel on GB300).
 template <int NB>
 __global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict__ brow,
                           long long nnzb, int p, int t, int scheme, int col_major,
                           const double* __restrict__ wrows, double* __restrict__ abar) {
   constexpr int B2 = NB * NB;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= nnzb * B2) return;
-  const long long e = tid / B2;
-  const int rc = (int)(tid - e * B2);
-  const int r = rc / NB, c = rc - r * NB;
+  if (tid >= nnzb * NB) return;
+  const long long e = tid / NB;
+  const int c = (int)(tid - e * NB);
   const double* src = vals + (size_t)e * B2;
-  const bool scaled_row = scheme != 2 && (r == p || (scheme == 0 && r == t));
-  double out;
-  if (!scaled_row) {
-    out = col_major ? src[c * NB + r] : src[r * NB + c];
-  } else {
-    const double* w = wrows + (size_t)brow[e] * 2 * NB + (r == p ? 0 : NB);
-    double acc = 0.0;
-    for (int k = 0; k < NB; ++k) {
-      double a = col_major ? src[c * NB + k] : src[k * NB + c];
-      acc = acc + w[k] * a;
-    }
-    out = acc;
+  double col[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) col[k] = col_major ? src[c * NB + k] : src[k * NB + c];
+  double* dst = abar + (size_t)e * B2 + c;
+#pragma unroll
+  for (int r = 0; r < NB; ++r) dst[r * NB] = col[r];
+  if (scheme == 2) return;
+  const double* w = wrows + (size_t)brow[e] * 2 * NB;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) acc = acc + w[k] * col[k];
+  dst[p * NB] = acc;
+  if (scheme == 0) {
+    double acc2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc2 = acc2 + w[NB + k] * col[k];
+    dst[t * NB] = acc2;
   }
-  abar[tid] = out;
 }
 
 template <int NB>
@@ -247,7 +251,7 @@ void build_scaling_nb(Handle* h, const double* vals, bool col_major) {
   DBuf<int> brow(h, h->nnzb);
   k_block_rows<<<grid_for(N, 256), 256, 0, h->stream>>>(N, h->rp.p, brow.p);
   MSS_LAUNCH_CK("k_block_rows");
-  long long tot = (long long)h->nnzb * NB * NB;
+  long long tot = (long long)h->nnzb * NB;
   k_apply_w<NB><<<grid_for(tot, 256), 256, 0, h->stream>>>(vals, brow.p, h->nnzb, h->p, h->t,
                                                            scheme, col_major, h->wrows.p,
                                                            h->abar.p);

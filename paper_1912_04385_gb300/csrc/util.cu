@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -11,7 +12,16 @@ namespace mss {
 [[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long* t_capture_count = nullptr;
+void count_launch() {
+  if (t_capture_count) {
+    ++*t_capture_count;
+    return;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void capture_count(long long* c) { t_capture_count = c; }
 long long launch_count(bool reset) {
   return reset ? g_launches.exchange(0) : g_launches.load();
 }
@@ -28,7 +38,7 @@ static cudaEvent_t take_event(Handle* h) {
 }
 
 TraceScope::TraceScope(Handle* hh, int k) : h(hh), kind(k) {
-  if (!h->trace) return;
+  if (!h->trace || h->capturing) return;   // no event nodes inside a solve graph
   a = take_event(h);
   MSS_CK(cudaEventRecord(a, h->stream));
 }
@@ -55,6 +65,7 @@ void trace_drain(Handle* h) {
 }
 
 Handle::~Handle() {
+  if (sgraph) cudaGraphExecDestroy(sgraph);
   for (auto& r : ev_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -80,10 +91,10 @@ void* dev_alloc(Handle* h, size_t bytes) {
       fail(MSS_ERR_INVALID_ARG, "allocator returned memory not aligned to 256 bytes");
     return p;
   }
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, device_pool(h->device), h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    fail(MSS_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    fail(MSS_ERR_OOM, "pool allocation of " + std::to_string(bytes) + " bytes failed");
   }
   return p;
 }
@@ -91,7 +102,34 @@ void* dev_alloc(Handle* h, size_t bytes) {
 void dev_free(Handle* h, void* p) {
   if (!p) return;
   if (h->free_fn) h->free_fn(p, h->ctx);
-  else cudaFree(p);
+  else cudaFreeAsync(p, h->stream);
+}
+
+// One stream-ordered memory pool per device for handles without hooks (and
+// for the set-up's worker streams). Freed blocks stay in the pool for reuse
+// (release threshold: unlimited) until mss_destroy trims it.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t device_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (dev < 0 || dev >= 64) fail(MSS_ERR_CUDA, "device index out of range");
+  if (!g_pools[dev]) {
+    cudaMemPoolProps pr = {};
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = dev;
+    MSS_CK(cudaMemPoolCreate(&g_pools[dev], &pr));
+    unsigned long long keep = ~0ull;
+    MSS_CK(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+  }
+  return g_pools[dev];
+}
+
+void trim_pools() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (auto& pl : g_pools)
+    if (pl) cudaMemPoolTrimTo(pl, 0);
 }
 
 // ---- exclusive scan (three passes over tiles of SCAN_TILE ints) ------------

@@ -21,13 +21,16 @@ ERR_CUDA, ERR_OOM, ERR_AMG, ERR_NOT_SETUP = -5, -6, -7, -8
 SCHEMES = {"cptr3": 0, "cpr": 1, "ilu0": 2}
 SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+DRIVERS = {"host": 0, "graph": 1}
 
 # every exported symbol declared in include/mss.h
 EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
            "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
            "mss_residual_norm", "mss_residual_norm_noalloc", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
            "mss_bilu_num_colours", "mss_bilu_ordering", "mss_kernel_launches",
-           "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error"]
+           "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error",
+           "mss_batch_create", "mss_batch_destroy", "mss_batch_solve", "mss_batch_tuned",
+           "mss_batch_last_error"]
 
 TRACE_KINDS = {"spmv": 0, "bilu_fwd": 1, "bilu_bwd": 2, "vcycle": 3, "ortho": 4,
                "setup_scale": 5, "setup_amg": 6, "setup_bilu": 7, "apply": 8}
@@ -40,7 +43,7 @@ class Options(C.Structure):
                 ("amg_max_coarse", C.c_int32), ("amg_max_levels", C.c_int32),
                 ("interp_max_elems", C.c_int32), ("restart", C.c_int32),
                 ("precision", C.c_int32), ("ilu_strip", C.c_int32),
-                ("orthog", C.c_int32), ("pad_", C.c_int32),
+                ("orthog", C.c_int32), ("driver", C.c_int32),
                 ("amg_theta", C.c_double), ("jacobi_omega", C.c_double),
                 ("cheb_lo_ratio", C.c_double), ("cheb_hi_factor", C.c_double),
                 ("seed", C.c_uint64), ("learned_interp", C.c_void_p)]
@@ -63,6 +66,19 @@ class Bsr(C.Structure):
 
 class Layout(C.Structure):
     _fields_ = [("p_idx", C.c_int32), ("t_idx", C.c_int32), ("col_major_blocks", C.c_int32)]
+
+
+class System(C.Structure):
+    _fields_ = [("J", Bsr), ("nb", C.c_int32), ("layout", Layout), ("b", C.c_void_p),
+                ("x", C.c_void_p)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("bucket", C.c_int32), ("threads", C.c_int32), ("driver", C.c_int32),
+                ("lane", C.c_int32), ("latency_ms", C.c_double), ("finish_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -110,6 +126,14 @@ def load(path: Path | str | None = None):
     L.mss_status_string.argtypes = [C.c_int]
     L.mss_last_error.restype = C.c_char_p
     L.mss_last_error.argtypes = [P]
+    L.mss_batch_create.argtypes = [C.POINTER(P), C.c_int, C.c_int]
+    L.mss_batch_destroy.argtypes = [P]
+    L.mss_batch_destroy.restype = None
+    L.mss_batch_solve.argtypes = [P, C.c_int, C.POINTER(System), C.POINTER(Options), C.c_double,
+                                  C.c_int, C.POINTER(Result), C.POINTER(BatchInfo)]
+    L.mss_batch_tuned.argtypes = [P, C.c_int, P]
+    L.mss_batch_last_error.restype = C.c_char_p
+    L.mss_batch_last_error.argtypes = [P]
     if path is None:
         _lib = L
     return L
@@ -122,8 +146,8 @@ class MssError(RuntimeError):
 
 
 def options(**kw) -> Options:
-    """Library defaults with keyword overrides (scheme, smoother and precision
-    accept names)."""
+    """Library defaults with keyword overrides (scheme, smoother, precision and
+    driver accept names)."""
     o = Options()
     load().mss_options_default(C.byref(o))
     for k, v in kw.items():
@@ -133,6 +157,8 @@ def options(**kw) -> Options:
             v = SMOOTHERS[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "driver" and isinstance(v, str):
+            v = DRIVERS[v]
         if not hasattr(o, k) or k in ("pad_", "learned_interp"):
             raise KeyError(k)
         setattr(o, k, v)
@@ -351,3 +377,65 @@ class Solver:
         self._check(self.lib.mss_bilu_ordering(self.h, _ptr(colour), _ptr(perm)),
                     "mss_bilu_ordering")
         return nc.value, colour, perm
+
+
+class Batch:
+    """Batched set-up and solve of independent systems (mss_batch_*): `lanes`
+    worker threads, each with its own handle and stream; the autotuner picks
+    threads per CTA and the solve driver per size bucket."""
+
+    def __init__(self, lanes: int = 8, autotune: bool = True):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.b = C.c_void_p()
+        st = self.lib.mss_batch_create(C.byref(self.b), int(lanes), int(autotune))
+        if st != OK:
+            raise MssError(st, "mss_batch_create -> " + self.lib.mss_status_string(st).decode())
+
+    def __del__(self):
+        if getattr(self, "b", None) and self.b.value:
+            self.lib.mss_batch_destroy(self.b)
+            self.b = None
+
+    def solve(self, systems, tol: float = 1e-6, maxit: int = 1000, opts: Options | None = None,
+              **kw):
+        """systems: sequence of dicts with CUDA tensors row_ptr, col_idx (int32),
+        vals, b (float64) and ints nb, p_idx, t_idx; an optional float64 tensor
+        x receives the solution. Returns (xs, results, infos) as lists."""
+        torch = self._torch
+        o = opts if opts is not None else options(**kw)
+        n = len(systems)
+        arr = (System * n)()
+        xs, keep = [], []
+        for i, sd in enumerate(systems):
+            rp, ci, v, b = sd["row_ptr"], sd["col_idx"], sd["vals"], sd["b"]
+            for t in (rp, ci, v, b):
+                if not t.is_cuda or not t.is_contiguous():
+                    raise ValueError("system arrays must be contiguous CUDA tensors")
+            x = sd.get("x")
+            if x is None:
+                x = torch.empty_like(b)
+            xs.append(x)
+            keep.append((rp, ci, v, b, x))
+            arr[i].J = Bsr(rp.numel() - 1, ci.numel(), _ptr(rp), _ptr(ci), _ptr(v))
+            arr[i].nb = int(sd["nb"])
+            arr[i].layout = Layout(int(sd.get("p_idx", 0)), int(sd.get("t_idx", 1)), 0)
+            arr[i].b = _ptr(b)
+            arr[i].x = _ptr(x)
+        res = (Result * max(n, 1))()
+        inf = (BatchInfo * max(n, 1))()
+        st = self.lib.mss_batch_solve(self.b, n, arr, C.byref(o), tol, maxit, res, inf)
+        if st != OK and all(res[i].status == OK for i in range(n)):
+            # the call failed before any system ran (per-system failures are
+            # reported in the results)
+            raise MssError(st, "mss_batch_solve -> " + self.lib.mss_batch_last_error(self.b).decode())
+        del keep
+        return xs, [res[i].as_dict() for i in range(n)], [inf[i].as_dict() for i in range(n)]
+
+    def tuned(self):
+        """[(bucket, nb, threads, driver)] chosen by the autotuner so far."""
+        k = self.lib.mss_batch_tuned(self.b, 0, None)
+        buf = (C.c_int32 * (4 * max(k, 1)))()
+        k = self.lib.mss_batch_tuned(self.b, k, buf)
+        return [tuple(buf[4 * i:4 * i + 4]) for i in range(k)]
