@@ -116,7 +116,11 @@ typedef struct {
   double cheb_lo_ratio;     /* Chebyshev interval [bound/ratio, factor*bound] (30) */
   double cheb_hi_factor;    /* (1.0) */
   uint64_t seed;            /* PMIS measure and colouring priorities */
-  const void* learned_interp; /* reserved, must be NULL */
+  const void* learned_interp; /* NULL: classical interpolation everywhere (default).
+                               Else a device pointer to mss_gnn_num_params()
+                               floats: the network below predicts level 0's
+                               interpolation weights of the temperature
+                               hierarchy (CPTR3 only). Read during mss_setup. */
 } mss_options;
 
 typedef struct {
@@ -352,6 +356,62 @@ int mss_batch_tuned(mss_batch* b, int cap, int32_t* out);
 
 /* Message for the last failing call on `b`. */
 const char* mss_batch_last_error(const mss_batch* b);
+
+/* ---- learned temperature interpolation (not in the paper) -----------------
+ * The paper's temperature stage is classical AMG (Sec. 5.1). Here a
+ * message-passing network of width 32 on the graph of the level-0 temperature
+ * operator A = C_TT predicts a relative correction s_ij of every classical
+ * interpolation weight p_ij (F point i, C point j): w_ij = p_ij (1 + s_ij),
+ * so a network with a zero read-out is classical interpolation exactly.
+ *   x_i  = [a_ii / mean a_kk, sum_j a_ij / a_ii]                (node input)
+ *   e_ij = [a_ij/a_ii, a_ji/a_jj, |a_ij| / max_k|a_ik|, cf_i, cf_j] (edge input)
+ *   H0 = relu(X Wn + bn), G = relu(E We + be)
+ *   l = 1..3: M_i = sum_j G_ij * H_j, H^l = relu([H^{l-1} | M] W_l + b_l)
+ *   z = relu([H3_i | H3_j | G_ij] Wo + bo), s_ij = z . wr + br
+ * Training loss on test vectors e_k (nu damped-Jacobi sweeps on A e = 0 from
+ * given starts): L = sum_k ||A (e_k - P e_k|C)||^2 / sum_k ||A e_k||^2.
+ * Parameters: one float vector, in order Wn 2x32, bn 32, We 5x32, be 32,
+ * W1 64x32, b1 32, W2 64x32, b2 32, W3 64x32, b3 32, Wo 96x32, bo 32, wr 32,
+ * br 1 (matrices row-major [in x out]). Dense layers run on BF16 tensor cores
+ * with FP32 accumulation; the loss is FP64. */
+int mss_gnn_num_params(void);
+
+typedef struct mss_gnn mss_gnn;
+
+/* A training graph from h's current set-up (CPTR3 with at least two
+ * temperature levels): level 0's operator, C/F split and classical
+ * interpolation are copied, so neither later set-ups nor the destruction of
+ * h affect it. The graph has its own stream and takes memory from the
+ * library's device pool. The calls below synchronise the device on entry
+ * (their inputs may come from any stream) and the graph's stream on return.
+ * Errors: NOT_SETUP, INVALID_ARG (no such hierarchy; a pattern without one
+ * diagonal per row or not structurally symmetric). */
+int mss_gnn_create(mss_handle* h, mss_gnn** g);
+void mss_gnn_destroy(mss_gnn* g);
+
+/* nodes n, off-diagonal edges m, interpolation entries t of F rows (host
+ * pointers, may be NULL). */
+int mss_gnn_info(const mss_gnn* g, int32_t* n, int32_t* m, int32_t* t);
+
+/* Test vectors: starts (device, n x K row-major, K in [1, 64]) smoothed by nu
+ * damped-Jacobi sweeps with weight omega. */
+int mss_gnn_set_vectors(mss_gnn* g, int K, const double* starts, int nu, double omega);
+
+/* w (device, t doubles): the learned weights, entries in row order of P. */
+int mss_gnn_weights(mss_gnn* g, const float* params, double* w);
+
+/* loss (host, may be NULL) and its gradient (device, mss_gnn_num_params()
+ * floats, may be NULL) for params (device). Errors: NOT_SETUP without test
+ * vectors. */
+int mss_gnn_loss_grad(mss_gnn* g, const float* params, double* loss, float* grad);
+
+/* One Adam step (Kingma and Ba) on device arrays of mss_gnn_num_params()
+ * floats, on g's stream; step counts from 1. */
+int mss_gnn_adam(mss_gnn* g, float* params, float* m1, float* m2, const float* grad, int step,
+                 float lr, float beta1, float beta2, float eps);
+
+/* Message for the last failing call on `g`. */
+const char* mss_gnn_last_error(const mss_gnn* g);
 
 /* Human-readable name of a status code (static string). */
 const char* mss_status_string(int status);

@@ -13,6 +13,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <memory>
+
 #include "common.cuh"
 
 namespace mss {
@@ -451,7 +453,7 @@ void level_prepare(Handle* h, Level& L) {
 }  // namespace
 
 void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const int* ci0,
-               const double* vals0) {
+               const double* vals0, const float* learned) {
   const mss_options& o = h->opt;
   H.lev.clear();
   H.lev.reserve(32);
@@ -538,6 +540,12 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     k_seg_copy<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, scr_ci.p, scr_v.p, L.prp.p,
                                                         L.pci.p, L.pv.p);
     MSS_LAUNCH_CK("k_seg_copy");
+    if (learned && l == 0) {
+      // learned weights on classical interpolation's pattern (level 0 only)
+      std::unique_ptr<GnnGraph, void (*)(GnnGraph*)> g(
+          gnn_create(h, n, rp, ci, v, L.cf.p, L.prp.p, L.pci.p, L.pv.p, nnz), gnn_destroy);
+      gnn_apply_to_p(g.get(), learned, L.pv.p);
+    }
     transpose(h, n, nc, L.prp.p, L.pci.p, L.pv.p, L.nnzP, L.rrp, L.rci, &L.rv);
     // Galerkin product A_c = R (A P)
     DBuf<int> aprp, apci;

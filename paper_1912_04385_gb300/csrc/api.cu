@@ -7,6 +7,7 @@
 #include <thread>
 #include <exception>
 #include <memory>
+#include <string>
 #include "common.cuh"
 
 struct mss_handle {
@@ -57,7 +58,7 @@ void check_options(const mss_options& o) {
   if (!(o.amg_theta > 0.0 && o.amg_theta <= 1.0)) bad("amg_theta");
   if (!(o.jacobi_omega > 0.0 && o.jacobi_omega < 2.0)) bad("jacobi_omega");
   if (!(o.cheb_lo_ratio > 1.0) || !(o.cheb_hi_factor > 0.0)) bad("Chebyshev interval");
-  if (o.learned_interp != nullptr) bad("learned_interp (reserved)");
+  if (o.learned_interp != nullptr && o.scheme != MSS_CPTR3) bad("learned_interp (CPTR3 only)");
 }
 
 // Worker handle i: its own non-blocking stream, allocations from the device
@@ -213,7 +214,10 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
     if (o.scheme != MSS_ILU0)
       fork.run(0, [&](Handle* a) { amg_build(a, H.amgP, N, nnzb, H.rp.p, H.ci.p, bpp.p); });
     if (o.scheme == MSS_CPTR3)
-      fork.run(1, [&](Handle* a) { amg_build(a, H.amgT, N, nnzb, H.rp.p, H.ci.p, ctt.p); });
+      fork.run(1, [&](Handle* a) {
+        amg_build(a, H.amgT, N, nnzb, H.rp.p, H.ci.p, ctt.p,
+                  static_cast<const float*>(o.learned_interp));
+      });
     std::exception_ptr mine;
     try {
       bilu_setup(h);                              // last stage
@@ -294,6 +298,36 @@ int solve_handle(Handle& H, const mss_bsr* J, const double* b, double* x, double
   return solve_impl(H, J, b, x, tol, maxit, out);
 }
 }  // namespace mss
+
+// The graph owns a private handle (its own stream, memory from the device
+// pool), so it does not depend on the lifetime of the handle it came from.
+struct mss_gnn {
+  std::unique_ptr<Handle> h;
+  GnnGraph* g = nullptr;
+  std::string last_error;
+  ~mss_gnn() {
+    if (h) cudaStreamSynchronize(h->stream);
+    if (g) gnn_destroy(g);
+  }
+};
+
+template <class F>
+static int gnn_guarded(mss_gnn* G, F&& f) {
+  try {
+    f();
+    G->last_error.clear();
+    return MSS_OK;
+  } catch (const Error& e) {
+    G->last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    G->last_error = "host allocation failed";
+    return MSS_ERR_OOM;
+  } catch (...) {
+    G->last_error = "unexpected internal error";
+    return MSS_ERR_CUDA;
+  }
+}
 
 extern "C" {
 
@@ -595,6 +629,84 @@ const char* mss_status_string(int s) {
 const char* mss_last_error(const mss_handle* hh) {
   if (!hh) return "null handle";
   return hh->h.last_error.c_str();
+}
+
+
+/* ---- learned temperature interpolation ------------------------------------ */
+int mss_gnn_num_params(void) { return gnn_num_params(); }
+
+int mss_gnn_create(mss_handle* hh, mss_gnn** out) {
+  if (!hh || !out) return MSS_ERR_INVALID_ARG;
+  *out = nullptr;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    need_ready(H);
+    if (!H.amgT.present() || H.amgT.lev.size() < 2)
+      fail(MSS_ERR_INVALID_ARG, "the set-up has no coarsened temperature hierarchy (CPTR3)");
+    Level& L = H.amgT.lev[0];
+    std::unique_ptr<mss_gnn> G(new mss_gnn());
+    G->h.reset(new Handle());
+    Handle& P = *G->h;
+    P.device = H.device;
+    P.num_sms = H.num_sms;
+    MSS_CK(cudaStreamCreateWithFlags(&P.owned.s, cudaStreamNonBlocking));
+    P.stream = P.owned.s;
+    order_streams(H.stream, P.stream);   // the hierarchy is complete before the copy
+    G->g = gnn_create(&P, L.n, L.rp.p, L.ci.p, L.v.p, L.cf.p, L.prp.p, L.pci.p, L.pv.p, L.nnz);
+    MSS_CK(cudaStreamSynchronize(P.stream));   // nothing of h is read after this
+    *out = G.release();
+  });
+}
+
+void mss_gnn_destroy(mss_gnn* g) { delete g; }
+
+int mss_gnn_info(const mss_gnn* g, int32_t* n, int32_t* m, int32_t* t) {
+  if (!g) return MSS_ERR_INVALID_ARG;
+  if (n) *n = gnn_nodes(g->g);
+  if (m) *m = gnn_edges(g->g);
+  if (t) *t = gnn_entries(g->g);
+  return MSS_OK;
+}
+
+int mss_gnn_set_vectors(mss_gnn* g, int K, const double* starts, int nu, double omega) {
+  if (!g || !starts) return MSS_ERR_INVALID_ARG;
+  return gnn_guarded(g, [&] {
+    MSS_CK(cudaDeviceSynchronize());   // starts may come from any stream
+    gnn_set_vectors(g->g, K, starts, nu, omega);
+    MSS_CK(cudaStreamSynchronize(g->h->stream));
+  });
+}
+
+int mss_gnn_weights(mss_gnn* g, const float* params, double* w) {
+  if (!g || !params || !w) return MSS_ERR_INVALID_ARG;
+  return gnn_guarded(g, [&] {
+    MSS_CK(cudaDeviceSynchronize());
+    gnn_weights(g->g, params, w);
+    MSS_CK(cudaStreamSynchronize(g->h->stream));
+  });
+}
+
+int mss_gnn_loss_grad(mss_gnn* g, const float* params, double* loss, float* grad) {
+  if (!g || !params) return MSS_ERR_INVALID_ARG;
+  return gnn_guarded(g, [&] {
+    MSS_CK(cudaDeviceSynchronize());
+    const double L = gnn_loss_grad(g->g, params, grad);
+    MSS_CK(cudaStreamSynchronize(g->h->stream));
+    if (loss) *loss = L;
+  });
+}
+
+int mss_gnn_adam(mss_gnn* g, float* params, float* m1, float* m2, const float* grad, int step,
+                 float lr, float beta1, float beta2, float eps) {
+  if (!g || !params || !m1 || !m2 || !grad) return MSS_ERR_INVALID_ARG;
+  return gnn_guarded(g, [&] {
+    gnn_adam(g->h.get(), params, m1, m2, grad, step, lr, beta1, beta2, eps);
+    MSS_CK(cudaStreamSynchronize(g->h->stream));
+  });
+}
+
+const char* mss_gnn_last_error(const mss_gnn* g) {
+  return g ? g->last_error.c_str() : "null graph";
 }
 
 }  // extern "C"

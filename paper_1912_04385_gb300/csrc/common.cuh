@@ -279,7 +279,7 @@ void extract_subsystem(Handle* h, int var, double* out);
 // amg_setup.cu
 // level 0: the n0-row CSR (rp0, ci0, vals0), read on h's stream
 void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const int* ci0,
-               const double* vals0);
+               const double* vals0, const float* learned = nullptr);
 
 // amg_cycle.cu
 void vcycle(Handle* h, Hierarchy& H, const double* b, double* x);
@@ -304,6 +304,22 @@ void last_stage_apply(Handle* h, const double* r, const double* xT, const double
 // mixed form: BF16 factor blocks, FP32 sweeps, FP64 r and y
 void last_stage_apply(Handle* h, const double* r, const float* xT, const float* vP, double* y);
 void pack_last_stage_mixed(Handle* h);
+
+// gnn.cu: learned interpolation for the temperature AMG (level 0)
+struct GnnGraph;
+int gnn_num_params();
+GnnGraph* gnn_create(Handle* h, int n, const int* rp, const int* ci, const double* a,
+                     const int* cf, const int* prp, const int* pci, const double* pv, int nnz);
+void gnn_destroy(GnnGraph* g);
+int gnn_entries(const GnnGraph* g);
+int gnn_nodes(const GnnGraph* g);
+int gnn_edges(const GnnGraph* g);
+void gnn_weights(GnnGraph* g, const float* params, double* w);
+void gnn_apply_to_p(GnnGraph* g, const float* params, double* pv);
+void gnn_set_vectors(GnnGraph* g, int K, const double* starts, int nu, double omega);
+double gnn_loss_grad(GnnGraph* g, const float* params, float* grad);
+void gnn_adam(Handle* h, float* params, float* m1, float* m2, const float* grad, int step,
+              float lr, float b1, float b2, float eps);
 
 // residual.cu
 void check_residual_args(const mss_bsr* J, int nb, const double* b, const double* x,

@@ -8,6 +8,7 @@ CPU or PyTorch fallback.
 from __future__ import annotations
 
 import ctypes as C
+import sys
 from pathlib import Path
 
 import numpy as np
@@ -30,7 +31,9 @@ EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss
            "mss_bilu_num_colours", "mss_bilu_ordering", "mss_kernel_launches",
            "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error",
            "mss_batch_create", "mss_batch_destroy", "mss_batch_solve", "mss_batch_tuned",
-           "mss_batch_last_error"]
+           "mss_batch_last_error", "mss_gnn_num_params", "mss_gnn_create", "mss_gnn_destroy",
+           "mss_gnn_info", "mss_gnn_set_vectors", "mss_gnn_weights", "mss_gnn_loss_grad",
+           "mss_gnn_adam", "mss_gnn_last_error"]
 
 TRACE_KINDS = {"spmv": 0, "bilu_fwd": 1, "bilu_bwd": 2, "vcycle": 3, "ortho": 4,
                "setup_scale": 5, "setup_amg": 6, "setup_bilu": 7, "apply": 8}
@@ -134,6 +137,18 @@ def load(path: Path | str | None = None):
     L.mss_batch_tuned.argtypes = [P, C.c_int, P]
     L.mss_batch_last_error.restype = C.c_char_p
     L.mss_batch_last_error.argtypes = [P]
+    L.mss_gnn_num_params.argtypes = []
+    L.mss_gnn_create.argtypes = [P, C.POINTER(P)]
+    L.mss_gnn_destroy.argtypes = [P]
+    L.mss_gnn_destroy.restype = None
+    L.mss_gnn_info.argtypes = [P, P, P, P]
+    L.mss_gnn_set_vectors.argtypes = [P, C.c_int, P, C.c_int, C.c_double]
+    L.mss_gnn_weights.argtypes = [P, P, P]
+    L.mss_gnn_loss_grad.argtypes = [P, P, P, P]
+    L.mss_gnn_adam.argtypes = [P, P, P, P, P, C.c_int, C.c_float, C.c_float, C.c_float,
+                               C.c_float]
+    L.mss_gnn_last_error.restype = C.c_char_p
+    L.mss_gnn_last_error.argtypes = [P]
     if path is None:
         _lib = L
     return L
@@ -159,7 +174,12 @@ def options(**kw) -> Options:
             v = PRECISIONS[v]
         if k == "driver" and isinstance(v, str):
             v = DRIVERS[v]
-        if not hasattr(o, k) or k in ("pad_", "learned_interp"):
+        if k == "learned_interp" and v is not None and not isinstance(v, int):
+            # a float32 CUDA tensor of mss_gnn_num_params() parameters
+            if v.dtype.is_floating_point is False or v.element_size() != 4 or not v.is_cuda:
+                raise ValueError("learned_interp must be a float32 CUDA tensor")
+            v = v.data_ptr()
+        if not hasattr(o, k) or k == "pad_":
             raise KeyError(k)
         setattr(o, k, v)
     return o
@@ -209,6 +229,8 @@ class Solver:
             self.h = None
 
     def __del__(self):
+        if sys.is_finalizing():   # the hooks would call into a half torn-down torch
+            return
         try:
             self.close()
         except Exception:
@@ -394,6 +416,8 @@ class Batch:
             raise MssError(st, "mss_batch_create -> " + self.lib.mss_status_string(st).decode())
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         if getattr(self, "b", None) and self.b.value:
             self.lib.mss_batch_destroy(self.b)
             self.b = None
@@ -439,3 +463,60 @@ class Batch:
         buf = (C.c_int32 * (4 * max(k, 1)))()
         k = self.lib.mss_batch_tuned(self.b, k, buf)
         return [tuple(buf[4 * i:4 * i + 4]) for i in range(k)]
+
+
+class Gnn:
+    """Training graph of the learned temperature interpolation (mss_gnn_*),
+    copied from a Solver's current CPTR3 set-up (independent of the Solver
+    afterwards). Parameters are float32 CUDA tensors of num_params() entries."""
+
+    def __init__(self, solver: "Solver"):
+        self.lib = solver.lib
+        self._torch = solver._torch
+        self.g = C.c_void_p()
+        solver._check(self.lib.mss_gnn_create(solver.h, C.byref(self.g)), "mss_gnn_create")
+        n, m, t = C.c_int32(), C.c_int32(), C.c_int32()
+        self.lib.mss_gnn_info(self.g, C.byref(n), C.byref(m), C.byref(t))
+        self.n, self.m, self.t = n.value, m.value, t.value
+
+    @staticmethod
+    def num_params() -> int:
+        return int(load().mss_gnn_num_params())
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        if getattr(self, "g", None) and self.g.value:
+            self.lib.mss_gnn_destroy(self.g)
+            self.g = None
+
+    def _check(self, st, what):
+        if st != OK:
+            raise MssError(st, f"{what} -> {self.lib.mss_status_string(st).decode()}: "
+                               f"{self.lib.mss_gnn_last_error(self.g).decode()}")
+
+    def set_vectors(self, starts, nu: int = 10, omega: float = 2.0 / 3.0):
+        """starts: float64 CUDA tensor (n, K)."""
+        torch = self._torch
+        starts = starts.contiguous()
+        if not starts.is_cuda or starts.dtype != torch.float64 or starts.shape[0] != self.n:
+            raise ValueError("starts must be a float64 CUDA tensor of shape (n, K)")
+        self._check(self.lib.mss_gnn_set_vectors(self.g, starts.shape[1], _ptr(starts), nu,
+                                                 omega), "mss_gnn_set_vectors")
+
+    def weights(self, params):
+        w = self._torch.empty(max(self.t, 1), dtype=self._torch.float64, device="cuda")
+        self._check(self.lib.mss_gnn_weights(self.g, _ptr(params), _ptr(w)), "mss_gnn_weights")
+        return w[:self.t]
+
+    def loss_grad(self, params, grad=None):
+        """(loss, grad): grad is filled when given (float32 CUDA tensor)."""
+        L = C.c_double(0.0)
+        self._check(self.lib.mss_gnn_loss_grad(self.g, _ptr(params), C.byref(L),
+                                               _ptr(grad) if grad is not None else None),
+                    "mss_gnn_loss_grad")
+        return L.value, grad
+
+    def adam(self, params, m1, m2, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self.lib.mss_gnn_adam(self.g, _ptr(params), _ptr(m1), _ptr(m2), _ptr(grad),
+                                          int(step), lr, beta1, beta2, eps), "mss_gnn_adam")
