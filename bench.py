@@ -45,6 +45,8 @@ def args_():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--maxit", type=int, default=1000)
+    ap.add_argument("--driver", default="graph", choices=["host", "graph"],
+                    help="FGMRES driver: host loop, or the whole solve as one CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--mixed-n", type=int, default=2048,
@@ -52,6 +54,7 @@ def args_():
     ap.add_argument("--batch", type=int, default=64,
                     help="systems in the batched-solve comparison (0: skip)")
     ap.add_argument("--batch-lanes", type=int, default=8)
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     return ap.parse_args()
@@ -61,7 +64,7 @@ def workload_config(a):
     return {"workload": f"cptr3-fgmres{a.restart}-{a.n}x{a.n}-nb6", "grid": [a.n, a.n], "nb": 6,
             "cells": a.n * a.n, "pe": list(PES), "sigma": 2.0, "corr_len": 16, "band": True,
             "seed": 0, "tol": a.tol, "scheme": "CPTR3 (T AMG, P AMG, strip-coloured BILU0, strips of 32)",
-            "restart": a.restart,
+            "restart": a.restart, "driver": a.driver,
             "l2": "inputs 1.5 GB per system >> 129 MB L2 (no flush needed)"}
 
 
@@ -174,12 +177,12 @@ def run_ours(a, rank, world, dist):
                     torch.from_numpy(s.vals.reshape(-1)).cuda(), torch.from_numpy(s.b).cuda()))
     torch.cuda.synchronize()
     solver = mss.Solver()
-    opts = mss.options(restart=a.restart)
+    opts = mss.options(restart=a.restart, driver=a.driver)
     stream = torch.cuda.current_stream()
 
-    def step(trace=False, info_out=None):
+    def step(trace=False, info_out=None, o=None):
         for k, (rp, ci, v, b) in enumerate(dev):
-            solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
+            solver.setup(rp, ci, v, 6, 0, 1, opts=opts if o is None else o)
             x, info = solver.solve(b, tol=a.tol, maxit=a.maxit)
             if info["status"] != 0:
                 raise RuntimeError(f"solve failed for Pe={PES[k]}: {info}")
@@ -210,8 +213,16 @@ def run_ours(a, rank, world, dist):
     wall_ms = (time.perf_counter() - t0) * 1e3
     launches = int(lib.mss_kernel_launches(1))
     tr = solver.trace_read(reset=True)
-    solver.trace(False)
     clk = clocks.stop()
+    trace_from = "the timed steps"
+    if a.driver == "graph":
+        # a solve graph holds no events: kernel-class times come from one
+        # host-driven step after the timed region (same kernels, same order)
+        step(o=mss.options(restart=a.restart, driver="host"))
+        torch.cuda.synchronize()
+        tr = solver.trace_read(reset=True)
+        trace_from = "one host-driven step after the timed region"
+    solver.trace(False)
     ms = e0.elapsed_time(e1)
     if dist is not None:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -265,11 +276,16 @@ def run_ours(a, rank, world, dist):
            "gpu_launches": launches,
            "roofline": roofline,
            "trace_ms": {k: [v[0], round(v[1], 3)] for k, v in tr.items()},
+           "trace_from": trace_from,
            "clocks": clk}
     bytes_apply = apply_alg_bytes(N, nnzb, 6, solver)
     out["precond_gbs"] = round(bytes_apply / (apply_ms / max(n_apply, 1) * 1e-3) / 1e9, 1)
     out["precond_alg_bytes"] = bytes_apply
 
+    # end to end through the C-ABI from pinned host buffers (right after the
+    # timed region, before the other legs fill the allocators)
+    if not a.no_e2e:
+        out["e2e"] = e2e(a, sysl, solver, opts, torch)
     # the same workload with the mixed-precision preconditioner
     if not a.no_mixed:
         out["mixed"] = mixed_leg(a, dev, solver, torch, stream)
@@ -277,9 +293,8 @@ def run_ours(a, rank, world, dist):
             out["mixed_config"] = mixed_config_leg(a, solver, torch, stream)
     if a.batch > 0:
         out["batch"] = batch_leg(a, torch)
-    # end to end through the C-ABI from pinned host buffers
-    if not a.no_e2e:
-        out["e2e"] = e2e(a, sysl, solver, opts, torch)
+    if not a.no_learned:
+        out["learned"] = learned_leg(a, dev, torch, stream)
     # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, sysl[1], steps=1)
@@ -392,6 +407,51 @@ def mixed_config_leg(a, solver, torch, stream):
     res["speedup_mixed_over_fp64"] = round(res["fp64"]["ms"] / res["mixed"]["ms"], 3)
     res["reference_iters"] = ir["iters"]
     return res
+
+
+def learned_leg(a, dev, torch, stream):
+    """Learned temperature interpolation against classical interpolation on the
+    1024x1024 systems at Pe 0.1 and 1000 (set-up + solve to the bench
+    tolerance, timed with CUDA events on the same stream)."""
+    from paper_1912_04385_gb300 import mss
+    path = ROOT / "paper_1912_04385_gb300" / "gnn_t_interp.npz"
+    if not path.exists():
+        return {"unavailable": "no trained parameters (paper_1912_04385_gb300/gnn_t_interp.npz)"}
+    z = np.load(path)
+    trained = torch.from_numpy(z["params_trained"] if "params_trained" in z else z["params"]).cuda()
+    selected = torch.from_numpy(z["params"]).cuda()
+    meta = json.loads(str(z["meta"]))
+    solver = mss.Solver()
+    out = {"params": "paper_1912_04385_gb300/gnn_t_interp.npz",
+           "trained_on": f"{meta['systems']} systems of {meta['grid']}x{meta['grid']}, "
+                         f"{meta['epochs']} epochs, loss norm {meta.get('norm', 'A')}",
+           "loss_first_last": [meta["loss_history"][0], meta["loss_history"][-1]],
+           "validation": meta["validation"],
+           "fallback_to_classical": meta["fallback_to_classical"], "systems": []}
+    for k, pe in enumerate(PES):
+        if pe not in (0.1, 1000.0):
+            continue
+        rp, ci, v, b = dev[k]
+        row = {"pe": pe}
+        for name, kw in (("classical", {}), ("trained", {"learned_interp": trained}),
+                         ("selected", {"learned_interp": selected})):
+            opts = mss.options(restart=a.restart, **kw)
+            solver.setup(rp, ci, v, 6, 0, 1, opts=opts)          # warm-up
+            solver.solve(b, tol=a.tol, maxit=a.maxit)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
+            x, info = solver.solve(b, tol=a.tol, maxit=a.maxit)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name] = {"iters": info["iters"], "ms": round(e0.elapsed_time(e1), 3),
+                         "status": info["status"]}
+        # fallback: classical whenever the trained network needs more iterations
+        better = row["trained"]["iters"] < row["classical"]["iters"]
+        row["with_fallback"] = dict(row["trained" if better else "classical"],
+                                    uses="trained" if better else "classical")
+        out["systems"].append(row)
+    return out
 
 
 def batch_systems(a):

@@ -369,7 +369,10 @@ const char* mss_batch_last_error(const mss_batch* b);
  *   l = 1..3: M_i = sum_j G_ij * H_j, H^l = relu([H^{l-1} | M] W_l + b_l)
  *   z = relu([H3_i | H3_j | G_ij] Wo + bo), s_ij = z . wr + br
  * Training loss on test vectors e_k (nu damped-Jacobi sweeps on A e = 0 from
- * given starts): L = sum_k ||A (e_k - P e_k|C)||^2 / sum_k ||A e_k||^2.
+ * given starts) with the defect d_k = e_k - P e_k|C (zero at C points):
+ * norm 0: L = sum_k ||A d_k||^2 / sum_k ||A e_k||^2 (residual);
+ * norm 1: L = sum_k sum_i |a_ii| d_ki^2 / sum_k sum_i |a_ii| e_ki^2 (the
+ * least-squares interpolation criterion of bootstrap AMG).
  * Parameters: one float vector, in order Wn 2x32, bn 32, We 5x32, be 32,
  * W1 64x32, b1 32, W2 64x32, b2 32, W3 64x32, b3 32, Wo 96x32, bo 32, wr 32,
  * br 1 (matrices row-major [in x out]). Dense layers run on BF16 tensor cores
@@ -394,8 +397,9 @@ void mss_gnn_destroy(mss_gnn* g);
 int mss_gnn_info(const mss_gnn* g, int32_t* n, int32_t* m, int32_t* t);
 
 /* Test vectors: starts (device, n x K row-major, K in [1, 64]) smoothed by nu
- * damped-Jacobi sweeps with weight omega. */
-int mss_gnn_set_vectors(mss_gnn* g, int K, const double* starts, int nu, double omega);
+ * damped-Jacobi sweeps with weight omega; norm selects the loss (0 or 1). */
+int mss_gnn_set_vectors(mss_gnn* g, int K, const double* starts, int nu, double omega,
+                        int norm);
 
 /* w (device, t doubles): the learned weights, entries in row order of P. */
 int mss_gnn_weights(mss_gnn* g, const float* params, double* w);

@@ -22,9 +22,10 @@ Network (width 32, every matrix product written out below):
                     z = relu([H3_i | H3_j | G_ij] Wo + bo),  s_ij = z . wr + br
 Loss (least-squares interpolation of smooth vectors, as in bootstrap AMG):
   test vectors e_k: nu damped-Jacobi sweeps on A e = 0 from the given starts;
-  d_k = e_k - P (e_k restricted to C) (zero at C points); r_k = A d_k;
-  L = sum_k ||r_k||^2 / sum_k ||A e_k||^2  (the denominator does not depend on
-  the parameters).
+  d_k = e_k - P (e_k restricted to C) (zero at C points);
+  norm "A": L = sum_k ||A d_k||^2 / sum_k ||A e_k||^2 (residual of the defect);
+  norm "D": L = sum_k sum_i |a_ii| d_ki^2 / sum_k sum_i |a_ii| e_ki^2.
+  The denominators do not depend on the parameters.
 
 Parameter vector layout (float, this order): Wn 2x32, bn 32, We 5x32, be 32,
 W1 64x32, b1 32, W2 64x32, b2 32, W3 64x32, b3 32, Wo 96x32, bo 32, wr 32, br 1.
@@ -184,22 +185,34 @@ def _residuals(w, g: Graph, evecs):
     return d, g.matvec(d)
 
 
-def loss(theta, g: Graph, evecs):
+def _op(g: Graph, x, norm):
+    """A x for the residual norm, |D|^(1/2) x for the diagonal norm."""
+    return g.matvec(x) if norm == "A" else np.sqrt(np.abs(g.diag))[:, None] * x
+
+
+def _op_t(g: Graph, x, norm):
+    return g.rmatvec(x) if norm == "A" else np.sqrt(np.abs(g.diag))[:, None] * x
+
+
+def loss(theta, g: Graph, evecs, norm="A"):
+    """norm "A": sum ||A d||^2 / sum ||A e||^2; "D": sum |a_ii| d^2 / sum |a_ii| e^2."""
     w = weights(theta, g)
-    _, r = _residuals(w, g, evecs)
-    den = np.sum(g.matvec(evecs) ** 2)
+    d, _ = _residuals(w, g, evecs)
+    r = _op(g, d, norm)
+    den = np.sum(_op(g, evecs, norm) ** 2)
     return float(np.sum(r ** 2) / den)
 
 
-def loss_and_grad(theta, g: Graph, evecs):
+def loss_and_grad(theta, g: Graph, evecs, norm="A"):
     """L and dL/dtheta by reverse-mode differentiation of forward()."""
     s, c = forward(theta, g)
     p = c["p"]
     w = g.tp * (1.0 + s)
-    d, r = _residuals(w, g, evecs)
-    den = np.sum(g.matvec(evecs) ** 2)
+    d, _ = _residuals(w, g, evecs)
+    r = _op(g, d, norm)
+    den = np.sum(_op(g, evecs, norm) ** 2)
     L = float(np.sum(r ** 2) / den)
-    dd = g.rmatvec(2.0 * r / den)                     # dL/dd
+    dd = _op_t(g, 2.0 * r / den, norm)               # dL/dd
     dd[g.cf == 1] = 0.0
     dw = -np.sum(dd[g.ti] * evecs[g.tj], axis=1)      # d_i = e_i - sum_j w_ij e_j
     ds = dw * g.tp

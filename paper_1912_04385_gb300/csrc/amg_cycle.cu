@@ -26,7 +26,10 @@ namespace {
 // M is the n x 2n augmented matrix [A | I] (row-major). Every block finds
 // the pivot of column k itself (same data, same decision); rows are not
 // swapped, the pivot row of column k is recorded instead. One grid-wide
-// barrier per column.
+// barrier per column. The identity half is stored by pivot order: slot k
+// holds the identity column of the k-th pivot row, which only becomes nonzero
+// when that row is chosen, so step k touches the left columns > k and the
+// slots <= k, n entries per row (n^3 multiply-adds in all, not 1.5 n^3).
 __global__ void k_gauss_jordan(int n, double* __restrict__ M, int* __restrict__ pivrow,
                                int* __restrict__ status) {
   extern __shared__ unsigned char used[];   // n flags, per block
@@ -70,7 +73,10 @@ __global__ void k_gauss_jordan(int n, double* __restrict__ M, int* __restrict__ 
       return;   // every block reaches the same decision, so none waits below
     }
     if (threadIdx.x == 0) used[p] = 1;
-    if (blockIdx.x == 0 && threadIdx.x == 0) pivrow[k] = p;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      pivrow[k] = p;
+      M[(size_t)p * ld + n + k] = 1.0;   // read from the next step on
+    }
     const double* prow = M + (size_t)p * ld;
     const double pk = prow[k];
     for (int i = gwarp; i < n; i += nwarps) {
@@ -78,20 +84,29 @@ __global__ void k_gauss_jordan(int n, double* __restrict__ M, int* __restrict__ 
       double* row = M + (size_t)i * ld;
       const double f = row[k] / pk;
       if (f == 0.0) continue;
-      for (int j = k + 1 + lane; j < ld; j += 32) row[j] = fma(-f, prow[j], row[j]);
+      // left columns k+1..n-1 and slots 0..k-1; slot k: 0 - f * 1
+      for (int j = k + 1 + lane; j < n + k; j += 32) row[j] = fma(-f, prow[j], row[j]);
+      if (lane == 0) row[n + k] = -f;
     }
     grid.sync();
     __syncthreads();
   }
 }
 
+// slot[c] = the step at which row c was the pivot
+__global__ void k_gj_slots(int n, const int* __restrict__ pivrow, int* __restrict__ slot) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) slot[pivrow[k]] = k;
+}
+
+// inv[k][c] = (identity column c of the pivot row of column k) / pivot
 __global__ void k_gj_extract(int n, const double* __restrict__ M, const int* __restrict__ pivrow,
-                             double* __restrict__ inv) {
+                             const int* __restrict__ slot, double* __restrict__ inv) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (long long)n * n) return;
   int k = (int)(tid / n), c = (int)(tid % n);
   int p = pivrow[k];
-  inv[tid] = M[(size_t)p * 2 * n + n + c] / M[(size_t)p * 2 * n + k];
+  inv[tid] = M[(size_t)p * 2 * n + n + slot[c]] / M[(size_t)p * 2 * n + k];
 }
 
 __global__ void k_dense_from_csr(int n, const int* __restrict__ rp, const int* __restrict__ ci,
@@ -100,7 +115,6 @@ __global__ void k_dense_from_csr(int n, const int* __restrict__ rp, const int* _
   if (i >= n) return;
   double* row = M + (size_t)i * 2 * n;
   for (int k = rp[i]; k < rp[i + 1]; ++k) row[ci[k]] = v[k];
-  row[n + i] = 1.0;
 }
 
 // ---- V-cycle kernels ----------------------------------------------------
@@ -417,7 +431,10 @@ void coarse_inverse(Handle* h, Hierarchy& H) {
   }
   if (st != 0) fail(MSS_ERR_AMG, "coarsest AMG operator is singular (column " +
                                      std::to_string(st - 1) + ")");
-  k_gj_extract<<<grid_for((long long)n * n, 256), 256, 0, h->stream>>>(n, M.p, piv.p,
+  DBuf<int> slot(h, n);
+  k_gj_slots<<<grid_for(n, 256), 256, 0, h->stream>>>(n, piv.p, slot.p);
+  MSS_LAUNCH_CK("k_gj_slots");
+  k_gj_extract<<<grid_for((long long)n * n, 256), 256, 0, h->stream>>>(n, M.p, piv.p, slot.p,
                                                                        H.coarse_inv.p);
   MSS_LAUNCH_CK("k_gj_extract");
 }

@@ -668,11 +668,12 @@ int mss_gnn_info(const mss_gnn* g, int32_t* n, int32_t* m, int32_t* t) {
   return MSS_OK;
 }
 
-int mss_gnn_set_vectors(mss_gnn* g, int K, const double* starts, int nu, double omega) {
+int mss_gnn_set_vectors(mss_gnn* g, int K, const double* starts, int nu, double omega,
+                        int norm) {
   if (!g || !starts) return MSS_ERR_INVALID_ARG;
   return gnn_guarded(g, [&] {
     MSS_CK(cudaDeviceSynchronize());   // starts may come from any stream
-    gnn_set_vectors(g->g, K, starts, nu, omega);
+    gnn_set_vectors(g->g, K, starts, nu, omega, norm);
     MSS_CK(cudaStreamSynchronize(g->h->stream));
   });
 }

@@ -316,7 +316,7 @@ int gnn_nodes(const GnnGraph* g);
 int gnn_edges(const GnnGraph* g);
 void gnn_weights(GnnGraph* g, const float* params, double* w);
 void gnn_apply_to_p(GnnGraph* g, const float* params, double* pv);
-void gnn_set_vectors(GnnGraph* g, int K, const double* starts, int nu, double omega);
+void gnn_set_vectors(GnnGraph* g, int K, const double* starts, int nu, double omega, int norm);
 double gnn_loss_grad(GnnGraph* g, const float* params, float* grad);
 void gnn_adam(Handle* h, float* params, float* m1, float* m2, const float* grad, int step,
               float lr, float b1, float b2, float eps);

@@ -11,8 +11,11 @@
 //   H0 = relu(X Wn + bn), G = relu(E We + be)
 //   l = 1..3: M_i = sum_j G_ij * H_j (elementwise), H^l = relu([H | M] W_l + b_l)
 //   z = relu([H3_i | H3_j | G_ij] Wo + bo), s_ij = z . wr + br
-// Loss over smooth test vectors e_k (damped Jacobi on A e = 0):
-//   L = sum_k ||A (e_k - P e_k|C)||^2 / sum_k ||A e_k||^2.
+// Loss over smooth test vectors e_k (damped Jacobi on A e = 0), with the
+// defect d_k = e_k - P e_k|C:
+//   residual norm:    L = sum_k ||A d_k||^2 / sum_k ||A e_k||^2, or
+//   diagonal norm:    L = sum_k sum_i |a_ii| d_ki^2 / sum_k sum_i |a_ii| e_ki^2
+//   (the least-squares interpolation criterion of bootstrap AMG).
 //
 // Dense layers run on the tensor cores (mma.sync m16n8k16, BF16 operands,
 // FP32 accumulation) with every FP32 operand split into two BF16 parts
@@ -406,7 +409,7 @@ __global__ void k_gnn_defect(int n, int K, const int* __restrict__ cf, const int
   d[id] = v;
 }
 
-// y = A x (trans = 0) or A^T x (trans = 1) for K columns, with partial sums of y^2
+// y = A x (mode 0), A^T x (mode 1) or |D|^(1/2) x (mode 2) for K columns
 __global__ void k_gnn_spmm(int n, int K, const int* __restrict__ rp, const int* __restrict__ ecol,
                            const double* __restrict__ eval, const int* __restrict__ rev,
                            const double* __restrict__ diag, const double* __restrict__ x,
@@ -414,6 +417,10 @@ __global__ void k_gnn_spmm(int n, int K, const int* __restrict__ rp, const int* 
   long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long long)n * K) return;
   const int i = (int)(id / K), k = (int)(id % K);
+  if (trans == 2) {
+    y[id] = sqrt(fabs(diag[i])) * x[id];
+    return;
+  }
   double v = diag[i] * x[id];
   for (int e = rp[i] - i; e < rp[i + 1] - i - 1; ++e) {
     const double a = trans ? eval[rev[e]] : eval[e];
@@ -593,6 +600,7 @@ struct GnnGraph {
   int n = 0, m = 0, T = 0, K = 0;
   DBuf<int> rp, ecol, rev, cf, trp, ti, tj, te, tpos, flag;
   DBuf<double> eval, diag, dmean, tp, ev, d, r, dd, scal;
+  int norm = 0;   // loss norm: 0 ||A d||^2 (residual), 1 sum |a_ii| d_i^2 (interpolation error)
   DBuf<float> X0, E, IN1, IN2, IN3, H3, G, R, Z, s, ds, dZ, dR, dH, dY, dIN, dG, dYe;
   DBuf<__nv_bfloat16> wt, wb;   // packed BF16 weights (forward / backward copies)
   explicit GnnGraph(Handle* hh) : h(hh) {}
@@ -773,10 +781,12 @@ void gnn_apply_to_p(GnnGraph* g, const float* prm, double* pv) {
   MSS_LAUNCH_CK("k_gnn_write_p");
 }
 
-void gnn_set_vectors(GnnGraph* gg, int K, const double* starts, int nu, double omega) {
+void gnn_set_vectors(GnnGraph* gg, int K, const double* starts, int nu, double omega, int norm) {
   GnnGraph& g = *gg;
   Handle* h = g.h;
   if (K < 1 || K > 64 || nu < 0) fail(MSS_ERR_INVALID_ARG, "K in [1, 64] and nu >= 0");
+  if (norm != 0 && norm != 1) fail(MSS_ERR_INVALID_ARG, "loss norm 0 (residual) or 1 (diagonal)");
+  g.norm = norm;
   const long long len = (long long)g.n * K;
   g.K = K;
   g.ev.reset(h, len);
@@ -792,9 +802,10 @@ void gnn_set_vectors(GnnGraph* gg, int K, const double* starts, int nu, double o
   g.r.reset(h, len);
   g.dd.reset(h, len);
   g.scal.reset(h, 2);
-  // denominator sum_k ||A e_k||^2
+  // denominator sum_k ||op e_k||^2, op = A or |D|^(1/2)
   k_gnn_spmm<<<grid_for(len, 256), 256, 0, h->stream>>>(g.n, K, g.rp.p, g.ecol.p, g.eval.p,
-                                                        g.rev.p, g.diag.p, g.ev.p, g.r.p, 0);
+                                                        g.rev.p, g.diag.p, g.ev.p, g.r.p,
+                                                        norm ? 2 : 0);
   MSS_LAUNCH_CK("k_gnn_spmm");
   k_gnn_sumsq<<<1, 256, 0, h->stream>>>(len, g.r.p, 1.0, g.scal.p + 1);
   MSS_LAUNCH_CK("k_gnn_sumsq");
@@ -811,7 +822,8 @@ double gnn_loss_grad(GnnGraph* gg, const float* prm, float* grad) {
                                                          g.ev.p, g.d.p);
   MSS_LAUNCH_CK("k_gnn_defect");
   k_gnn_spmm<<<grid_for(len, 256), 256, 0, h->stream>>>(g.n, g.K, g.rp.p, g.ecol.p, g.eval.p,
-                                                       g.rev.p, g.diag.p, g.d.p, g.r.p, 0);
+                                                       g.rev.p, g.diag.p, g.d.p, g.r.p,
+                                                       g.norm ? 2 : 0);
   MSS_LAUNCH_CK("k_gnn_spmm");
   k_gnn_sumsq<<<1, 256, 0, h->stream>>>(len, g.r.p, 1.0, g.scal.p);
   MSS_LAUNCH_CK("k_gnn_sumsq");
@@ -820,11 +832,12 @@ double gnn_loss_grad(GnnGraph* gg, const float* prm, float* grad) {
   MSS_CK(cudaStreamSynchronize(h->stream));
   const double L = sc[0] / sc[1];
   if (!grad) return L;
-  // dL/dd = A^T (2 r / den)
+  // dL/dd = op^T (2 r / den)
   k_gnn_scale<<<grid_for(len, 256), 256, 0, h->stream>>>(len, g.r.p, g.scal.p + 1, 2.0);
   MSS_LAUNCH_CK("k_gnn_scale");
   k_gnn_spmm<<<grid_for(len, 256), 256, 0, h->stream>>>(g.n, g.K, g.rp.p, g.ecol.p, g.eval.p,
-                                                       g.rev.p, g.diag.p, g.r.p, g.dd.p, 1);
+                                                       g.rev.p, g.diag.p, g.r.p, g.dd.p,
+                                                       g.norm ? 2 : 1);
   MSS_LAUNCH_CK("k_gnn_spmm");
   MSS_CK(cudaMemsetAsync(grad, 0, sizeof(float) * gp::total, h->stream));
   const size_t T1 = g.T > 0 ? g.T : 1, m1 = g.m > 0 ? g.m : 1;

@@ -142,7 +142,7 @@ def load(path: Path | str | None = None):
     L.mss_gnn_destroy.argtypes = [P]
     L.mss_gnn_destroy.restype = None
     L.mss_gnn_info.argtypes = [P, P, P, P]
-    L.mss_gnn_set_vectors.argtypes = [P, C.c_int, P, C.c_int, C.c_double]
+    L.mss_gnn_set_vectors.argtypes = [P, C.c_int, P, C.c_int, C.c_double, C.c_int]
     L.mss_gnn_weights.argtypes = [P, P, P]
     L.mss_gnn_loss_grad.argtypes = [P, P, P, P]
     L.mss_gnn_adam.argtypes = [P, P, P, P, P, C.c_int, C.c_float, C.c_float, C.c_float,
@@ -495,14 +495,16 @@ class Gnn:
             raise MssError(st, f"{what} -> {self.lib.mss_status_string(st).decode()}: "
                                f"{self.lib.mss_gnn_last_error(self.g).decode()}")
 
-    def set_vectors(self, starts, nu: int = 10, omega: float = 2.0 / 3.0):
-        """starts: float64 CUDA tensor (n, K)."""
+    def set_vectors(self, starts, nu: int = 10, omega: float = 2.0 / 3.0, norm: str = "A"):
+        """starts: float64 CUDA tensor (n, K); norm "A" (residual) or "D"
+        (diagonal-weighted interpolation error)."""
         torch = self._torch
         starts = starts.contiguous()
         if not starts.is_cuda or starts.dtype != torch.float64 or starts.shape[0] != self.n:
             raise ValueError("starts must be a float64 CUDA tensor of shape (n, K)")
         self._check(self.lib.mss_gnn_set_vectors(self.g, starts.shape[1], _ptr(starts), nu,
-                                                 omega), "mss_gnn_set_vectors")
+                                                 omega, {"A": 0, "D": 1}[norm]),
+                    "mss_gnn_set_vectors")
 
     def weights(self, params):
         w = self._torch.empty(max(self.t, 1), dtype=self._torch.float64, device="cuda")

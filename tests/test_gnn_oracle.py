@@ -25,13 +25,14 @@ def _graph(nx=9, ny=7, nb=4, pe=10.0, seed=2):
     return gnn.Graph(*L0.A, L0.cf, *L0.P)
 
 
-def test_gradient_matches_finite_differences():
+@pytest.mark.parametrize("norm", ["A", "D"])
+def test_gradient_matches_finite_differences(norm):
     g = _graph()
     th = gnn.init_params(1, readout_scale=1.0)
     rng = np.random.default_rng(0)
     ev = gnn.smooth_vectors(g, rng.standard_normal((g.n, 3)))
-    L, gr = gnn.loss_and_grad(th, g, ev)
-    assert np.isclose(L, gnn.loss(th, g, ev), rtol=1e-14)
+    L, gr = gnn.loss_and_grad(th, g, ev, norm)
+    assert np.isclose(L, gnn.loss(th, g, ev, norm), rtol=1e-14)
     # a few parameters of every group
     offs = np.cumsum([0] + [int(np.prod(s)) for _, s in gnn.SHAPES])
     idx = np.concatenate([rng.choice(np.arange(offs[k], offs[k + 1]), min(6, offs[k + 1] - offs[k]),
@@ -43,7 +44,7 @@ def test_gradient_matches_finite_differences():
         tm = th.copy()
         tp[k] += h
         tm[k] -= h
-        fd = (gnn.loss(tp, g, ev) - gnn.loss(tm, g, ev)) / (2 * h)
+        fd = (gnn.loss(tp, g, ev, norm) - gnn.loss(tm, g, ev, norm)) / (2 * h)
         assert abs(fd - gr[k]) <= 1e-6 * max(abs(gr[k]), 1e-2 * scale), (k, fd, gr[k])
 
 
@@ -74,6 +75,9 @@ def test_loss_zero_in_range_of_p_and_full_defect():
     dF[g.cf == 1] = 0.0
     want = np.sum(g.matvec(dF) ** 2) / np.sum(g.matvec(e2) ** 2)
     assert np.isclose(gnn.loss(th2, g, e2), want, rtol=1e-13)
+    dg = np.abs(g.diag)[:, None]
+    want_d = np.sum(dg * dF ** 2) / np.sum(dg * e2 ** 2)
+    assert np.isclose(gnn.loss(th2, g, e2, "D"), want_d, rtol=1e-13)
 
 
 def test_features_of_1d_laplacian():

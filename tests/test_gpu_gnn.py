@@ -53,8 +53,8 @@ def _params(seed, scale):
     return th32, torch.from_numpy(th32).cuda()
 
 
-@pytest.mark.parametrize("case", range(len(CASES)))
-def test_forward_loss_grad_match_oracle(mss, case):
+@pytest.mark.parametrize("case,norm", [(0, "A"), (1, "A"), (0, "D"), (1, "D")])
+def test_forward_loss_grad_match_oracle(mss, case, norm):
     s = _sys(CASES[case])
     g = mss.Solver().setup_system(s, amg_max_coarse=40)
     G = mss.Gnn(g)
@@ -67,14 +67,14 @@ def test_forward_loss_grad_match_oracle(mss, case):
     wo = gnn.weights(th, og)
     ew = np.max(np.abs(w - wo)) / np.max(np.abs(wo))
     starts = np.random.default_rng(case).standard_normal((og.n, 4))
-    G.set_vectors(torch.from_numpy(starts).cuda(), nu=10)
+    G.set_vectors(torch.from_numpy(starts).cuda(), nu=10, norm=norm)
     grad = torch.empty(gnn.NPARAMS, dtype=torch.float32, device="cuda")
     L, _ = G.loss_grad(tht, grad)
     ev = gnn.smooth_vectors(og, starts, nu=10)
-    Lo, go = gnn.loss_and_grad(th, og, ev)
+    Lo, go = gnn.loss_and_grad(th, og, ev, norm)
     gg = grad.cpu().numpy().astype(np.float64)
     eg = np.linalg.norm(gg - go) / np.linalg.norm(go)
-    print(f"case {case}: weights {ew:.2e}, loss {L:.6e} vs {Lo:.6e}, grad {eg:.2e}")
+    print(f"case {case} norm {norm}: weights {ew:.2e}, loss {L:.6e} vs {Lo:.6e}, grad {eg:.2e}")
     assert ew <= 1e-3
     assert abs(L - Lo) <= 1e-4 * Lo
     assert eg <= 1e-3
@@ -136,7 +136,7 @@ def test_adam_lowers_the_loss(mss):
     g = mss.Solver().setup_system(s, amg_max_coarse=40)
     G = mss.Gnn(g)
     rng = np.random.default_rng(9)
-    G.set_vectors(torch.from_numpy(rng.standard_normal((G.n, 8))).cuda(), nu=10)
+    G.set_vectors(torch.from_numpy(rng.standard_normal((G.n, 8))).cuda(), nu=10, norm="D")
     th32, p = _params(5, 0.0)
     m1 = torch.zeros_like(p)
     m2 = torch.zeros_like(p)
@@ -148,3 +148,33 @@ def test_adam_lowers_the_loss(mss):
     L1, _ = G.loss_grad(p, grad)
     print(f"loss {L0:.4e} -> {L1:.4e}")
     assert L1 < 0.97 * L0
+
+
+def test_selection_never_worse_than_classical(mss):
+    # the trained network is kept only if it needs no more iterations than
+    # classical interpolation on the validation systems; otherwise the zero
+    # read-out (classical) is selected -- so the selected form never loses
+    from paper_1912_04385_gb300 import train_gnn as T
+
+    def tup(s):
+        return (s.row_ptr, s.col_idx, np.ascontiguousarray(s.vals).reshape(-1), s.b)
+
+    train = [tup(_sys(dict(nx=40, ny=40, nb=6, pe=pe, sigma=2.0, band=True, seed=20 + k)))
+             for k, pe in enumerate((0.3, 30.0, 300.0, 3.0))]
+    val = [tup(_sys(dict(nx=48, ny=48, nb=6, pe=pe, sigma=2.0, band=True, seed=40 + k)))
+           for k, pe in enumerate((1.0, 500.0))]
+    graphs = T.build_graphs(torch, mss, train, 4, 20, 3, "D")
+    p = torch.from_numpy(T.initial_params(3)).cuda()
+    m1, m2, g = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    step = 0
+    for _ in range(3):
+        for G in graphs:
+            G.loss_grad(p, g)
+            step += 1
+            G.adam(p, m1, m2, g, step, lr=3e-4)
+    sel, it_c, it_l, _, _, fallback = T.select(torch, mss, val, p)
+    its, _ = T.iterations(torch, mss, val, params=torch.from_numpy(sel).cuda())
+    print(f"classical {it_c}, trained {it_l}, selected {its}, fallback {fallback}")
+    assert sum(its) <= sum(it_c)
+    if fallback:
+        assert its == it_c
