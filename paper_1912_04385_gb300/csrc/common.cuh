@@ -213,11 +213,13 @@ struct Handle {
   ~Handle();
 };
 
-// Records an event pair around its lifetime when tracing is on.
+// Records an event pair around its lifetime when tracing is on, and always
+// an NVTX range named after the kind (outside stream capture).
 struct TraceScope {
   Handle* h;
   int kind;
   cudaEvent_t a = nullptr;
+  bool ranged = false;        // an NVTX range was pushed
   TraceScope(Handle* hh, int k);
   ~TraceScope();
 };

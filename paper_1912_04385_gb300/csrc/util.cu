@@ -5,6 +5,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace mss {
@@ -37,13 +39,23 @@ static cudaEvent_t take_event(Handle* h) {
   return e;
 }
 
+// NVTX range names of the trace kinds (host-side ranges for nsys/ncu timelines;
+// no cost without an attached tool)
+static const char* const kTraceNames[TR_KINDS] = {
+    "mss.spmv", "mss.bilu_fwd", "mss.bilu_bwd", "mss.vcycle", "mss.ortho",
+    "mss.setup_scale", "mss.setup_amg", "mss.setup_bilu", "mss.apply"};
+
 TraceScope::TraceScope(Handle* hh, int k) : h(hh), kind(k) {
-  if (!h->trace || h->capturing) return;   // no event nodes inside a solve graph
+  if (h->capturing) return;   // no event nodes (and no host ranges) inside a solve graph
+  nvtxRangePushA(kTraceNames[k]);
+  ranged = true;
+  if (!h->trace) return;
   a = take_event(h);
   MSS_CK(cudaEventRecord(a, h->stream));
 }
 
 TraceScope::~TraceScope() {
+  if (ranged) nvtxRangePop();
   if (!a) return;
   cudaEvent_t b = take_event(h);
   cudaEventRecord(b, h->stream);
