@@ -209,11 +209,14 @@ int mss_stage_apply(mss_handle* h, int which, const double* r, double* y);
 int mss_fgmres_solve(mss_handle* h, const mss_bsr* J, const double* b, double* x, double tol,
                      int maxit, mss_result* out);
 
-/* End-to-end solve from HOST buffers: copies J (host arrays in an mss_bsr)
- * and b to the device, runs mss_setup and mss_fgmres_solve, and copies x
- * back to the host. Device copies are owned by the handle and released at
- * the next call or in mss_destroy. Errors: as mss_setup and
- * mss_fgmres_solve. */
+/* End-to-end solve from HOST buffers: copies J's pattern (host arrays in an
+ * mss_bsr) and b to the device, runs mss_setup and mss_fgmres_solve, and
+ * copies x back to the host. When J's values are in pinned host memory the
+ * device can address (cudaHostAlloc, cudaHostRegister), the set-up's scaling
+ * kernels read them in place over the host link, without a staging copy; the
+ * host arrays must then stay unchanged until the call returns. Device copies
+ * are owned by the handle and released at the next call or in mss_destroy.
+ * Errors: as mss_setup and mss_fgmres_solve. */
 int mss_solve_host(mss_handle* h, const mss_bsr* J_host, int nb, mss_layout layout,
                    const mss_options* opt, const double* b_host, double* x_host, double tol,
                    int maxit, mss_result* out);

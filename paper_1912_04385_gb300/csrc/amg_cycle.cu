@@ -13,6 +13,9 @@
 #include <cmath>
 #include <cstring>
 
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -115,6 +118,166 @@ __global__ void k_dense_from_csr(int n, const int* __restrict__ rp, const int* _
   if (i >= n) return;
   double* row = M + (size_t)i * 2 * n;
   for (int k = rp[i]; k < rp[i + 1]; ++k) row[ci[k]] = v[k];
+}
+
+// ---- coarse inverse: blocked Gauss-Jordan without pivoting -----------------
+// In-place inversion by b x b blocks (b = 32): for each diagonal block K,
+//   D = A_KK^-1;  A_Kj <- D A_Kj;  A_ij <- A_ij - A_iK A_Kj;  A_iK <- -A_iK D;
+//   A_KK <- D   (i, j outside K),
+// which leaves A^-1 in place after the last block (n^3 multiply-adds). No
+// grid-wide barrier: five ordinary launches per block, so it can run beside
+// the other hierarchy's set-up. Without pivoting it needs every diagonal
+// block's pivots to stay away from zero; a pivot below 1e-10 times its
+// column's magnitude sets *status and the caller falls back to the pivoting
+// Gauss-Jordan above.
+constexpr int GB = 32;     // block size
+constexpr int GT = 64;     // tile of the panel and trailing updates
+
+__global__ void k_dense_square(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                               const double* __restrict__ v, double* __restrict__ M) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double* row = M + (size_t)i * n;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) row[ci[k]] = v[k];
+}
+
+// D = A_KK^-1 by Gauss-Jordan in shared memory (one block of 256 threads)
+__global__ void k_bgj_diag(int n, const double* __restrict__ M, int k0, int kw,
+                           double* __restrict__ D, int* __restrict__ status) {
+  __shared__ double a[GB][GB + 1];
+  __shared__ double cmax[GB];
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
+    const int r = e / GB, c = e % GB;
+    a[r][c] = (r < kw && c < kw) ? M[(size_t)(k0 + r) * n + k0 + c] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (threadIdx.x < GB) {
+    double m = 0.0;
+    for (int r = 0; r < GB; ++r) m = fmax(m, fabs(a[r][threadIdx.x]));
+    cmax[threadIdx.x] = m;
+  }
+  __syncthreads();
+  for (int k = 0; k < GB; ++k) {
+    const double p = a[k][k];
+    const bool bad = !(fabs(p) > 1e-10 * cmax[k]) || !isfinite(p);
+    if (bad) {
+      if (threadIdx.x == 0) atomicExch(status, 1);
+      return;   // the whole block returns: the status is uniform per block
+    }
+    const double ip = 1.0 / p;
+    __syncthreads();
+    // f_r = a[r][k] for r != k, read before the column is overwritten
+    double f[GB * GB / 256 > 0 ? GB * GB / 256 : 1];
+    int t = 0;
+    for (int e = threadIdx.x; e < GB * GB; e += blockDim.x, ++t) {
+      const int r = e / GB;
+      f[t] = a[r][k];
+    }
+    __syncthreads();
+    // pivot row: a[k][c] = a[k][c] / p, a[k][k] = 1 / p
+    if (threadIdx.x < GB) a[k][threadIdx.x] = threadIdx.x == k ? ip : a[k][threadIdx.x] * ip;
+    __syncthreads();
+    t = 0;
+    for (int e = threadIdx.x; e < GB * GB; e += blockDim.x, ++t) {
+      const int r = e / GB, c = e % GB;
+      if (r == k) continue;
+      a[r][c] = c == k ? -f[t] * ip : a[r][c] - f[t] * a[k][c];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) D[e] = a[e / GB][e % GB];
+}
+
+// row panel: A_Kj <- D A_Kj for column tile j (columns of block K skipped)
+__global__ void k_bgj_row(int n, double* __restrict__ M, int k0, int kw,
+                          const double* __restrict__ D) {
+  __shared__ double d[GB][GB];
+  __shared__ double x[GB][GT];
+  const int j0 = blockIdx.x * GT;
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) d[e / GB][e % GB] = D[e];
+  for (int e = threadIdx.x; e < GB * GT; e += blockDim.x) {
+    const int r = e / GT, c = e % GT, j = j0 + c;
+    x[r][c] = (r < kw && j < n) ? M[(size_t)(k0 + r) * n + j] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < GB * GT; e += blockDim.x) {
+    const int r = e / GT, c = e % GT, j = j0 + c;
+    if (r >= kw || j >= n || (j >= k0 && j < k0 + kw)) continue;
+    double s = 0.0;
+    for (int k = 0; k < kw; ++k) s += d[r][k] * x[k][c];
+    M[(size_t)(k0 + r) * n + j] = s;
+  }
+}
+
+// trailing update on a GT x GT tile: A_ij -= A_iK A_Kj (i, j outside block K),
+// each of the 256 threads owns a 4 x 4 patch
+__global__ void k_bgj_trail(int n, double* __restrict__ M, int k0, int kw) {
+  __shared__ double ai[GT][GB + 1];
+  __shared__ double bk[GB][GT];
+  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+  for (int e = threadIdx.x; e < GT * GB; e += blockDim.x) {
+    const int r = e / GB, k = e % GB, i = i0 + r;
+    ai[r][k] = (i < n && k < kw) ? M[(size_t)i * n + k0 + k] : 0.0;
+  }
+  for (int e = threadIdx.x; e < GB * GT; e += blockDim.x) {
+    const int k = e / GT, c = e % GT, j = j0 + c;
+    bk[k][c] = (j < n && k < kw) ? M[(size_t)(k0 + k) * n + j] : 0.0;
+  }
+  __syncthreads();
+  const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
+  double acc[4][4] = {};
+  for (int k = 0; k < kw; ++k) {
+    double av[4], bv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      av[u] = ai[tr + u][k];
+      bv[u] = bk[k][tc + u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[u][w] = fma(av[u], bv[w], acc[u][w]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tr + u;
+    if (i >= n || (i >= k0 && i < k0 + kw)) continue;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int j = j0 + tc + w;
+      if (j >= n || (j >= k0 && j < k0 + kw)) continue;
+      M[(size_t)i * n + j] -= acc[u][w];
+    }
+  }
+}
+
+// column panel: A_iK <- -A_iK D for row tile i (rows of block K skipped)
+__global__ void k_bgj_col(int n, double* __restrict__ M, int k0, int kw,
+                          const double* __restrict__ D) {
+  __shared__ double d[GB][GB];
+  __shared__ double x[GT][GB + 1];
+  const int i0 = blockIdx.x * GT;
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) d[e / GB][e % GB] = D[e];
+  for (int e = threadIdx.x; e < GT * GB; e += blockDim.x) {
+    const int r = e / GB, c = e % GB, i = i0 + r;
+    x[r][c] = (i < n && c < kw) ? M[(size_t)i * n + k0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < GT * GB; e += blockDim.x) {
+    const int r = e / GB, c = e % GB, i = i0 + r;
+    if (c >= kw || i >= n || (i >= k0 && i < k0 + kw)) continue;
+    double s = 0.0;
+    for (int k = 0; k < kw; ++k) s += x[r][k] * d[k][c];
+    M[(size_t)i * n + k0 + c] = -s;
+  }
+}
+
+__global__ void k_bgj_store(int n, double* __restrict__ M, int k0, int kw,
+                            const double* __restrict__ D) {
+  for (int e = threadIdx.x; e < kw * kw; e += blockDim.x) {
+    const int r = e / kw, c = e % kw;
+    M[(size_t)(k0 + r) * n + k0 + c] = D[r * GB + c];
+  }
 }
 
 // ---- V-cycle kernels ----------------------------------------------------
@@ -391,6 +554,35 @@ unsigned stride_grid(long long n) {
 
 static std::mutex g_coop_mu;
 
+// Blocked Gauss-Jordan without pivoting into H.coarse_inv; false when a pivot
+// was too small (H.coarse_inv is then to be recomputed with pivoting).
+static bool coarse_inverse_blocked(Handle* h, Hierarchy& H) {
+  Level& C = H.lev.back();
+  const int n = C.n;
+  double* M = H.coarse_inv.p;
+  MSS_CK(cudaMemsetAsync(M, 0, sizeof(double) * (size_t)n * n, h->stream));
+  k_dense_square<<<grid_for(n, 128), 128, 0, h->stream>>>(n, C.rp.p, C.ci.p, C.v.p, M);
+  MSS_LAUNCH_CK("k_dense_square");
+  DBuf<double> D(h, GB * GB);
+  DBuf<int> status(h, 1);
+  fill_int(h, status.p, 0, 1);
+  const int tiles = (n + GT - 1) / GT;
+  for (int k0 = 0; k0 < n; k0 += GB) {
+    const int kw = n - k0 < GB ? n - k0 : GB;
+    k_bgj_diag<<<1, 256, 0, h->stream>>>(n, M, k0, kw, D.p, status.p);
+    MSS_LAUNCH_CK("k_bgj_diag");
+    k_bgj_row<<<tiles, 256, 0, h->stream>>>(n, M, k0, kw, D.p);
+    MSS_LAUNCH_CK("k_bgj_row");
+    k_bgj_trail<<<dim3(tiles, tiles), 256, 0, h->stream>>>(n, M, k0, kw);
+    MSS_LAUNCH_CK("k_bgj_trail");
+    k_bgj_col<<<tiles, 256, 0, h->stream>>>(n, M, k0, kw, D.p);
+    MSS_LAUNCH_CK("k_bgj_col");
+    k_bgj_store<<<1, 256, 0, h->stream>>>(n, M, k0, kw, D.p);
+    MSS_LAUNCH_CK("k_bgj_store");
+  }
+  return read_int(h, status.p) == 0;
+}
+
 void coarse_inverse(Handle* h, Hierarchy& H) {
   Level& C = H.lev.back();
   const int n = C.n;
@@ -398,6 +590,17 @@ void coarse_inverse(Handle* h, Hierarchy& H) {
                                       " rows; raise amg_max_levels or amg_max_coarse");
   H.nc = n;
   H.coarse_inv.reset(h, (size_t)n * n);
+  {
+    static const bool times = std::getenv("MSS_SETUP_TIMES") != nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool ok = coarse_inverse_blocked(h, H);
+    if (times)
+      std::fprintf(stderr, "mss coarse inverse (blocked): n = %d, %s, %.2f ms\n", n,
+                   ok ? "ok" : "small pivot, falling back",
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                       .count());
+    if (ok) return;
+  }
   DBuf<double> M(h, (size_t)n * 2 * n);
   DBuf<int> piv(h, n), status(h, 1);
   MSS_CK(cudaMemsetAsync(M.p, 0, sizeof(double) * (size_t)n * 2 * n, h->stream));
@@ -423,11 +626,19 @@ void coarse_inverse(Handle* h, Hierarchy& H) {
     // one cooperative grid at a time in the process: the set-up builds two
     // hierarchies on concurrent streams, and two device-filling cooperative
     // grids must not wait on each other's residency
+    static const bool times = std::getenv("MSS_SETUP_TIMES") != nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lk(g_coop_mu);
+    const auto t1 = std::chrono::steady_clock::now();
     MSS_CK(cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(blocks),
                                        dim3(threads), args, smem, h->stream));
     count_launch();
     st = read_int(h, status.p);   // synchronises: the grid has finished
+    if (times)
+      std::fprintf(stderr, "mss coarse inverse: n = %d, waited %.2f ms, ran %.2f ms\n", n,
+                   std::chrono::duration<double, std::milli>(t1 - t0).count(),
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1)
+                       .count());
   }
   if (st != 0) fail(MSS_ERR_AMG, "coarsest AMG operator is singular (column " +
                                      std::to_string(st - 1) + ")");

@@ -2,6 +2,8 @@
 // orchestration (Sec. 4 scaling, subsystem extraction, AMG, last stage) and
 // the solve entry points. Internal errors become status codes here.
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <new>
 
 #include <thread>
@@ -210,22 +212,49 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
       ctt.reset(h, nnzb);
       extract_subsystem(h, H.t, ctt.p);           // C_TT
     }
+    // MSS_SETUP_TIMES=1 prints the phases' host times (diagnostics)
+    static const bool times = std::getenv("MSS_SETUP_TIMES") != nullptr;
+    const auto tf = std::chrono::steady_clock::now();
+    auto since = [&] {
+      return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf)
+          .count();
+    };
+    double tp = 0, tt = 0, tb = 0;
     Fork fork(H);
     if (o.scheme != MSS_ILU0)
-      fork.run(0, [&](Handle* a) { amg_build(a, H.amgP, N, nnzb, H.rp.p, H.ci.p, bpp.p); });
+      fork.run(0, [&](Handle* a) {
+        amg_build(a, H.amgP, N, nnzb, H.rp.p, H.ci.p, bpp.p);
+        if (times) {
+          cudaStreamSynchronize(a->stream);
+          tp = since();
+        }
+      });
     if (o.scheme == MSS_CPTR3)
       fork.run(1, [&](Handle* a) {
         amg_build(a, H.amgT, N, nnzb, H.rp.p, H.ci.p, ctt.p,
                   static_cast<const float*>(o.learned_interp));
+        if (times) {
+          cudaStreamSynchronize(a->stream);
+          tt = since();
+        }
       });
     std::exception_ptr mine;
     try {
       bilu_setup(h);                              // last stage
+      if (times) {
+        cudaStreamSynchronize(H.stream);
+        tb = since();
+      }
     } catch (...) {
       mine = std::current_exception();
     }
     fork.join();                                  // rethrows a worker's error
     if (mine) std::rethrow_exception(mine);
+    if (times)
+      std::fprintf(stderr, "mss setup: fork at %.2f ms; P hierarchy %.2f, T hierarchy %.2f, "
+                           "last stage %.2f, join %.2f ms after the fork\n",
+                   std::chrono::duration<double, std::milli>(tf - t0).count(), tp, tt, tb,
+                   since());
   }
   H.rT.reset(h, N);
   H.xT.reset(h, N);
@@ -471,18 +500,30 @@ int mss_solve_host(mss_handle* hh, const mss_bsr* Jh, int nb, mss_layout layout,
     const size_t N = (size_t)Jh->n_rows, nnzb = (size_t)Jh->nnzb, nb2 = (size_t)nb * nb;
     if (H.host_rp.n < N + 1) H.host_rp.reset(h, N + 1);
     if (H.host_ci.n < nnzb) H.host_ci.reset(h, nnzb);
-    if (H.host_vals.n < nnzb * nb2) H.host_vals.reset(h, nnzb * nb2);
     if (H.host_b.n < N * nb) H.host_b.reset(h, N * nb);
     if (H.host_x.n < N * nb) H.host_x.reset(h, N * nb);
     MSS_CK(cudaMemcpyAsync(H.host_rp.p, Jh->row_ptr, sizeof(int) * (N + 1),
                            cudaMemcpyHostToDevice, H.stream));
     MSS_CK(cudaMemcpyAsync(H.host_ci.p, Jh->col_idx, sizeof(int) * nnzb, cudaMemcpyHostToDevice,
                            H.stream));
-    MSS_CK(cudaMemcpyAsync(H.host_vals.p, Jh->vals, sizeof(double) * nnzb * nb2,
-                           cudaMemcpyHostToDevice, H.stream));
+    // The block values are read once, by the scaling kernels: when they sit in
+    // pinned host memory that the device can address, those kernels read them
+    // in place over the host link instead of after a staging copy.
+    const double* vals = nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, Jh->vals) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer != nullptr) {
+      vals = static_cast<const double*>(at.devicePointer);
+    } else {
+      cudaGetLastError();   // pageable memory: not an error, copy it
+      if (H.host_vals.n < nnzb * nb2) H.host_vals.reset(h, nnzb * nb2);
+      MSS_CK(cudaMemcpyAsync(H.host_vals.p, Jh->vals, sizeof(double) * nnzb * nb2,
+                             cudaMemcpyHostToDevice, H.stream));
+      vals = H.host_vals.p;
+    }
     MSS_CK(cudaMemcpyAsync(H.host_b.p, b_host, sizeof(double) * N * nb, cudaMemcpyHostToDevice,
                            H.stream));
-    mss_bsr Jd{Jh->n_rows, Jh->nnzb, H.host_rp.p, H.host_ci.p, H.host_vals.p};
+    mss_bsr Jd{Jh->n_rows, Jh->nnzb, H.host_rp.p, H.host_ci.p, vals};
     do_setup(H, &Jd, nb, layout, opt);
     st = solve_impl(H, &Jd, H.host_b.p, H.host_x.p, tol, maxit, out);
     MSS_CK(cudaMemcpyAsync(x_host, H.host_x.p, sizeof(double) * N * nb, cudaMemcpyDeviceToHost,

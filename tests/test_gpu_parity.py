@@ -248,3 +248,23 @@ def test_residual_norm_entry_point(mss, nb):
     assert abs(bn - ref_b) <= 1e-12 * ref_b
     r2, bn2 = g.residual_norm(rp, ci, v, nb, _t(s.b), _t(x))
     assert r2 == r and bn2 == bn
+
+
+@pytest.mark.parametrize("scheme,smoother,precision", [("cptr3", "jacobi", "fp64"),
+                                                       ("cptr3", "chebyshev", "fp64"),
+                                                       ("cpr", "jacobi", "fp64")])
+def test_larger_hierarchy(mss, scheme, smoother, precision):
+    # a 6,144-cell system: several AMG levels above 4,096 rows, stage and
+    # whole-preconditioner parity, and the FGMRES iteration bar
+    s = sy.make_system(96, 64, 4, pe=10.0, sigma=2.0, band=True, seed=12)
+    g = _gpu(mss, s, scheme=scheme, smoother=smoother, amg_max_coarse=100)
+    o = _orc(s, scheme=scheme, smoother=smoother, max_coarse=100)
+    r = np.random.default_rng(12).standard_normal(s.n_cells * s.nb)
+    rt = _t(r)
+    for which in ([0, 1] if scheme == "cptr3" else [1]):
+        assert _rel(_n(g.stage(which, rt)), o.stage(which, r)) < APPLY_TOL, which
+    assert _rel(_n(g.apply(rt)), o.apply(r)) < APPLY_TOL
+    xo, io = o.fgmres(o.scale_rhs(s.b), tol=1e-8, maxit=300, restart=50)
+    g2 = _gpu(mss, s, scheme=scheme, smoother=smoother, amg_max_coarse=100, restart=50)
+    xg, ig = g2.solve(_t(s.b), tol=1e-8, maxit=300)
+    assert abs(ig["iters"] - io["iters"]) <= 1
