@@ -41,7 +41,8 @@ def args_():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--grid", "--n", dest="n", type=int, default=1024,
+                    help="grid side of the benchmark systems (--n is an alias)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--maxit", type=int, default=1000)
@@ -161,6 +162,24 @@ def load_traffic(kernel):
     return None
 
 
+# ---- rank aggregation (replicas: no data-path collective) ------------------------
+def max_over_ranks(value, dist):
+    """The slowest rank's time (all ranks get it); the identity with one rank."""
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_system_ms(ms, systems_per_rank, world):
+    """Whole-job time per system: every rank solved systems_per_rank systems
+    in (at most) ms, so the job did systems_per_rank * world systems."""
+    return ms / (systems_per_rank * world)
+
+
 # ---- our arm --------------------------------------------------------------------
 def run_ours(a, rank, world, dist):
     import torch
@@ -223,13 +242,9 @@ def run_ours(a, rank, world, dist):
         tr = solver.trace_read(reset=True)
         trace_from = "one host-driven step after the timed region"
     solver.trace(False)
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     nsys = a.steps * len(PES)
-    value = ms / (nsys * world)
+    value = per_system_ms(ms, nsys, world)
     iters = [i["iters"] for i in infos[:len(PES)]]
 
     # roofline of the dominant single-kernel class (traced live above)
@@ -625,6 +640,11 @@ def cpu_baseline(a, s, steps=1):
         vals.append((t_setup, t_iter))
     t_setup = float(np.median([v[0] for v in vals]))
     t_iter = float(np.median([v[1] for v in vals]))
+    if iters is None and a.n <= 256:
+        # no stored count for this size: small enough to run the oracle out
+        o = oracle.OracleSolver.from_system(s, restart=a.restart)
+        _, info = o.fgmres(o.scale_rhs(s.b), tol=a.tol, maxit=a.maxit, restart=a.restart)
+        iters = info["iters"]
     n_it = iters if iters is not None else 0
     est_ms = (t_setup + n_it * t_iter) * 1e3
     return {"value": round(est_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
@@ -656,7 +676,8 @@ def run_reference(a, rank, world):
             "data": "synthetic (seeded generator)",
             "config": {**workload_config(a), "parallelism": "cpu oracle, 1 thread"},
             "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1,
-                             "kind": "oracle", "sample": cb["sample"] if cb else ""},
+                             "kind": "oracle", "sample": cb["sample"] if cb else "",
+                             "iters": cb["iters"] if cb else None},
             "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

@@ -503,14 +503,19 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     int undecided = read_int(h, und.p);
     int rounds = 0;
     while (undecided > 0) {
-      if (++rounds > n + 1) fail(MSS_ERR_AMG, "PMIS did not terminate");
-      k_pmis_select<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, strp.p, stci.p,
-                                                             lam.p, state.p, newc.p);
-      MSS_LAUNCH_CK("k_pmis_select");
-      fill_int(h, und.p, 0, 1);
-      k_pmis_update<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, state.p, newc.p,
-                                                             und.p);
-      MSS_LAUNCH_CK("k_pmis_update");
+      // three synchronous rounds per read-back: a round with nothing
+      // undecided changes nothing, so the split is the one of round-by-round
+      // checking with fewer host synchronisations
+      for (int r = 0; r < 3; ++r) {
+        if (++rounds > n + 3) fail(MSS_ERR_AMG, "PMIS did not terminate");
+        k_pmis_select<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, strp.p, stci.p,
+                                                               lam.p, state.p, newc.p);
+        MSS_LAUNCH_CK("k_pmis_select");
+        fill_int(h, und.p, 0, 1);
+        k_pmis_update<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, state.p, newc.p,
+                                                               und.p);
+        MSS_LAUNCH_CK("k_pmis_update");
+      }
       undecided = read_int(h, und.p);
     }
     Level& L = H.lev[l];

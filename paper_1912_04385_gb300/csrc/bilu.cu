@@ -643,14 +643,18 @@ void bilu_setup_nb(Handle* h) {
     const uint64_t key = strips ? KEY_STRIP : KEY_CELL;
     int remaining = ns, rounds = 0;
     while (remaining > 0) {
-      if (++rounds > ns + 1) fail(MSS_ERR_CUDA, "colouring did not terminate");
-      k_jp_pick<<<grid_for(ns, 128), 128, 0, h->stream>>>(ns, S, N, h->rp.p, h->ci.p,
-                                                          h->opt.seed, key, scol.p, pick.p);
-      MSS_LAUNCH_CK("k_jp_pick");
-      fill_int(h, left.p, 0, 1);
-      k_jp_commit<<<grid_for(ns, 256), 256, 0, h->stream>>>(ns, pick.p, scol.p, left.p,
-                                                            maxcol.p);
-      MSS_LAUNCH_CK("k_jp_commit");
+      // three rounds per read-back: once every strip is coloured a round
+      // picks nothing, so the colouring is the round-by-round one
+      for (int r = 0; r < 3; ++r) {
+        if (++rounds > ns + 3) fail(MSS_ERR_CUDA, "colouring did not terminate");
+        k_jp_pick<<<grid_for(ns, 128), 128, 0, h->stream>>>(ns, S, N, h->rp.p, h->ci.p,
+                                                            h->opt.seed, key, scol.p, pick.p);
+        MSS_LAUNCH_CK("k_jp_pick");
+        fill_int(h, left.p, 0, 1);
+        k_jp_commit<<<grid_for(ns, 256), 256, 0, h->stream>>>(ns, pick.p, scol.p, left.p,
+                                                              maxcol.p);
+        MSS_LAUNCH_CK("k_jp_commit");
+      }
       remaining = read_int(h, left.p);
     }
     h->ncol = read_int(h, maxcol.p) + 1;
