@@ -14,6 +14,9 @@
 #include <cstring>
 
 #include <memory>
+#include <cstdlib>
+#include <cstdio>
+#include <chrono>
 
 #include "common.cuh"
 
@@ -452,9 +455,34 @@ void level_prepare(Handle* h, Level& L) {
 
 }  // namespace
 
+// Host time per set-up phase, printed when MSS_SETUP_TIMES is set (each mark
+// synchronises the stream, so only for diagnostics).
+struct PhaseClock {
+  Handle* h;
+  bool on;
+  std::chrono::steady_clock::time_point t;
+  double acc[7] = {};
+  explicit PhaseClock(Handle* hh)
+      : h(hh), on(std::getenv("MSS_SETUP_TIMES") != nullptr), t(std::chrono::steady_clock::now()) {}
+  void mark(int k) {
+    if (!on) return;
+    cudaStreamSynchronize(h->stream);
+    const auto now = std::chrono::steady_clock::now();
+    acc[k] += std::chrono::duration<double, std::milli>(now - t).count();
+    t = now;
+  }
+  ~PhaseClock() {
+    if (on)
+      std::fprintf(stderr, "mss amg build (ms): prepare %.2f strength %.2f pmis %.2f interp %.2f "
+                           "transpose %.2f rap %.2f coarse %.2f\n",
+                   acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6]);
+  }
+};
+
 void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const int* ci0,
                const double* vals0, const float* learned) {
   const mss_options& o = h->opt;
+  PhaseClock pc(h);
   H.lev.clear();
   H.lev.reserve(32);
   {
@@ -472,6 +500,7 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
   const int max_levels = o.amg_max_levels < 1 ? 1 : (o.amg_max_levels > 25 ? 25 : o.amg_max_levels);
   for (int l = 0;; ++l) {
     level_prepare(h, H.lev[l]);
+    pc.mark(0);
     int n = H.lev[l].n, nnz = H.lev[l].nnz;
     if (n <= o.amg_max_coarse || l + 1 >= max_levels) break;
     const int* rp = H.lev[l].rp.p;
@@ -491,6 +520,7 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     DBuf<int> strp, stci;
     transpose(h, n, n, srp.p, sci.p, nullptr, ns, strp, stci, nullptr);
     // PMIS; |S_i^T| are the row lengths of the transposed strength graph
+    pc.mark(1);
     DBuf<int> tcount(h, n);
     k_row_lengths<<<grid_for(n, 256), 256, 0, h->stream>>>(n, strp.p, tcount.p);
     MSS_LAUNCH_CK("k_row_lengths");
@@ -518,6 +548,7 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
       }
       undecided = read_int(h, und.p);
     }
+    pc.mark(2);
     Level& L = H.lev[l];
     L.cf.reset(h, n);
     k_pmis_finalize<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, state.p, L.cf.p);
@@ -551,7 +582,9 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
           gnn_create(h, n, rp, ci, v, L.cf.p, L.prp.p, L.pci.p, L.pv.p, nnz), gnn_destroy);
       gnn_apply_to_p(g.get(), learned, L.pv.p);
     }
+    pc.mark(3);
     transpose(h, n, nc, L.prp.p, L.pci.p, L.pv.p, L.nnzP, L.rrp, L.rci, &L.rv);
+    pc.mark(4);
     // Galerkin product A_c = R (A P)
     DBuf<int> aprp, apci;
     DBuf<double> apv;
@@ -562,8 +595,11 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     sparse_product(h, nc, L.rrp.p, L.rci.p, L.rv.p, aprp.p, apci.p, apv.p, next.rp, next.ci,
                    next.v, next.nnz);
     H.lev.push_back(std::move(next));
+    pc.mark(5);
   }
+  pc.mark(0);
   coarse_inverse(h, H);
+  pc.mark(6);
 }
 
 }  // namespace mss
