@@ -84,7 +84,8 @@ typedef struct {
                                cells, coloured, natural order inside a strip;
                                MSS_MULTICOLOR: every cell coloured on its own */
   int32_t smoother;         /* MSS_JACOBI (default) | MSS_CHEBYSHEV */
-  int32_t nu_pre, nu_post;  /* smoothing sweeps per V-cycle leg (1, 1) */
+  int32_t nu_pre, nu_post;  /* smoothing sweeps per V-cycle leg (2, 2: HSL_MI20's defaults,
+                               which Sec. 5.1 names) */
   int32_t cheb_degree;      /* Chebyshev polynomial degree (2) */
   int32_t amg_max_coarse;   /* direct solve at or below this size (1000, Sec. 5.1) */
   int32_t amg_max_levels;   /* at most this many levels (25) */
@@ -112,7 +113,7 @@ typedef struct {
                                launched once per solve and read back once. Same
                                kernels, same order, same results. */
   double amg_theta;         /* strength threshold (0.25) */
-  double jacobi_omega;      /* Jacobi damping (2/3) */
+  double jacobi_omega;      /* Jacobi damping (0.8, HSL_MI20's default) */
   double cheb_lo_ratio;     /* Chebyshev interval [bound/ratio, factor*bound] (30) */
   double cheb_hi_factor;    /* (1.0) */
   uint64_t seed;            /* PMIS measure and colouring priorities */

@@ -77,8 +77,8 @@ void or_opts_default(or_opts* o) {
   o->stage3 = 0;
   o->ilu_order = 2;      /* strips of ilu_strip cells (reading) */
   o->smoother = 0;
-  o->nu_pre = 1;
-  o->nu_post = 1;
+  o->nu_pre = 2;          /* HSL_MI20 defaults (Sec. 5.1): 2 pre-, 2 post-sweeps */
+  o->nu_post = 2;
   o->cheb_degree = 2;
   o->max_coarse = 1000;   /* Sec. 5.1: maximum coarse problem size 1000 */
   o->max_levels = 25;
@@ -86,7 +86,7 @@ void or_opts_default(or_opts* o) {
   o->restart = 30;
   o->ilu_strip = 32;
   o->theta = 0.25;
-  o->omega = 2.0 / 3.0;
+  o->omega = 0.8;          /* HSL_MI20's default Jacobi damping */
   o->cheb_lo_ratio = 30.0;
   o->cheb_hi_factor = 1.0;
   o->seed = 0x5eedULL;

@@ -370,8 +370,8 @@ int mss_options_default(mss_options* o) {
   o->ilu_strip = 32;
   o->orthog = MSS_CGS1;
   o->smoother = MSS_JACOBI;
-  o->nu_pre = 1;
-  o->nu_post = 1;
+  o->nu_pre = 2;    // HSL_MI20 defaults (Sec. 5.1): two pre- and two post-smoothing
+  o->nu_post = 2;   // sweeps, Jacobi damping 0.8
   o->cheb_degree = 2;
   o->amg_max_coarse = 1000;
   o->amg_max_levels = 25;
@@ -380,7 +380,7 @@ int mss_options_default(mss_options* o) {
   o->precision = MSS_FP64;
   o->driver = MSS_DRIVER_HOST;
   o->amg_theta = 0.25;
-  o->jacobi_omega = 2.0 / 3.0;
+  o->jacobi_omega = 0.8;
   o->cheb_lo_ratio = 30.0;
   o->cheb_hi_factor = 1.0;
   o->seed = 0x5eedULL;
