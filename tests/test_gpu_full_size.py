@@ -68,3 +68,42 @@ def test_full_size_iterations_and_residual(mss, k):
     y = g.spmv(x).cpu().numpy()
     ref = g.scale_rhs(torch.from_numpy(Ax).cuda()).cpu().numpy()
     assert np.max(np.abs(y - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_full_size_graph_driver_equals_host_loop(mss):
+    # the launch configuration bench.py times: the whole solve as one graph
+    gold = json.loads(GOLDEN.read_text())
+    rec = gold["systems"][1]
+    s = sy.plain_at_scale(gold["grid"], pe=rec["pe"], seed=0)
+    rp = torch.from_numpy(s.row_ptr).cuda()
+    ci = torch.from_numpy(s.col_idx).cuda()
+    v = torch.from_numpy(s.vals.reshape(-1)).cuda()
+    b = torch.from_numpy(s.b).cuda()
+    gh = mss.Solver().setup(rp, ci, v, 6, 0, 1, restart=gold["restart"])
+    xh, ih = gh.solve(b, tol=gold["tol"], maxit=1000)
+    del gh
+    gg = mss.Solver().setup(rp, ci, v, 6, 0, 1, restart=gold["restart"], driver="graph")
+    xg, ig = gg.solve(b, tol=gold["tol"], maxit=1000)
+    assert ig["iters"] == ih["iters"] and abs(ig["iters"] - rec["iters"]) <= 1
+    assert torch.equal(xg, xh)
+
+
+def test_mixed_precision_workload_2048(mss):
+    # 2048 x 2048 (25 M unknowns), sigma 3, Pe 10: the mixed form reaches the
+    # FP64 tolerance on the scaled system within two iterations of FP64
+    s = sy.plain_at_scale(2048, pe=10.0, seed=0, sigma=3.0)
+    rp = torch.from_numpy(s.row_ptr).cuda()
+    ci = torch.from_numpy(s.col_idx).cuda()
+    v = torch.from_numpy(s.vals.reshape(-1)).cuda()
+    b = torch.from_numpy(s.b).cuda()
+    del s
+    g = mss.Solver()
+    g.setup(rp, ci, v, 6, 0, 1, restart=50, driver="graph")
+    x64, i64 = g.solve(b, tol=1e-6, maxit=1000)
+    g.setup(rp, ci, v, 6, 0, 1, restart=50, driver="graph", precision="mixed")
+    xm, im = g.solve(b, tol=1e-6, maxit=1000)
+    assert i64["status"] == 0 and im["status"] == 0
+    assert im["rel_res_true"] <= 1e-6
+    assert im["iters"] <= i64["iters"] + 2
+    rel = float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
+    assert rel < 1e-2, rel
