@@ -438,7 +438,7 @@ void level_prepare(Handle* h, Level& L) {
                                                         bound.p, bad.p);
   MSS_LAUNCH_CK("k_dinv_bound");
   unsigned long long bits = 0;
-  MSS_CK(cudaMemcpyAsync(&bits, bound.p, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  read_back(h, &bits, bound.p, sizeof(bits));
   int badrow = read_int(h, bad.p);
   if (badrow != 0x7fffffff)
     fail(MSS_ERR_AMG, "AMG level of size " + std::to_string(n) + ": zero diagonal in row " +

@@ -64,13 +64,18 @@ void check_options(const mss_options& o) {
 }
 
 // Worker handle i: its own non-blocking stream, allocations from the device
-// pool, the main handle's sizes and options.
+// pool, the main handle's sizes and options. The workers build the AMG
+// hierarchies, the longer branches of the set-up; their streams take the
+// device's highest priority, so their blocks are dispatched ahead of the
+// factorisation's whenever both wait for an SM.
 Handle* worker(Handle& H, int i) {
   if (!H.aux[i]) {
     std::unique_ptr<Handle> a(new Handle());
     a->device = H.device;
     a->num_sms = H.num_sms;
-    MSS_CK(cudaStreamCreateWithFlags(&a->owned.s, cudaStreamNonBlocking));
+    int least = 0, greatest = 0;
+    MSS_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    MSS_CK(cudaStreamCreateWithPriority(&a->owned.s, cudaStreamNonBlocking, greatest));
     a->stream = a->owned.s;
     H.aux[i] = std::move(a);
   }

@@ -126,8 +126,21 @@ struct OwnedStream {
   }
 };
 
+// Page-locked staging for the host's small read-backs (flags, counts, the
+// solve state). Copies to pageable memory are staged by the driver and, with
+// several set-up threads, serialise behind whichever stream is the slowest to
+// reach its copy; a pinned word is read with a plain stream synchronisation.
+struct PinnedHost {
+  void* p = nullptr;
+  ~PinnedHost() {
+    if (p) cudaFreeHost(p);
+  }
+};
+constexpr size_t kPinnedBytes = 256;
+
 struct Handle {
   OwnedStream owned;
+  PinnedHost pin;
   // binding
   cudaStream_t stream = nullptr;
   // Worker handles of the concurrent set-up (T and P hierarchies built on
@@ -265,6 +278,12 @@ inline unsigned grid_for(long long n, int threads) {
 
 // util.cu
 void exclusive_scan(Handle* h, const int* in, int* out, int n);   // out has n + 1 entries
+// bytes <= kPinnedBytes from device memory to dst through the pinned staging
+// word; synchronises the handle's stream
+void read_back(Handle* h, void* dst, const void* dptr, size_t bytes);
+// bytes <= kPinnedBytes from src to device memory through the staging word;
+// synchronises the handle's stream
+void write_to_device(Handle* h, void* dptr, const void* src, size_t bytes);
 int read_int(Handle* h, const int* dptr);                         // synchronises
 double read_double(Handle* h, const double* dptr);
 void fill_int(Handle* h, int* p, int value, long long n);

@@ -828,8 +828,7 @@ double gnn_loss_grad(GnnGraph* gg, const float* prm, float* grad) {
   k_gnn_sumsq<<<1, 256, 0, h->stream>>>(len, g.r.p, 1.0, g.scal.p);
   MSS_LAUNCH_CK("k_gnn_sumsq");
   double sc[2];
-  MSS_CK(cudaMemcpyAsync(sc, g.scal.p, sizeof(sc), cudaMemcpyDeviceToHost, h->stream));
-  MSS_CK(cudaStreamSynchronize(h->stream));
+  read_back(h, sc, g.scal.p, sizeof(sc));
   const double L = sc[0] / sc[1];
   if (!grad) return L;
   // dL/dd = op^T (2 r / den)

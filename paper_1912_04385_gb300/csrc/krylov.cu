@@ -559,8 +559,7 @@ void seq_tail(Handle* h, const Krylov& K, double* x, cudaGraphConditionalHandle 
 
 GState read_state(Handle* h, const Krylov& K) {
   GState s;
-  MSS_CK(cudaMemcpyAsync(&s, K.st, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
-  MSS_CK(cudaStreamSynchronize(h->stream));
+  read_back(h, &s, K.st, sizeof(GState));
   return s;
 }
 
@@ -568,8 +567,7 @@ void write_params(Handle* h, const Krylov& K, double tol, int maxit) {
   GState s{};
   s.tol = tol;
   s.maxit = maxit;
-  MSS_CK(cudaMemcpyAsync(K.st, &s, sizeof(GState), cudaMemcpyHostToDevice, h->stream));
-  MSS_CK(cudaStreamSynchronize(h->stream));   // s lives on this stack frame
+  write_to_device(h, K.st, &s, sizeof(GState));
 }
 
 int finish(const GState& s, mss_result* out) {

@@ -256,17 +256,35 @@ void exclusive_scan(Handle* h, const int* in, int* out, int n) {
   // hooks are stream-ordered (or cudaFree, which synchronises).
 }
 
+static void* staging(Handle* h, size_t bytes) {
+  if (bytes > kPinnedBytes) fail(MSS_ERR_INVALID_ARG, "read-back larger than the staging word");
+  if (!h->pin.p) MSS_CK(cudaMallocHost(&h->pin.p, kPinnedBytes));
+  return h->pin.p;
+}
+
+void read_back(Handle* h, void* dst, const void* dptr, size_t bytes) {
+  void* s = staging(h, bytes);
+  MSS_CK(cudaMemcpyAsync(s, dptr, bytes, cudaMemcpyDeviceToHost, h->stream));
+  MSS_CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(dst, s, bytes);
+}
+
+void write_to_device(Handle* h, void* dptr, const void* src, size_t bytes) {
+  void* s = staging(h, bytes);
+  std::memcpy(s, src, bytes);
+  MSS_CK(cudaMemcpyAsync(dptr, s, bytes, cudaMemcpyHostToDevice, h->stream));
+  MSS_CK(cudaStreamSynchronize(h->stream));   // the staging word is reused
+}
+
 int read_int(Handle* h, const int* dptr) {
   int v = 0;
-  MSS_CK(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  MSS_CK(cudaStreamSynchronize(h->stream));
+  read_back(h, &v, dptr, sizeof(int));
   return v;
 }
 
 double read_double(Handle* h, const double* dptr) {
   double v = 0;
-  MSS_CK(cudaMemcpyAsync(&v, dptr, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  MSS_CK(cudaStreamSynchronize(h->stream));
+  read_back(h, &v, dptr, sizeof(double));
   return v;
 }
 
