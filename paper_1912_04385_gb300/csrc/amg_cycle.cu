@@ -356,22 +356,27 @@ __global__ void k_residual(int n, const int* __restrict__ rp, const int* __restr
   r[i] = b[i] - s;
 }
 
+// b = R r on the next level and, with x1, that level's first Jacobi sweep
+// from zero x1 = omega D^-1 b (the expression the sweep kernels use)
 template <class V, class C>
-__global__ void k_csr_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                           const V* __restrict__ v, const C* __restrict__ x,
-                           C* __restrict__ y) {
+__global__ void k_restrict(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const V* __restrict__ v, const C* __restrict__ r,
+                           C* __restrict__ b, const C* __restrict__ dinv, C omega,
+                           C* __restrict__ x1) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * x[ci[k]];
-  y[i] = s;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * r[ci[k]];
+  b[i] = s;
+  if (x1) x1[i] = omega * dinv[i] * s;
 }
 
-// xout = x + P xc
+// xout = x + P xc (x and xout may be the same vector: each entry is read
+// and written by its own thread only)
 template <class V, class C>
 __global__ void k_prolong(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                           const V* __restrict__ v, const C* __restrict__ xc,
-                          const C* __restrict__ x, C* __restrict__ xout) {
+                          const C* x, C* xout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   C s = 0;
@@ -395,9 +400,13 @@ __global__ void k_dense_gemv(int n, const C* __restrict__ A, const C* __restrict
 
 template <class C>
 __global__ void k_gather_var(int N, int nb, const double* __restrict__ v, int var,
-                             C* __restrict__ out) {
+                             C* __restrict__ out, const C* __restrict__ dinv, C omega,
+                             C* __restrict__ x1) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) out[i] = (C)v[(size_t)i * nb + var];
+  if (i >= N) return;
+  const C bi = (C)v[(size_t)i * nb + var];
+  out[i] = bi;
+  if (x1) x1[i] = omega * dinv[i] * bi;
 }
 
 __global__ void k_scatter_var_zero(int N, int nb, const double* __restrict__ s, int var,
@@ -413,12 +422,15 @@ template <class C>
 __global__ void k_pattern_sub(int N, int nb, const int* __restrict__ rp,
                               const int* __restrict__ ci, const C* __restrict__ vals,
                               const C* __restrict__ x, const double* __restrict__ r, int var,
-                              C* __restrict__ out) {
+                              C* __restrict__ out, const C* __restrict__ dinv, C omega,
+                              C* __restrict__ x1) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   C s = 0;
   for (int k = rp[i]; k < rp[i + 1]; ++k) s += vals[k] * x[ci[k]];
-  out[i] = (C)r[(size_t)i * nb + var] - s;
+  const C bi = (C)r[(size_t)i * nb + var] - s;
+  out[i] = bi;
+  if (x1) x1[i] = omega * dinv[i] * bi;
 }
 
 __global__ void k_to_float(long long n, const double* __restrict__ in, float* __restrict__ out) {
@@ -504,8 +516,19 @@ struct Sweeper {
   }
 };
 
+// Does the V-cycle on level l start with a Jacobi sweep from zero whose
+// result the producer of b can write? (Jacobi smoothing, not the coarsest.)
+bool has_sweep0(const Hierarchy& H, const mss_options& o, int l) {
+  return o.smoother == MSS_JACOBI && l < (int)H.lev.size() - 1;
+}
+
+// V-cycle on level l for right-hand side b; the result goes to out. With
+// x_has_sweep0, out already holds the first pre-smoothing sweep from zero,
+// omega D^-1 b, written by the kernel that formed b (the restriction on
+// coarser levels), so the remaining sweeps are plain Jacobi sweeps; the
+// values are those of the sweeps run from zero here.
 template <class V, class C>
-void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out) {
+void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out, bool x_has_sweep0) {
   Level& Lev = H.lev[l];
   const LV<V, C> L = view(Lev, (C*)nullptr);
   const mss_options& o = h->opt;
@@ -523,7 +546,14 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out) {
   // ---- pre-smoothing from zero, then the residual
   C* cur = out;
   C* alt = L.x2;
-  if (o.smoother == MSS_JACOBI && o.nu_pre == 1) {
+  if (o.smoother == MSS_JACOBI && x_has_sweep0) {
+    for (int s = 1; s < o.nu_pre; ++s) {
+      sw.jacobi(b, cur, alt);
+      std::swap(cur, alt);
+    }
+    k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
+    MSS_LAUNCH_CK("k_residual");
+  } else if (o.smoother == MSS_JACOBI && o.nu_pre == 1) {
     k_jacobi0_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(
         n, L.rp, L.ci, L.v, L.dinv, b, (C)o.jacobi_omega, out, L.r);
     MSS_LAUNCH_CK("k_jacobi0_residual");
@@ -535,10 +565,8 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out) {
       sw.jacobi(b, cur, alt);
       std::swap(cur, alt);
     }
-    if (o.nu_pre > 1) {
-      k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
-      MSS_LAUNCH_CK("k_residual");
-    }
+    k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
+    MSS_LAUNCH_CK("k_residual");
   } else {
     MSS_CK(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)n, h->stream));
     for (int s = 0; s < o.nu_pre; ++s) {
@@ -548,13 +576,23 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out) {
     k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
     MSS_LAUNCH_CK("k_residual");
   }
-  // ---- restriction and the coarse correction
-  k_csr_spmv<V, C><<<grid_for(L.nc, h->tb), h->tb, 0, h->stream>>>(L.nc, L.rrp, L.rci, L.rv, L.r, cb);
-  MSS_LAUNCH_CK("k_csr_spmv(R)");
-  vcycle_level<V, C>(h, H, l + 1, cb, cx);
-  k_prolong<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.prp, L.pci, L.pv, cx, cur, alt);
+  // ---- restriction (with the coarse level's first sweep) and the coarse
+  // correction
+  const bool next0 = has_sweep0(H, o, l + 1);
+  const LV<V, C> Lc = view(Cl, (C*)nullptr);
+  k_restrict<V, C><<<grid_for(L.nc, h->tb), h->tb, 0, h->stream>>>(
+      L.nc, L.rrp, L.rci, L.rv, L.r, cb, Lc.dinv, (C)o.jacobi_omega, next0 ? cx : nullptr);
+  MSS_LAUNCH_CK("k_restrict");
+  vcycle_level<V, C>(h, H, l + 1, cb, cx, next0);
+  // ---- prolongation into the vector from which the post-smoothing sweeps,
+  // alternating between the two vectors, end in out
+  const int writes = o.nu_post * (o.smoother == MSS_JACOBI ? 1 : o.cheb_degree);
+  C* target = writes % 2 == 0 ? out : L.x2;
+  k_prolong<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.prp, L.pci, L.pv, cx, cur,
+                                                               target);
   MSS_LAUNCH_CK("k_prolong");
-  std::swap(cur, alt);
+  cur = target;
+  alt = target == out ? L.x2 : out;
   // ---- post-smoothing
   for (int s = 0; s < o.nu_post; ++s) {
     if (o.smoother == MSS_JACOBI) {
@@ -710,23 +748,35 @@ void pack_hierarchy_mixed(Handle* h, Hierarchy& H) {
   to_float(h, H.coarse_inv.p, H.coarse_invf.p, (long long)H.nc * H.nc);
 }
 
-void vcycle(Handle* h, Hierarchy& H, const double* b, double* x) {
-  TraceScope ts(h, TR_VCYCLE);
-  vcycle_level<double, double>(h, H, 0, b, x);
+Sweep0<double> sweep0(Handle* h, Hierarchy& H, double* x) {
+  if (!has_sweep0(H, h->opt, 0)) return {};
+  return {H.lev[0].dinv.p, h->opt.jacobi_omega, x};
 }
 
-void vcycle_mixed(Handle* h, Hierarchy& H, const float* b, float* x) {
-  TraceScope ts(h, TR_VCYCLE);
-  vcycle_level<__nv_bfloat16, float>(h, H, 0, b, x);
+Sweep0<float> sweep0_mixed(Handle* h, Hierarchy& H, float* x) {
+  if (!has_sweep0(H, h->opt, 0)) return {};
+  return {H.lev[0].dinvf.p, (float)h->opt.jacobi_omega, x};
 }
 
-void gather_var(Handle* h, const double* v, int var, double* out) {
-  k_gather_var<double><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, v, var, out);
+void vcycle(Handle* h, Hierarchy& H, const double* b, double* x, bool x_has_sweep0) {
+  TraceScope ts(h, TR_VCYCLE);
+  vcycle_level<double, double>(h, H, 0, b, x, x_has_sweep0 && has_sweep0(H, h->opt, 0));
+}
+
+void vcycle_mixed(Handle* h, Hierarchy& H, const float* b, float* x, bool x_has_sweep0) {
+  TraceScope ts(h, TR_VCYCLE);
+  vcycle_level<__nv_bfloat16, float>(h, H, 0, b, x, x_has_sweep0 && has_sweep0(H, h->opt, 0));
+}
+
+void gather_var(Handle* h, const double* v, int var, double* out, Sweep0<double> s0) {
+  k_gather_var<double><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, v, var, out,
+                                                                       s0.dinv, s0.omega, s0.x);
   MSS_LAUNCH_CK("k_gather_var");
 }
 
-void gather_var(Handle* h, const double* v, int var, float* out) {
-  k_gather_var<float><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, v, var, out);
+void gather_var(Handle* h, const double* v, int var, float* out, Sweep0<float> s0) {
+  k_gather_var<float><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, v, var, out,
+                                                                      s0.dinv, s0.omega, s0.x);
   MSS_LAUNCH_CK("k_gather_var");
 }
 
@@ -737,16 +787,16 @@ void scatter_var_zero(Handle* h, const double* s, int var, double* out) {
 }
 
 void csr_block_pattern_spmv_sub(Handle* h, const double* vals, const double* x, const double* r,
-                                int var, double* out) {
-  k_pattern_sub<double><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, h->rp.p,
-                                                                    h->ci.p, vals, x, r, var, out);
+                                int var, double* out, Sweep0<double> s0) {
+  k_pattern_sub<double><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(
+      h->N, h->nb, h->rp.p, h->ci.p, vals, x, r, var, out, s0.dinv, s0.omega, s0.x);
   MSS_LAUNCH_CK("k_pattern_sub");
 }
 
 void csr_block_pattern_spmv_sub(Handle* h, const float* vals, const float* x, const double* r,
-                                int var, float* out) {
-  k_pattern_sub<float><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, h->rp.p, h->ci.p,
-                                                                   vals, x, r, var, out);
+                                int var, float* out, Sweep0<float> s0) {
+  k_pattern_sub<float><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(
+      h->N, h->nb, h->rp.p, h->ci.p, vals, x, r, var, out, s0.dinv, s0.omega, s0.x);
   MSS_LAUNCH_CK("k_pattern_sub");
 }
 

@@ -303,16 +303,29 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
                const double* vals0, const float* learned = nullptr);
 
 // amg_cycle.cu
-void vcycle(Handle* h, Hierarchy& H, const double* b, double* x);
-void vcycle_mixed(Handle* h, Hierarchy& H, const float* b, float* x);   // BF16 / FP32
+// The first Jacobi sweep from zero on level 0 of a hierarchy, x = omega D^-1 b,
+// written by the kernel that forms b (x == nullptr: not used, because the
+// smoother is not Jacobi or level 0 is the coarsest level).
+template <class C>
+struct Sweep0 {
+  const C* dinv = nullptr;
+  C omega = 0;
+  C* x = nullptr;
+};
+Sweep0<double> sweep0(Handle* h, Hierarchy& H, double* x);
+Sweep0<float> sweep0_mixed(Handle* h, Hierarchy& H, float* x);
+// x_has_sweep0: x already holds sweep0's result for this b
+void vcycle(Handle* h, Hierarchy& H, const double* b, double* x, bool x_has_sweep0 = false);
+void vcycle_mixed(Handle* h, Hierarchy& H, const float* b, float* x,   // BF16 / FP32
+                  bool x_has_sweep0 = false);
 void pack_hierarchy_mixed(Handle* h, Hierarchy& H);
-void gather_var(Handle* h, const double* v, int var, double* out);
-void gather_var(Handle* h, const double* v, int var, float* out);
+void gather_var(Handle* h, const double* v, int var, double* out, Sweep0<double> s0 = {});
+void gather_var(Handle* h, const double* v, int var, float* out, Sweep0<float> s0 = {});
 void scatter_var_zero(Handle* h, const double* s, int var, double* out);
 void csr_block_pattern_spmv_sub(Handle* h, const double* vals, const double* x,
-                                const double* r, int var, double* out);
+                                const double* r, int var, double* out, Sweep0<double> s0 = {});
 void csr_block_pattern_spmv_sub(Handle* h, const float* vals, const float* x, const double* r,
-                                int var, float* out);
+                                int var, float* out, Sweep0<float> s0 = {});
 void to_float(Handle* h, const double* in, float* out, long long n);
 void to_bf16(Handle* h, const double* in, __nv_bfloat16* out, long long n);
 

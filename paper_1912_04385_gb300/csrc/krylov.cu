@@ -722,22 +722,26 @@ static void precond_apply_mixed(Handle* h, const double* r, double* y) {
     last_stage_apply(h, r, (const float*)nullptr, (const float*)nullptr, y);
     return;
   }
+  // each kernel that forms a V-cycle's right-hand side also writes its first
+  // Jacobi sweep from zero into the V-cycle's output vector
   if (scheme == MSS_CPR) {
-    gather_var(h, r, h->p, h->rTf.p);
-    vcycle_mixed(h, h->amgP, h->rTf.p, h->vPf.p);
+    gather_var(h, r, h->p, h->rTf.p, sweep0_mixed(h, h->amgP, h->vPf.p));
+    vcycle_mixed(h, h->amgP, h->rTf.p, h->vPf.p, true);
     last_stage_apply(h, r, (const float*)nullptr, h->vPf.p, y);
     return;
   }
   if (h->opt.stage_order == MSS_STAGE_T_FIRST) {
-    gather_var(h, r, h->t, h->rTf.p);
-    vcycle_mixed(h, h->amgT, h->rTf.p, h->xTf.p);
-    csr_block_pattern_spmv_sub(h, h->aptf.p, h->xTf.p, r, h->p, h->zPf.p);
-    vcycle_mixed(h, h->amgP, h->zPf.p, h->vPf.p);
+    gather_var(h, r, h->t, h->rTf.p, sweep0_mixed(h, h->amgT, h->xTf.p));
+    vcycle_mixed(h, h->amgT, h->rTf.p, h->xTf.p, true);
+    csr_block_pattern_spmv_sub(h, h->aptf.p, h->xTf.p, r, h->p, h->zPf.p,
+                               sweep0_mixed(h, h->amgP, h->vPf.p));
+    vcycle_mixed(h, h->amgP, h->zPf.p, h->vPf.p, true);
   } else {
-    gather_var(h, r, h->p, h->rTf.p);
-    vcycle_mixed(h, h->amgP, h->rTf.p, h->vPf.p);
-    csr_block_pattern_spmv_sub(h, h->atpf.p, h->vPf.p, r, h->t, h->zPf.p);
-    vcycle_mixed(h, h->amgT, h->zPf.p, h->xTf.p);
+    gather_var(h, r, h->p, h->rTf.p, sweep0_mixed(h, h->amgP, h->vPf.p));
+    vcycle_mixed(h, h->amgP, h->rTf.p, h->vPf.p, true);
+    csr_block_pattern_spmv_sub(h, h->atpf.p, h->vPf.p, r, h->t, h->zPf.p,
+                               sweep0_mixed(h, h->amgT, h->xTf.p));
+    vcycle_mixed(h, h->amgT, h->zPf.p, h->xTf.p, true);
   }
   last_stage_apply(h, r, h->xTf.p, h->vPf.p, y);
 }
@@ -754,22 +758,26 @@ void precond_apply(Handle* h, const double* r, double* y) {
     last_stage_apply(h, r, (const double*)nullptr, (const double*)nullptr, y);
     return;
   }
+  // each kernel that forms a V-cycle's right-hand side also writes its first
+  // Jacobi sweep from zero into the V-cycle's output vector
   if (scheme == MSS_CPR) {
-    gather_var(h, r, h->p, h->rT.p);
-    vcycle(h, h->amgP, h->rT.p, h->vP.p);                  // x = M1 r (pressure)
+    gather_var(h, r, h->p, h->rT.p, sweep0(h, h->amgP, h->vP.p));
+    vcycle(h, h->amgP, h->rT.p, h->vP.p, true);            // x = M1 r (pressure)
     last_stage_apply(h, r, (const double*)nullptr, h->vP.p, y);          // y = x + M2 (r - Abar x)
     return;
   }
   if (h->opt.stage_order == MSS_STAGE_T_FIRST) {
-    gather_var(h, r, h->t, h->rT.p);
-    vcycle(h, h->amgT, h->rT.p, h->xT.p);                  // x = M1 r (temperature)
-    csr_block_pattern_spmv_sub(h, h->apt.p, h->xT.p, r, h->p, h->zP.p);   // z_P
-    vcycle(h, h->amgP, h->zP.p, h->vP.p);                  // v = M2 z (pressure)
+    gather_var(h, r, h->t, h->rT.p, sweep0(h, h->amgT, h->xT.p));
+    vcycle(h, h->amgT, h->rT.p, h->xT.p, true);            // x = M1 r (temperature)
+    csr_block_pattern_spmv_sub(h, h->apt.p, h->xT.p, r, h->p, h->zP.p,    // z_P
+                               sweep0(h, h->amgP, h->vP.p));
+    vcycle(h, h->amgP, h->zP.p, h->vP.p, true);            // v = M2 z (pressure)
   } else {
-    gather_var(h, r, h->p, h->rT.p);
-    vcycle(h, h->amgP, h->rT.p, h->vP.p);                  // x = M1 r (pressure)
-    csr_block_pattern_spmv_sub(h, h->atp.p, h->vP.p, r, h->t, h->zP.p);   // z_T
-    vcycle(h, h->amgT, h->zP.p, h->xT.p);                  // v = M2 z (temperature)
+    gather_var(h, r, h->p, h->rT.p, sweep0(h, h->amgP, h->vP.p));
+    vcycle(h, h->amgP, h->rT.p, h->vP.p, true);            // x = M1 r (pressure)
+    csr_block_pattern_spmv_sub(h, h->atp.p, h->vP.p, r, h->t, h->zP.p,    // z_T
+                               sweep0(h, h->amgT, h->xT.p));
+    vcycle(h, h->amgT, h->zP.p, h->xT.p, true);            // v = M2 z (temperature)
   }
   last_stage_apply(h, r, h->xT.p, h->vP.p, y);             // y = x + v + M3 u
 }
