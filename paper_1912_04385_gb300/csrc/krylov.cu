@@ -60,16 +60,22 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle c, int use, 
   if (use) cudaGraphSetConditional(c, v ? 1u : 0u);
 }
 
-// partial[i * G + b] = sum over block b's chunk of V_i . w, i <= j;
-// with wnorm, partial[(j + 1) * G + b] = chunk sum of w . w
-__global__ void k_mdot(long long n, long long chunk, const double* __restrict__ V, long long ld,
-                       const GState* __restrict__ st, const double* __restrict__ w, int wnorm,
-                       double* __restrict__ partial) {
-  __shared__ double red[KT / 32];
-  const int nv = st->j + 1;
-  const long long s0 = (long long)blockIdx.x * chunk;
-  const long long s1 = s0 + chunk < n ? s0 + chunk : n;
-  const int G = gridDim.x;
+// Sum of v over the warp (the lanes' tree of block_sum).
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;   // valid in lane 0
+}
+
+constexpr int kMaxRows = 128;   // projections per block: restart + 1 <= 121, and the norm
+
+// Projections of w on the block's chunk, rows i0 <= i < nv, four at a time:
+// the warps' sums go to tab[row][warp]; the block sums are formed after one
+// barrier (warp by warp, as in block_sum).
+__device__ __forceinline__ void chunk_projections(const double* __restrict__ V, long long ld,
+                                                  const double* __restrict__ w, long long s0,
+                                                  long long s1, int nv, double* tab) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = KT / 32;
   int i = 0;
   for (; i + 4 <= nv; i += 4) {
     const double* v0 = V + (size_t)i * ld;
@@ -81,30 +87,55 @@ __global__ void k_mdot(long long n, long long chunk, const double* __restrict__ 
       a2 += v0[2 * ld + e] * we;
       a3 += v0[3 * ld + e] * we;
     }
-    a0 = block_sum(a0, red);
-    a1 = block_sum(a1, red);
-    a2 = block_sum(a2, red);
-    a3 = block_sum(a3, red);
-    if (threadIdx.x == 0) {
-      partial[(size_t)i * G + blockIdx.x] = a0;
-      partial[(size_t)(i + 1) * G + blockIdx.x] = a1;
-      partial[(size_t)(i + 2) * G + blockIdx.x] = a2;
-      partial[(size_t)(i + 3) * G + blockIdx.x] = a3;
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    a3 = warp_sum(a3);
+    if (lane == 0) {
+      tab[i * NW + wid] = a0;
+      tab[(i + 1) * NW + wid] = a1;
+      tab[(i + 2) * NW + wid] = a2;
+      tab[(i + 3) * NW + wid] = a3;
     }
   }
   for (; i < nv; ++i) {
     const double* v0 = V + (size_t)i * ld;
     double a0 = 0;
     for (long long e = s0 + threadIdx.x; e < s1; e += KT) a0 += v0[e] * w[e];
-    a0 = block_sum(a0, red);
-    if (threadIdx.x == 0) partial[(size_t)i * G + blockIdx.x] = a0;
+    a0 = warp_sum(a0);
+    if (lane == 0) tab[i * NW + wid] = a0;
   }
+}
+
+// partial[row * G + b] = sum over the warps of tab[row], rows < nrows
+__device__ __forceinline__ void store_rows(const double* tab, int nrows, double* partial) {
+  constexpr int NW = KT / 32;
+  __syncthreads();
+  const int G = gridDim.x;
+  for (int t = threadIdx.x; t < nrows; t += KT) {
+    double s = 0.0;
+    for (int wv = 0; wv < NW; ++wv) s += tab[t * NW + wv];
+    partial[(size_t)t * G + blockIdx.x] = s;
+  }
+}
+
+// partial[i * G + b] = sum over block b's chunk of V_i . w, i <= j;
+// with wnorm, partial[(j + 1) * G + b] = chunk sum of w . w
+__global__ void k_mdot(long long n, long long chunk, const double* __restrict__ V, long long ld,
+                       const GState* __restrict__ st, const double* __restrict__ w, int wnorm,
+                       double* __restrict__ partial) {
+  __shared__ double tab[kMaxRows * (KT / 32)];
+  const int nv = st->j + 1;
+  const long long s0 = (long long)blockIdx.x * chunk;
+  const long long s1 = s0 + chunk < n ? s0 + chunk : n;
+  chunk_projections(V, ld, w, s0, s1, nv, tab);
   if (wnorm) {
     double a0 = 0;
     for (long long e = s0 + threadIdx.x; e < s1; e += KT) a0 += w[e] * w[e];
-    a0 = block_sum(a0, red);
-    if (threadIdx.x == 0) partial[(size_t)nv * G + blockIdx.x] = a0;
+    a0 = warp_sum(a0);
+    if ((threadIdx.x & 31) == 0) tab[nv * (KT / 32) + (threadIdx.x >> 5)] = a0;
   }
+  store_rows(tab, nv + (wnorm ? 1 : 0), partial);
 }
 
 // w -= sum_{i<=j} h_i V_i on the block's chunk, then either the projections
@@ -119,7 +150,6 @@ __global__ void k_update(long long n, long long chunk, const double* __restrict_
   __syncthreads();
   const long long s0 = (long long)blockIdx.x * chunk;
   const long long s1 = s0 + chunk < n ? s0 + chunk : n;
-  const int G = gridDim.x;
   double nrm = 0.0;
   for (long long e = s0 + threadIdx.x; e < s1; e += KT) {
     double acc = w[e];
@@ -132,37 +162,11 @@ __global__ void k_update(long long n, long long chunk, const double* __restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
     return;
   }
-  __syncthreads();
   // projections of the updated chunk (each thread re-reads its own elements)
-  int i = 0;
-  for (; i + 4 <= nv; i += 4) {
-    const double* v0 = V + (size_t)i * ld;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (long long e = s0 + threadIdx.x; e < s1; e += KT) {
-      double we = w[e];
-      a0 += v0[e] * we;
-      a1 += v0[ld + e] * we;
-      a2 += v0[2 * ld + e] * we;
-      a3 += v0[3 * ld + e] * we;
-    }
-    a0 = block_sum(a0, red);
-    a1 = block_sum(a1, red);
-    a2 = block_sum(a2, red);
-    a3 = block_sum(a3, red);
-    if (threadIdx.x == 0) {
-      partial[(size_t)i * G + blockIdx.x] = a0;
-      partial[(size_t)(i + 1) * G + blockIdx.x] = a1;
-      partial[(size_t)(i + 2) * G + blockIdx.x] = a2;
-      partial[(size_t)(i + 3) * G + blockIdx.x] = a3;
-    }
-  }
-  for (; i < nv; ++i) {
-    const double* v0 = V + (size_t)i * ld;
-    double a0 = 0;
-    for (long long e = s0 + threadIdx.x; e < s1; e += KT) a0 += v0[e] * w[e];
-    a0 = block_sum(a0, red);
-    if (threadIdx.x == 0) partial[(size_t)i * G + blockIdx.x] = a0;
-  }
+  __shared__ double tab[kMaxRows * (KT / 32)];
+  __syncthreads();
+  chunk_projections(V, ld, w, s0, s1, nv, tab);
+  store_rows(tab, nv, partial);
 }
 
 // out[i] = sum_b partial[row_i * G + b] in a fixed order. mode 0: rows
