@@ -131,7 +131,8 @@ __global__ void k_dense_from_csr(int n, const int* __restrict__ rp, const int* _
 // column's magnitude sets *status and the caller falls back to the pivoting
 // Gauss-Jordan above.
 constexpr int GB = 32;     // block size
-constexpr int GT = 64;     // tile of the panel and trailing updates
+constexpr int GT = 32;     // tile of the trailing update
+constexpr int GP = 8;      // columns (rows) of the row (column) panel per CTA
 
 __global__ void k_dense_square(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                const double* __restrict__ v, double* __restrict__ M) {
@@ -141,77 +142,83 @@ __global__ void k_dense_square(int n, const int* __restrict__ rp, const int* __r
   for (int k = rp[i]; k < rp[i + 1]; ++k) row[ci[k]] = v[k];
 }
 
-// D = A_KK^-1 by Gauss-Jordan in shared memory (one block of 256 threads)
-__global__ void k_bgj_diag(int n, const double* __restrict__ M, int k0, int kw,
-                           double* __restrict__ D, int* __restrict__ status) {
+// D = A_KK^-1 by Gauss-Jordan in shared memory, one thread per entry
+// (GB x GB threads; row r is warp r, so a row's entries, its column-k entry
+// included, are read and written by one warp). Per pivot k, warp k has
+// formed the reciprocal and the scaled pivot row (double-buffered), one
+// block barrier publishes them, every other row is updated, and warp k + 1
+// forms the next pivot row from its updated row while the others finish.
+__global__ void __launch_bounds__(GB * GB)
+k_bgj_diag(int n, const double* __restrict__ M, int k0, int kw, double* __restrict__ D,
+           int* __restrict__ status) {
   __shared__ double a[GB][GB + 1];
   __shared__ double cmax[GB];
-  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
-    const int r = e / GB, c = e % GB;
-    a[r][c] = (r < kw && c < kw) ? M[(size_t)(k0 + r) * n + k0 + c] : (r == c ? 1.0 : 0.0);
-  }
+  __shared__ double prow[2][GB];
+  __shared__ int sbad[2];
+  const int r = threadIdx.x / GB, c = threadIdx.x % GB;
+  a[r][c] = (r < kw && c < kw) ? M[(size_t)(k0 + r) * n + k0 + c] : (r == c ? 1.0 : 0.0);
   __syncthreads();
   if (threadIdx.x < GB) {
     double m = 0.0;
-    for (int r = 0; r < GB; ++r) m = fmax(m, fabs(a[r][threadIdx.x]));
+    for (int rr = 0; rr < GB; ++rr) m = fmax(m, fabs(a[rr][threadIdx.x]));
     cmax[threadIdx.x] = m;
   }
   __syncthreads();
-  for (int k = 0; k < GB; ++k) {
+  // warp k: pivot k's reciprocal (lane 0) and scaled row into prow[k & 1]
+  auto publish = [&](int k) {
     const double p = a[k][k];
     const bool bad = !(fabs(p) > 1e-10 * cmax[k]) || !isfinite(p);
-    if (bad) {
+    double ip = 0.0;
+    if (c == 0 && !bad) ip = 1.0 / p;
+    ip = __shfl_sync(0xffffffffu, ip, 0);
+    prow[k & 1][c] = c == k ? ip : a[k][c] * ip;
+    if (c == 0) sbad[k & 1] = bad ? 1 : 0;
+  };
+  if (r == 0) publish(0);
+  __syncthreads();
+  for (int k = 0; k < GB; ++k) {
+    const int buf = k & 1;
+    if (sbad[buf]) {
       if (threadIdx.x == 0) atomicExch(status, 1);
-      return;   // the whole block returns: the status is uniform per block
+      return;   // the whole block returns: the flag is uniform per block
     }
-    const double ip = 1.0 / p;
-    __syncthreads();
-    // f_r = a[r][k] for r != k, read before the column is overwritten
-    double f[GB * GB / 256 > 0 ? GB * GB / 256 : 1];
-    int t = 0;
-    for (int e = threadIdx.x; e < GB * GB; e += blockDim.x, ++t) {
-      const int r = e / GB;
-      f[t] = a[r][k];
+    if (r == k) {
+      a[k][c] = prow[buf][c];
+    } else {
+      const double f = a[r][k];      // column k, before the step
+      __syncwarp();
+      // entry (r, k) becomes -f / p: the same update with a = -0 and the
+      // pivot row's entry 1 / p
+      const double ar = c == k ? -0.0 : a[r][c];
+      a[r][c] = ar - f * prow[buf][c];
     }
-    __syncthreads();
-    // pivot row: a[k][c] = a[k][c] / p, a[k][k] = 1 / p
-    if (threadIdx.x < GB) a[k][threadIdx.x] = threadIdx.x == k ? ip : a[k][threadIdx.x] * ip;
-    __syncthreads();
-    t = 0;
-    for (int e = threadIdx.x; e < GB * GB; e += blockDim.x, ++t) {
-      const int r = e / GB, c = e % GB;
-      if (r == k) continue;
-      a[r][c] = c == k ? -f[t] * ip : a[r][c] - f[t] * a[k][c];
-    }
+    __syncwarp();
+    if (r == k + 1) publish(k + 1);
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) D[e] = a[e / GB][e % GB];
+  D[threadIdx.x] = a[r][c];
 }
 
-// row panel: A_Kj <- D A_Kj for column tile j (columns of block K skipped)
-__global__ void k_bgj_row(int n, double* __restrict__ M, int k0, int kw,
-                          const double* __restrict__ D) {
-  __shared__ double d[GB][GB];
-  __shared__ double x[GB][GT];
-  const int j0 = blockIdx.x * GT;
+// row panel: A_Kj <- D A_Kj for GP columns j per CTA (columns of block K
+// skipped); GB x GP threads, one entry each
+__global__ void __launch_bounds__(GB * GP)
+k_bgj_row(int n, double* __restrict__ M, int k0, int kw, const double* __restrict__ D) {
+  __shared__ double d[GB][GB + 1];
+  __shared__ double x[GB][GP];
+  const int j0 = blockIdx.x * GP;
   for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) d[e / GB][e % GB] = D[e];
-  for (int e = threadIdx.x; e < GB * GT; e += blockDim.x) {
-    const int r = e / GT, c = e % GT, j = j0 + c;
-    x[r][c] = (r < kw && j < n) ? M[(size_t)(k0 + r) * n + j] : 0.0;
-  }
+  const int r = threadIdx.x / GP, cc = threadIdx.x % GP, j = j0 + cc;
+  x[r][cc] = (r < kw && j < n) ? M[(size_t)(k0 + r) * n + j] : 0.0;
   __syncthreads();
-  for (int e = threadIdx.x; e < GB * GT; e += blockDim.x) {
-    const int r = e / GT, c = e % GT, j = j0 + c;
-    if (r >= kw || j >= n || (j >= k0 && j < k0 + kw)) continue;
-    double s = 0.0;
-    for (int k = 0; k < kw; ++k) s += d[r][k] * x[k][c];
-    M[(size_t)(k0 + r) * n + j] = s;
-  }
+  if (r >= kw || j >= n || (j >= k0 && j < k0 + kw)) return;
+  double s = 0.0;
+  for (int k = 0; k < kw; ++k) s += d[r][k] * x[k][cc];
+  M[(size_t)(k0 + r) * n + j] = s;
 }
 
 // trailing update on a GT x GT tile: A_ij -= A_iK A_Kj (i, j outside block K),
-// each of the 256 threads owns a 4 x 4 patch
-__global__ void k_bgj_trail(int n, double* __restrict__ M, int k0, int kw) {
+// each of the 256 threads owns a 2 x 2 patch
+__global__ void __launch_bounds__(256) k_bgj_trail(int n, double* __restrict__ M, int k0, int kw) {
   __shared__ double ai[GT][GB + 1];
   __shared__ double bk[GB][GT];
   const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
@@ -224,26 +231,26 @@ __global__ void k_bgj_trail(int n, double* __restrict__ M, int k0, int kw) {
     bk[k][c] = (j < n && k < kw) ? M[(size_t)(k0 + k) * n + j] : 0.0;
   }
   __syncthreads();
-  const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
-  double acc[4][4] = {};
+  const int tr = (threadIdx.x / 16) * 2, tc = (threadIdx.x % 16) * 2;
+  double acc[2][2] = {};
   for (int k = 0; k < kw; ++k) {
-    double av[4], bv[4];
+    double av[2], bv[2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2; ++u) {
       av[u] = ai[tr + u][k];
       bv[u] = bk[k][tc + u];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 2; ++u)
 #pragma unroll
-      for (int w = 0; w < 4; ++w) acc[u][w] = fma(av[u], bv[w], acc[u][w]);
+      for (int w = 0; w < 2; ++w) acc[u][w] = fma(av[u], bv[w], acc[u][w]);
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 2; ++u) {
     const int i = i0 + tr + u;
     if (i >= n || (i >= k0 && i < k0 + kw)) continue;
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < 2; ++w) {
       const int j = j0 + tc + w;
       if (j >= n || (j >= k0 && j < k0 + kw)) continue;
       M[(size_t)i * n + j] -= acc[u][w];
@@ -251,25 +258,21 @@ __global__ void k_bgj_trail(int n, double* __restrict__ M, int k0, int kw) {
   }
 }
 
-// column panel: A_iK <- -A_iK D for row tile i (rows of block K skipped)
-__global__ void k_bgj_col(int n, double* __restrict__ M, int k0, int kw,
-                          const double* __restrict__ D) {
-  __shared__ double d[GB][GB];
-  __shared__ double x[GT][GB + 1];
-  const int i0 = blockIdx.x * GT;
+// column panel: A_iK <- -A_iK D for GP rows i per CTA (rows of block K
+// skipped); GP x GB threads, one entry each
+__global__ void __launch_bounds__(GB * GP)
+k_bgj_col(int n, double* __restrict__ M, int k0, int kw, const double* __restrict__ D) {
+  __shared__ double d[GB][GB + 1];
+  __shared__ double x[GP][GB + 1];
+  const int i0 = blockIdx.x * GP;
   for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) d[e / GB][e % GB] = D[e];
-  for (int e = threadIdx.x; e < GT * GB; e += blockDim.x) {
-    const int r = e / GB, c = e % GB, i = i0 + r;
-    x[r][c] = (i < n && c < kw) ? M[(size_t)i * n + k0 + c] : 0.0;
-  }
+  const int rr = threadIdx.x / GB, c = threadIdx.x % GB, i = i0 + rr;
+  x[rr][c] = (i < n && c < kw) ? M[(size_t)i * n + k0 + c] : 0.0;
   __syncthreads();
-  for (int e = threadIdx.x; e < GT * GB; e += blockDim.x) {
-    const int r = e / GB, c = e % GB, i = i0 + r;
-    if (c >= kw || i >= n || (i >= k0 && i < k0 + kw)) continue;
-    double s = 0.0;
-    for (int k = 0; k < kw; ++k) s += x[r][k] * d[k][c];
-    M[(size_t)i * n + k0 + c] = -s;
-  }
+  if (c >= kw || i >= n || (i >= k0 && i < k0 + kw)) return;
+  double s = 0.0;
+  for (int k = 0; k < kw; ++k) s += x[rr][k] * d[k][c];
+  M[(size_t)i * n + k0 + c] = -s;
 }
 
 __global__ void k_bgj_store(int n, double* __restrict__ M, int k0, int kw,
@@ -628,15 +631,16 @@ static bool coarse_inverse_blocked(Handle* h, Hierarchy& H) {
   DBuf<int> status(h, 1);
   fill_int(h, status.p, 0, 1);
   const int tiles = (n + GT - 1) / GT;
+  const int panels = (n + GP - 1) / GP;
   for (int k0 = 0; k0 < n; k0 += GB) {
     const int kw = n - k0 < GB ? n - k0 : GB;
-    k_bgj_diag<<<1, 256, 0, h->stream>>>(n, M, k0, kw, D.p, status.p);
+    k_bgj_diag<<<1, GB * GB, 0, h->stream>>>(n, M, k0, kw, D.p, status.p);
     MSS_LAUNCH_CK("k_bgj_diag");
-    k_bgj_row<<<tiles, 256, 0, h->stream>>>(n, M, k0, kw, D.p);
+    k_bgj_row<<<panels, GB * GP, 0, h->stream>>>(n, M, k0, kw, D.p);
     MSS_LAUNCH_CK("k_bgj_row");
     k_bgj_trail<<<dim3(tiles, tiles), 256, 0, h->stream>>>(n, M, k0, kw);
     MSS_LAUNCH_CK("k_bgj_trail");
-    k_bgj_col<<<tiles, 256, 0, h->stream>>>(n, M, k0, kw, D.p);
+    k_bgj_col<<<panels, GB * GP, 0, h->stream>>>(n, M, k0, kw, D.p);
     MSS_LAUNCH_CK("k_bgj_col");
     k_bgj_store<<<1, 256, 0, h->stream>>>(n, M, k0, kw, D.p);
     MSS_LAUNCH_CK("k_bgj_store");
