@@ -290,6 +290,182 @@ __global__ void k_interp(int n, const int* __restrict__ rp, const int* __restric
   plen[i] = len;
 }
 
+// The same interpolation with one warp per row, for the coarse levels whose
+// long rows serialise a thread: the strong C list is collected by ballots in
+// column order, the strong F neighbours are taken in column order, and for
+// each the scans of its row (its diagonal, the weight sum sigma, the
+// distribution) run across the lanes. Every sum is still formed in the
+// definition's order (sigma and d by the warp in lane order, each num[q]
+// once per neighbour, neighbours in order); the scaling, truncation and
+// compaction are the thread version's code on lane 0.
+__device__ __forceinline__ int find_c(const int* cset, int nC, int m) {
+  for (int q = 0; q < nC; ++q)
+    if (cset[q] == m) return q;
+  return -1;
+}
+
+__global__ void __launch_bounds__(256)
+k_interp_warp(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+              const double* __restrict__ v, const unsigned char* __restrict__ strong,
+              const int* __restrict__ cf, const int* __restrict__ cidx, int maxel,
+              int* __restrict__ scr_ci, double* __restrict__ scr_v, int* __restrict__ scr_k,
+              int* __restrict__ plen) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long iw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (iw >= n) return;                       // uniform per warp
+  const int i = (int)iw;
+  const int b = rp[i], e = rp[i + 1];
+  int* cset = scr_ci + b;
+  double* num = scr_v + b;
+  int* keep = scr_k + b;
+  if (cf[i]) {
+    if (lane == 0) {
+      cset[0] = cidx[i];
+      num[0] = 1.0;
+      plen[i] = 1;
+    }
+    return;
+  }
+  // strong C neighbours in column order, and the diagonal
+  int nC = 0;
+  double aii = 0.0;
+  for (int k0 = b; k0 < e; k0 += 32) {
+    const int k = k0 + lane;
+    int j = -1;
+    double vk = 0.0;
+    bool isC = false;
+    if (k < e) {
+      j = ci[k];
+      vk = v[k];
+      isC = j != i && strong[k] && cf[j];
+    }
+    const unsigned dm = __ballot_sync(FULL, k < e && j == i);
+    if (dm) aii = __shfl_sync(FULL, vk, 31 - __clz(dm));   // the last one, as a sequential scan
+    const unsigned cm = __ballot_sync(FULL, isC);
+    if (isC) {
+      const int pos = nC + __popc(cm & ((1u << lane) - 1u));
+      cset[pos] = j;
+      num[pos] = vk;
+    }
+    nC += __popc(cm);
+  }
+  if (nC == 0) {
+    if (lane == 0) plen[i] = 0;
+    return;
+  }
+  __syncwarp();
+  // weak terms into d, strong F neighbours distributed, in column order
+  double d = aii;
+  for (int k0 = b; k0 < e; k0 += 32) {
+    const int k = k0 + lane;
+    int j = -1, kind = 0;                    // 1 weak, 2 strong F
+    double vk = 0.0;
+    if (k < e) {
+      j = ci[k];
+      vk = v[k];
+      if (j != i) {
+        const bool sk = strong[k];
+        const bool cj = cf[j];
+        kind = sk ? (cj ? 0 : 2) : 1;
+      }
+    }
+    unsigned live = __ballot_sync(FULL, kind != 0);
+    while (live) {
+      const int t = __ffs(live) - 1;
+      live &= live - 1;
+      const int kd = __shfl_sync(FULL, kind, t);
+      const double aik = __shfl_sync(FULL, vk, t);
+      if (kd == 1) {
+        d = d + aik;
+        continue;
+      }
+      const int jj = __shfl_sync(FULL, j, t);
+      const int fb = rp[jj], fe = rp[jj + 1];
+      double akk = 0.0;
+      for (int f0 = fb; f0 < fe; f0 += 32) {
+        const int f = f0 + lane;
+        const bool isd = f < fe && ci[f] == jj;
+        const unsigned m = __ballot_sync(FULL, isd);
+        const double vf = isd ? v[f] : 0.0;
+        if (m) akk = __shfl_sync(FULL, vf, 31 - __clz(m));
+      }
+      double sigma = 0.0;
+      for (int f0 = fb; f0 < fe; f0 += 32) {
+        const int f = f0 + lane;
+        double akm = 0.0;
+        bool add = false;
+        if (f < fe) {
+          const int mm = ci[f];
+          akm = v[f];
+          add = mm != jj && find_c(cset, nC, mm) >= 0 && opposite_sign(akk, akm);
+        }
+        unsigned am = __ballot_sync(FULL, add);
+        while (am) {
+          const int t2 = __ffs(am) - 1;
+          am &= am - 1;
+          sigma = sigma + __shfl_sync(FULL, akm, t2);
+        }
+      }
+      if (sigma == 0.0) {
+        d = d + aik;
+      } else {
+        for (int f0 = fb; f0 < fe; f0 += 32) {
+          const int f = f0 + lane;
+          if (f < fe) {
+            const int mm = ci[f];
+            const double akm = v[f];
+            if (mm != jj && opposite_sign(akk, akm)) {
+              const int q = find_c(cset, nC, mm);
+              if (q >= 0) {
+                double tq = aik * akm;
+                tq = tq / sigma;
+                num[q] = num[q] + tq;
+              }
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  if (lane != 0) return;
+  if (d == 0.0 || !isfinite(d)) {
+    plen[i] = 0;
+    return;
+  }
+  for (int q = 0; q < nC; ++q) num[q] = -num[q] / d;
+  for (int q = 0; q < nC; ++q) keep[q] = 1;
+  if (maxel > 0 && nC > maxel) {
+    double total = 0.0;
+    for (int q = 0; q < nC; ++q) total = total + num[q];
+    for (int q = 0; q < nC; ++q) keep[q] = 0;
+    for (int r = 0; r < maxel; ++r) {
+      int best = -1;
+      for (int q = 0; q < nC; ++q) {
+        if (keep[q]) continue;
+        if (best < 0 || fabs(num[q]) > fabs(num[best])) best = q;
+      }
+      keep[best] = 1;
+    }
+    double kept = 0.0;
+    for (int q = 0; q < nC; ++q) if (keep[q]) kept = kept + num[q];
+    if (kept != 0.0) {
+      const double sc = total / kept;
+      for (int q = 0; q < nC; ++q) if (keep[q]) num[q] = num[q] * sc;
+    }
+  }
+  int len = 0;
+  for (int q = 0; q < nC; ++q)
+    if (keep[q]) {
+      cset[len] = cidx[cset[q]];
+      num[len] = num[q];
+      ++len;
+    }
+  plen[i] = len;
+}
+
 __global__ void k_seg_copy(int n, const int* __restrict__ src_off, const int* __restrict__ src_ci,
                            const double* __restrict__ src_v, const int* __restrict__ dst_rp,
                            int* __restrict__ dst_ci, double* __restrict__ dst_v) {
@@ -564,10 +740,17 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     // interpolation
     DBuf<int> scr_ci(h, nnz), scr_k(h, nnz), plen(h, n);
     DBuf<double> scr_v(h, nnz);
-    k_interp<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, strong.p, L.cf.p, cidx.p,
-                                                      o.interp_max_elems, scr_ci.p, scr_v.p,
-                                                      scr_k.p, plen.p);
-    MSS_LAUNCH_CK("k_interp");
+    if (n <= 65536 && nnz > 8LL * n) {   // few, long rows: one warp per row
+      k_interp_warp<<<grid_for((long long)n * 32, 256), 256, 0, h->stream>>>(
+          n, rp, ci, v, strong.p, L.cf.p, cidx.p, o.interp_max_elems, scr_ci.p, scr_v.p, scr_k.p,
+          plen.p);
+      MSS_LAUNCH_CK("k_interp_warp");
+    } else {
+      k_interp<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, strong.p, L.cf.p, cidx.p,
+                                                        o.interp_max_elems, scr_ci.p, scr_v.p,
+                                                        scr_k.p, plen.p);
+      MSS_LAUNCH_CK("k_interp");
+    }
     L.prp.reset(h, n + 1);
     exclusive_scan(h, plen.p, L.prp.p, n);
     L.nnzP = read_int(h, L.prp.p + n);
