@@ -10,6 +10,7 @@
 // BF16 and FP32 copies are packed from it).
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -320,7 +321,78 @@ __global__ void k_jacobi0_twice(int n, const int* __restrict__ rp, const int* __
   x[i] = x1 + omega * (dinv[i] * (b[i] - s));
 }
 
+// Row operations of the V-cycle, shared by the per-level kernels and the
+// fused coarse-level kernel (so both give the same values). LD reads the
+// vectors: plain loads in the per-level kernels; in the fused kernel, whose
+// blocks read what other blocks wrote before a grid barrier, loads that
+// bypass the non-coherent L1.
+struct LdPlain {
+  template <class T>
+  __device__ __forceinline__ static T ld(const T* p) { return *p; }
+};
+struct LdL2 {
+  template <class T>
+  __device__ __forceinline__ static T ld(const T* p) { return __ldcg(p); }
+};
+
 // x_out = x_in + omega D^-1 (b - A x_in)
+template <class V, class C, class LD>
+__device__ __forceinline__ void jacobi_row(int i, const int* __restrict__ rp,
+                                           const int* __restrict__ ci, const V* __restrict__ v,
+                                           const C* __restrict__ dinv, const C* b, C omega,
+                                           const C* xin, C* xout) {
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * LD::ld(xin + ci[k]);
+  xout[i] = LD::ld(xin + i) + omega * (dinv[i] * (LD::ld(b + i) - s));
+}
+
+// r = b - A x
+template <class V, class C, class LD>
+__device__ __forceinline__ void residual_row(int i, const int* __restrict__ rp,
+                                             const int* __restrict__ ci,
+                                             const V* __restrict__ v, const C* b, const C* x,
+                                             C* r) {
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * LD::ld(x + ci[k]);
+  r[i] = LD::ld(b + i) - s;
+}
+
+// b = R r on the next level and, with x1, that level's first Jacobi sweep
+// from zero x1 = omega D^-1 b (the expression the sweep kernels use)
+template <class V, class C, class LD>
+__device__ __forceinline__ void restrict_row(int i, const int* __restrict__ rp,
+                                             const int* __restrict__ ci,
+                                             const V* __restrict__ v, const C* r, C* b,
+                                             const C* __restrict__ dinv, C omega, C* x1) {
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * LD::ld(r + ci[k]);
+  b[i] = s;
+  if (x1) x1[i] = omega * dinv[i] * s;
+}
+
+// xout = x + P xc (x and xout may be the same vector: each entry is read
+// and written by its own thread only)
+template <class V, class C, class LD>
+__device__ __forceinline__ void prolong_row(int i, const int* __restrict__ rp,
+                                            const int* __restrict__ ci,
+                                            const V* __restrict__ v, const C* xc, const C* x,
+                                            C* xout) {
+  C s = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * LD::ld(xc + ci[k]);
+  xout[i] = LD::ld(x + i) + s;
+}
+
+// x_row = (Ainv b)_row by one warp: lanes over the row, then a tree
+template <class C, class LD>
+__device__ __forceinline__ C gemv_row(int row, int lane, int n, const C* __restrict__ A,
+                                      const C* b) {
+  const C* a = A + (size_t)row * n;
+  C s = 0;
+  for (int j = lane; j < n; j += 32) s += a[j] * LD::ld(b + j);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return s;
+}
+
 template <class V, class C>
 __global__ void k_jacobi(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                          const V* __restrict__ v, const C* __restrict__ dinv,
@@ -328,9 +400,7 @@ __global__ void k_jacobi(int n, const int* __restrict__ rp, const int* __restric
                          C* __restrict__ xout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * xin[ci[k]];
-  xout[i] = xin[i] + omega * (dinv[i] * (b[i] - s));
+  jacobi_row<V, C, LdPlain>(i, rp, ci, v, dinv, b, omega, xin, xout);
 }
 
 // Chebyshev step: r = b - A x_in; d = c1 d + c2 D^-1 r; x_out = x_in + d
@@ -354,13 +424,9 @@ __global__ void k_residual(int n, const int* __restrict__ rp, const int* __restr
                            const C* __restrict__ x, C* __restrict__ r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * x[ci[k]];
-  r[i] = b[i] - s;
+  residual_row<V, C, LdPlain>(i, rp, ci, v, b, x, r);
 }
 
-// b = R r on the next level and, with x1, that level's first Jacobi sweep
-// from zero x1 = omega D^-1 b (the expression the sweep kernels use)
 template <class V, class C>
 __global__ void k_restrict(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                            const V* __restrict__ v, const C* __restrict__ r,
@@ -368,23 +434,16 @@ __global__ void k_restrict(int n, const int* __restrict__ rp, const int* __restr
                            C* __restrict__ x1) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * r[ci[k]];
-  b[i] = s;
-  if (x1) x1[i] = omega * dinv[i] * s;
+  restrict_row<V, C, LdPlain>(i, rp, ci, v, r, b, dinv, omega, x1);
 }
 
-// xout = x + P xc (x and xout may be the same vector: each entry is read
-// and written by its own thread only)
 template <class V, class C>
 __global__ void k_prolong(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                           const V* __restrict__ v, const C* __restrict__ xc,
                           const C* x, C* xout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * xc[ci[k]];
-  xout[i] = x[i] + s;
+  prolong_row<V, C, LdPlain>(i, rp, ci, v, xc, x, xout);
 }
 
 // x = Ainv b, one warp per row
@@ -394,11 +453,130 @@ __global__ void k_dense_gemv(int n, const C* __restrict__ A, const C* __restrict
   int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (row >= n) return;
-  const C* a = A + (size_t)row * n;
-  C s = 0;
-  for (int j = lane; j < n; j += 32) s += a[j] * b[j];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  const C s = gemv_row<C, LdPlain>(row, lane, n, A, b);
   if (lane == 0) x[row] = s;
+}
+
+// ---- fused coarse levels -------------------------------------------------
+// With the host-driven solve, the levels from the first one with at most
+// kTailRows rows down to the coarsest run in one cooperative launch: the
+// per-level steps of the V-cycle
+// (Jacobi sweeps, residual, restriction with the next level's first sweep,
+// the coarse product, prolongation, post-sweeps) as grid-stride loops over
+// rows, separated by grid barriers. Each barrier's wait is bounded: past the
+// limit it sets *err, every block leaves the kernel, and the solve reports
+// the error.
+constexpr int kTailRows = 32768;
+constexpr unsigned kBarrierSpins = 1u << 20;   // polls of L2: well under a second
+
+template <class V, class C>
+struct TailLevel {
+  int n, nc;
+  const int *rp, *ci, *prp, *pci, *rrp, *rci;
+  const V *v, *pv, *rv;
+  const C* dinv;
+  C *b, *x, *x2, *r;
+};
+
+template <class C>
+struct TailCoarse {
+  int n;
+  const C* ainv;
+  C *b, *x;
+};
+
+// One word per barrier sequence: every block adds 1, block 0 adds 2^31 minus
+// (blocks - 1), so the word's top bit flips once all blocks have arrived and
+// its low bits return to their value. Thread 0 of each block spins on the
+// top bit (bounded; *err is checked every 256 polls). Returns false once
+// *err is set.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int bad;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vb = bar;
+    volatile int* verr = err;
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+    __threadfence();
+    const unsigned old = atomicAdd(bar, add);
+    unsigned spins = 0;
+    int e = 0;
+    while (((old ^ *vb) & 0x80000000u) == 0) {
+      if ((++spins & 255u) == 0) {
+        e = *verr;
+        if (e) break;
+        if (spins > kBarrierSpins) {
+          atomicExch(err, 1);
+          e = 1;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    bad = e ? 1 : *verr;
+  }
+  __syncthreads();
+  return bad == 0;
+}
+
+template <class V, class C>
+__global__ void __launch_bounds__(256)
+k_vcycle_tail(const TailLevel<V, C>* __restrict__ lev, int nlev, TailCoarse<C> co, int nu_pre,
+              int nu_post, C omega, unsigned* bar, int* err) {
+  constexpr int kMaxTail = 32;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nthr = gridDim.x * blockDim.x;
+  bool cur_alt[kMaxTail];            // the level's current vector: x (false) or x2 (true)
+  for (int l = 0; l < nlev; ++l) {
+    const TailLevel<V, C> L = lev[l];
+    C* cur = L.x;                    // holds the first sweep from zero
+    C* alt = L.x2;
+    for (int s = 1; s < nu_pre; ++s) {
+      for (int i = tid; i < L.n; i += nthr)
+        jacobi_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.dinv, L.b, omega, cur, alt);
+      if (!grid_barrier(bar, err)) return;
+      C* t = cur;
+      cur = alt;
+      alt = t;
+    }
+    for (int i = tid; i < L.n; i += nthr) residual_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.b, cur, L.r);
+    if (!grid_barrier(bar, err)) return;
+    C* nb = l + 1 < nlev ? lev[l + 1].b : co.b;
+    C* nx = l + 1 < nlev ? lev[l + 1].x : nullptr;
+    const C* nd = l + 1 < nlev ? lev[l + 1].dinv : nullptr;
+    for (int i = tid; i < L.nc; i += nthr)
+      restrict_row<V, C, LdL2>(i, L.rrp, L.rci, L.rv, L.r, nb, nd, omega, nx);
+    if (!grid_barrier(bar, err)) return;
+    cur_alt[l] = cur != L.x;
+  }
+  {
+    const int lane = threadIdx.x & 31;
+    for (int row = tid >> 5; row < co.n; row += nthr >> 5) {
+      const C s = gemv_row<C, LdL2>(row, lane, co.n, co.ainv, co.b);
+      if (lane == 0) co.x[row] = s;
+    }
+    if (!grid_barrier(bar, err)) return;
+  }
+  for (int l = nlev - 1; l >= 0; --l) {
+    const TailLevel<V, C> L = lev[l];
+    const C* xc = l + 1 < nlev ? lev[l + 1].x : co.x;
+    C* cur = cur_alt[l] ? L.x2 : L.x;
+    C* target = nu_post % 2 == 0 ? L.x : L.x2;
+    for (int i = tid; i < L.n; i += nthr)
+      prolong_row<V, C, LdL2>(i, L.prp, L.pci, L.pv, xc, cur, target);
+    if (!grid_barrier(bar, err)) return;
+    cur = target;
+    C* alt = target == L.x ? L.x2 : L.x;
+    for (int s = 0; s < nu_post; ++s) {
+      for (int i = tid; i < L.n; i += nthr)
+        jacobi_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.dinv, L.b, omega, cur, alt);
+      if (!grid_barrier(bar, err)) return;
+      C* t = cur;
+      cur = alt;
+      alt = t;
+    }
+  }
 }
 
 template <class C>
@@ -530,12 +708,50 @@ bool has_sweep0(const Hierarchy& H, const mss_options& o, int l) {
 // omega D^-1 b, written by the kernel that formed b (the restriction on
 // coarser levels), so the remaining sweeps are plain Jacobi sweeps; the
 // values are those of the sweeps run from zero here.
+const unsigned char* tail_desc(Hierarchy& H, double*) { return H.tdesc.p; }
+const unsigned char* tail_desc(Hierarchy& H, float*) { return H.tdescf.p; }
+
+template <class V, class C>
+void launch_tail(Handle* h, Hierarchy& H) {
+  const int nlev = (int)H.lev.size() - 1 - H.tail;
+  Level& Cl = H.lev.back();
+  TailCoarse<C> co{Cl.n, coarse_inv(H, (C*)nullptr), level_b(Cl, (C*)nullptr),
+                   level_x(Cl, (C*)nullptr)};
+  const TailLevel<V, C>* lev =
+      reinterpret_cast<const TailLevel<V, C>*>(tail_desc(H, (C*)nullptr));
+  int nu_pre = h->opt.nu_pre, nu_post = h->opt.nu_post;
+  C omega = (C)h->opt.jacobi_omega;
+  unsigned* bar = H.tbar.p;
+  int* err = H.terr.p;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)H.tail_grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = h->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  MSS_CK(cudaLaunchKernelEx(&cfg, k_vcycle_tail<V, C>, lev, nlev, co, nu_pre, nu_post, omega, bar,
+                            err));
+  MSS_LAUNCH_CK("k_vcycle_tail");
+}
+
 template <class V, class C>
 void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out, bool x_has_sweep0) {
   Level& Lev = H.lev[l];
   const LV<V, C> L = view(Lev, (C*)nullptr);
   const mss_options& o = h->opt;
   const int n = L.n;
+  if (l == H.tail && x_has_sweep0 && !h->capturing && tail_desc(H, (C*)nullptr)) {
+    // b and the first sweep were written by the previous level's restriction
+    // into this level's vectors, which the fused launch reads. Launches from
+    // the host cost several microseconds each, more than a grid barrier; in
+    // a captured graph a launch boundary costs about a microsecond, less
+    // than a grid barrier (measured), so graphs keep the per-level kernels.
+    launch_tail<V, C>(h, H);
+    return;
+  }
   if (l == (int)H.lev.size() - 1) {
     k_dense_gemv<C><<<grid_for((long long)n * 32, 256), 256, 0, h->stream>>>(
         n, coarse_inv(H, (C*)nullptr), b, out);
@@ -760,6 +976,57 @@ Sweep0<double> sweep0(Handle* h, Hierarchy& H, double* x) {
 Sweep0<float> sweep0_mixed(Handle* h, Hierarchy& H, float* x) {
   if (!has_sweep0(H, h->opt, 0)) return {};
   return {H.lev[0].dinvf.p, (float)h->opt.jacobi_omega, x};
+}
+
+template <class V, class C>
+TailLevel<V, C> tail_level(Level& L) {
+  const LV<V, C> w = view(L, (C*)nullptr);
+  return {w.n, w.nc, w.rp, w.ci, w.prp, w.pci, w.rrp, w.rci, w.v, w.pv, w.rv, w.dinv,
+          level_b(L, (C*)nullptr), level_x(L, (C*)nullptr), w.x2, w.r};
+}
+
+template <class V, class C>
+void upload_tail(Handle* h, Hierarchy& H, DBuf<unsigned char>& dst) {
+  std::vector<TailLevel<V, C>> hv;
+  for (int l = H.tail; l + 1 < (int)H.lev.size(); ++l) hv.push_back(tail_level<V, C>(H.lev[l]));
+  const size_t bytes = sizeof(TailLevel<V, C>) * hv.size();
+  dst.reset(h, bytes);
+  MSS_CK(cudaMemcpyAsync(dst.p, hv.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+  MSS_CK(cudaStreamSynchronize(h->stream));   // hv lives on this frame
+}
+
+void prepare_tail(Handle* h, Hierarchy& H) {
+  H.tail = -1;
+  H.tdesc.release();
+  H.tdescf.release();
+  const int nl = (int)H.lev.size();
+  if (h->opt.smoother != MSS_JACOBI || nl < 3) return;
+  int t = -1;
+  for (int l = 1; l + 1 < nl; ++l)
+    if (H.lev[l].n <= kTailRows) {
+      t = l;
+      break;
+    }
+  if (t < 0) return;
+  int per_sm = 0;
+  MSS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vcycle_tail<double, double>,
+                                                       256, 0));
+  if (per_sm < 1) return;
+  int want = (H.lev[t].n + 255) / 256;
+  H.tail_grid = std::max(1, std::min(want, h->num_sms));
+  H.tail = t;
+  H.tbar.reset(h, 1);
+  H.terr.reset(h, 1);
+  MSS_CK(cudaMemsetAsync(H.tbar.p, 0, sizeof(unsigned), h->stream));
+  MSS_CK(cudaMemsetAsync(H.terr.p, 0, sizeof(int), h->stream));
+  upload_tail<double, double>(h, H, H.tdesc);
+  if (h->opt.precision == MSS_MIXED) upload_tail<__nv_bfloat16, float>(h, H, H.tdescf);
+}
+
+void check_tail(Handle* h, Hierarchy& H) {
+  if (H.tail < 0 || !H.terr.p) return;
+  if (read_int(h, H.terr.p) != 0)
+    fail(MSS_ERR_CUDA, "a grid barrier of the fused coarse V-cycle levels exceeded its wait limit");
 }
 
 void vcycle(Handle* h, Hierarchy& H, const double* b, double* x, bool x_has_sweep0) {

@@ -283,6 +283,8 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
     H.zPf.reset(h, N);
     H.vPf.reset(h, N);
   }
+  if (H.amgT.present()) prepare_tail(h, H.amgT);
+  if (H.amgP.present()) prepare_tail(h, H.amgP);
   MSS_CK(cudaStreamSynchronize(H.stream));
   H.J = *J;
   H.ready = true;
@@ -456,6 +458,8 @@ int mss_apply(mss_handle* hh, const double* r, double* y) {
     need_ready(hh->h);
     if (!r || !y || r == y) fail(MSS_ERR_INVALID_ARG, "r and y must be distinct");
     precond_apply(&hh->h, r, y);
+    check_tail(&hh->h, hh->h.amgT);
+    check_tail(&hh->h, hh->h.amgP);
   });
 }
 
@@ -474,6 +478,7 @@ int mss_stage_apply(mss_handle* hh, int which, const double* r, double* y) {
     gather_var(&H, r, var, H.rT.p);
     vcycle(&H, A, H.rT.p, H.xT.p);
     scatter_var_zero(&H, H.xT.p, var, y);
+    check_tail(&H, A);
   });
 }
 

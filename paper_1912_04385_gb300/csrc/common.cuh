@@ -114,6 +114,14 @@ struct Hierarchy {
   DBuf<double> coarse_inv;    // dense inverse of the coarsest operator, row-major
   DBuf<float> coarse_invf;    // its FP32 copy (mixed precision)
   int nc = 0;                 // size of the coarsest level
+  // fused coarse levels: the first level of the tail (-1: none), its launch
+  // width, device descriptors of the tail levels (FP64 and mixed), the grid
+  // barrier's words and its error flag
+  int tail = -1;
+  int tail_grid = 0;
+  DBuf<unsigned char> tdesc, tdescf;
+  DBuf<unsigned> tbar;
+  DBuf<int> terr;
   bool present() const { return !lev.empty(); }
 };
 
@@ -319,6 +327,11 @@ void vcycle(Handle* h, Hierarchy& H, const double* b, double* x, bool x_has_swee
 void vcycle_mixed(Handle* h, Hierarchy& H, const float* b, float* x,   // BF16 / FP32
                   bool x_has_sweep0 = false);
 void pack_hierarchy_mixed(Handle* h, Hierarchy& H);
+// the fused coarse-level launch's descriptors (after the set-up and, for the
+// mixed form, after pack_hierarchy_mixed); no tail when it would not pay
+void prepare_tail(Handle* h, Hierarchy& H);
+// fails with MSS_ERR_CUDA if a grid barrier of the fused coarse levels gave up
+void check_tail(Handle* h, Hierarchy& H);
 void gather_var(Handle* h, const double* v, int var, double* out, Sweep0<double> s0 = {});
 void gather_var(Handle* h, const double* v, int var, float* out, Sweep0<float> s0 = {});
 void scatter_var_zero(Handle* h, const double* s, int var, double* out);

@@ -789,8 +789,11 @@ void precond_apply(Handle* h, const double* r, double* y) {
 
 int fgmres(Handle* h, const double* b, double* x, double tol, int maxit, mss_result* out) {
   Krylov K = workspace(h);
-  if (h->opt.driver == MSS_DRIVER_GRAPH) return fgmres_graph(h, K, b, x, tol, maxit, out);
-  return fgmres_host(h, K, b, x, tol, maxit, out);
+  const int st = h->opt.driver == MSS_DRIVER_GRAPH ? fgmres_graph(h, K, b, x, tol, maxit, out)
+                                                   : fgmres_host(h, K, b, x, tol, maxit, out);
+  check_tail(h, h->amgT);
+  check_tail(h, h->amgP);
+  return st;
 }
 
 }  // namespace mss

@@ -268,3 +268,25 @@ def test_larger_hierarchy(mss, scheme, smoother, precision):
     g2 = _gpu(mss, s, scheme=scheme, smoother=smoother, amg_max_coarse=100, restart=50)
     xg, ig = g2.solve(_t(s.b), tol=1e-8, maxit=300)
     assert abs(ig["iters"] - io["iters"]) <= 1
+
+
+@pytest.mark.parametrize("driver", ["host", "graph"])
+def test_zero_rhs_and_empty_matrix(mss, driver):
+    # b = 0: nothing to iterate; x = 0, no iterations, status OK
+    s = _sys(CASES[1])
+    g = _gpu(mss, s, driver=driver, restart=100, amg_max_coarse=40)
+    x, info = g.solve(_t(np.zeros_like(s.b)), tol=1e-8, maxit=50)
+    assert info["status"] == 0 and info["iters"] == 0
+    assert not np.any(_n(x))
+    # the same handle still solves a nonzero right-hand side afterwards
+    x, info = g.solve(_t(s.b), tol=1e-8, maxit=400)
+    o = _orc(s, restart=100, max_coarse=40)
+    xo, io = o.fgmres(o.scale_rhs(s.b), tol=1e-8, maxit=400, restart=100)
+    assert info["status"] == 0 and abs(info["iters"] - io["iters"]) <= 1
+    # no cells: rejected at set-up
+    z = torch.zeros(1, dtype=torch.int32, device="cuda")
+    e0 = torch.zeros(0, dtype=torch.int32, device="cuda")
+    v0 = torch.zeros(0, dtype=torch.float64, device="cuda")
+    with pytest.raises(mss.MssError) as e:
+        mss.Solver().setup(z, e0, v0, 4)
+    assert e.value.status == mss.ERR_INVALID_ARG
