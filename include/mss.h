@@ -284,6 +284,13 @@ int mss_bilu_num_colours(mss_handle* h, int32_t* ncolours);
  * into caller-owned device arrays of N entries. */
 int mss_bilu_ordering(mss_handle* h, int32_t* colour, int32_t* perm);
 
+/* Runs, on the handle's stream, one wait of the grid barrier used by the
+ * fused coarse V-cycle levels that can never complete (it expects a block
+ * that is not launched). The wait gives up after its poll limit (well under
+ * a second), sets the barrier's error flag and the kernel returns, leaving
+ * the context usable. *timed_out (host) = 1 when that happened. */
+int mss_probe_wait_limit(mss_handle* h, int32_t* timed_out);
+
 /* ---- measurement --------------------------------------------------------- */
 /* Number of kernel launches made by this library in this process since the
  * last call with reset != 0 (the count before the reset is returned). */

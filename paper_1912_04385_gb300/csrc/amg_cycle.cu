@@ -490,13 +490,13 @@ struct TailCoarse {
 // its low bits return to their value. Thread 0 of each block spins on the
 // top bit (bounded; *err is checked every 256 polls). Returns false once
 // *err is set.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks) {
   __shared__ int bad;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vb = bar;
     volatile int* verr = err;
-    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1) : 1u;
     __threadfence();
     const unsigned old = atomicAdd(bar, add);
     unsigned spins = 0;
@@ -520,6 +520,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
   return bad == 0;
 }
 
+// A barrier that expects a second block which is never launched: its wait
+// runs out, sets *err and returns (the bounded-wait path, exercised by a test).
+__global__ void k_wait_probe(unsigned* bar, int* err) { grid_barrier(bar, err, 2u); }
+
 template <class V, class C>
 __global__ void __launch_bounds__(256)
 k_vcycle_tail(const TailLevel<V, C>* __restrict__ lev, int nlev, TailCoarse<C> co, int nu_pre,
@@ -535,19 +539,19 @@ k_vcycle_tail(const TailLevel<V, C>* __restrict__ lev, int nlev, TailCoarse<C> c
     for (int s = 1; s < nu_pre; ++s) {
       for (int i = tid; i < L.n; i += nthr)
         jacobi_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.dinv, L.b, omega, cur, alt);
-      if (!grid_barrier(bar, err)) return;
+      if (!grid_barrier(bar, err, gridDim.x)) return;
       C* t = cur;
       cur = alt;
       alt = t;
     }
     for (int i = tid; i < L.n; i += nthr) residual_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.b, cur, L.r);
-    if (!grid_barrier(bar, err)) return;
+    if (!grid_barrier(bar, err, gridDim.x)) return;
     C* nb = l + 1 < nlev ? lev[l + 1].b : co.b;
     C* nx = l + 1 < nlev ? lev[l + 1].x : nullptr;
     const C* nd = l + 1 < nlev ? lev[l + 1].dinv : nullptr;
     for (int i = tid; i < L.nc; i += nthr)
       restrict_row<V, C, LdL2>(i, L.rrp, L.rci, L.rv, L.r, nb, nd, omega, nx);
-    if (!grid_barrier(bar, err)) return;
+    if (!grid_barrier(bar, err, gridDim.x)) return;
     cur_alt[l] = cur != L.x;
   }
   {
@@ -556,7 +560,7 @@ k_vcycle_tail(const TailLevel<V, C>* __restrict__ lev, int nlev, TailCoarse<C> c
       const C s = gemv_row<C, LdL2>(row, lane, co.n, co.ainv, co.b);
       if (lane == 0) co.x[row] = s;
     }
-    if (!grid_barrier(bar, err)) return;
+    if (!grid_barrier(bar, err, gridDim.x)) return;
   }
   for (int l = nlev - 1; l >= 0; --l) {
     const TailLevel<V, C> L = lev[l];
@@ -565,13 +569,13 @@ k_vcycle_tail(const TailLevel<V, C>* __restrict__ lev, int nlev, TailCoarse<C> c
     C* target = nu_post % 2 == 0 ? L.x : L.x2;
     for (int i = tid; i < L.n; i += nthr)
       prolong_row<V, C, LdL2>(i, L.prp, L.pci, L.pv, xc, cur, target);
-    if (!grid_barrier(bar, err)) return;
+    if (!grid_barrier(bar, err, gridDim.x)) return;
     cur = target;
     C* alt = target == L.x ? L.x2 : L.x;
     for (int s = 0; s < nu_post; ++s) {
       for (int i = tid; i < L.n; i += nthr)
         jacobi_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.dinv, L.b, omega, cur, alt);
-      if (!grid_barrier(bar, err)) return;
+      if (!grid_barrier(bar, err, gridDim.x)) return;
       C* t = cur;
       cur = alt;
       alt = t;
@@ -1021,6 +1025,16 @@ void prepare_tail(Handle* h, Hierarchy& H) {
   MSS_CK(cudaMemsetAsync(H.terr.p, 0, sizeof(int), h->stream));
   upload_tail<double, double>(h, H, H.tdesc);
   if (h->opt.precision == MSS_MIXED) upload_tail<__nv_bfloat16, float>(h, H, H.tdescf);
+}
+
+int wait_limit_probe(Handle* h) {
+  DBuf<unsigned> bar(h, 1);
+  DBuf<int> err(h, 1);
+  MSS_CK(cudaMemsetAsync(bar.p, 0, sizeof(unsigned), h->stream));
+  MSS_CK(cudaMemsetAsync(err.p, 0, sizeof(int), h->stream));
+  k_wait_probe<<<1, 32, 0, h->stream>>>(bar.p, err.p);
+  MSS_LAUNCH_CK("k_wait_probe");
+  return read_int(h, err.p);
 }
 
 void check_tail(Handle* h, Hierarchy& H) {

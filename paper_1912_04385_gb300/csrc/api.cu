@@ -639,6 +639,11 @@ int mss_bilu_ordering(mss_handle* hh, int32_t* colour, int32_t* perm) {
 
 long long mss_kernel_launches(int reset) { return launch_count(reset != 0); }
 
+int mss_probe_wait_limit(mss_handle* hh, int32_t* timed_out) {
+  if (!hh || !timed_out) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] { *timed_out = wait_limit_probe(&hh->h) != 0 ? 1 : 0; });
+}
+
 int mss_trace_enable(mss_handle* hh, int enable) {
   if (!hh) return MSS_ERR_INVALID_ARG;
   return guarded(hh, [&] {

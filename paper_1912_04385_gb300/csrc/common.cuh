@@ -332,6 +332,8 @@ void pack_hierarchy_mixed(Handle* h, Hierarchy& H);
 void prepare_tail(Handle* h, Hierarchy& H);
 // fails with MSS_ERR_CUDA if a grid barrier of the fused coarse levels gave up
 void check_tail(Handle* h, Hierarchy& H);
+// runs one grid-barrier wait that cannot complete; returns its error flag
+int wait_limit_probe(Handle* h);
 void gather_var(Handle* h, const double* v, int var, double* out, Sweep0<double> s0 = {});
 void gather_var(Handle* h, const double* v, int var, float* out, Sweep0<float> s0 = {});
 void scatter_var_zero(Handle* h, const double* s, int var, double* out);

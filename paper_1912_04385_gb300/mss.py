@@ -28,7 +28,7 @@ DRIVERS = {"host": 0, "graph": 1}
 EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
            "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
            "mss_residual_norm", "mss_residual_norm_noalloc", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
-           "mss_bilu_num_colours", "mss_bilu_ordering", "mss_kernel_launches",
+           "mss_bilu_num_colours", "mss_bilu_ordering", "mss_probe_wait_limit", "mss_kernel_launches",
            "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error",
            "mss_batch_create", "mss_batch_destroy", "mss_batch_solve", "mss_batch_tuned",
            "mss_batch_last_error", "mss_gnn_num_params", "mss_gnn_create", "mss_gnn_destroy",
@@ -121,6 +121,7 @@ def load(path: Path | str | None = None):
     L.mss_amg_level_copy.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P, P, P]
     L.mss_bilu_num_colours.argtypes = [P, P]
     L.mss_bilu_ordering.argtypes = [P, P, P]
+    L.mss_probe_wait_limit.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     L.mss_kernel_launches.restype = C.c_longlong
     L.mss_kernel_launches.argtypes = [C.c_int]
     L.mss_trace_enable.argtypes = [P, C.c_int]
@@ -333,6 +334,13 @@ class Solver:
         if st not in (OK, ERR_NOT_CONVERGED):
             self._check(st, "mss_solve_host")
         return x, res.as_dict()
+
+    def probe_wait_limit(self) -> bool:
+        """Runs one grid-barrier wait that cannot complete; True when it gave
+        up at its limit and the kernel returned."""
+        t = C.c_int32(0)
+        self._check(self.lib.mss_probe_wait_limit(self.h, C.byref(t)), "mss_probe_wait_limit")
+        return bool(t.value)
 
     # ---- measurement ------------------------------------------------------
     def trace(self, enable: bool = True):

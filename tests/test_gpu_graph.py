@@ -144,3 +144,13 @@ def test_pool_allocator_handle_and_repeated_setup(mss):
     gp.setup_system(_sys(CASES[2]), scheme="cpr")
     x2, i2 = gp.solve(_t(_sys(CASES[2]).b), tol=1e-8, maxit=300)
     assert i2["status"] == 0
+
+
+def test_grid_barrier_wait_runs_out(mss):
+    # a barrier wait that nothing completes gives up at its limit, the kernel
+    # returns with the error flag set, and the context stays usable
+    s = _sys(CASES[0])
+    g = mss.Solver().setup_system(s, amg_max_coarse=40)
+    assert g.probe_wait_limit()
+    x, info = g.solve(torch.from_numpy(s.b).cuda(), tol=1e-8, maxit=300)
+    assert info["status"] == 0
