@@ -342,6 +342,9 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
 // by two), so a fetch has two steps to land; the addresses depend only on the
 // position.
 constexpr int kChainDepth = 2;   // chain rows prefetched ahead (4 measured no faster)
+// Chain passes have few warps (32 / NB strips each) and are bound by the FP64
+// pipe of the SMs they run on: two-warp CTAs spread them over all SMs.
+constexpr int kChainThreads = 64;
 
 template <int NB, class C>
 struct ChainRow {
@@ -735,7 +738,8 @@ void bilu_setup_nb(Handle* h) {
   for (int c = 0; c < h->ncol; ++c) {
     const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
     if (s1 <= s0) continue;
-    k_bilu_factor<NB><<<grid_for((long long)(s1 - s0) * 32, 256), 256, 0, h->stream>>>(
+    // two-warp CTAs: the FP64-bound strips spread over all SMs
+    k_bilu_factor<NB><<<grid_for((long long)(s1 - s0) * 32, 64), 64, 0, h->stream>>>(
         s0, s1, h->st_first.p, h->st_len.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p, h->fdinv.p,
         bjac ? 1 : 0, bad.p);
     MSS_LAUNCH_CK("k_bilu_factor");
@@ -796,7 +800,8 @@ void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, con
     MSS_LAUNCH_CK("k_bilu_fwd_par");
     if (chains) {
       const long long sw = (s1 - s0 + RPW - 1) / RPW;
-      k_bilu_fwd_chain<NB, V, C><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
+      k_bilu_fwd_chain<NB, V, C><<<grid_for(sw * 32, kChainThreads), kChainThreads, 0,
+                                   h->stream>>>(
           s0, s1, h->st_first.p, h->st_len.p, h->fslo.p, h->fdp.p, h->fpos.p, F.fv, F.cL,
           h->cflag.p, F.w);
       MSS_LAUNCH_CK("k_bilu_fwd_chain");
@@ -814,7 +819,8 @@ void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, con
       MSS_LAUNCH_CK("k_bilu_bwd_par");
     }
     const long long sw = (s1 - s0 + RPW - 1) / RPW;
-    k_bilu_bwd_chain<NB, V, C><<<grid_for(sw * 32, T), T, 0, h->stream>>>(
+    k_bilu_bwd_chain<NB, V, C><<<grid_for(sw * 32, kChainThreads), kChainThreads, 0,
+                                 h->stream>>>(
         s0, s1, h->st_first.p, h->st_len.p, h->fdp.p, h->fshi.p, h->fpos.p, F.fv, F.fdinv, F.cG,
         h->cflag.p, F.w, bjac ? 0 : 1);
     MSS_LAUNCH_CK("k_bilu_bwd_chain");
