@@ -738,8 +738,7 @@ void bilu_setup_nb(Handle* h) {
   for (int c = 0; c < h->ncol; ++c) {
     const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
     if (s1 <= s0) continue;
-    // two-warp CTAs: the FP64-bound strips spread over all SMs
-    k_bilu_factor<NB><<<grid_for((long long)(s1 - s0) * 32, 64), 64, 0, h->stream>>>(
+    k_bilu_factor<NB><<<grid_for((long long)(s1 - s0) * 32, 256), 256, 0, h->stream>>>(
         s0, s1, h->st_first.p, h->st_len.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p, h->fdinv.p,
         bjac ? 1 : 0, bad.p);
     MSS_LAUNCH_CK("k_bilu_factor");
