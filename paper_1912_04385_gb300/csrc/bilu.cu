@@ -30,37 +30,55 @@ constexpr uint64_t KEY_CELL = 0xFFFFULL << 32;    // priorities of single cells
 constexpr uint64_t KEY_STRIP = 0xFFFEULL << 32;   // priorities of strips
 
 // ---- Jones-Plassmann colouring of strips of S consecutive cells -----------
-// (S = 1 with the cell key is the point-multicolour order)
+// (S = 1 with the cell key is the point-multicolour order). One warp per
+// strip, the lanes over the strip's cells: an uncoloured strip whose
+// priority beats every uncoloured neighbour strip picks the smallest colour
+// no neighbour strip has.
 __global__ void k_jp_pick(int ns, int S, int n, const int* __restrict__ rp,
                           const int* __restrict__ ci, uint64_t seed, uint64_t key,
                           const int* __restrict__ scol, int* __restrict__ pick) {
-  int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= ns) return;
+  const int lane = threadIdx.x & 31;
+  const long long a = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (a >= ns) return;                     // uniform per warp
   int chosen = -1;
   if (scol[a] < 0) {
-    const int lo = a * S, hi = min(lo + S, n);
+    const int lo = (int)a * S, hi = min(lo + S, n);
     const uint64_t pa = splitmix64(seed, key | (uint64_t)(unsigned)a);
     bool best = true;
-    for (int i = lo; i < hi && best; ++i)
+    for (int i = lo + lane; i < hi && best; i += 32)
       for (int k = rp[i]; k < rp[i + 1] && best; ++k) {
-        int b = ci[k] / S;
+        const int b = ci[k] / S;
         if (b == a || scol[b] >= 0) continue;
-        uint64_t pb = splitmix64(seed, key | (uint64_t)(unsigned)b);
+        const uint64_t pb = splitmix64(seed, key | (uint64_t)(unsigned)b);
         if (pb > pa || (pb == pa && b > a)) best = false;
       }
-    if (best) {
-      for (int c = 0;; ++c) {
-        bool used = false;
-        for (int i = lo; i < hi && !used; ++i)
-          for (int k = rp[i]; k < rp[i + 1]; ++k) {
-            int b = ci[k] / S;
-            if (b != a && scol[b] == c) { used = true; break; }
-          }
-        if (!used) { chosen = c; break; }
+    if (__all_sync(0xffffffffu, best)) {
+      // colours of the neighbour strips below 64 as a bit set, then the
+      // smallest free one (a search past 64 when all of those are taken)
+      unsigned long long used = 0;
+      for (int i = lo + lane; i < hi; i += 32)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+          const int b = ci[k] / S;
+          const int cb = b != a ? scol[b] : -1;
+          if (cb >= 0 && cb < 64) used |= 1ULL << cb;
+        }
+      for (int o = 16; o > 0; o >>= 1) used |= __shfl_xor_sync(0xffffffffu, used, o);
+      if (~used != 0ULL) {
+        chosen = __ffsll((long long)~used) - 1;
+      } else {
+        for (int c = 64;; ++c) {
+          bool hit = false;
+          for (int i = lo + lane; i < hi && !hit; i += 32)
+            for (int k = rp[i]; k < rp[i + 1]; ++k) {
+              const int b = ci[k] / S;
+              if (b != a && scol[b] == c) { hit = true; break; }
+            }
+          if (!__any_sync(0xffffffffu, hit)) { chosen = c; break; }
+        }
       }
     }
   }
-  pick[a] = chosen;
+  if (lane == 0) pick[a] = chosen;
 }
 
 __global__ void k_jp_commit(int ns, const int* __restrict__ pick, int* __restrict__ scol,
@@ -438,25 +456,46 @@ template <int NB>
 __global__ void k_strip_upper_scale(int n, const int* __restrict__ fdp,
                                     const int* __restrict__ fshi,
                                     const double* __restrict__ fdinv, double* __restrict__ fv) {
+  // NB lanes per row q (32 / NB rows per warp), lane r forms row r of
+  // U_qq^{-1} U_qj with the sums in ascending m; a block is read by all lanes
+  // of its row before any of them writes
   constexpr int B2 = NB * NB;
+  constexpr int RPW = 32 / NB;
   const int lane = threadIdx.x & 31;
-  const long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (q >= n) return;
-  const double* Ui = fdinv + (size_t)q * B2;
-  for (int g = fdp[q] + 1; g < fshi[q]; ++g) {
-    double* U = fv + (size_t)g * B2;
-    double out[(B2 + 31) / 32];
-    int tt = 0;
-    for (int idx = lane; idx < B2; idx += 32, ++tt) {
-      const int r = idx / NB, c = idx - r * NB;
-      double s = 0.0;
+  const int sub = lane / NB, r = lane - sub * NB;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long qq = warp * RPW + sub;
+  const bool active = sub < RPW && qq < n;
+  const int q = active ? (int)qq : 0;
+  int g0 = 0, cnt = 0;
+  double ui[NB];
 #pragma unroll
-      for (int m = 0; m < NB; ++m) s += Ui[r * NB + m] * U[m * NB + c];
-      out[tt] = s;
+  for (int m = 0; m < NB; ++m) ui[m] = 0.0;
+  if (active) {
+    g0 = fdp[q] + 1;
+    cnt = fshi[q] - g0;
+#pragma unroll
+    for (int m = 0; m < NB; ++m) ui[m] = fdinv[(size_t)q * B2 + r * NB + m];
+  }
+  const int maxc = warp_max(cnt);
+  for (int it = 0; it < maxc; ++it) {
+    const bool on = it < cnt;
+    double out[NB];
+    if (on) {
+      const double* U = fv + (size_t)(g0 + it) * B2;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < NB; ++m) s += ui[m] * U[m * NB + c];
+        out[c] = s;
+      }
     }
     __syncwarp();
-    tt = 0;
-    for (int idx = lane; idx < B2; idx += 32, ++tt) U[idx] = out[tt];
+    if (on) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c) fv[(size_t)(g0 + it) * B2 + r * NB + c] = out[c];
+    }
     __syncwarp();
   }
 }
@@ -650,8 +689,8 @@ void bilu_setup_nb(Handle* h) {
       // picks nothing, so the colouring is the round-by-round one
       for (int r = 0; r < 3; ++r) {
         if (++rounds > ns + 3) fail(MSS_ERR_CUDA, "colouring did not terminate");
-        k_jp_pick<<<grid_for(ns, 128), 128, 0, h->stream>>>(ns, S, N, h->rp.p, h->ci.p,
-                                                            h->opt.seed, key, scol.p, pick.p);
+        k_jp_pick<<<grid_for((long long)ns * 32, 128), 128, 0, h->stream>>>(
+            ns, S, N, h->rp.p, h->ci.p, h->opt.seed, key, scol.p, pick.p);
         MSS_LAUNCH_CK("k_jp_pick");
         fill_int(h, left.p, 0, 1);
         k_jp_commit<<<grid_for(ns, 256), 256, 0, h->stream>>>(ns, pick.p, scol.p, left.p,
@@ -749,8 +788,9 @@ void bilu_setup_nb(Handle* h) {
                                      std::to_string(badq));
   if (!bjac) {
     if (strips && S > 1) {
-      k_strip_upper_scale<NB><<<grid_for((long long)N * 32, 256), 256, 0, h->stream>>>(
-          N, h->fdp.p, h->fshi.p, h->fdinv.p, h->fv.p);
+      constexpr int RPW = 32 / NB;
+      k_strip_upper_scale<NB><<<grid_for(((long long)N + RPW - 1) / RPW * 32, 256), 256, 0,
+                                 h->stream>>>(N, h->fdp.p, h->fshi.p, h->fdinv.p, h->fv.p);
       MSS_LAUNCH_CK("k_strip_upper_scale");
     }
     // chain blocks (zero blocks and no flags when strips are single cells)
