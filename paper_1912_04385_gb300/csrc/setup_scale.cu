@@ -93,13 +93,18 @@ __device__ bool gj_inverse(int m, double* a, double* inv) {
 template <int NB>
 __global__ void k_build_w(const double* __restrict__ vals, const int* __restrict__ diag, int N,
                           int p, int t, int scheme, int col_major, double* __restrict__ wrows,
-                          int* __restrict__ flag) {
+                          int* __restrict__ flag, double* __restrict__ dcopy) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double D[NB * NB];
   const double* src = vals + (size_t)diag[i] * NB * NB;
   for (int r = 0; r < NB; ++r)
     for (int c = 0; c < NB; ++c) D[r * NB + c] = col_major ? src[c * NB + r] : src[r * NB + c];
+  if (dcopy) {   // the block as stored, for k_apply_w (host-resident values are read once)
+    for (int r = 0; r < NB; ++r)
+      for (int c = 0; c < NB; ++c)
+        dcopy[(size_t)i * NB * NB + (col_major ? c * NB + r : r * NB + c)] = D[r * NB + c];
+  }
   double wp[NB], wt[NB];
   for (int k = 0; k < NB; ++k) {
     wp[k] = (k == p) ? 1.0 : 0.0;
@@ -179,13 +184,18 @@ __global__ void k_block_rows(int N, const int* __restrict__ rp, int* __restrict_
 template <int NB>
 __global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict__ brow,
                           long long nnzb, int p, int t, int scheme, int col_major,
-                          const double* __restrict__ wrows, double* __restrict__ abar) {
+                          const double* __restrict__ wrows, double* __restrict__ abar,
+                          const int* __restrict__ diag, const double* __restrict__ dcopy) {
   constexpr int B2 = NB * NB;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= nnzb * NB) return;
   const long long e = tid / NB;
   const int c = (int)(tid - e * NB);
   const double* src = vals + (size_t)e * B2;
+  if (dcopy) {   // diagonal blocks from the device copy k_build_w made
+    const int i = brow[e];
+    if (diag[i] == e) src = dcopy + (size_t)i * B2;
+  }
   double col[NB];
 #pragma unroll
   for (int k = 0; k < NB; ++k) col[k] = col_major ? src[c * NB + k] : src[k * NB + c];
@@ -241,8 +251,16 @@ void build_scaling_nb(Handle* h, const double* vals, bool col_major) {
   int scheme = h->opt.scheme;
   DBuf<int> flag(h, 1);
   fill_int(h, flag.p, 0x7fffffff, 1);
+  // values in host memory are read over the host link: k_build_w keeps a
+  // device copy of the diagonal blocks so that k_apply_w reads each block once
+  DBuf<double> dcopy;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, vals) == cudaSuccess && at.type == cudaMemoryTypeHost)
+    dcopy.reset(h, (size_t)N * NB * NB);
+  else
+    cudaGetLastError();
   k_build_w<NB><<<grid_for(N, 128), 128, 0, h->stream>>>(vals, h->diag.p, N, h->p, h->t, scheme,
-                                                         col_major, h->wrows.p, flag.p);
+                                                         col_major, h->wrows.p, flag.p, dcopy.p);
   MSS_LAUNCH_CK("k_build_w");
   int bad = read_int(h, flag.p);
   if (bad != 0x7fffffff)
@@ -254,7 +272,7 @@ void build_scaling_nb(Handle* h, const double* vals, bool col_major) {
   long long tot = (long long)h->nnzb * NB;
   k_apply_w<NB><<<grid_for(tot, 256), 256, 0, h->stream>>>(vals, brow.p, h->nnzb, h->p, h->t,
                                                            scheme, col_major, h->wrows.p,
-                                                           h->abar.p);
+                                                           h->abar.p, h->diag.p, dcopy.p);
   MSS_LAUNCH_CK("k_apply_w");
 }
 
