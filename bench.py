@@ -21,6 +21,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 from pathlib import Path
@@ -83,7 +84,7 @@ class Clocks:
     def __init__(self, enabled, device):
         self.p = None
         self.device = device
-        self.path = ROOT / "gpurun_out" / f"clocks_rank{device}.csv"
+        self.path = Path(tempfile.gettempdir()) / f"mss_bench_clocks_rank{device}.csv"
         if not enabled:
             return
         try:
@@ -281,7 +282,7 @@ def run_ours(a, rank, world, dist):
     out = {"metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded generator, see DESIGN.md)",
+           "data": "synthetic (seeded 5-point thermal-compositional generator; no dataset)",
            "config": {**workload_config(a), "parallelism": f"replicas x{world}"},
            "iters": iters, "iters_mean": float(np.mean(iters)),
            "wall_ms_per_system": round(wall_ms / (nsys * world), 3),
