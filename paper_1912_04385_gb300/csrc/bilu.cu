@@ -355,11 +355,13 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
 
 // forward, chain: w_q -= sum_{in-strip lower} L_qk w_k, rows in order. The
 // coupling to the previous row comes from the dense per-position copy cL and
-// the previous row's values held in the lanes' registers. Rows are fetched
-// two steps ahead into two alternating register buffers (the loop is unrolled
-// by two), so a fetch has two steps to land; the addresses depend only on the
-// position.
-constexpr int kChainDepth = 2;   // chain rows prefetched ahead (4 measured no faster)
+// the previous row's values held in the lanes' registers. Two rows are held
+// in registers and each is refilled two rows ahead right after its use; the
+// addresses are offsets from the strip's first row (a third fewer
+// instructions per step than per-row 64-bit addressing; the step's latency
+// is made of them). The backward chain keeps a ring of kChainDepth rows
+// fetched ahead by position (4 and 8 rows ahead measured no faster).
+constexpr int kChainDepth = 2;   // chain rows prefetched ahead
 // Chain passes have few warps (32 / NB strips each) and are bound by the FP64
 // pipe of the SMs they run on: two-warp CTAs spread them over all SMs.
 constexpr int kChainThreads = 64;
@@ -400,50 +402,60 @@ __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_firs
   const int len = active ? st_len[kk] : 0;
   const int maxlen = warp_max(len);
   const int base = sub * NB;
-  // ring of kChainDepth rows in flight: the loads of row q+D are issued
-  // while row q is computed (D rows of DRAM latency hidden per chain step)
-  ChainRow<NB, C> buf[kChainDepth];
+  // the strip's rows for this lane: t at wl[i * NB], the chain row at
+  // ml[i * B2 + c], the flag at fl[i]; two rows held in registers (even and
+  // odd steps), each refilled two rows ahead right after its use
+  C* wl = w + (size_t)first * NB + comp;
+  const V* ml = cL + (size_t)first * B2 + comp * NB;
+  const int* fl = cflag + first;
+  C t0 = 0, t1 = 0, m0[NB], m1[NB];
+  int f0 = 0, f1 = 0;
 #pragma unroll
-  for (int u = 0; u < kChainDepth; ++u) {
-    buf[u].t = 0;
-    buf[u].fl = 0;
+  for (int c = 0; c < NB; ++c) m0[c] = m1[c] = 0;
+  if (len > 0) {
+    t0 = wl[0];
+    f0 = fl[0];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) buf[u].m[c] = 0;
-    if (u < len) chain_fetch(buf[u], w, cL, cflag, (size_t)first + u, comp);
+    for (int c = 0; c < NB; ++c) m0[c] = cvt<C>(ml[c]);
+  }
+  if (len > 1) {
+    t1 = wl[NB];
+    f1 = fl[1];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) m1[c] = cvt<C>(ml[B2 + c]);
   }
   C prev = 0;                               // component comp of w_{q-1}
-  auto step = [&](int it, ChainRow<NB, C>& R) {
-    const bool on = it < len;
-    const int q = first + it;
-    C acc = R.t;
-    C mc[NB];
-#pragma unroll
-    for (int c = 0; c < NB; ++c) mc[c] = R.m[c];
-    const int fl = R.fl;
-    if (it + kChainDepth < len) chain_fetch(R, w, cL, cflag, (size_t)q + kChainDepth, comp);
+  auto step = [&](int it, C& t, C (&m)[NB], int& f) {
     C pc[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) pc[c] = __shfl_sync(0xffffffffu, prev, (base + c) & 31);
-    if (on) {
+    if (it < len) {
+      C acc = t;
 #pragma unroll
-      for (int c = 0; c < NB; ++c) acc -= mc[c] * pc[c];
-      if (fl & 1) {                          // other in-strip couplings, from memory
-        for (int f = fslo[q]; f < fdp[q]; ++f) {
-          const V* Lr = fv + (size_t)f * B2 + comp * NB;
-          const C* wk = w + (size_t)fpos[f] * NB;
+      for (int c = 0; c < NB; ++c) acc -= m[c] * pc[c];
+      if (f & 1) {                           // other in-strip couplings, from memory
+        const int q = first + it;
+        for (int g = fslo[q]; g < fdp[q]; ++g) {
+          const V* Lr = fv + (size_t)g * B2 + comp * NB;
+          const C* wk = w + (size_t)fpos[g] * NB;
 #pragma unroll
           for (int c = 0; c < NB; ++c) acc -= cvt<C>(Lr[c]) * wk[c];
         }
       }
-      w[(size_t)q * NB + comp] = acc;
+      wl[it * NB] = acc;
       prev = acc;
+    }
+    if (it + 2 < len) {
+      t = wl[(it + 2) * NB];
+      f = fl[it + 2];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) m[c] = cvt<C>(ml[(it + 2) * B2 + c]);
     }
     __syncwarp();
   };
-  for (int it = 0; it < maxlen; it += kChainDepth) {
-#pragma unroll
-    for (int u = 0; u < kChainDepth; ++u)
-      if (it + u < maxlen) step(it + u, buf[u]);
+  for (int it = 0; it < maxlen; it += 2) {
+    step(it, t0, m0, f0);
+    if (it + 1 < maxlen) step(it + 1, t1, m1, f1);
   }
 }
 
