@@ -290,3 +290,22 @@ def test_zero_rhs_and_empty_matrix(mss, driver):
     with pytest.raises(mss.MssError) as e:
         mss.Solver().setup(z, e0, v0, 4)
     assert e.value.status == mss.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("nu", [(1, 1), (3, 1), (1, 0), (2, 3)])
+def test_smoothing_counts(mss, nu):
+    # other V(nu_pre, nu_post) counts: the first sweep written by the kernel
+    # that forms b, extra pre-sweeps, the prolongation's target for an even or
+    # odd number of post-sweeps, both on the per-level kernels (graph) and on
+    # the fused coarse levels (host loop)
+    s = _sys(CASES[1])
+    kw = dict(scheme="cptr3", amg_max_coarse=40, nu_pre=nu[0], nu_post=nu[1])
+    g = _gpu(mss, s, **kw)
+    o = _orc(s, scheme="cptr3", max_coarse=40, nu_pre=nu[0], nu_post=nu[1])
+    r = np.random.default_rng(11).standard_normal(s.n_cells * s.nb)
+    assert _rel(_n(g.apply(_t(r))), o.apply(r)) < APPLY_TOL
+    gg = _gpu(mss, s, driver="graph", **kw)
+    xh, ih = g.solve(_t(s.b), tol=1e-8, maxit=400)
+    xg, ig = gg.solve(_t(s.b), tol=1e-8, maxit=400)
+    assert ih["status"] == 0 and ih["iters"] == ig["iters"]
+    assert torch.equal(xh, xg)
