@@ -460,12 +460,11 @@ __global__ void k_dense_gemv(int n, const C* __restrict__ A, const C* __restrict
 // ---- fused coarse levels -------------------------------------------------
 // With the host-driven solve, the levels from the first one with at most
 // kTailRows rows down to the coarsest run in one cooperative launch: the
-// per-level steps of the V-cycle
-// (Jacobi sweeps, residual, restriction with the next level's first sweep,
-// the coarse product, prolongation, post-sweeps) as grid-stride loops over
-// rows, separated by grid barriers. Each barrier's wait is bounded: past the
-// limit it sets *err, every block leaves the kernel, and the solve reports
-// the error.
+// per-level steps of the V-cycle (Jacobi sweeps, residual, restriction with
+// the next level's first sweep, the coarse product, prolongation,
+// post-sweeps) as grid-stride loops over rows, separated by grid barriers.
+// Each barrier's wait is bounded: past the limit it sets *err, every block
+// leaves the kernel, and the solve reports the error.
 constexpr int kTailRows = 32768;
 constexpr unsigned kBarrierSpins = 1u << 20;   // polls of L2: well under a second
 
