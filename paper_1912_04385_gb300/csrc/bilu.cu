@@ -18,7 +18,7 @@
 //   y = x + v + M3 u
 // directly. A strip is swept by NB lanes (lane c owns component c), so a
 // row's nb x nb blocks are read as contiguous rows by adjacent lanes; the
-// factorisation gives each strip a whole warp.
+// factorisation uses the same layout (lane r holds row r of each block).
 #include <algorithm>
 
 #include "common.cuh"
@@ -208,14 +208,43 @@ __global__ void k_factor_values(long long nnzb, const int* __restrict__ fsrc,
   }
 }
 
-// IKJ block ILU(0), one warp per strip, the strip's rows in order. Lower
-// neighbours belong to earlier colours or to earlier rows of the same strip
-// and are final; their U^{-1} diagonal blocks are in fdinv. The nb x nb block
-// products and the Gauss-Jordan inverse of the pivot block (no pivoting) are
-// spread over the lanes. diag_only: block Jacobi.
+// Row r of an nb x nb row-major block (16-byte loads and stores when the rows
+// are whole 16-byte units: the blocks start 256-byte aligned).
+template <int NB>
+__device__ __forceinline__ void ld_row(const double* p, double (&x)[NB]) {
+  if constexpr (NB % 2 == 0) {
+    const double2* p2 = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < NB / 2; ++i) {
+      const double2 v = p2[i];
+      x[2 * i] = v.x;
+      x[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) x[i] = p[i];
+  }
+}
+template <int NB>
+__device__ __forceinline__ void st_row(double* p, const double (&x)[NB]) {
+  if constexpr (NB % 2 == 0) {
+    double2* p2 = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int i = 0; i < NB / 2; ++i) p2[i] = make_double2(x[2 * i], x[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) p[i] = x[i];
+  }
+}
+
+// The same factorisation with a whole warp per strip: the block products and
+// the Gauss-Jordan elimination on [U_qq | I] are spread over the 32 lanes.
+// Fewer instructions per row than NB lanes per strip, so it is the faster
+// form for colours too small to fill the SMs, where the row-by-row latency
+// of each strip decides the time.
 template <int NB>
 __global__ void __launch_bounds__(256)
-k_bilu_factor(int s0, int s1, const int* __restrict__ st_first, const int* __restrict__ st_len,
+k_bilu_factor_warp(int s0, int s1, const int* __restrict__ st_first, const int* __restrict__ st_len,
               const int* __restrict__ frp, const int* __restrict__ fdp,
               const int* __restrict__ fpos, double* __restrict__ fv,
               double* __restrict__ fdinv, int diag_only, int* __restrict__ bad) {
@@ -303,6 +332,141 @@ k_bilu_factor(int s0, int s1, const int* __restrict__ st_first, const int* __res
 __device__ __forceinline__ int warp_max(int v) {
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// IKJ block ILU(0) of one colour's strips, each strip's rows in order. A strip
+// is owned by NB lanes (32 / NB strips per warp) and lane r holds row r of
+// every block of the current row, so each FP64 instruction does useful work
+// on almost every lane. Lower neighbours belong to earlier colours or to
+// earlier rows of the same strip and are final; their U^{-1} diagonal blocks
+// are in fdinv. For each lower entry k of row q:
+//   L_qk = A_qk U_kk^{-1},  A_qj -= L_qk U_kj  for every j > k in both rows,
+// then U_qq (kept in registers) is inverted by Gauss-Jordan without pivoting,
+// in place, the pivot row passed between the NB lanes by shuffles (the same
+// operations, in the same order, as elimination on [U_qq | I]). A zero or
+// non-finite pivot stops the strip and records the smallest such position
+// in *bad. diag_only: block Jacobi (no lower entries are used).
+constexpr int kRowCols = 8;       // columns of the current row held in registers
+// A colour with fewer than kSmallColour x (32 / NB) strips per SM is factored
+// with a whole warp per strip (k_bilu_factor_warp).
+constexpr int kSmallColour = 4;
+
+template <int NB>
+__global__ void __launch_bounds__(32, 16)
+k_bilu_factor(int s0, int s1, const int* __restrict__ st_first, const int* __restrict__ st_len,
+              const int* __restrict__ frp, const int* __restrict__ fdp,
+              const int* __restrict__ fpos, double* __restrict__ fv,
+              double* __restrict__ fdinv, int diag_only, int* __restrict__ bad) {
+  constexpr int B2 = NB * NB;
+  constexpr int G = 32 / NB;                 // strips per warp
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / NB, r = lane - sub * NB, base = sub * NB;
+  const long long k = s0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32 * G + sub;
+  const bool own = sub < G && k < s1;
+  const int first = own ? st_first[k] : 0;
+  const int len = own ? st_len[k] : 0;
+  const int maxlen = warp_max(len);
+  bool alive = own;
+  for (int t = 0; t < maxlen; ++t) {
+    const bool act = alive && t < len;
+    const int q = first + t;
+    int b = 0, d = 0, e = 0;
+    double dq[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) dq[c] = 0.0;
+    if (act) {
+      b = frp[q];
+      e = frp[q + 1];
+      d = fdp[q];
+      ld_row<NB>(fv + (size_t)d * B2 + r * NB, dq);
+    }
+    int cols[kRowCols];                    // row q's first columns, -1 past its end
+#pragma unroll
+    for (int i = 0; i < kRowCols; ++i) cols[i] = b + i < e ? fpos[b + i] : -1;
+    if (!diag_only) {
+      for (int f = b; f < d; ++f) {        // no lane exchange inside: may diverge
+        const int kk = fpos[f];
+        const double* Ui = fdinv + (size_t)kk * B2;
+        double w[NB], l[NB], u[NB];
+        ld_row<NB>(fv + (size_t)f * B2 + r * NB, w);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) l[c] = 0.0;
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+          ld_row<NB>(Ui + m * NB, u);
+#pragma unroll
+          for (int c = 0; c < NB; ++c) l[c] += w[m] * u[c];
+        }
+        st_row<NB>(fv + (size_t)f * B2 + r * NB, l);
+        const int g1 = frp[kk + 1];
+        for (int g = fdp[kk] + 1; g < g1; ++g) {
+          const int j = fpos[g];
+          int hit = -1;
+#pragma unroll
+          for (int i = 0; i < kRowCols; ++i)
+            if (cols[i] == j) hit = b + i;
+          if (hit < 0)
+            for (int h2 = b + kRowCols; h2 < e; ++h2)
+              if (fpos[h2] == j) {
+                hit = h2;
+                break;
+              }
+          if (hit < 0) continue;
+          const double* U = fv + (size_t)g * B2;
+          double sacc[NB];
+#pragma unroll
+          for (int c = 0; c < NB; ++c) sacc[c] = 0.0;
+#pragma unroll
+          for (int m = 0; m < NB; ++m) {
+            ld_row<NB>(U + m * NB, u);
+#pragma unroll
+            for (int c = 0; c < NB; ++c) sacc[c] += l[m] * u[c];
+          }
+          if (hit == d) {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) dq[c] -= sacc[c];
+          } else {
+            double* X = fv + (size_t)hit * B2 + r * NB;
+            double x[NB];
+            ld_row<NB>(X, x);
+#pragma unroll
+            for (int c = 0; c < NB; ++c) x[c] -= sacc[c];
+            st_row<NB>(X, x);
+          }
+        }
+      }
+    }
+    if (act) st_row<NB>(fv + (size_t)d * B2 + r * NB, dq);   // U_qq
+    // Gauss-Jordan, in place: after pivot ks, columns < ks of dq hold the
+    // inverse's columns and columns > ks the reduced matrix.
+    bool ok = true;
+#pragma unroll
+    for (int ks = 0; ks < NB; ++ks) {
+      double pn[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) pn[j] = __shfl_sync(0xffffffffu, dq[j], (base + ks) & 31);
+      const double piv = pn[ks];
+      ok = ok && piv != 0.0 && isfinite(piv);
+      const double rpiv = 1.0 / piv;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) pn[j] = j == ks ? rpiv : pn[j] * rpiv;
+      const double fr = dq[ks];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const double x = j == ks ? 0.0 : dq[j];
+        dq[j] = r == ks ? pn[j] : x - fr * pn[j];
+      }
+    }
+    if (act) {
+      if (ok) {
+        st_row<NB>(fdinv + (size_t)q * B2 + r * NB, dq);
+      } else {
+        if (r == 0) atomicMin(bad, q);
+        alive = false;
+      }
+    }
+    __syncwarp();     // row q's blocks, written lane by lane, are read whole by row q + 1
+  }
 }
 
 // ---- sweeps ----------------------------------------------------------------
@@ -796,16 +960,25 @@ void bilu_setup_nb(Handle* h) {
                                                   h->fv.p, h->fcs.p);
     MSS_LAUNCH_CK("k_factor_values");
   }
-  // ---- factorisation, colour by colour (one warp per strip)
+  // ---- factorisation, colour by colour (NB lanes per strip, one-warp CTAs so
+  // that small colours spread over the SMs)
   DBuf<int> bad(h, 1);
   fill_int(h, bad.p, 0x7fffffff, 1);
   for (int c = 0; c < h->ncol; ++c) {
     const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
     if (s1 <= s0) continue;
-    k_bilu_factor<NB><<<grid_for((long long)(s1 - s0) * 32, 256), 256, 0, h->stream>>>(
-        s0, s1, h->st_first.p, h->st_len.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p, h->fdinv.p,
-        bjac ? 1 : 0, bad.p);
-    MSS_LAUNCH_CK("k_bilu_factor");
+    constexpr int G = 32 / NB;
+    if ((long long)(s1 - s0) < (long long)kSmallColour * G * h->num_sms) {
+      k_bilu_factor_warp<NB><<<grid_for((long long)(s1 - s0) * 32, 256), 256, 0, h->stream>>>(
+          s0, s1, h->st_first.p, h->st_len.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p,
+          h->fdinv.p, bjac ? 1 : 0, bad.p);
+      MSS_LAUNCH_CK("k_bilu_factor_warp");
+    } else {
+      k_bilu_factor<NB><<<(unsigned)((s1 - s0 + G - 1) / G), 32, 0, h->stream>>>(
+          s0, s1, h->st_first.p, h->st_len.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p,
+          h->fdinv.p, bjac ? 1 : 0, bad.p);
+      MSS_LAUNCH_CK("k_bilu_factor");
+    }
   }
   const int badq = read_int(h, bad.p);
   if (badq != 0x7fffffff)
