@@ -237,11 +237,12 @@ __device__ __forceinline__ void st_row(double* p, const double (&x)[NB]) {
   }
 }
 
-// The same factorisation with a whole warp per strip: the block products and
-// the Gauss-Jordan elimination on [U_qq | I] are spread over the 32 lanes.
-// Fewer instructions per row than NB lanes per strip, so it is the faster
-// form for colours too small to fill the SMs, where the row-by-row latency
-// of each strip decides the time.
+// Block ILU(0) of one colour with a whole warp per strip (the operations of
+// k_bilu_factor below, in the same order): the block products and the
+// Gauss-Jordan elimination on [U_qq | I] are spread over the 32 lanes. Fewer
+// instructions per row than NB lanes per strip, so it is the faster form for
+// colours too small to fill the SMs, where the row-by-row latency of each
+// strip decides the time.
 template <int NB>
 __global__ void __launch_bounds__(256)
 k_bilu_factor_warp(int s0, int s1, const int* __restrict__ st_first, const int* __restrict__ st_len,
@@ -529,9 +530,7 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
 // Chain passes have few warps (32 / NB strips each) and are bound by the FP64
 // pipe of the SMs they run on: two-warp CTAs spread them over all SMs.
 constexpr int kChainThreads = 64;
-// Rows of a chain held in registers: row i's loads are issued D steps ahead of its use.
-// D = 3 and 4 time the same as 2 at 1M cells.
-constexpr int kChainRows = 2;
+constexpr int kChainRows = 2;     // rows of a chain held in registers (the refill distance)
 
 template <int NB, class V, class C>
 __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_first,
