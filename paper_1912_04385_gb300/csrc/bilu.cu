@@ -526,7 +526,9 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
 // addresses as offsets from the strip's first row (fewer instructions than
 // per-row 64-bit addressing; the chains are 18-20 % shorter than with a ring
 // of rows addressed by position; 4 and 8 rows ahead measured no faster). The
-// backward chain does the same in reverse.
+// previous row's values pass through shuffles, so a step has no warp barrier;
+// only a row with other in-strip couplings, read from memory, first
+// synchronises the strip's lanes. The backward chain does the same in reverse.
 // Chain passes have few warps (32 / NB strips each) and are bound by the FP64
 // pipe of the SMs they run on: two-warp CTAs spread them over all SMs.
 constexpr int kChainThreads = 64;
@@ -549,6 +551,7 @@ __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_firs
   const int len = active ? st_len[kk] : 0;
   const int maxlen = warp_max(len);
   const int base = sub * NB;
+  const unsigned gmask = ((1u << NB) - 1u) << base;   // the strip's lanes
   // the strip's rows for this lane: t at wl[i * NB], the chain row at
   // ml[i * B2 + c], the flag at fl[i]; two rows held in registers (even and
   // odd steps), each refilled two rows ahead right after its use
@@ -594,6 +597,7 @@ __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_firs
 #pragma unroll
       for (int c = 0; c < NB; ++c) acc -= mc[c] * pc[c];
       if (fc & 1) {                          // other in-strip couplings, from memory
+        __syncwarp(gmask);                   // rows written by the strip's other lanes
         const int q = first + it;
         for (int g = fslo[q]; g < fdp[q]; ++g) {
           const V* Lr = fv + (size_t)g * B2 + comp * NB;
@@ -605,7 +609,6 @@ __global__ void k_bilu_fwd_chain(int s0, int s1, const int* __restrict__ st_firs
       wl[it * NB] = acc;
       prev = acc;
     }
-    __syncwarp();
   };
   for (int it = 0; it < maxlen; it += D) {
 #pragma unroll
@@ -750,6 +753,7 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
   const int len = active ? st_len[kk] : 0;
   const int maxlen = warp_max(len);
   const int base = sub * NB;
+  const unsigned gmask = ((1u << NB) - 1u) << base;   // the strip's lanes
   if (!upper) {
     for (int it = 0; it < maxlen; ++it) {
       const bool on = it < len;
@@ -813,6 +817,7 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
 #pragma unroll
       for (int c = 0; c < NB; ++c) x -= mc[c] * nc[c];
       if (fc & 2) {                          // other in-strip couplings, from memory
+        __syncwarp(gmask);                   // rows written by the strip's other lanes
         const int q = first + r;
         for (int g = fdp[q] + 1; g < fshi[q]; ++g) {
           const V* Gr = fv + (size_t)g * B2 + comp * NB;
@@ -824,7 +829,6 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
       wl[r * NB] = x;
       nxt = x;
     }
-    __syncwarp();
   };
   for (int it = 0; it < maxlen; it += D) {
 #pragma unroll
