@@ -1518,6 +1518,14 @@ int or_amg_get(const amg_t* h, int l, int* arp, int* aci, double* av, int* cf, i
 
 void or_amg_vcycle(amg_t* h, const double* b, double* x) { vcycle(h, 0, b, x); }
 
+/* nu applications of the configured smoother on level l, starting from the
+ * caller's x (tests pin the smoothers against their error polynomials). */
+int or_amg_smooth(amg_t* h, int l, const double* b, double* x, int nu) {
+  if (l < 0 || l >= h->nlev || nu < 0) return OR_ERR_ARG;
+  smooth(h, &h->lev[l], b, x, nu);
+  return OR_OK;
+}
+
 /* Strength, PMIS and interpolation on a scalar CSR matrix with an optional
  * forced C/F split (cf_in != NULL). Fills cf_out and the P arrays (caller
  * sizes pci/pv with nnz(A) entries). Returns nnz(P) or a negative status. */

@@ -67,6 +67,7 @@ def lib():
         L.or_amg_sizes.argtypes = [_P, C.c_int, _P]
         L.or_amg_get.argtypes = [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P]
         L.or_amg_vcycle.argtypes = [_P, _P, _P]
+        L.or_amg_smooth.argtypes = [_P, C.c_int, _P, _P, C.c_int]
         L.or_interp_only.argtypes = [C.c_int, _P, _P, _P, C.c_double, C.c_int, C.c_uint64,
                                      _P, _P, _P, _P, _P, _P]
         L.or_colour.argtypes = [C.c_int, _P, _P, C.c_uint64, _P]
@@ -269,6 +270,15 @@ class OracleAMG:
         b = _f64(b)
         x = np.zeros_like(b)
         lib().or_amg_vcycle(self._h, _ptr(b), _ptr(x))
+        return x
+
+    def smooth(self, b, x0, nu=1, level=0):
+        """nu applications of the configured smoother on one level from x0."""
+        b = _f64(b)
+        x = _f64(x0).copy()
+        st = lib().or_amg_smooth(self._h, level, _ptr(b), _ptr(x), nu)
+        if st != 0:
+            raise OracleError(st, "or_amg_smooth")
         return x
 
 

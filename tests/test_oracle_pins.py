@@ -7,8 +7,9 @@ produce, the composition identity Eq. multistageprec, the exactness of the
 three-stage preconditioner on an upper-block-triangular matrix (the
 "N^-1 ~ L^-1, M^-1 ~ (DU)^-1" principle of Sec. 4), exactness of block ILU(0)
 on block-tridiagonal matrices, closed-form AMG interpolation weights, the
-Galerkin product against a dense product, and GMRES's minimal-residual
-property against a brute-force least-squares solve.
+Galerkin product against a dense product, the smoothers' error polynomials
+on known eigenvectors, and GMRES's minimal-residual property against a
+brute-force least-squares solve.
 """
 from pathlib import Path
 
@@ -399,6 +400,75 @@ def _vcycle_factor(h, A, n, its=12, seed=0):
         x = x + h.vcycle(r)
         norms.append(np.linalg.norm(A @ x))
     return (norms[-1] / norms[-5]) ** 0.25
+
+
+def _chebyshev_t(k, x):
+    """Chebyshev polynomial of the first kind by its three-term recurrence."""
+    t0, t1 = 1.0, x
+    if k == 0:
+        return t0
+    for _ in range(k - 1):
+        t0, t1 = t1, 2.0 * x * t1 - t0
+    return t1
+
+
+@pytest.mark.parametrize("smoother,degree,nu", [("jacobi", 0, 1), ("jacobi", 0, 3),
+                                                ("chebyshev", 1, 1), ("chebyshev", 2, 1),
+                                                ("chebyshev", 3, 2)])
+def test_smoother_error_polynomial_on_eigenvectors(smoother, degree, nu):
+    # 1-D Dirichlet Laplacian tridiag(-1, 2, -1): D^-1 A has the sine
+    # eigenvectors v_k with eigenvalues mu_k = 1 - cos(k pi / (n + 1)), and
+    # the Gershgorin bound of D^-1 A is 2. One damped Jacobi sweep maps the
+    # error by 1 - omega mu; one Chebyshev semi-iteration of degree d on
+    # [lo, hi] by T_d((theta - mu) / delta) / T_d(theta / delta)
+    # (theta, delta the centre and half-width). From x0 = 0 with b = A v_k the
+    # error is -v_k, so nu applications leave x = (1 - p(mu_k)^nu) v_k.
+    n = 31
+    rp, ci, v = sy.poisson_csr(n)
+    A = csr_dense(rp, ci, v)
+    kw = dict(smoother=smoother, max_levels=1)
+    if degree:
+        kw["cheb_degree"] = degree
+    h = oracle.OracleAMG(rp, ci, v, **kw)
+    o = h.opts
+    hi, lo = o.cheb_hi_factor * 2.0, 2.0 / o.cheb_lo_ratio
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    j = np.arange(1, n + 1)
+    for k in (1, 4, 16, 27, 31):
+        vk = np.sin(j * k * np.pi / (n + 1))
+        mu = 1.0 - np.cos(k * np.pi / (n + 1))
+        if smoother == "jacobi":
+            p = 1.0 - o.omega * mu
+        else:
+            p = _chebyshev_t(degree, (theta - mu) / delta) / _chebyshev_t(degree, theta / delta)
+        x = h.smooth(A @ vk, np.zeros(n), nu=nu)
+        np.testing.assert_allclose(x, (1.0 - p ** nu) * vk, rtol=0, atol=1e-13)
+
+
+def test_sgs_is_the_symmetric_gauss_seidel_splitting():
+    # one symmetric Gauss-Seidel application is x + M^-1 (b - A x) with
+    # M = (D + L) D^-1 (D + U), A = L + D + U (forward sweep, then backward)
+    rng = np.random.default_rng(11)
+    rp, ci, v, A = _neumann_laplacian(5, 4, rng)
+    A = A + np.eye(A.shape[0])          # nonsingular, still an M-matrix
+    rp, ci, v = [], [], []
+    rp.append(0)
+    for i in range(A.shape[0]):
+        nz = np.nonzero(A[i])[0]
+        ci += list(nz); v += list(A[i, nz]); rp.append(len(ci))
+    rp, ci, v = np.array(rp), np.array(ci), np.array(v)
+    h = oracle.OracleAMG(rp, ci, v, smoother="sgs", max_levels=1)
+    D = np.diag(np.diag(A))
+    L = np.tril(A, -1)
+    U = np.triu(A, 1)
+    M = (D + L) @ np.linalg.inv(D) @ (D + U)
+    b = rng.normal(size=A.shape[0])
+    x0 = rng.normal(size=A.shape[0])
+    x = h.smooth(b, x0, nu=1)
+    np.testing.assert_allclose(x, x0 + np.linalg.solve(M, b - A @ x0), rtol=0, atol=1e-12)
+    # a dropped backward sweep is plain forward Gauss-Seidel: not this result
+    xf = x0 + np.linalg.solve(D + L, b - A @ x0)
+    assert np.abs(x - xf).max() > 1e-3
 
 
 @pytest.mark.parametrize("smoother", ["jacobi", "chebyshev", "sgs"])
