@@ -277,7 +277,7 @@ def run_ours(a, rank, world, dist):
                 "avg_launch_ms": round(per_launch_ms, 5), "avg_call_ms": round(per_call_ms, 5),
                 "hbm_achieved_gbs": round(gbs, 1), "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": round(gbs / hbm_peak, 4)}
-    # preconditioner apply: algorithmic bytes (survey accounting) over traced time
+    # preconditioner apply: algorithmic bytes (apply_alg_bytes) over traced time
     n_apply, apply_ms = tr["apply"]
     out = {"metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 3),
