@@ -33,6 +33,7 @@ sys.path.insert(0, str(ROOT))
 
 PES = (0.1, 10.0, 1000.0)
 METRIC = "time-to-1e-6 rel. residual (ms) at 1M cells; FGMRES iters; precond HBM GB/s"
+DATA = "synthetic (seeded 5-point thermal-compositional generator; no dataset)"
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz
 
 
@@ -282,7 +283,7 @@ def run_ours(a, rank, world, dist):
     out = {"metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded 5-point thermal-compositional generator; no dataset)",
+           "data": DATA,
            "config": {**workload_config(a), "parallelism": f"replicas x{world}"},
            "iters": iters, "iters_mean": float(np.mean(iters)),
            "wall_ms_per_system": round(wall_ms / (nsys * world), 3),
@@ -690,7 +691,7 @@ def run_reference(a, rank, world):
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": round(total * 1e3 / a.steps, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded generator)",
+            "data": DATA,
             "config": {**workload_config(a), "parallelism": "cpu oracle, 1 thread"},
             "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1,
                              "kind": "oracle", "sample": cb["sample"] if cb else "",
