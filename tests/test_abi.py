@@ -58,3 +58,39 @@ def test_binding_fails_loudly_without_library(tmp_path):
     from paper_1912_04385_gb300 import mss
     with pytest.raises(RuntimeError):
         mss.load(tmp_path / "missing.so")
+
+
+# library field -> oracle field, for the settings both implement
+_SHARED = {"scheme": "scheme", "stage_order": "stage_order", "stage3": "stage3",
+           "ilu_order": "ilu_order", "smoother": "smoother", "nu_pre": "nu_pre",
+           "nu_post": "nu_post", "cheb_degree": "cheb_degree",
+           "amg_max_coarse": "max_coarse", "amg_max_levels": "max_levels",
+           "interp_max_elems": "interp_max", "restart": "restart", "ilu_strip": "ilu_strip",
+           "amg_theta": "theta", "jacobi_omega": "omega", "cheb_lo_ratio": "cheb_lo_ratio",
+           "cheb_hi_factor": "cheb_hi_factor", "seed": "seed"}
+
+
+def test_library_and_oracle_defaults_agree(lib_path):
+    # the two sides are written separately; parity runs on the defaults, so a
+    # default that drifts on one side only would surface as a GPU mismatch
+    import oracle
+    from paper_1912_04385_gb300 import mss
+    lo, oo = mss.options(), oracle.options()
+    for lk, ok in _SHARED.items():
+        assert getattr(lo, lk) == getattr(oo, ok), (lk, getattr(lo, lk), getattr(oo, ok))
+    for name in ("cptr3", "cpr", "ilu0"):
+        assert mss.SCHEMES[name] == oracle.oracle.SCHEME[name]
+    for name in ("jacobi", "chebyshev"):
+        assert mss.SMOOTHERS[name] == oracle.oracle.SMOOTHER[name]
+
+
+def test_options_names_and_unknown_keys(lib_path):
+    from paper_1912_04385_gb300 import mss
+    o = mss.options(scheme="cpr", smoother="chebyshev", precision="mixed", driver="graph",
+                    restart=50, amg_theta=0.5)
+    assert (o.scheme, o.smoother, o.precision, o.driver) == (1, 1, 1, 1)
+    assert o.restart == 50 and o.amg_theta == 0.5
+    with pytest.raises(KeyError):
+        mss.options(no_such_option=1)
+    with pytest.raises(KeyError):
+        mss.options(scheme="no_such_scheme")
