@@ -298,6 +298,9 @@ def run_ours(a, rank, world, dist):
     bytes_apply = apply_alg_bytes(N, nnzb, 6, solver, opts)
     out["precond_gbs"] = round(bytes_apply / (apply_ms / max(n_apply, 1) * 1e-3) / 1e9, 1)
     out["precond_alg_bytes"] = bytes_apply
+    out["precond_roofline"] = precond_roofline(
+        bytes_apply, apply_alg_flops(N, nnzb, 6, solver, opts), apply_ms / max(n_apply, 1),
+        hbm_peak)
 
     # end to end through the C-ABI from pinned host buffers (right after the
     # timed region, before the other legs fill the allocators)
@@ -590,6 +593,43 @@ def apply_alg_bytes(N, nnzb, nb, solver, opts):
     tot += alg["bilu_fwd"]["bytes"] + alg["bilu_bwd"]["bytes"]
     tot += 2 * N * 8                                            # gather r_T
     return int(tot)
+
+
+def apply_alg_flops(N, nnzb, nb, solver, opts):
+    """Algorithmic FP64 flops of one CPTR3 application, counted like
+    apply_alg_bytes: per V-cycle level 2 per stored entry of A for each A pass
+    (the Jacobi sweeps after the first and the residual), 3 per row for each
+    sweep's update, 2 per entry of P and of R; the coarsest level a dense GEMV
+    (2 n^2); z_P 2 per block; both last-stage sweeps."""
+    a_passes = opts.nu_pre + opts.nu_post
+    tot = 0
+    for which in (0, 1):
+        levs = solver.amg_levels(which)
+        for l, L in enumerate(levs):
+            n = L["A"][0].numel() - 1
+            nnz = L["A"][1].numel()
+            if l == len(levs) - 1:
+                tot += 2 * n * n
+                continue
+            nnzp = L["P"][1].numel()
+            tot += a_passes * (2 * nnz + 3 * n) + 2 * (2 * nnzp)
+    tot += 2 * nnzb                                             # z_P
+    alg = algorithmic(N, nnzb, nb)
+    tot += alg["bilu_fwd"]["flops"] + alg["bilu_bwd"]["flops"]
+    return int(tot)
+
+
+def precond_roofline(bytes_apply, flops_apply, apply_ms, hbm_gbs, fp64_tflops=FP64_PEAK_TFLOPS):
+    """Roofline time of one application, max(bytes / HBM bandwidth, flops /
+    FP64 peak), against its traced time; frac = roofline time / traced time."""
+    t_hbm = bytes_apply / (hbm_gbs * 1e9) * 1e3
+    t_fp64 = flops_apply / (fp64_tflops * 1e12) * 1e3
+    t_roof = max(t_hbm, t_fp64)
+    return {"bytes": int(bytes_apply), "flops": int(flops_apply),
+            "t_hbm_ms": round(t_hbm, 4), "t_fp64_ms": round(t_fp64, 4),
+            "bound": "alu" if t_fp64 >= t_hbm else "hbm", "t_roofline_ms": round(t_roof, 4),
+            "achieved_ms": round(apply_ms, 4),
+            "frac": round(t_roof / apply_ms, 4) if apply_ms > 0 else None}
 
 
 def e2e(a, sysl, solver, opts, torch):
