@@ -54,7 +54,8 @@ typedef struct {
   int exact_sub;     /* 1: M_TT = C_TT^-1 and M_PP = B_PP^-1 by dense LU */
   int stage3;        /* 0: block ILU(0) of the scaled matrix, 1: block Jacobi */
   int ilu_order;     /* 0: multicolour (Jones-Plassmann), 1: natural, 2: strips */
-  int smoother;      /* 0: damped Jacobi, 1: Chebyshev, 2: symmetric Gauss-Seidel */
+  int smoother;      /* 0: damped Jacobi, 1: Chebyshev, 2: symmetric Gauss-Seidel,
+                        3: multicolour symmetric Gauss-Seidel */
   int nu_pre, nu_post;
   int cheb_degree;
   int max_coarse, max_levels, interp_max;
@@ -414,6 +415,9 @@ typedef struct {
   double lam_max;
   double *b, *x, *r, *t1, *t2;
   int nc;
+  int ncolour;             /* multicolour Gauss-Seidel: colours of A's graph */
+  int* cstart;             /* colour c holds mcorder[cstart[c] .. cstart[c + 1]) */
+  int* mcorder;            /* points in colour-major order, ascending inside a colour */
 } level_t;
 
 typedef struct {
@@ -646,6 +650,7 @@ static void level_free(level_t* L) {
   csr_free(&L->A); csr_free(&L->P); csr_free(&L->R);
   free(L->strong); free(L->cf); free(L->cidx); free(L->dinv);
   free(L->b); free(L->x); free(L->r); free(L->t1); free(L->t2);
+  free(L->cstart); free(L->mcorder);
   memset(L, 0, sizeof(*L));
 }
 
@@ -689,6 +694,33 @@ static double spectrum_bound(level_t* L) {
   return lam;
 }
 
+static int jp_colour(int n, const int* rp, const int* ci, uint64_t seed, int* colour,
+                     int* ncol_out);
+
+/* Colour-major order of a level's points for multicolour Gauss-Seidel: the
+ * Jones-Plassmann colouring of A's graph (the same routine and priorities as
+ * the point-multicolour ILU order), points ascending inside each colour. */
+static int level_colours(level_t* L, uint64_t seed) {
+  int n = L->A.n;
+  int* col = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!col) return OR_ERR_MEM;
+  int ncol = 0, st = jp_colour(n, L->A.rp, L->A.ci, seed, col, &ncol);
+  if (st != OR_OK) { free(col); return st; }
+  L->ncolour = ncol;
+  L->cstart = (int*)calloc((size_t)ncol + 1, sizeof(int));
+  L->mcorder = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!L->cstart || !L->mcorder) { free(col); return OR_ERR_MEM; }
+  for (int i = 0; i < n; ++i) L->cstart[col[i] + 1] += 1;
+  for (int c = 0; c < ncol; ++c) L->cstart[c + 1] += L->cstart[c];
+  int* fill = (int*)malloc(sizeof(int) * (size_t)(ncol > 0 ? ncol : 1));
+  if (!fill) { free(col); return OR_ERR_MEM; }
+  for (int c = 0; c < ncol; ++c) fill[c] = L->cstart[c];
+  for (int i = 0; i < n; ++i) L->mcorder[fill[col[i]]++] = i;
+  free(fill);
+  free(col);
+  return OR_OK;
+}
+
 /* Build the hierarchy for a scalar CSR matrix (copied). */
 static int amg_build(int n, const int* rp, const int* ci, const double* v, const or_opts* o,
                      amg_t** out) {
@@ -706,6 +738,7 @@ static int amg_build(int n, const int* rp, const int* ci, const double* v, const
     L = &h->lev[l];
     if ((st = level_vectors(L)) != OR_OK) goto fail;
     if (o->smoother == 1) L->lam_max = spectrum_bound(L);
+    if (o->smoother == 3 && (st = level_colours(L, o->seed)) != OR_OK) goto fail;
     if (L->A.n <= o->max_coarse || l + 1 >= o->max_levels || l + 1 >= OR_MAXLEV) break;
     L->strong = (unsigned char*)malloc((size_t)(L->A.nnz > 0 ? L->A.nnz : 1));
     L->cf = (int*)malloc(sizeof(int) * (size_t)L->A.n);
@@ -797,10 +830,29 @@ static void smooth_sgs(level_t* L, const double* b, double* x) {
     }
 }
 
+/* multicolour symmetric Gauss-Seidel: the colours in order, then in reverse.
+ * Points of one colour are not coupled, so each colour's updates read only
+ * other colours' values and may run in any order (or all at once). */
+static void smooth_mcsgs(level_t* L, const double* b, double* x) {
+  const csr_t* A = &L->A;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < L->ncolour; ++k) {
+      int c = pass == 0 ? k : L->ncolour - 1 - k;
+      for (int q = L->cstart[c]; q < L->cstart[c + 1]; ++q) {
+        int i = L->mcorder[q];
+        double s = b[i];
+        for (int e = A->rp[i]; e < A->rp[i + 1]; ++e)
+          if (A->ci[e] != i) s -= A->v[e] * x[A->ci[e]];
+        x[i] = s * L->dinv[i];
+      }
+    }
+}
+
 static void smooth(amg_t* h, level_t* L, const double* b, double* x, int nu) {
   for (int k = 0; k < nu; ++k) {
     if (h->o.smoother == 1) smooth_cheb(L, b, x, &h->o);
     else if (h->o.smoother == 2) smooth_sgs(L, b, x);
+    else if (h->o.smoother == 3) smooth_mcsgs(L, b, x);
     else smooth_jacobi(L, b, x, h->o.omega);
   }
 }
@@ -840,7 +892,7 @@ static int jp_colour(int n, const int* rp, const int* ci, uint64_t seed, int* co
                      int* ncol_out) {
   uint64_t* pr = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
   int* pick = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
-  if (!pr || !pick) return OR_ERR_MEM;
+  if (!pr || !pick) { free(pr); free(pick); return OR_ERR_MEM; }
   for (int i = 0; i < n; ++i) {
     pr[i] = or_splitmix(seed, (0xFFFFULL << 32) | (uint64_t)(unsigned)i);
     colour[i] = -1;

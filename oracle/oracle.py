@@ -16,7 +16,7 @@ from .build import build_oracle
 OK, ERR_ARG, ERR_SINGULAR, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_MEM, ERR_AMG = 0, -1, -2, -3, -4, -5, -6
 
 SCHEME = {"cptr3": 0, "cpr": 1, "ilu0": 2}
-SMOOTHER = {"jacobi": 0, "chebyshev": 1, "sgs": 2}
+SMOOTHER = {"jacobi": 0, "chebyshev": 1, "sgs": 2, "mcsgs": 3}
 
 
 class OrOpts(C.Structure):

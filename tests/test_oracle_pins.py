@@ -101,7 +101,7 @@ def test_ilu0_scheme_has_no_scaling():
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("scheme", ["cptr3", "cpr"])
 @pytest.mark.parametrize("stage3", [0, 1])
-@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev", "sgs"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev", "sgs", "mcsgs"])
 def test_algorithm_matches_multistage_formula(scheme, stage3, smoother):
     s = sy.make_system(5, 4, 4, pe=1.0, seed=5)
     # a small coarse size forces a real multilevel V-cycle inside the stages
@@ -471,7 +471,40 @@ def test_sgs_is_the_symmetric_gauss_seidel_splitting():
     assert np.abs(x - xf).max() > 1e-3
 
 
-@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev", "sgs"])
+@pytest.mark.parametrize("grid", [(9, 1), (6, 5), (12, 7)])
+def test_mcsgs_is_sgs_in_the_colour_major_order(grid):
+    # multicolour symmetric Gauss-Seidel is symmetric Gauss-Seidel on the
+    # matrix permuted to colour-major order (points ascending inside a colour),
+    # with the colours of the separately pinned Jones-Plassmann routine:
+    # x + P^T M^-1 P (b - A x), M = (D + L) D^-1 (D + U) of P A P^T
+    rng = np.random.default_rng(13)
+    rp, ci, v, A = _neumann_laplacian(*grid, rng)
+    A = A + np.eye(A.shape[0])
+    rp, ci, v = [0], [], []
+    for i in range(A.shape[0]):
+        nz = np.nonzero(A[i])[0]
+        ci += list(nz); v += list(A[i, nz]); rp.append(len(ci))
+    rp, ci, v = np.array(rp), np.array(ci), np.array(v)
+    h = oracle.OracleAMG(rp, ci, v, smoother="mcsgs", max_levels=1)
+    col = np.asarray(oracle.colour(rp, ci, seed=h.opts.seed)[0])
+    perm = np.lexsort((np.arange(len(col)), col))       # colour-major, ascending inside
+    Ap = A[np.ix_(perm, perm)]
+    D = np.diag(np.diag(Ap))
+    M = (D + np.tril(Ap, -1)) @ np.linalg.inv(D) @ (D + np.triu(Ap, 1))
+    b = rng.normal(size=A.shape[0])
+    x0 = rng.normal(size=A.shape[0])
+    x = h.smooth(b, x0, nu=1)
+    want = x0.copy()
+    want[perm] += np.linalg.solve(M, (b - A @ x0)[perm])
+    np.testing.assert_allclose(x, want, rtol=0, atol=1e-12)
+    # more than one colour, and not the lexicographic sweep
+    assert col.max() >= 1
+    hs = oracle.OracleAMG(rp, ci, v, smoother="sgs", max_levels=1)
+    if grid[1] > 1:
+        assert np.abs(hs.smooth(b, x0, nu=1) - x).max() > 1e-6
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev", "sgs", "mcsgs"])
 def test_2d_poisson_vcycle_convergence(smoother):
     import scipy.sparse as sp
     facs = []
@@ -484,7 +517,7 @@ def test_2d_poisson_vcycle_convergence(smoother):
     # PMIS with direct classical interpolation: factors near 0.6 and a mild
     # growth with size (sGS most); a wrong sign, a transposed restriction or
     # a dropped interpolation term drives them to or above 1.
-    bound = {"jacobi": 0.72, "chebyshev": 0.62, "sgs": 0.70}[smoother]
+    bound = {"jacobi": 0.72, "chebyshev": 0.62, "sgs": 0.70, "mcsgs": 0.70}[smoother]
     assert max(facs) < bound, facs
     assert facs[-1] - facs[0] < 0.2, facs
 
