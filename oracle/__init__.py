@@ -5,7 +5,7 @@ baseline / reference leg of ``bench.py`` may import it. It shares no code
 with the CUDA library and never serves as a fallback for it.
 """
 from .oracle import (OracleAMG, OracleError, OracleSolver, colour, interp_only, options,
-                     splitmix)
+                     pmis_rounds, splitmix)
 
 __all__ = ["OracleAMG", "OracleError", "OracleSolver", "colour", "interp_only", "options",
-           "splitmix"]
+           "pmis_rounds", "splitmix"]

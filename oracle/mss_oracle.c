@@ -456,10 +456,12 @@ static void amg_strength(const csr_t* A, double theta, unsigned char* strong) {
  * whose (lambda, index) exceeds that of all undecided strong neighbours (in
  * either direction) becomes C, then undecided points that depend strongly on
  * a new C point become F. Afterwards an F point that depends strongly on some
- * point but on no C point is made C. Parity: index work, compared bit-exactly;
+ * point but on no C point is made C. pre / rnd (may be NULL) receive the
+ * split before that fix-up (1 C, 0 F) and the round in which each point was
+ * decided (0: influences nobody, F from the start). Parity: index work, compared bit-exactly;
  * pinned by the split invariants and the Poisson convergence tests. */
 static int amg_pmis(const csr_t* A, const unsigned char* strong, uint64_t seed, int level,
-                    int* cf) {
+                    int* cf, int* pre, int* rnd) {
   int n = A->n;
   int* cnt = (int*)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
   double* lam = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -482,12 +484,15 @@ static int amg_pmis(const csr_t* A, const unsigned char* strong, uint64_t seed, 
     uint64_t key = ((uint64_t)(unsigned)level << 32) | (uint64_t)(unsigned)i;
     lam[i] = (double)cnt[i] + or_unit(or_splitmix(seed, key));
     state[i] = cnt[i] == 0 ? 0 : -1;
+    if (rnd) rnd[i] = 0;
   }
+  int round = 0;
 #define OR_GT(a, b) (lam[a] > lam[b] || (lam[a] == lam[b] && (a) > (b)))
   for (;;) {
     int undecided = 0;
     for (int i = 0; i < n; ++i) undecided += state[i] == -1;
     if (!undecided) break;
+    ++round;
     for (int i = 0; i < n; ++i) {
       newc[i] = 0;
       if (state[i] != -1) continue;
@@ -502,14 +507,23 @@ static int amg_pmis(const csr_t* A, const unsigned char* strong, uint64_t seed, 
       }
       newc[i] = ismax;
     }
-    for (int i = 0; i < n; ++i) if (newc[i]) state[i] = 1;
+    for (int i = 0; i < n; ++i)
+      if (newc[i]) {
+        state[i] = 1;
+        if (rnd) rnd[i] = round;
+      }
     for (int i = 0; i < n; ++i) {
       if (state[i] != -1) continue;
       for (int e = S.rp[i]; e < S.rp[i + 1]; ++e)
-        if (newc[S.ci[e]]) { state[i] = 0; break; }
+        if (newc[S.ci[e]]) {
+          state[i] = 0;
+          if (rnd) rnd[i] = round;
+          break;
+        }
     }
   }
 #undef OR_GT
+  if (pre) for (int i = 0; i < n; ++i) pre[i] = state[i];
   /* F points with strong dependencies but no strong C point become C */
   for (int i = 0; i < n; ++i) {
     newc[i] = 0;
@@ -745,7 +759,7 @@ static int amg_build(int n, const int* rp, const int* ci, const double* v, const
     L->cidx = (int*)malloc(sizeof(int) * (size_t)L->A.n);
     if (!L->strong || !L->cf || !L->cidx) { st = OR_ERR_MEM; goto fail; }
     amg_strength(&L->A, o->theta, L->strong);
-    if ((st = amg_pmis(&L->A, L->strong, o->seed, l, L->cf)) != OR_OK) goto fail;
+    if ((st = amg_pmis(&L->A, L->strong, o->seed, l, L->cf, NULL, NULL)) != OR_OK) goto fail;
     int nc = 0;
     for (int i = 0; i < L->A.n; ++i) L->cidx[i] = L->cf[i] ? nc++ : -1;
     L->nc = nc;
@@ -1591,7 +1605,7 @@ int or_interp_only(int n, const int* rp, const int* ci, const double* v, double 
   amg_strength(&A, theta, strong);
   if (cf_in) memcpy(cf_out, cf_in, sizeof(int) * (size_t)n);
   else {
-    int st = amg_pmis(&A, strong, seed, 0, cf_out);
+    int st = amg_pmis(&A, strong, seed, 0, cf_out, NULL, NULL);
     if (st) return st;
   }
   int nc = 0;
@@ -1607,6 +1621,21 @@ int or_interp_only(int n, const int* rp, const int* ci, const double* v, double 
   csr_free(&P);
   free(strong); free(cidx);
   return nnz;
+}
+
+/* Strength and PMIS on a scalar CSR matrix for level `level`, with the
+ * rounds exposed (tests): strong_out per nonzero, pre (split before the
+ * F-to-C fix-up), rnd (round of each decision), cf_out (final split). */
+int or_pmis_rounds(int n, const int* rp, const int* ci, const double* v, double theta,
+                   uint64_t seed, int level, int* strong_out, int* pre, int* rnd, int* cf_out) {
+  csr_t A = {n, n, rp[n], (int*)rp, (int*)ci, (double*)v};
+  unsigned char* strong = (unsigned char*)malloc((size_t)(rp[n] > 0 ? rp[n] : 1));
+  if (!strong) return OR_ERR_MEM;
+  amg_strength(&A, theta, strong);
+  int st = amg_pmis(&A, strong, seed, level, cf_out, pre, rnd);
+  for (int e = 0; e < rp[n]; ++e) strong_out[e] = strong[e];
+  free(strong);
+  return st;
 }
 
 /* Jones-Plassmann colouring on a block pattern (exported for the tests). */

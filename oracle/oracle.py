@@ -71,6 +71,8 @@ def lib():
         L.or_interp_only.argtypes = [C.c_int, _P, _P, _P, C.c_double, C.c_int, C.c_uint64,
                                      _P, _P, _P, _P, _P, _P]
         L.or_colour.argtypes = [C.c_int, _P, _P, C.c_uint64, _P]
+        L.or_pmis_rounds.argtypes = [C.c_int, _P, _P, _P, C.c_double, C.c_uint64, C.c_int,
+                                     _P, _P, _P, _P]
         L.or_hash.restype = C.c_uint64
         L.or_hash.argtypes = [C.c_uint64, C.c_uint64]
         _lib = L
@@ -300,6 +302,20 @@ def interp_only(row_ptr, col_idx, vals, theta=0.25, maxel=4, seed=0x5eed, cf=Non
     if st < 0:
         raise OracleError(st, "or_interp_only")
     return cf_out, strong.astype(bool), (prp, pci[:st], pv[:st])
+
+
+def pmis_rounds(row_ptr, col_idx, vals, theta=0.25, seed=0x5eed, level=0):
+    """Strength and PMIS with the rounds exposed: (strong mask, split before
+    the F-to-C fix-up, round of each decision, final split)."""
+    rp, ci, v = _i32(row_ptr), _i32(col_idx), _f64(vals)
+    n = rp.shape[0] - 1
+    strong = np.empty(max(ci.shape[0], 1), np.int32)
+    pre, rnd, cf = (np.empty(max(n, 1), np.int32) for _ in range(3))
+    st = lib().or_pmis_rounds(n, _ptr(rp), _ptr(ci), _ptr(v), theta, seed, level, _ptr(strong),
+                              _ptr(pre), _ptr(rnd), _ptr(cf))
+    if st:
+        raise OracleError(st, "or_pmis_rounds")
+    return strong[:ci.shape[0]].astype(bool), pre[:n], rnd[:n], cf[:n]
 
 
 def colour(row_ptr, col_idx, seed=0x5eed):

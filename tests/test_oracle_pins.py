@@ -364,6 +364,140 @@ def test_pmis_split_invariants_and_determinism():
     assert 0.15 < cf.mean() < 0.6
 
 
+# ---- PMIS by its definition (De Sterck, Yang, Heys 2006) -------------------
+def _strength_sets(rp, ci, strong):
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    S = [set() for _ in range(n)]
+    ST = [set() for _ in range(n)]
+    for e in np.flatnonzero(strong):
+        S[rows[e]].add(int(ci[e]))
+        ST[int(ci[e])].add(int(rows[e]))
+    return S, ST
+
+
+def _pmis_measure(ST, seed, level):
+    # lambda_i = |S_i^T| + u_i, u_i the top 53 bits of SplitMix64(seed, level << 32 | i)
+    return np.array([len(ST[i]) + (oracle.splitmix(seed, (level << 32) | i) >> 11)
+                     * (1.0 / 9007199254740992.0) for i in range(len(ST))])
+
+
+def _pmis_violations(S, ST, lam, pre, rnd):
+    """Every rule of synchronous PMIS that (pre, rnd) breaks. In round r every
+    undecided point whose (lambda, index) beats all undecided points of
+    S_i u S_i^T becomes C, then undecided points with a strong dependency on a
+    new C point become F; points that influence nobody are F from round 0.
+    So the C points of one round are independent in S u S^T, but a point that
+    only influences an earlier C point stays undecided and may become C."""
+    n = len(S)
+
+    def gt(a, b):
+        return lam[a] > lam[b] or (lam[a] == lam[b] and a > b)
+
+    bad = []
+    for i in range(n):
+        nbr = S[i] | ST[i]
+        r = int(rnd[i])
+        if pre[i] not in (0, 1):
+            bad.append(("undecided", i))
+            continue
+        if (r == 0) != (len(ST[i]) == 0) or (r == 0 and pre[i] != 0):
+            bad.append(("round 0", i))
+            continue
+        if r == 0:
+            continue
+        bigger = [j for j in nbr if gt(j, i)]
+        if pre[i] == 1:
+            if any(pre[j] == 1 and rnd[j] == r for j in nbr):
+                bad.append(("C points of one round coupled", i))
+            if any(pre[j] == 1 and rnd[j] < r for j in S[i]):
+                bad.append(("C point depends on an earlier C point", i))
+            if any(rnd[j] >= r for j in bigger):
+                bad.append(("C point not the maximum of its round", i))
+            if r >= 2 and not any(rnd[j] == r - 1 for j in bigger):
+                bad.append(("C point could have been chosen earlier", i))
+        else:
+            if not any(pre[j] == 1 and rnd[j] == r for j in S[i]):
+                bad.append(("F point without a new strong C point", i))
+            if any(pre[j] == 1 and rnd[j] < r for j in S[i]):
+                bad.append(("F point decided late", i))
+            if not any(rnd[j] >= r for j in bigger):
+                bad.append(("F point was the maximum of its round", i))
+    return bad
+
+
+def _planted_pmis(S, ST, lam, both_directions=True, ties_to_larger=True):
+    # a plain PMIS with a switchable mistake, to show the rules above catch it
+    n = len(S)
+
+    def gt(a, b):
+        return lam[a] > lam[b] or (lam[a] == lam[b] and ((a > b) == ties_to_larger))
+
+    state = [0 if not ST[i] else -1 for i in range(n)]
+    rnd = [0] * n
+    r = 0
+    while -1 in state:
+        r += 1
+        nbr = (lambda i: S[i] | ST[i]) if both_directions else (lambda i: S[i])
+        newc = {i for i in range(n) if state[i] == -1
+                and not any(state[j] == -1 and gt(j, i) for j in nbr(i))}
+        for i in newc:
+            state[i], rnd[i] = 1, r
+        for i in range(n):
+            if state[i] == -1 and S[i] & newc:
+                state[i], rnd[i] = 0, r
+    return np.array(state), np.array(rnd)
+
+
+def _temperature_levels():
+    # the advection-dominated temperature operator: a strength graph that is
+    # far from symmetric, where S and S^T neighbours differ
+    s = sy.make_system(24, 20, 4, pe=1000.0, sigma=1.0, corr_len=4.0, seed=8)
+    o = oracle.OracleSolver.from_system(s, scheme="cptr3", max_coarse=20)
+    return o.amg_levels(0)
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_pmis_rounds_follow_the_definition(level):
+    lev = _temperature_levels()
+    rp, ci, v = lev[level].A
+    strong, pre, rnd, cf = oracle.pmis_rounds(rp, ci, v, seed=0x5eed, level=level)
+    S, ST = _strength_sets(rp, ci, strong)
+    assert any(S[i] != ST[i] for i in range(len(S)))       # non-symmetric strength
+    lam = _pmis_measure(ST, 0x5eed, level)
+    assert _pmis_violations(S, ST, lam, pre, rnd) == []
+    assert rnd.max() >= 2                                    # several rounds exercised
+    # the F-to-C fix-up: an F point with strong dependencies but no C among them
+    fix = [i for i in range(len(S)) if pre[i] == 0 and S[i] and not any(pre[j] for j in S[i])]
+    expect = pre.copy()
+    expect[fix] = 1
+    assert np.array_equal(cf, expect)
+    # and this is the split the hierarchy uses on that level
+    assert np.array_equal(cf, lev[level].cf)
+
+
+def test_pmis_definition_rejects_planted_mistakes():
+    lev = _temperature_levels()
+    rp, ci, v = lev[0].A
+    strong, pre, rnd, _ = oracle.pmis_rounds(rp, ci, v, seed=0x5eed, level=0)
+    S, ST = _strength_sets(rp, ci, strong)
+    lam = _pmis_measure(ST, 0x5eed, 0)
+    # the maximum taken over S_i only (dependencies, not influences)
+    st, rd = _planted_pmis(S, ST, lam, both_directions=False)
+    assert _pmis_violations(S, ST, lam, st, rd) != []
+    # integer measures (many ties): ties broken towards the smaller index
+    lam_i = np.array([float(len(t)) for t in ST])
+    st, rd = _planted_pmis(S, ST, lam_i, ties_to_larger=False)
+    assert _pmis_violations(S, ST, lam_i, st, rd) != []
+    st, rd = _planted_pmis(S, ST, lam_i)                       # the rule as stated
+    assert _pmis_violations(S, ST, lam_i, st, rd) == []
+    # a measure counting dependencies |S_i| in place of influences |S_i^T|
+    lam_s = np.array([len(S[i]) + (lam[i] - len(ST[i])) for i in range(len(S))])
+    assert not np.array_equal(lam_s, lam)
+    st, rd = _planted_pmis(S, ST, lam_s)
+    assert _pmis_violations(S, ST, lam, st, rd) != []
+
+
 def test_galerkin_coarse_operator_matches_dense_product():
     s = sy.make_system(24, 20, 4, pe=10.0, sigma=1.0, corr_len=4.0, seed=8)
     o = oracle.OracleSolver.from_system(s, scheme="cptr3", max_coarse=20)
