@@ -58,6 +58,7 @@ enum { MSS_JACOBI = 0, MSS_CHEBYSHEV = 1 };          /* AMG smoother */
 enum { MSS_FP64 = 0, MSS_MIXED = 1 };                /* preconditioner arithmetic */
 enum { MSS_CGS1 = 0, MSS_CGS2 = 1 };                 /* Arnoldi orthogonalisation */
 enum { MSS_DRIVER_HOST = 0, MSS_DRIVER_GRAPH = 1 };  /* who runs the FGMRES loop */
+enum { MSS_FACTOR_AUTO = 0, MSS_FACTOR_WARP = 1, MSS_FACTOR_LANES = 2 }; /* ILU(0) kernel */
 
 /* A BSR matrix; the arrays are device memory owned by the caller. */
 typedef struct {
@@ -112,6 +113,14 @@ typedef struct {
                                nodes, the decisions taken by device kernels),
                                launched once per solve and read back once. Same
                                kernels, same order, same results. */
+  int32_t factor_form;      /* which kernel factors a colour of the block ILU(0):
+                               MSS_FACTOR_AUTO (default) picks per colour by its
+                               size (a warp per strip for colours too small to
+                               fill the SMs, nb lanes per strip otherwise);
+                               MSS_FACTOR_WARP / MSS_FACTOR_LANES force one form
+                               for every colour. Both perform the same operations
+                               in the same order, so the factors are the same
+                               bits whichever form runs. */
   double amg_theta;         /* strength threshold (0.25) */
   double jacobi_omega;      /* Jacobi damping (0.8, HSL_MI20's default) */
   double cheb_lo_ratio;     /* Chebyshev interval [bound/ratio, factor*bound] (30) */
@@ -283,6 +292,16 @@ int mss_bilu_num_colours(mss_handle* h, int32_t* ncolours);
 /* Copy the cell colours and the ordering (perm[k] = cell at position k)
  * into caller-owned device arrays of N entries. */
 int mss_bilu_ordering(mss_handle* h, int32_t* colour, int32_t* perm);
+
+/* Copy the block ILU(0) factors of Eq. CPTR3M3 (the CPR second stage) in
+ * colour-major positions: fv (device, nnzb*nb*nb, row-major blocks, rows in
+ * position order, blocks of a row in ascending column position) holds the
+ * strictly lower blocks L_qk (unit diagonal implied), the pivot block U_qq
+ * and the upper blocks U_qj, except that the upper blocks coupling two cells
+ * of one strip hold U_qq^{-1} U_qj (the form the strip chains read);
+ * fdinv (device, N*nb*nb) holds U_qq^{-1} per position. Either pointer may
+ * be NULL. Errors: NOT_SETUP; INVALID_ARG for block Jacobi (no factors). */
+int mss_bilu_factors(mss_handle* h, double* fv, double* fdinv);
 
 /* Runs, on the handle's stream, one wait of the grid barrier used by the
  * fused coarse V-cycle levels that can never complete (it expects a block

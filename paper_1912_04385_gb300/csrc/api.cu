@@ -57,6 +57,7 @@ void check_options(const mss_options& o) {
   if (o.restart < 1 || o.restart > 120) bad("restart (1..120)");
   if (o.precision != MSS_FP64 && o.precision != MSS_MIXED) bad("precision");
   if (o.driver != MSS_DRIVER_HOST && o.driver != MSS_DRIVER_GRAPH) bad("driver");
+  if (o.factor_form < MSS_FACTOR_AUTO || o.factor_form > MSS_FACTOR_LANES) bad("factor_form");
   if (!(o.amg_theta > 0.0 && o.amg_theta <= 1.0)) bad("amg_theta");
   if (!(o.jacobi_omega > 0.0 && o.jacobi_omega < 2.0)) bad("jacobi_omega");
   if (!(o.cheb_lo_ratio > 1.0) || !(o.cheb_hi_factor > 0.0)) bad("Chebyshev interval");
@@ -386,6 +387,7 @@ int mss_options_default(mss_options* o) {
   o->restart = 30;
   o->precision = MSS_FP64;
   o->driver = MSS_DRIVER_HOST;
+  o->factor_form = MSS_FACTOR_AUTO;
   o->amg_theta = 0.25;
   o->jacobi_omega = 0.8;
   o->cheb_lo_ratio = 30.0;
@@ -633,6 +635,19 @@ int mss_bilu_ordering(mss_handle* hh, int32_t* colour, int32_t* perm) {
     need_ready(H);
     if (colour) copy_dev(&H, colour, H.colour.p, sizeof(int) * (size_t)H.N);
     if (perm) copy_dev(&H, perm, H.perm.p, sizeof(int) * (size_t)H.N);
+    MSS_CK(cudaStreamSynchronize(H.stream));
+  });
+}
+
+int mss_bilu_factors(mss_handle* hh, double* fv, double* fdinv) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] {
+    Handle& H = hh->h;
+    need_ready(H);
+    if (H.opt.stage3 == MSS_BLOCK_JACOBI)
+      fail(MSS_ERR_INVALID_ARG, "block Jacobi has no ILU factors");
+    if (fv) copy_dev(&H, fv, H.fv.p, sizeof(double) * H.fv.n);
+    if (fdinv) copy_dev(&H, fdinv, H.fdinv.p, sizeof(double) * H.fdinv.n);
     MSS_CK(cudaStreamSynchronize(H.stream));
   });
 }

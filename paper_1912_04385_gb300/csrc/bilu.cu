@@ -971,7 +971,11 @@ void bilu_setup_nb(Handle* h) {
     const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
     if (s1 <= s0) continue;
     constexpr int G = 32 / NB;
-    if ((long long)(s1 - s0) < (long long)kSmallColour * G * h->num_sms) {
+    const int form = h->opt.factor_form;
+    const bool warp_form =
+        form == MSS_FACTOR_WARP ||
+        (form == MSS_FACTOR_AUTO && (long long)(s1 - s0) < (long long)kSmallColour * G * h->num_sms);
+    if (warp_form) {
       k_bilu_factor_warp<NB><<<grid_for((long long)(s1 - s0) * 32, 256), 256, 0, h->stream>>>(
           s0, s1, h->st_first.p, h->st_len.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p,
           h->fdinv.p, bjac ? 1 : 0, bad.p);

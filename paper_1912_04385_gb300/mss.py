@@ -23,12 +23,13 @@ SCHEMES = {"cptr3": 0, "cpr": 1, "ilu0": 2}
 SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 DRIVERS = {"host": 0, "graph": 1}
+FACTOR_FORMS = {"auto": 0, "warp": 1, "lanes": 2}
 
 # every exported symbol declared in include/mss.h
 EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
            "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
            "mss_residual_norm", "mss_residual_norm_noalloc", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
-           "mss_bilu_num_colours", "mss_bilu_ordering", "mss_probe_wait_limit", "mss_kernel_launches",
+           "mss_bilu_num_colours", "mss_bilu_ordering", "mss_bilu_factors", "mss_probe_wait_limit", "mss_kernel_launches",
            "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error",
            "mss_batch_create", "mss_batch_destroy", "mss_batch_solve", "mss_batch_tuned",
            "mss_batch_last_error", "mss_gnn_num_params", "mss_gnn_create", "mss_gnn_destroy",
@@ -46,7 +47,7 @@ class Options(C.Structure):
                 ("amg_max_coarse", C.c_int32), ("amg_max_levels", C.c_int32),
                 ("interp_max_elems", C.c_int32), ("restart", C.c_int32),
                 ("precision", C.c_int32), ("ilu_strip", C.c_int32),
-                ("orthog", C.c_int32), ("driver", C.c_int32),
+                ("orthog", C.c_int32), ("driver", C.c_int32), ("factor_form", C.c_int32),
                 ("amg_theta", C.c_double), ("jacobi_omega", C.c_double),
                 ("cheb_lo_ratio", C.c_double), ("cheb_hi_factor", C.c_double),
                 ("seed", C.c_uint64), ("learned_interp", C.c_void_p)]
@@ -121,6 +122,7 @@ def load(path: Path | str | None = None):
     L.mss_amg_level_copy.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P, P, P]
     L.mss_bilu_num_colours.argtypes = [P, P]
     L.mss_bilu_ordering.argtypes = [P, P, P]
+    L.mss_bilu_factors.argtypes = [P, P, P]
     L.mss_probe_wait_limit.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     L.mss_kernel_launches.restype = C.c_longlong
     L.mss_kernel_launches.argtypes = [C.c_int]
@@ -175,6 +177,8 @@ def options(**kw) -> Options:
             v = PRECISIONS[v]
         if k == "driver" and isinstance(v, str):
             v = DRIVERS[v]
+        if k == "factor_form" and isinstance(v, str):
+            v = FACTOR_FORMS[v]
         if k == "learned_interp" and v is not None and not isinstance(v, int):
             # a float32 CUDA tensor of mss_gnn_num_params() parameters
             if v.dtype.is_floating_point is False or v.element_size() != 4 or not v.is_cuda:
@@ -407,6 +411,15 @@ class Solver:
         self._check(self.lib.mss_bilu_ordering(self.h, _ptr(colour), _ptr(perm)),
                     "mss_bilu_ordering")
         return nc.value, colour, perm
+
+    def bilu_factors(self):
+        """(fv, fdinv): the block ILU(0) factors in colour-major positions,
+        shapes (nnzb, nb, nb) and (N, nb, nb) (see mss_bilu_factors)."""
+        torch = self._torch
+        fv = torch.empty(self.nnzb * self.nb * self.nb, dtype=torch.float64, device="cuda")
+        fd = torch.empty(self.N * self.nb * self.nb, dtype=torch.float64, device="cuda")
+        self._check(self.lib.mss_bilu_factors(self.h, _ptr(fv), _ptr(fd)), "mss_bilu_factors")
+        return fv.view(self.nnzb, self.nb, self.nb), fd.view(self.N, self.nb, self.nb)
 
 
 class Batch:

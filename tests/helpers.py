@@ -43,3 +43,24 @@ def operator_matrix(apply, n):
         M[:, k] = apply(e)
         e[k] = 0.0
     return M
+
+
+def stored_factor_form(bilu, strip):
+    """The block ILU(0) factors of the oracle (``OracleSolver.bilu()``) in the
+    form the library stores them (``mss_bilu_factors``): the same L and U
+    blocks in colour-major positions, except that an upper block coupling two
+    cells of one strip holds U_qq^{-1} U_qj; plus U_qq^{-1} per position.
+    strip: cells per strip of the ordering (1 for point multicolour). Format
+    conversion only: the inverses are numpy's."""
+    perm, rp, ci, v = bilu["perm"], bilu["row_ptr"], bilu["col_idx"], bilu["vals"]
+    n = perm.size
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    dpos = np.flatnonzero(ci == rows)
+    assert dpos.size == n
+    fdinv = np.linalg.inv(v[dpos])
+    fv = v.copy()
+    if strip > 1:
+        sid = perm // strip
+        m = (ci > rows) & (sid[ci] == sid[rows])
+        fv[m] = np.einsum("kij,kjl->kil", fdinv[rows[m]], v[m])
+    return fv, fdinv

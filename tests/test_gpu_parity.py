@@ -23,6 +23,10 @@ torch = pytest.importorskip("torch")
 
 APPLY_TOL = 1e-12
 SOL_TOL = 1e-8
+# Factors in the max norm relative to the largest entry: both sides run the
+# same IKJ elimination and no-pivot Gauss-Jordan, differing only in rounding
+# (FMA on the GPU, numpy's inverse for U_qq^-1 on the oracle side).
+FACTOR_TOL = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -112,6 +116,30 @@ def test_ordering_bit_exact(mss, case, order, strip):
     assert nc == f["ncolours"]
     assert np.array_equal(_n(colour), f["colour"])
     assert np.array_equal(_n(perm), f["perm"])
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("order,strip", [(2, 32), (2, 5), (0, 1)])
+def test_factor_forms(mss, case, order, strip):
+    # Both factorisation kernels, forced on every colour: the same bits as
+    # each other, the oracle's factors element by element, and the last stage
+    # (which reads them) against the oracle's.
+    from tests.helpers import stored_factor_form
+    s = _sys(CASES[case])
+    kw = dict(ilu_order=order, ilu_strip=strip)
+    gw = _gpu(mss, s, factor_form="warp", **kw)
+    gl = _gpu(mss, s, factor_form="lanes", **kw)
+    fw, dw = gw.bilu_factors()
+    fl, dl = gl.bilu_factors()
+    assert torch.equal(fw, fl) and torch.equal(dw, dl)
+    o = _orc(s, **kw)
+    efv, edinv = stored_factor_form(o.bilu(), strip if order == 2 else 1)
+    assert _rel(_n(fl), efv) < FACTOR_TOL
+    assert _rel(_n(dl), edinv) < FACTOR_TOL
+    r = np.random.default_rng(case).standard_normal(s.n_cells * s.nb)
+    ref = o.stage(2, r)
+    for g in (gw, gl):
+        assert _rel(_n(g.stage(2, _t(r))), ref) < APPLY_TOL
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
