@@ -16,8 +16,9 @@
 namespace mss {
 namespace {
 
-// Largest number of cells (BSR block rows) the no-allocation call accepts.
-constexpr int kNoAllocMaxCells = 1 << 20;
+// Largest number of cells (BSR block rows) the no-allocation call accepts:
+// the limit the public header announces.
+constexpr int kNoAllocMaxCells = MSS_NOALLOC_MAX_CELLS;
 
 // Per-cell partial sums (2 per cell): 16 MiB that every GPU which loads the
 // library keeps until the process exits. All calls share it; it keeps the

@@ -49,7 +49,7 @@ def test_apply_flops_hand_count():
 
 
 def test_precond_roofline_takes_the_slower_bound():
-    # 6.8 TB at 6800 GB/s is 1000 ms; 0.5 PFLOP at 1 TFLOP/s is 500 ms
+    # 6.8 TB at 6800 GB/s is 1000 ms; 0.5 PFLOP at 1 TFLOP/s is 500000 ms (500 s)
     r = bench.precond_roofline(bytes_apply=6.8e12, flops_apply=0.5e15, apply_ms=2000.0,
                                hbm_gbs=6800.0, fp64_tflops=1.0)
     assert r["t_hbm_ms"] == pytest.approx(1000.0) and r["t_fp64_ms"] == pytest.approx(500000.0)

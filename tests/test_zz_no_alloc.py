@@ -90,3 +90,41 @@ def test_noalloc_rejects_sizes_beyond_the_limit():
         assert calls["alloc"] == 0
     finally:
         lib.mss_destroy(h)
+
+
+def test_noalloc_at_the_limit():
+    # exactly MSS_NOALLOC_MAX_CELLS cells (the 1024 x 1024 grid): the kernels
+    # write and read the whole static array; a diagonal-only BSR with nb = 2
+    # keeps the inputs small (about 40 MB)
+    from paper_1912_04385_gb300 import build, mss
+    build.build()
+    lib, h, calls, keep = _counting_handle(mss)
+    try:
+        n = 1 << 20
+        nb = 2
+        rp = torch.arange(n + 1, dtype=torch.int32, device="cuda")
+        ci = torch.arange(n, dtype=torch.int32, device="cuda")
+        g = torch.Generator(device="cpu").manual_seed(3)
+        v = torch.randn(n * nb * nb, generator=g, dtype=torch.float64).cuda()
+        b = torch.randn(n * nb, generator=g, dtype=torch.float64).cuda()
+        x = torch.randn(n * nb, generator=g, dtype=torch.float64).cuda()
+        J = mss.Bsr(n, n, rp.data_ptr(), ci.data_ptr(), v.data_ptr())
+        ref = torch.empty(2, dtype=torch.float64, device="cuda")
+        out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+        assert lib.mss_residual_norm(h, C.byref(J), nb, b.data_ptr(), x.data_ptr(),
+                                     ref.data_ptr()) == 0
+        before = dict(calls)
+        st = lib.mss_residual_norm_noalloc(h, C.byref(J), nb, b.data_ptr(), x.data_ptr(),
+                                           out.data_ptr())
+        assert st == 0, lib.mss_last_error(h)
+        torch.cuda.synchronize()
+        assert calls == before
+        r, o = ref.cpu().numpy(), out.cpu().numpy()
+        assert np.all(np.abs(o - r) <= TOL * np.abs(r)), (o, r)
+        # and against the definition, block by block on the host
+        blocks = v.view(n, nb, nb).cpu().numpy()
+        res = b.cpu().numpy().reshape(n, nb) - np.einsum("kij,kj->ki", blocks,
+                                                         x.cpu().numpy().reshape(n, nb))
+        assert abs(o[0] - np.linalg.norm(res)) <= TOL * np.linalg.norm(res)
+    finally:
+        lib.mss_destroy(h)
