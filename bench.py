@@ -58,6 +58,10 @@ def args_():
                     help="systems in the batched-solve comparison (0: skip)")
     ap.add_argument("--batch-lanes", type=int, default=8)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-newton", action="store_true",
+                    help="skip the Newton-loop reuse leg")
+    ap.add_argument("--no-smoothers", action="store_true",
+                    help="skip the multicolour Gauss-Seidel legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     return ap.parse_args()
@@ -311,6 +315,13 @@ def run_ours(a, rank, world, dist):
         out["mixed"] = mixed_leg(a, dev, solver, torch, stream)
         if a.mixed_n > 0:
             out["mixed_config"] = mixed_config_leg(a, solver, torch, stream)
+    if not a.no_newton:
+        out["newton"] = newton_leg(a, dev, solver, torch)
+    if not a.no_smoothers:
+        # the paper's smoother (symmetric Gauss-Seidel, multicolour form)
+        out["mcsgs"] = variant_leg(a, dev, solver, torch, stream, smoother="mcsgs")
+        out["mcsgs_v11"] = variant_leg(a, dev, solver, torch, stream, smoother="mcsgs",
+                                       nu_pre=1, nu_post=1)
     if a.batch > 0:
         out["batch"] = batch_leg(a, torch)
     if not a.no_learned:
@@ -376,6 +387,89 @@ def mixed_leg(a, dev, solver, torch, stream):
             "trace_ms": {k: [v[0], round(v[1], 3)] for k, v in tr.items()},
             "storage": "bf16 blocks, fp32 vectors and sweeps, fp64 Krylov",
             "driver": a.driver}
+
+
+def variant_leg(a, dev, solver, torch, stream, **kw):
+    """The benchmark systems with other options (FP64): ms per system (CUDA
+    events around set-up + solve), iterations, and the kernel-class times of
+    one host-driven pass."""
+    from paper_1912_04385_gb300 import mss
+    opts = mss.options(restart=a.restart, driver=a.driver, **kw)
+    host = mss.options(restart=a.restart, driver="host", **kw)
+
+    def step(o, infos=None):
+        for rp, ci, v, b in dev:
+            solver.setup(rp, ci, v, 6, 0, 1, opts=o)
+            x, info = solver.solve(b, tol=a.tol, maxit=a.maxit)
+            if info["status"] != 0:
+                raise RuntimeError(f"solve with {kw} failed: {info}")
+            if infos is not None:
+                infos.append(info)
+
+    for _ in range(max(1, a.warmup)):
+        step(opts)
+    torch.cuda.synchronize()
+    infos = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step(opts, infos)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    solver.trace(True)
+    solver.trace_read(reset=True)
+    step(host)
+    torch.cuda.synchronize()
+    tr = solver.trace_read(reset=True)
+    solver.trace(False)
+    n_apply, apply_ms = tr["apply"]
+    n_vc, vc_ms = tr["vcycle"]
+    return {"options": kw, "ms_per_system": round(ms / (a.steps * len(dev)), 3),
+            "iters": [i["iters"] for i in infos[:len(dev)]],
+            "setup_ms_mean": round(float(np.mean([i["setup_ms"] for i in infos])), 3),
+            "solve_ms_mean": round(float(np.mean([i["solve_ms"] for i in infos])), 3),
+            "apply_ms_mean": round(apply_ms / max(n_apply, 1), 4),
+            "vcycle_ms_mean": round(vc_ms / max(n_vc, 1), 4), "driver": a.driver}
+
+
+def newton_leg(a, dev, solver, torch, pes=(12.0, 14.4, 17.28)):
+    """Newton-loop reuse (Sec. 2.5): after the Pe = 10 benchmark system, later
+    Jacobians on the same grid (same pattern) from the same generator with a
+    drifting Peclet number, each handled by a new mss_setup, by
+    mss_update_values keeping the pattern, and by mss_update_values keeping
+    the coarsening too. Host wall ms of the set-up call (it returns with the
+    set-up complete) and the iterations of the solve that follows."""
+    from paper_1912_04385_gb300 import mss
+    from paper_1912_04385_gb300 import synthetic as sy
+    rp, ci, v, b = dev[1]
+    opts = mss.options(restart=a.restart, driver=a.driver)
+    jac = []
+    for pe in pes:
+        s = sy.plain_at_scale(a.n, pe=pe, seed=0)
+        jac.append((torch.from_numpy(s.vals.reshape(-1)).cuda(), torch.from_numpy(s.b).cuda()))
+    out = {}
+    for mode in ("setup", "pattern", "coarsening"):
+        solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
+        solver.solve(b, tol=a.tol, maxit=a.maxit)
+        ms, its = [], []
+        for vk, bk in jac:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode == "setup":
+                solver.setup(rp, ci, vk, 6, 0, 1, opts=opts)
+            else:
+                solver.update_values(vk, reuse=mode)
+            ms.append((time.perf_counter() - t0) * 1e3)
+            x, info = solver.solve(bk, tol=a.tol, maxit=a.maxit)
+            if info["status"] != 0:
+                raise RuntimeError(f"Newton-sequence solve failed ({mode}): {info}")
+            its.append(info["iters"])
+        out[mode] = {"setup_ms": [round(t, 3) for t in ms], "iters": its}
+    out["sequence"] = (f"the {a.n}x{a.n} Pe=10 system, then Pe " +
+                       ", ".join(f"{p:g}" for p in pes) + " on the same grid; host ms of the "
+                       "set-up call")
+    return out
 
 
 def mixed_config_leg(a, solver, torch, stream):

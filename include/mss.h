@@ -54,7 +54,9 @@ enum { MSS_CPTR3 = 0, MSS_CPR = 1, MSS_ILU0 = 2 };   /* preconditioner scheme */
 enum { MSS_STAGE_T_FIRST = 0, MSS_STAGE_P_FIRST = 1 }; /* CPTR3 stage order */
 enum { MSS_BILU0 = 0, MSS_BLOCK_JACOBI = 1 };        /* last stage */
 enum { MSS_MULTICOLOR = 0, MSS_STRIPS = 2 };         /* block ILU(0) ordering */
-enum { MSS_JACOBI = 0, MSS_CHEBYSHEV = 1 };          /* AMG smoother */
+enum { MSS_JACOBI = 0, MSS_CHEBYSHEV = 1, MSS_MCSGS = 3 }; /* AMG smoother (2: lexicographic
+                                                       symmetric Gauss-Seidel, sequential,
+                                                       has no GPU form) */
 enum { MSS_FP64 = 0, MSS_MIXED = 1 };                /* preconditioner arithmetic */
 enum { MSS_CGS1 = 0, MSS_CGS2 = 1 };                 /* Arnoldi orthogonalisation */
 enum { MSS_DRIVER_HOST = 0, MSS_DRIVER_GRAPH = 1 };  /* who runs the FGMRES loop */
@@ -84,7 +86,12 @@ typedef struct {
   int32_t ilu_order;        /* MSS_STRIPS (default): strips of ilu_strip consecutive
                                cells, coloured, natural order inside a strip;
                                MSS_MULTICOLOR: every cell coloured on its own */
-  int32_t smoother;         /* MSS_JACOBI (default) | MSS_CHEBYSHEV */
+  int32_t smoother;         /* MSS_JACOBI (default) | MSS_CHEBYSHEV | MSS_MCSGS:
+                               symmetric Gauss-Seidel, the smoother of the paper's
+                               AMG (Sec. 5.1), in multicolour form: per level the
+                               points are coloured (Jones-Plassmann, `seed`), one
+                               application sweeps the colours in order and then
+                               in reverse, a colour's points updated at once */
   int32_t nu_pre, nu_post;  /* smoothing sweeps per V-cycle leg (2, 2: HSL_MI20's defaults,
                                which Sec. 5.1 names) */
   int32_t cheb_degree;      /* Chebyshev polynomial degree (2) */
@@ -185,6 +192,28 @@ void mss_destroy(mss_handle* h);
  * pivoting), AMG, OOM, CUDA. */
 int mss_setup(mss_handle* h, const mss_bsr* J, int nb, mss_layout layout,
               const mss_options* opt);
+
+/* New values of the same matrix pattern, as in a Newton loop (Sec. 2.5: the
+ * Jacobian is re-evaluated at every Newton iteration and time step on a fixed
+ * grid, so its block pattern does not change). J has the set-up's n_rows,
+ * nnzb and pattern (checked on the device: INVALID_ARG otherwise; the
+ * arrays may be other copies); its values replace the set-up's. The
+ * symbolic set-up is kept -- the validated pattern, the diagonal positions,
+ * the last stage's colouring, ordering and factor pattern -- and the rest is
+ * recomputed: the scaling, B_PP and C_TT, the AMG hierarchies, the
+ * factorisation and the reduced-precision copies.
+ *   reuse = MSS_REUSE_PATTERN: the result is the one mss_setup gives for J,
+ *           bit for bit (every kept part depends on the pattern only);
+ *   reuse = MSS_REUSE_COARSENING: every AMG level also keeps its C/F split,
+ *           so strength, interpolation weights and the Galerkin operators are
+ *           recomputed on the earlier coarse grids (an F point left without
+ *           a strong C point interpolates nothing).
+ * Options are the set-up's (a learned_interp pointer must still be valid).
+ * Afterwards mss_fgmres_solve takes J (not the set-up's mss_bsr). Errors:
+ * NOT_SETUP, INVALID_ARG, SINGULAR_BLOCK, AMG, OOM, CUDA; after an error the
+ * handle needs mss_setup again. */
+enum { MSS_REUSE_PATTERN = 0, MSS_REUSE_COARSENING = 1 };
+int mss_update_values(mss_handle* h, const mss_bsr* J, int reuse);
 
 /* bbar = N^{-1} b (Eq. splitPrec1), device vectors of length N*nb.
  * Errors: NOT_SETUP, INVALID_ARG. */

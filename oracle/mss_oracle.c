@@ -735,9 +735,13 @@ static int level_colours(level_t* L, uint64_t seed) {
   return OR_OK;
 }
 
-/* Build the hierarchy for a scalar CSR matrix (copied). */
+/* Build the hierarchy for a scalar CSR matrix (copied). With `frozen` (a
+ * hierarchy of an earlier matrix with the same pattern; NULL otherwise) every
+ * level that frozen coarsened keeps frozen's C/F split instead of running
+ * PMIS: strength, interpolation and the Galerkin products are recomputed from
+ * the new values (Newton-loop reuse, reading of Sec. 2.5). */
 static int amg_build(int n, const int* rp, const int* ci, const double* v, const or_opts* o,
-                     amg_t** out) {
+                     const amg_t* frozen, amg_t** out) {
   amg_t* h = (amg_t*)calloc(1, sizeof(amg_t));
   if (!h) return OR_ERR_MEM;
   h->o = *o;
@@ -759,7 +763,10 @@ static int amg_build(int n, const int* rp, const int* ci, const double* v, const
     L->cidx = (int*)malloc(sizeof(int) * (size_t)L->A.n);
     if (!L->strong || !L->cf || !L->cidx) { st = OR_ERR_MEM; goto fail; }
     amg_strength(&L->A, o->theta, L->strong);
-    if ((st = amg_pmis(&L->A, L->strong, o->seed, l, L->cf, NULL, NULL)) != OR_OK) goto fail;
+    if (frozen && l < frozen->nlev && frozen->lev[l].cf && frozen->lev[l].A.n == L->A.n)
+      memcpy(L->cf, frozen->lev[l].cf, sizeof(int) * (size_t)L->A.n);
+    else if ((st = amg_pmis(&L->A, L->strong, o->seed, l, L->cf, NULL, NULL)) != OR_OK)
+      goto fail;
     int nc = 0;
     for (int i = 0; i < L->A.n; ++i) L->cidx[i] = L->cf[i] ? nc++ : -1;
     L->nc = nc;
@@ -1215,13 +1222,13 @@ static int dense_subsystem(const or_solver* s, int var, double** lu, int** piv) 
   return lu_factor(N, *lu, *piv);
 }
 
-static int build_amg_for(or_solver* s, int var, amg_t** out) {
+static int build_amg_for(or_solver* s, int var, const amg_t* frozen, amg_t** out) {
   int N = s->N, nb2 = s->nb * s->nb;
   double* v = (double*)malloc(sizeof(double) * (size_t)(s->nnzb > 0 ? s->nnzb : 1));
   if (!v) return OR_ERR_MEM;
   /* scalar subsystem: (var, var) entry of every scaled block (B_PP, C_TT) */
   for (int e = 0; e < s->nnzb; ++e) v[e] = s->Abar[(size_t)e * nb2 + var * s->nb + var];
-  int st = amg_build(N, s->rp, s->ci, v, &s->o, out);
+  int st = amg_build(N, s->rp, s->ci, v, &s->o, frozen, out);
   free(v);
   return st;
 }
@@ -1229,8 +1236,9 @@ static int build_amg_for(or_solver* s, int var, amg_t** out) {
 /* Set-up: scaling (Eqs. CPR / CPTR31 / CPTR32), subsystem extraction (B_PP
  * Eq. CPR and CPTR31, C_TT Eq. CPTR32), AMG or exact sub-solvers, and the
  * last stage (block ILU(0) of the scaled matrix, Eq. CPTR3M3). */
-or_solver* or_setup(int N, int nb, const int* rp, const int* ci, const double* vals, int p,
-                    int t, const or_opts* o, int* status) {
+static or_solver* setup_impl(int N, int nb, const int* rp, const int* ci, const double* vals,
+                             int p, int t, const or_opts* o, const amg_t* frozT,
+                             const amg_t* frozP, int* status) {
   int st = OR_OK;
   *status = OR_OK;
   if (N < 0 || nb < 2 || nb > 32 || p < 0 || p >= nb || t < 0 || t >= nb || p == t) {
@@ -1288,8 +1296,8 @@ or_solver* or_setup(int N, int nb, const int* rp, const int* ci, const double* v
       if ((st = dense_subsystem(s, p, &s->luP, &s->pivP)) != OR_OK) goto fail;
       if (o->scheme == 0 && (st = dense_subsystem(s, t, &s->luT, &s->pivT)) != OR_OK) goto fail;
     } else {
-      if ((st = build_amg_for(s, p, &s->amgP)) != OR_OK) goto fail;
-      if (o->scheme == 0 && (st = build_amg_for(s, t, &s->amgT)) != OR_OK) goto fail;
+      if ((st = build_amg_for(s, p, frozP, &s->amgP)) != OR_OK) goto fail;
+      if (o->scheme == 0 && (st = build_amg_for(s, t, frozT, &s->amgT)) != OR_OK) goto fail;
     }
   }
   if (o->stage3 == 0) {
@@ -1306,6 +1314,25 @@ fail:
   *status = st;
   or_free(s);
   return NULL;
+}
+
+or_solver* or_setup(int N, int nb, const int* rp, const int* ci, const double* vals, int p,
+                    int t, const or_opts* o, int* status) {
+  return setup_impl(N, nb, rp, ci, vals, p, t, o, NULL, NULL, status);
+}
+
+/* The set-up for new values on the pattern of `old` (Newton-loop reuse,
+ * Sec. 2.5: the grid, hence the pattern, stays fixed across Newton
+ * iterations and time steps). reuse = 0: everything is recomputed, exactly
+ * as or_setup does (the ordering depends on the pattern only); reuse = 1:
+ * the AMG levels keep old's C/F splits. */
+or_solver* or_update(const or_solver* old, const double* vals, int reuse, int* status) {
+  if (!old || (reuse != 0 && reuse != 1)) {
+    *status = OR_ERR_ARG;
+    return NULL;
+  }
+  return setup_impl(old->N, old->nb, old->rp, old->ci, vals, old->p, old->t, &old->o,
+                    reuse ? old->amgT : NULL, reuse ? old->amgP : NULL, status);
 }
 
 /* scalar sub-solver on unknown `var`: y_var = M_var^{-1} r_var */
@@ -1553,7 +1580,7 @@ int or_bilu_get(const or_solver* s, int* colour, int* perm, int* frp, int* fci, 
 amg_t* or_amg_create(int n, const int* rp, const int* ci, const double* v, const or_opts* o,
                      int* status) {
   amg_t* h = NULL;
-  *status = amg_build(n, rp, ci, v, o, &h);
+  *status = amg_build(n, rp, ci, v, o, NULL, &h);
   return h;
 }
 

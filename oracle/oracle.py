@@ -49,6 +49,8 @@ def lib():
         L.or_setup.argtypes = [C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int,
                                C.POINTER(OrOpts), C.POINTER(C.c_int)]
         L.or_free.argtypes = [_P]
+        L.or_update.restype = _P
+        L.or_update.argtypes = [_P, _P, C.c_int, C.POINTER(C.c_int)]
         L.or_get_scaled.argtypes = [_P, _P, _P]
         L.or_scale_rhs.argtypes = [_P, _P, _P]
         L.or_spmv.argtypes = [_P, _P, _P]
@@ -141,6 +143,19 @@ class OracleSolver:
     @classmethod
     def from_system(cls, sysm, **kw):
         return cls(sysm.row_ptr, sysm.col_idx, sysm.vals, sysm.nb, sysm.p_idx, sysm.t_idx, **kw)
+
+    def updated(self, vals, reuse: int = 0) -> "OracleSolver":
+        """A new solver for new block values on this solver's pattern
+        (or_update): reuse = 0 recomputes everything, reuse = 1 keeps every
+        AMG level's C/F split."""
+        new = object.__new__(OracleSolver)
+        new._keep = (self._keep[0], self._keep[1], _f64(vals))
+        new.N, new.nb, new.nnzb, new.opts = self.N, self.nb, self.nnzb, self.opts
+        st = C.c_int(0)
+        new._h = lib().or_update(self._h, _ptr(new._keep[2]), int(reuse), C.byref(st))
+        if not new._h:
+            raise OracleError(st.value, "or_update")
+        return new
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -418,6 +418,24 @@ __global__ void k_cheb(int n, const int* __restrict__ rp, const int* __restrict_
   xout[i] = xin[i] + di;
 }
 
+// One colour of a Gauss-Seidel sweep, in place: x_i = (b_i - sum_{j != i}
+// a_ij x_j) / a_ii for the points i of the colour. A colour's points are not
+// coupled, so every row reads only other colours' values.
+template <class V, class C>
+__global__ void k_mcgs(int q0, int q1, const int* __restrict__ order, const int* __restrict__ rp,
+                       const int* __restrict__ ci, const V* __restrict__ v,
+                       const C* __restrict__ dinv, const C* __restrict__ b, C* x) {
+  const int q = q0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= q1) return;
+  const int i = order[q];
+  C s = b[i];
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    const int j = ci[k];
+    if (j != i) s -= cvt<C>(v[k]) * x[j];
+  }
+  x[i] = s * dinv[i];
+}
+
 template <class V, class C>
 __global__ void k_residual(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                            const V* __restrict__ v, const C* __restrict__ b,
@@ -641,15 +659,19 @@ struct LV {
   const C* dinv;
   C *x2, *r, *d;
   double lam;
+  const int* mcorder;                 // multicolour Gauss-Seidel order (or null)
+  const std::vector<int>* cstart;     // its colour boundaries (host)
 };
 
 LV<double, double> view(Level& L, double*) {
   return {L.n, L.nc, L.rp.p, L.ci.p, L.prp.p, L.pci.p, L.rrp.p, L.rci.p,
-          L.v.p, L.pv.p, L.rv.p, L.dinv.p, L.x2.p, L.r.p, L.d.p, L.lam};
+          L.v.p, L.pv.p, L.rv.p, L.dinv.p, L.x2.p, L.r.p, L.d.p, L.lam,
+          L.mcorder.p, &L.cstart};
 }
 LV<__nv_bfloat16, float> view(Level& L, float*) {
   return {L.n, L.nc, L.rp.p, L.ci.p, L.prp.p, L.pci.p, L.rrp.p, L.rci.p,
-          L.vh.p, L.pvh.p, L.rvh.p, L.dinvf.p, L.x2f.p, L.rf.p, L.df.p, L.lam};
+          L.vh.p, L.pvh.p, L.rvh.p, L.dinvf.p, L.x2f.p, L.rf.p, L.df.p, L.lam,
+          L.mcorder.p, &L.cstart};
 }
 double* level_b(Level& L, double*) { return L.b.p; }
 float* level_b(Level& L, float*) { return L.bf.p; }
@@ -669,6 +691,23 @@ struct Sweeper {
     k_jacobi<V, C><<<grid_for(L.n, h->tb), h->tb, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.dinv, b,
                                                             (C)o.jacobi_omega, xin, xout);
     MSS_LAUNCH_CK("k_jacobi");
+  }
+  // symmetric multicolour Gauss-Seidel, in place on x: the colours in
+  // order, then in reverse. The reverse pass starts with the colour the
+  // forward pass ended with, whose recomputation from unchanged neighbours
+  // gives the same values, so it is not repeated.
+  void mcsgs(const C* b, C* x) {
+    const std::vector<int>& cs = *L.cstart;
+    const int nc = (int)cs.size() - 1;
+    auto colour = [&](int c) {
+      const int q0 = cs[c], q1 = cs[c + 1];
+      if (q1 <= q0) return;
+      k_mcgs<V, C><<<grid_for(q1 - q0, h->tb), h->tb, 0, h->stream>>>(q0, q1, L.mcorder, L.rp,
+                                                                       L.ci, L.v, L.dinv, b, x);
+      MSS_LAUNCH_CK("k_mcgs");
+    };
+    for (int c = 0; c < nc; ++c) colour(c);
+    for (int c = nc - 2; c >= 0; --c) colour(c);
   }
   // Chebyshev polynomial of degree o.cheb_degree; ping-pongs between x and
   // alt, returns the buffer holding the result
@@ -789,6 +828,11 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out, bool x_has
     }
     k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
     MSS_LAUNCH_CK("k_residual");
+  } else if (o.smoother == MSS_MCSGS) {
+    MSS_CK(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)n, h->stream));
+    for (int s = 0; s < o.nu_pre; ++s) sw.mcsgs(b, cur);
+    k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
+    MSS_LAUNCH_CK("k_residual");
   } else {
     MSS_CK(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)n, h->stream));
     for (int s = 0; s < o.nu_pre; ++s) {
@@ -808,7 +852,10 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out, bool x_has
   vcycle_level<V, C>(h, H, l + 1, cb, cx, next0);
   // ---- prolongation into the vector from which the post-smoothing sweeps,
   // alternating between the two vectors, end in out
-  const int writes = o.nu_post * (o.smoother == MSS_JACOBI ? 1 : o.cheb_degree);
+  // (Gauss-Seidel sweeps work in place)
+  const int writes = o.smoother == MSS_MCSGS
+                         ? 0
+                         : o.nu_post * (o.smoother == MSS_JACOBI ? 1 : o.cheb_degree);
   C* target = writes % 2 == 0 ? out : L.x2;
   k_prolong<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.prp, L.pci, L.pv, cx, cur,
                                                                target);
@@ -820,6 +867,8 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out, bool x_has
     if (o.smoother == MSS_JACOBI) {
       sw.jacobi(b, cur, alt);
       std::swap(cur, alt);
+    } else if (o.smoother == MSS_MCSGS) {
+      sw.mcsgs(b, cur);
     } else {
       C* res = sw.cheb(b, cur, alt);
       if (res != cur) std::swap(cur, alt);

@@ -629,6 +629,39 @@ void level_prepare(Handle* h, Level& L) {
   L.d.reset(h, n);
 }
 
+__global__ void k_flag_eq(int n, const int* __restrict__ a, int c, int* __restrict__ f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = a[i] == c ? 1 : 0;
+}
+
+__global__ void k_place_eq(int n, const int* __restrict__ a, int c, int base,
+                           const int* __restrict__ rank, int* __restrict__ order) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && a[i] == c) order[base + rank[i]] = i;
+}
+
+// Multicolour Gauss-Seidel order of a level: Jones-Plassmann colours of A's
+// graph, then the points colour-major, ascending inside each colour.
+void level_colours(Handle* h, Level& L) {
+  const int n = L.n;
+  DBuf<int> col(h, n), flag(h, n), rank(h, n + 1);
+  L.ncolour = colour_points(h, n, L.rp.p, L.ci.p, h->opt.seed, col.p);
+  L.cstart.assign(L.ncolour + 1, 0);
+  L.mcorder.reset(h, n);
+  int base = 0;
+  for (int c = 0; c < L.ncolour; ++c) {
+    k_flag_eq<<<grid_for(n, 256), 256, 0, h->stream>>>(n, col.p, c, flag.p);
+    MSS_LAUNCH_CK("k_flag_eq");
+    exclusive_scan(h, flag.p, rank.p, n);
+    k_place_eq<<<grid_for(n, 256), 256, 0, h->stream>>>(n, col.p, c, base, rank.p, L.mcorder.p);
+    MSS_LAUNCH_CK("k_place_eq");
+    L.cstart[c] = base;
+    base += read_int(h, rank.p + n);
+  }
+  L.cstart[L.ncolour] = base;
+  if (base != n) fail(MSS_ERR_CUDA, "AMG level colours do not cover every point");
+}
+
 }  // namespace
 
 // Host time per set-up phase, printed when MSS_SETUP_TIMES is set (each mark
@@ -656,7 +689,7 @@ struct PhaseClock {
 };
 
 void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const int* ci0,
-               const double* vals0, const float* learned) {
+               const double* vals0, const float* learned, std::vector<DBuf<int>>* frozen_cf) {
   const mss_options& o = h->opt;
   PhaseClock pc(h);
   H.lev.clear();
@@ -695,6 +728,13 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     MSS_LAUNCH_CK("k_fill_strong");
     DBuf<int> strp, stci;
     transpose(h, n, n, srp.p, sci.p, nullptr, ns, strp, stci, nullptr);
+    Level& L = H.lev[l];
+    // Newton-loop reuse: the level keeps the C/F split of the earlier set-up
+    const bool frozen = frozen_cf && l < (int)frozen_cf->size() &&
+                        (*frozen_cf)[l].p != nullptr && (*frozen_cf)[l].n == (size_t)n;
+    if (frozen) {
+      L.cf = std::move((*frozen_cf)[l]);
+    } else {
     // PMIS; |S_i^T| are the row lengths of the transposed strength graph
     pc.mark(1);
     DBuf<int> tcount(h, n);
@@ -725,10 +765,10 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
       undecided = read_int(h, und.p);
     }
     pc.mark(2);
-    Level& L = H.lev[l];
     L.cf.reset(h, n);
     k_pmis_finalize<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, state.p, L.cf.p);
     MSS_LAUNCH_CK("k_pmis_finalize");
+    }
     DBuf<int> cidx(h, n + 1);
     exclusive_scan(h, L.cf.p, cidx.p, n);
     int nc = read_int(h, cidx.p + n);
@@ -783,6 +823,8 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
   pc.mark(0);
   coarse_inverse(h, H);
   pc.mark(6);
+  if (o.smoother == MSS_MCSGS)   // the coarsest level is solved directly, not smoothed
+    for (size_t l = 0; l + 1 < H.lev.size(); ++l) level_colours(h, H.lev[l]);
 }
 
 }  // namespace mss

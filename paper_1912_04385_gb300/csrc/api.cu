@@ -47,7 +47,8 @@ void check_options(const mss_options& o) {
   if (o.ilu_order != MSS_MULTICOLOR && o.ilu_order != MSS_STRIPS) bad("ilu_order");
   if (o.ilu_strip < 1 || o.ilu_strip > 1024) bad("ilu_strip (1..1024)");
   if (o.orthog != MSS_CGS1 && o.orthog != MSS_CGS2) bad("orthog");
-  if (o.smoother != MSS_JACOBI && o.smoother != MSS_CHEBYSHEV) bad("smoother");
+  if (o.smoother != MSS_JACOBI && o.smoother != MSS_CHEBYSHEV && o.smoother != MSS_MCSGS)
+    bad("smoother");
   if (o.nu_pre < 0 || o.nu_pre > 16 || o.nu_post < 0 || o.nu_post > 16) bad("nu_pre/nu_post");
   if (o.smoother == MSS_JACOBI && o.nu_pre < 1) bad("nu_pre (Jacobi needs >= 1)");
   if (o.cheb_degree < 1 || o.cheb_degree > 16) bad("cheb_degree");
@@ -164,42 +165,28 @@ void release_setup(Handle& H) {
   H.ncol = 0;
 }
 
-void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_options* opt) {
-  auto t0 = std::chrono::steady_clock::now();
-  if (!J || !J->row_ptr || !J->col_idx || !J->vals) fail(MSS_ERR_INVALID_ARG, "null matrix");
-  if (J->n_rows < 1 || J->nnzb < J->n_rows) fail(MSS_ERR_INVALID_ARG, "bad matrix sizes");
-  if (nb < 2 || nb > 8) fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 8]");
-  if (layout.p_idx < 0 || layout.p_idx >= nb || layout.t_idx < 0 || layout.t_idx >= nb ||
-      layout.p_idx == layout.t_idx)
-    fail(MSS_ERR_INVALID_ARG, "p_idx and t_idx must be distinct indices in [0, nb)");
-  mss_options o;
-  if (opt) o = *opt;
-  else mss_options_default(&o);
-  check_options(o);
-  release_setup(H);
-  H.opt = o;
-  H.N = J->n_rows;
-  H.nnzb = J->nnzb;
-  H.nb = nb;
-  H.p = layout.p_idx;
-  H.t = layout.t_idx;
+void need_ready(const Handle& H) {
+  if (!H.ready) fail(MSS_ERR_NOT_SETUP, "mss_setup has not completed on this handle");
+}
+
+// The value-dependent set-up on a validated pattern (H.rp, H.ci, H.diag):
+// the scaling and extraction (Eqs. CPR, CPTR31, CPTR32), the two AMG
+// hierarchies on worker threads beside the last stage on this thread (with
+// its ordering and factor pattern when `ordering`, else on the existing
+// ones), the reduced-precision copies and the fused coarse levels. cfT / cfP:
+// C/F splits kept from an earlier set-up (Newton-loop reuse), or null.
+void numeric_setup(Handle& H, const double* vals, bool ordering, std::vector<DBuf<int>>* cfT,
+                   std::vector<DBuf<int>>* cfP) {
+  const mss_options& o = H.opt;
   const int N = H.N, nnzb = H.nnzb;
   Handle* h = &H;
-  H.rp.reset(h, N + 1);
-  H.ci.reset(h, nnzb);
-  H.diag.reset(h, N);
   {
     TraceScope ts(h, TR_SETUP_SCALE);
-    copy_dev(h, H.rp.p, J->row_ptr, sizeof(int) * ((size_t)N + 1));
-    copy_dev(h, H.ci.p, J->col_idx, sizeof(int) * (size_t)nnzb);
-    validate_pattern(h, H.rp.p, H.ci.p, N, nnzb, H.diag.p);
     // left scaling (Eq. splitPrec1 with Eq. CPR or Eqs. CPTR31/CPTR32)
-    H.wrows.reset(h, (size_t)N * 2 * nb);
-    H.abar.reset(h, (size_t)nnzb * nb * nb);
-    build_scaling(h, J->vals, layout.col_major_blocks != 0);
+    build_scaling(h, vals, H.col_major);
     if (o.scheme == MSS_CPTR3) {
-      H.apt.reset(h, nnzb);
-      H.atp.reset(h, nnzb);
+      if (H.apt.n != (size_t)nnzb) H.apt.reset(h, nnzb);
+      if (H.atp.n != (size_t)nnzb) H.atp.reset(h, nnzb);
       extract_subsystem(h, -1, H.apt.p);
       extract_subsystem(h, -2, H.atp.p);
     }
@@ -229,7 +216,7 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
     Fork fork(H);
     if (o.scheme != MSS_ILU0)
       fork.run(0, [&](Handle* a) {
-        amg_build(a, H.amgP, N, nnzb, H.rp.p, H.ci.p, bpp.p);
+        amg_build(a, H.amgP, N, nnzb, H.rp.p, H.ci.p, bpp.p, nullptr, cfP);
         if (times) {
           cudaStreamSynchronize(a->stream);
           tp = since();
@@ -238,7 +225,7 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
     if (o.scheme == MSS_CPTR3)
       fork.run(1, [&](Handle* a) {
         amg_build(a, H.amgT, N, nnzb, H.rp.p, H.ci.p, ctt.p,
-                  static_cast<const float*>(o.learned_interp));
+                  static_cast<const float*>(o.learned_interp), cfT);
         if (times) {
           cudaStreamSynchronize(a->stream);
           tt = since();
@@ -246,7 +233,8 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
       });
     std::exception_ptr mine;
     try {
-      bilu_setup(h);                              // last stage
+      if (ordering) bilu_setup(h);                // last stage
+      else bilu_refactor(h);
       if (times) {
         cudaStreamSynchronize(H.stream);
         tb = since();
@@ -257,16 +245,16 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
     fork.join();                                  // rethrows a worker's error
     if (mine) std::rethrow_exception(mine);
     if (times)
-      std::fprintf(stderr, "mss setup: fork at %.2f ms; P hierarchy %.2f, T hierarchy %.2f, "
-                           "last stage %.2f, join %.2f ms after the fork\n",
-                   std::chrono::duration<double, std::milli>(tf - t0).count(), tp, tt, tb,
-                   since());
+      std::fprintf(stderr, "mss setup: P hierarchy %.2f, T hierarchy %.2f, last stage %.2f, "
+                           "join %.2f ms after the fork\n", tp, tt, tb, since());
   }
-  H.rT.reset(h, N);
-  H.xT.reset(h, N);
-  H.zP.reset(h, N);
-  H.vP.reset(h, N);
-  H.w.reset(h, (size_t)N * nb);
+  if (H.rT.n != (size_t)N) {
+    H.rT.reset(h, N);
+    H.xT.reset(h, N);
+    H.zP.reset(h, N);
+    H.vP.reset(h, N);
+    H.w.reset(h, (size_t)N * H.nb);
+  }
   if (o.precision == MSS_MIXED) {
     // reduced-precision copies of everything the preconditioner reads
     TraceScope ts(h, TR_SETUP_BILU);
@@ -279,23 +267,117 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
       to_float(h, H.atp.p, H.atpf.p, nnzb);
     }
     pack_last_stage_mixed(h);
-    H.rTf.reset(h, N);
-    H.xTf.reset(h, N);
-    H.zPf.reset(h, N);
-    H.vPf.reset(h, N);
+    if (H.rTf.n != (size_t)N) {
+      H.rTf.reset(h, N);
+      H.xTf.reset(h, N);
+      H.zPf.reset(h, N);
+      H.vPf.reset(h, N);
+    }
   }
   if (H.amgT.present()) prepare_tail(h, H.amgT);
   if (H.amgP.present()) prepare_tail(h, H.amgP);
   MSS_CK(cudaStreamSynchronize(H.stream));
+}
+
+void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_options* opt) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!J || !J->row_ptr || !J->col_idx || !J->vals) fail(MSS_ERR_INVALID_ARG, "null matrix");
+  if (J->n_rows < 1 || J->nnzb < J->n_rows) fail(MSS_ERR_INVALID_ARG, "bad matrix sizes");
+  if (nb < 2 || nb > 8) fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 8]");
+  if (layout.p_idx < 0 || layout.p_idx >= nb || layout.t_idx < 0 || layout.t_idx >= nb ||
+      layout.p_idx == layout.t_idx)
+    fail(MSS_ERR_INVALID_ARG, "p_idx and t_idx must be distinct indices in [0, nb)");
+  mss_options o;
+  if (opt) o = *opt;
+  else mss_options_default(&o);
+  check_options(o);
+  release_setup(H);
+  H.opt = o;
+  H.N = J->n_rows;
+  H.nnzb = J->nnzb;
+  H.nb = nb;
+  H.p = layout.p_idx;
+  H.t = layout.t_idx;
+  H.col_major = layout.col_major_blocks != 0;
+  const int N = H.N, nnzb = H.nnzb;
+  Handle* h = &H;
+  H.rp.reset(h, N + 1);
+  H.ci.reset(h, nnzb);
+  H.diag.reset(h, N);
+  {
+    TraceScope ts(h, TR_SETUP_SCALE);
+    copy_dev(h, H.rp.p, J->row_ptr, sizeof(int) * ((size_t)N + 1));
+    copy_dev(h, H.ci.p, J->col_idx, sizeof(int) * (size_t)nnzb);
+    validate_pattern(h, H.rp.p, H.ci.p, N, nnzb, H.diag.p);
+  }
+  H.wrows.reset(h, (size_t)N * 2 * nb);
+  H.abar.reset(h, (size_t)nnzb * nb * nb);
+  numeric_setup(H, J->vals, true, nullptr, nullptr);
   H.J = *J;
   H.ready = true;
   H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                    .count();
 }
 
-void need_ready(const Handle& H) {
-  if (!H.ready) fail(MSS_ERR_NOT_SETUP, "mss_setup has not completed on this handle");
+__global__ void k_same_pattern(int N, int nnzb, const int* __restrict__ rpa,
+                               const int* __restrict__ cia, const int* __restrict__ rpb,
+                               const int* __restrict__ cib, int* __restrict__ diff) {
+  const long long n = (long long)(N + 1 > nnzb ? N + 1 : nnzb);
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    if (k <= N && rpa[k] != rpb[k]) *diff = 1;
+    if (k < nnzb && cia[k] != cib[k]) *diff = 1;
+  }
 }
+
+// New values on the set-up's pattern (Newton-loop reuse, Sec. 2.5): the
+// pattern check, then the numeric set-up on the kept symbolic one (pattern,
+// diagonal positions, last-stage ordering and factor pattern); with
+// MSS_REUSE_COARSENING the AMG levels also keep their C/F splits.
+void do_update(Handle& H, const mss_bsr* J, int reuse) {
+  auto t0 = std::chrono::steady_clock::now();
+  need_ready(H);
+  if (!J || !J->row_ptr || !J->col_idx || !J->vals) fail(MSS_ERR_INVALID_ARG, "null matrix");
+  if (reuse != MSS_REUSE_PATTERN && reuse != MSS_REUSE_COARSENING)
+    fail(MSS_ERR_INVALID_ARG, "reuse must be MSS_REUSE_PATTERN or MSS_REUSE_COARSENING");
+  if (J->n_rows != H.N || J->nnzb != H.nnzb)
+    fail(MSS_ERR_INVALID_ARG, "the matrix sizes differ from the set-up's");
+  Handle* h = &H;
+  {
+    DBuf<int> diff(h, 1);
+    fill_int(h, diff.p, 0, 1);
+    const long long n = std::max((long long)H.N + 1, (long long)H.nnzb);
+    unsigned g = grid_for(n, 256);
+    if (g > 4096u) g = 4096u;
+    k_same_pattern<<<g, 256, 0, h->stream>>>(H.N, H.nnzb, H.rp.p, H.ci.p, J->row_ptr, J->col_idx,
+                                             diff.p);
+    MSS_LAUNCH_CK("k_same_pattern");
+    if (read_int(h, diff.p) != 0)
+      fail(MSS_ERR_INVALID_ARG, "the pattern differs from the set-up's (call mss_setup)");
+  }
+  H.ready = false;
+  if (H.sgraph) {   // the solve graph holds pointers into the old hierarchies
+    cudaGraphExecDestroy(H.sgraph);
+    H.sgraph = nullptr;
+  }
+  std::vector<DBuf<int>> cfT, cfP;
+  if (reuse == MSS_REUSE_COARSENING) {
+    for (auto& L : H.amgT.lev) cfT.push_back(std::move(L.cf));
+    for (auto& L : H.amgP.lev) cfP.push_back(std::move(L.cf));
+  }
+  // the old hierarchies came from the workers' streams: free them there only
+  // after everything queued on the handle's stream
+  for (auto& a : H.aux)
+    if (a) order_streams(H.stream, a->stream);
+  H.amgT = Hierarchy();
+  H.amgP = Hierarchy();
+  numeric_setup(H, J->vals, false, cfT.empty() ? nullptr : &cfT, cfP.empty() ? nullptr : &cfP);
+  H.J = *J;
+  H.ready = true;
+  H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                   .count();
+}
+
 
 Hierarchy& pick(Handle& H, int which) {
   if (which == 0 && H.amgT.present()) return H.amgT;
@@ -433,6 +515,11 @@ int mss_setup(mss_handle* hh, const mss_bsr* J, int nb, mss_layout layout,
               const mss_options* opt) {
   if (!hh) return MSS_ERR_INVALID_ARG;
   return guarded(hh, [&] { do_setup(hh->h, J, nb, layout, opt); });
+}
+
+int mss_update_values(mss_handle* hh, const mss_bsr* J, int reuse) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] { do_update(hh->h, J, reuse); });
 }
 
 int mss_scale_rhs(mss_handle* hh, const double* b, double* bbar) {

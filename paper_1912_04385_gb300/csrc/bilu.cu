@@ -955,6 +955,19 @@ void bilu_setup_nb(Handle* h) {
         h->fcell.p, h->fsrc.p, h->fdp.p, h->fslo.p, h->fshi.p);
     MSS_LAUNCH_CK("k_factor_pattern");
   }
+}
+
+// Numeric part of the last stage on the symbolic set-up above (ordering,
+// strips, factor pattern): factor values and column slices from Abar, the
+// factorisation colour by colour, the in-strip upper scaling and the chain
+// blocks. Run again alone when only the values change.
+template <int NB>
+void bilu_numeric_nb(Handle* h) {
+  const int N = h->N;
+  const int nnzb = h->nnzb;
+  const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
+  const bool strips = !bjac && h->opt.ilu_order == MSS_STRIPS;
+  const int S = strips ? h->opt.ilu_strip : 1;
   {
     long long tot = (long long)nnzb * NB * NB;
     unsigned g = grid_for(tot, 256);
@@ -1092,9 +1105,34 @@ void last_stage_nb(Handle* h, const double* r, const C* xT, const C* vP, double*
 
 }  // namespace
 
+int colour_points(Handle* h, int n, const int* rp, const int* ci, uint64_t seed, int* colour) {
+  fill_int(h, colour, -1, n);
+  DBuf<int> pick(h, n), left(h, 1), maxcol(h, 1);
+  fill_int(h, maxcol.p, -1, 1);
+  int remaining = n, rounds = 0;
+  while (remaining > 0) {
+    for (int r = 0; r < 3; ++r) {   // three rounds per read-back, as for the strips
+      if (++rounds > n + 3) fail(MSS_ERR_CUDA, "colouring did not terminate");
+      k_jp_pick<<<grid_for((long long)n * 32, 128), 128, 0, h->stream>>>(n, 1, n, rp, ci, seed,
+                                                                          KEY_CELL, colour, pick.p);
+      MSS_LAUNCH_CK("k_jp_pick");
+      fill_int(h, left.p, 0, 1);
+      k_jp_commit<<<grid_for(n, 256), 256, 0, h->stream>>>(n, pick.p, colour, left.p, maxcol.p);
+      MSS_LAUNCH_CK("k_jp_commit");
+    }
+    remaining = read_int(h, left.p);
+  }
+  return read_int(h, maxcol.p) + 1;
+}
+
 void bilu_setup(Handle* h) {
   TraceScope ts(h, TR_SETUP_BILU);
-  MSS_NB_DISPATCH(h->nb, bilu_setup_nb<NB>(h));
+  MSS_NB_DISPATCH(h->nb, (bilu_setup_nb<NB>(h), bilu_numeric_nb<NB>(h)));
+}
+
+void bilu_refactor(Handle* h) {
+  TraceScope ts(h, TR_SETUP_BILU);
+  MSS_NB_DISPATCH(h->nb, bilu_numeric_nb<NB>(h));
 }
 
 void last_stage_apply(Handle* h, const double* r, const double* xT, const double* vP, double* y) {

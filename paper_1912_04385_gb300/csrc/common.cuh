@@ -107,6 +107,11 @@ struct Level {
   // mixed precision: BF16 copies of A, P, R values, FP32 D^-1 and vectors
   DBuf<__nv_bfloat16> vh, pvh, rvh;
   DBuf<float> dinvf, bf, xf, x2f, rf, df;
+  // multicolour Gauss-Seidel: points in colour-major order (ascending inside
+  // a colour) and the first position of each colour (host, ncolour + 1)
+  int ncolour = 0;
+  std::vector<int> cstart;
+  DBuf<int> mcorder;
 };
 
 struct Hierarchy {
@@ -164,6 +169,7 @@ struct Handle {
   // problem
   bool ready = false;
   int N = 0, nb = 0, nnzb = 0, p = 0, t = 1;
+  bool col_major = false;      // layout of the set-up's blocks
   mss_options opt{};
   int tb = 256;                // threads per CTA of the apply-path kernels (a multiple
                                // of 32; no result depends on it); set by the autotuner
@@ -306,9 +312,12 @@ void scale_vector(Handle* h, const double* b, double* bbar);
 void extract_subsystem(Handle* h, int var, double* out);
 
 // amg_setup.cu
-// level 0: the n0-row CSR (rp0, ci0, vals0), read on h's stream
+// level 0: the n0-row CSR (rp0, ci0, vals0), read on h's stream. frozen_cf
+// (optional): C/F splits of an earlier hierarchy of a matrix with the same
+// pattern, moved into the levels they fit instead of running PMIS.
 void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const int* ci0,
-               const double* vals0, const float* learned = nullptr);
+               const double* vals0, const float* learned = nullptr,
+               std::vector<DBuf<int>>* frozen_cf = nullptr);
 
 // amg_cycle.cu
 // The first Jacobi sweep from zero on level 0 of a hierarchy, x = omega D^-1 b,
@@ -345,7 +354,13 @@ void to_float(Handle* h, const double* in, float* out, long long n);
 void to_bf16(Handle* h, const double* in, __nv_bfloat16* out, long long n);
 
 // bilu.cu
+// Jones-Plassmann colouring of the points of a structurally symmetric CSR
+// graph (the priorities of the point-multicolour ILU order); returns the
+// number of colours
+int colour_points(Handle* h, int n, const int* rp, const int* ci, uint64_t seed, int* colour);
 void bilu_setup(Handle* h);
+// the numeric part alone (new values of Abar, same pattern and ordering)
+void bilu_refactor(Handle* h);
 // fused last stage: u = r - Abar[:,t] xT - Abar[:,p] vP (terms absent when the
 // pointer is NULL), y = xadd + M3 u where xadd puts xT at t and vP at p.
 void last_stage_apply(Handle* h, const double* r, const double* xT, const double* vP,

@@ -20,13 +20,13 @@ ERR_INVALID_ARG, ERR_SINGULAR_BLOCK, ERR_NOT_CONVERGED, ERR_BREAKDOWN = -1, -2, 
 ERR_CUDA, ERR_OOM, ERR_AMG, ERR_NOT_SETUP = -5, -6, -7, -8
 
 SCHEMES = {"cptr3": 0, "cpr": 1, "ilu0": 2}
-SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
+SMOOTHERS = {"jacobi": 0, "chebyshev": 1, "mcsgs": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 DRIVERS = {"host": 0, "graph": 1}
 FACTOR_FORMS = {"auto": 0, "warp": 1, "lanes": 2}
 
 # every exported symbol declared in include/mss.h
-EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_scale_rhs",
+EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_update_values", "mss_scale_rhs",
            "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
            "mss_residual_norm", "mss_residual_norm_noalloc", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
            "mss_bilu_num_colours", "mss_bilu_ordering", "mss_bilu_factors", "mss_probe_wait_limit", "mss_kernel_launches",
@@ -106,6 +106,7 @@ def load(path: Path | str | None = None):
     L.mss_destroy.argtypes = [P]
     L.mss_destroy.restype = None
     L.mss_setup.argtypes = [P, C.POINTER(Bsr), C.c_int, Layout, C.POINTER(Options)]
+    L.mss_update_values.argtypes = [P, C.POINTER(Bsr), C.c_int]
     L.mss_scale_rhs.argtypes = [P, P, P]
     L.mss_spmv.argtypes = [P, P, P]
     L.mss_apply.argtypes = [P, P, P]
@@ -268,6 +269,25 @@ class Solver:
         self._check(self.lib.mss_setup(self.h, C.byref(self._J), nb,
                                        Layout(p_idx, t_idx, int(col_major)), C.byref(o)),
                     "mss_setup")
+        return self
+
+    def update_values(self, vals, row_ptr=None, col_idx=None, reuse: str = "pattern"):
+        """New block values on the set-up's pattern (mss_update_values);
+        reuse "pattern" (same result as a new set-up) or "coarsening" (the
+        AMG levels keep their C/F splits). The pattern tensors default to the
+        set-up's."""
+        torch = self._torch
+        rp0, ci0, _ = self._Jt
+        rp = rp0 if row_ptr is None else row_ptr
+        ci = ci0 if col_idx is None else col_idx
+        if not vals.is_cuda or not vals.is_contiguous() or vals.dtype != torch.float64:
+            raise ValueError("vals must be a contiguous float64 CUDA tensor")
+        J = Bsr(rp.numel() - 1, ci.numel(), _ptr(rp), _ptr(ci), _ptr(vals))
+        self._check(self.lib.mss_update_values(self.h, C.byref(J),
+                                               {"pattern": 0, "coarsening": 1}[reuse]),
+                    "mss_update_values")
+        self._J = J
+        self._Jt = (rp, ci, vals)
         return self
 
     def setup_system(self, sysm, **kw):

@@ -80,7 +80,7 @@ def test_library_and_oracle_defaults_agree(lib_path):
         assert getattr(lo, lk) == getattr(oo, ok), (lk, getattr(lo, lk), getattr(oo, ok))
     for name in ("cptr3", "cpr", "ilu0"):
         assert mss.SCHEMES[name] == oracle.oracle.SCHEME[name]
-    for name in ("jacobi", "chebyshev"):
+    for name in ("jacobi", "chebyshev", "mcsgs"):
         assert mss.SMOOTHERS[name] == oracle.oracle.SMOOTHER[name]
 
 

@@ -144,3 +144,18 @@ def test_precision_option_checked(mss):
     with pytest.raises(mss.MssError) as e:
         mss.Solver().setup_system(s, precision=7)
     assert e.value.status == mss.ERR_INVALID_ARG
+
+
+def test_mixed_multicolour_gauss_seidel(mss):
+    # the multicolour Gauss-Seidel smoother in the mixed form (BF16 operators,
+    # FP32 sweeps) still reaches the FP64 tolerance
+    s = _sys(CASES[1])
+    kw = dict(scheme="cptr3", smoother="mcsgs", restart=60, amg_max_coarse=40)
+    g64 = mss.Solver().setup_system(s, **kw)
+    gmx = mss.Solver().setup_system(s, precision="mixed", **kw)
+    x64, i64 = g64.solve(_t(s.b), tol=1e-8, maxit=600)
+    xmx, imx = gmx.solve(_t(s.b), tol=1e-8, maxit=600)
+    assert i64["status"] == 0 and imx["status"] == 0, (i64, imx)
+    assert imx["rel_res_true"] <= 1e-8 and abs(imx["iters"] - i64["iters"]) <= 2
+    A = _bsr(s)
+    assert np.linalg.norm(s.b - A @ _n(xmx)) <= 1e-6 * np.linalg.norm(s.b)

@@ -280,6 +280,7 @@ def test_residual_norm_entry_point(mss, nb):
 
 @pytest.mark.parametrize("scheme,smoother,precision", [("cptr3", "jacobi", "fp64"),
                                                        ("cptr3", "chebyshev", "fp64"),
+                                                       ("cptr3", "mcsgs", "fp64"),
                                                        ("cpr", "jacobi", "fp64")])
 def test_larger_hierarchy(mss, scheme, smoother, precision):
     # a 6,144-cell system: several AMG levels above 4,096 rows, stage and
@@ -337,3 +338,31 @@ def test_smoothing_counts(mss, nu):
     xg, ig = gg.solve(_t(s.b), tol=1e-8, maxit=400)
     assert ih["status"] == 0 and ih["iters"] == ig["iters"]
     assert torch.equal(xh, xg)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("nu", [(2, 2), (1, 1), (0, 1)])
+def test_multicolour_gauss_seidel(mss, case, nu):
+    # the paper's AMG smoother (symmetric Gauss-Seidel, Sec. 5.1) in
+    # multicolour form: both AMG stages and the whole preconditioner against
+    # the oracle's smoother = 3, the FGMRES iteration bar, graph = host loop
+    s = _sys(CASES[case])
+    kw = dict(scheme="cptr3", smoother="mcsgs", amg_max_coarse=40, nu_pre=nu[0],
+              nu_post=nu[1], restart=100)
+    g = _gpu(mss, s, **kw)
+    o = _orc(s, scheme="cptr3", smoother="mcsgs", max_coarse=40, nu_pre=nu[0], nu_post=nu[1],
+             restart=100)
+    r = np.random.default_rng(case).standard_normal(s.n_cells * s.nb)
+    rt = _t(r)
+    for which in (0, 1):
+        assert _rel(_n(g.stage(which, rt)), o.stage(which, r)) < APPLY_TOL, which
+    assert _rel(_n(g.apply(rt)), o.apply(r)) < APPLY_TOL
+    if nu != (2, 2):
+        return
+    xo, io = o.fgmres(o.scale_rhs(s.b), tol=1e-8, maxit=400, restart=100)
+    xh, ih = g.solve(_t(s.b), tol=1e-8, maxit=400)
+    assert io["status"] == 0 and ih["status"] == 0
+    assert abs(ih["iters"] - io["iters"]) <= 1, (ih["iters"], io["iters"])
+    gg = _gpu(mss, s, driver="graph", **kw)
+    xg, ig = gg.solve(_t(s.b), tol=1e-8, maxit=400)
+    assert ig["iters"] == ih["iters"] and torch.equal(xg, xh)

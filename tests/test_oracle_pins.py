@@ -734,3 +734,59 @@ def test_cptr3_beats_cpr_on_unit_peclet():
         assert info["status"] == 0
         its[scheme] = info["iters"]
     assert its["cptr3"] < 0.6 * its["cpr"], its
+
+
+# ---- Newton-loop reuse (Sec. 2.5) -------------------------------------------
+def _newton_pair():
+    # two Jacobians on one grid (one pattern): a later time step with other
+    # coefficients (Pe) and other couplings (seed)
+    s1 = sy.make_system(30, 22, 5, pe=10.0, sigma=2.0, band=True, seed=3)
+    s2 = sy.make_system(30, 22, 5, pe=40.0, sigma=2.0, band=True, seed=4)
+    assert np.array_equal(s1.row_ptr, s2.row_ptr) and np.array_equal(s1.col_idx, s2.col_idx)
+    return s1, s2
+
+
+def test_update_without_reuse_is_a_new_setup():
+    s1, s2 = _newton_pair()
+    o1 = oracle.OracleSolver.from_system(s1, max_coarse=30)
+    u = o1.updated(s2.vals, reuse=0)
+    o2 = oracle.OracleSolver.from_system(s2, max_coarse=30)
+    assert np.array_equal(u.scaled()[0], o2.scaled()[0])
+    for which in (0, 1):
+        for a, b in zip(u.amg_levels(which), o2.amg_levels(which)):
+            assert all(np.array_equal(x, y) for x, y in zip(a.A, b.A))
+    r = np.random.default_rng(1).standard_normal(s2.n_cells * s2.nb)
+    assert np.array_equal(u.apply(r), o2.apply(r))
+
+
+def test_update_with_frozen_coarsening():
+    s1, s2 = _newton_pair()
+    o1 = oracle.OracleSolver.from_system(s1, max_coarse=30)
+    # unchanged values: PMIS would pick the same splits, so nothing changes
+    same = o1.updated(s1.vals, reuse=1)
+    r = np.random.default_rng(2).standard_normal(s1.n_cells * s1.nb)
+    assert np.array_equal(same.apply(r), o1.apply(r))
+    u = o1.updated(s2.vals, reuse=1)
+    fresh = oracle.OracleSolver.from_system(s2, max_coarse=30)
+    for which in (0, 1):
+        old, new, ref = o1.amg_levels(which), u.amg_levels(which), fresh.amg_levels(which)
+        assert len(new) == len(old)
+        # level 0 is the new subsystem (B_PP or C_TT of the new scaled matrix)
+        assert all(np.array_equal(x, y) for x, y in zip(new[0].A, ref[0].A))
+        assert any(not np.array_equal(a.cf, b.cf) for a, b in zip(new[:-1], ref[:-1]))
+        for l in range(len(new) - 1):
+            assert np.array_equal(new[l].cf, old[l].cf)
+            # interpolation: the classical formula on the kept split, through
+            # the stand-alone strength + interpolation entry point
+            cf, _, P = oracle.interp_only(*new[l].A, cf=old[l].cf)
+            assert all(np.array_equal(x, y) for x, y in zip(new[l].P, P))
+            # Galerkin product on the kept coarse grid
+            nc = int(cf.sum())
+            Pd = csr_dense(*new[l].P, ncols=nc)
+            Ad = csr_dense(*new[l].A)
+            Ac = csr_dense(*new[l + 1].A, ncols=nc)
+            assert np.allclose(Ac, Pd.T @ Ad @ Pd, rtol=0, atol=1e-12 * np.abs(Ac).max())
+    # still a convergent preconditioner for the new matrix
+    _, info = u.fgmres(u.scale_rhs(s2.b), tol=1e-8, maxit=300, restart=50)
+    _, ref_info = fresh.fgmres(fresh.scale_rhs(s2.b), tol=1e-8, maxit=300, restart=50)
+    assert info["status"] == 0 and info["iters"] <= ref_info["iters"] + 5
