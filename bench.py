@@ -58,6 +58,8 @@ def args_():
                     help="systems in the batched-solve comparison (0: skip)")
     ap.add_argument("--batch-lanes", type=int, default=8)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-condense", action="store_true",
+                    help="skip the static-condensation leg")
     ap.add_argument("--no-newton", action="store_true",
                     help="skip the Newton-loop reuse leg")
     ap.add_argument("--no-smoothers", action="store_true",
@@ -315,6 +317,8 @@ def run_ours(a, rank, world, dist):
         out["mixed"] = mixed_leg(a, dev, solver, torch, stream)
         if a.mixed_n > 0:
             out["mixed_config"] = mixed_config_leg(a, solver, torch, stream)
+    if not a.no_condense:
+        out["condense"] = condense_leg(a, torch)
     if not a.no_newton:
         out["newton"] = newton_leg(a, dev, solver, torch)
     if not a.no_smoothers:
@@ -469,6 +473,60 @@ def newton_leg(a, dev, solver, torch, pes=(12.0, 14.4, 17.28)):
     out["sequence"] = (f"the {a.n}x{a.n} Pe=10 system, then Pe " +
                        ", ".join(f"{p:g}" for p in pes) + " on the same grid; host ms of the "
                        "set-up call")
+    return out
+
+
+def condense_leg(a, torch, n1=6, n2=4, reps=10):
+    """Static condensation (Sec. 3) of a global system on the benchmark grid
+    with n1 primary and n2 secondary unknowns per cell: traced kernel times of
+    mss_condense and mss_recover and their algorithmic bytes, against HBM."""
+    from paper_1912_04385_gb300 import mss
+    from paper_1912_04385_gb300 import synthetic as sy
+    f = sy.make_full_system(a.n, a.n, n1, n2, seed=0, sigma=2.0, band=True, pe=10.0,
+                            j21_neighbors=True)
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(f, k))).cuda().reshape(-1)
+         for k in ("row_ptr", "col_idx", "j11", "j21", "j12", "j22", "r1", "r2")}
+    fd = dict(tensors=t, n1=n1, n2=n2)
+    N, nnzb = f.n_cells, f.nnzb
+    del f
+    g = mss.Solver()
+    d1 = torch.ones(N * n1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        g.condense(fd, t["r1"], t["r2"])
+        g.recover(fd, t["r2"], d1)
+    g.trace(True)
+    g.trace_read(reset=True)
+    for _ in range(reps):
+        g.condense(fd, t["r1"], t["r2"])
+        g.recover(fd, t["r2"], d1)
+    tr = g.trace_read(reset=True)
+    g.trace(False)
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else {"hbm_gbs": 6800.0}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # algorithmic bytes: every input and output once
+    bc = (4 * (N + 1) + 8 * nnzb * (n1 * n1 + n2 * n1) + 8 * N * (n1 * n2 + n2 * n2)
+          + 8 * N * (n1 + n2) + 8 * nnzb * n1 * n1 + 8 * N * n1)
+    br = (4 * (N + 1) + 4 * nnzb + 8 * nnzb * n2 * n1 + 8 * N * n2 * n2 + 8 * N * n2
+          + 8 * N * n1 + 8 * N * n2)
+    # algorithmic FP64 flops (2 per multiply-add): Gauss-Jordan of J22 on
+    # [J22 | I] (2 n2^3 FMA), T = J12 J22^-1, b, and T J21 per block
+    fc = 2 * (N * (2 * n2 ** 3 + n1 * n2 * n2 + n1 * n2) + nnzb * n1 * n1 * n2)
+    fr = 2 * (nnzb * n2 * n1 + N * n2 ** 3)
+    out = {"workload": f"{a.n}x{a.n} cells, n1={n1} primary + n2={n2} secondary unknowns, "
+                       f"J21 on the cell graph", "hbm_peak_gbs": hbm,
+           "fp64_peak_tflops": round(FP64_PEAK_TFLOPS, 4)}
+    for name, by, fl in (("condense", bc, fc), ("recover", br, fr)):
+        nl, ms = tr[name]
+        per = ms / max(nl, 1)
+        gbs = by / (per * 1e-3) / 1e9
+        t_hbm = by / (hbm * 1e9) * 1e3
+        t_alu = fl / (FP64_PEAK_TFLOPS * 1e12) * 1e3
+        out[name] = {"ms": round(per, 4), "alg_bytes": by, "alg_flops": fl, "gbs": round(gbs, 1),
+                     "hbm_frac": round(gbs / hbm, 4),
+                     "bound": "alu" if t_alu > t_hbm else "hbm",
+                     "t_roofline_ms": round(max(t_hbm, t_alu), 4),
+                     "frac": round(max(t_hbm, t_alu) / per, 4), "launches": nl}
     return out
 
 

@@ -295,6 +295,46 @@ int mss_residual_norm(mss_handle* h, const mss_bsr* J, int nb, const double* b, 
 int mss_residual_norm_noalloc(mss_handle* h, const mss_bsr* J, int nb, const double* b,
                               const double* x, double* norms);
 
+/* ---- static condensation (Sec. 3, Eqs. global and reduced) ---------------
+ * The simulator's global system [J11 J12; J21 J22] [d1; d2] = -[r1; r2] has
+ * n1 primary and n2 secondary unknowns per cell, the secondary ones coupled
+ * only inside their cell, so J12 and J22 are one block per cell. Eliminating
+ * them gives the primary system A d1 = b that mss_setup takes:
+ *   A = J11 - J12 J22^{-1} J21,  b = -r1 + J12 J22^{-1} r2,
+ * with the cell graph's block pattern; afterwards the secondary unknowns are
+ *   d2 = J22^{-1} (-r2 - J21 d1).
+ * J22 is inverted per cell without pivoting (Sec. 3 aligns the secondary
+ * equations with unknowns so that its pivots are nonzero). */
+#define MSS_CONDENSE_MAX_UNKNOWNS 16
+typedef struct {
+  int32_t n_rows;           /* cells N */
+  int32_t nnzb;             /* blocks of the cell graph */
+  const int32_t* row_ptr;   /* device, N + 1 (as mss_bsr) */
+  const int32_t* col_idx;   /* device, nnzb */
+  int32_t n1;               /* primary unknowns per cell, 1..16 */
+  int32_t n2;               /* secondary unknowns per cell, 0..16 */
+  const double* j11;        /* device, nnzb blocks n1 x n1, row-major */
+  const double* j21;        /* device, nnzb blocks n2 x n1 (secondary rows, primary columns) */
+  const double* j12;        /* device, N blocks n1 x n2 (cell-local) */
+  const double* j22;        /* device, N blocks n2 x n2 (cell-local) */
+} mss_full;
+
+/* a (device, nnzb * n1 * n1) receives A's blocks on J's pattern, b (device,
+ * N * n1) the reduced right-hand side; r1 (N * n1) and r2 (N * n2, may be
+ * NULL when n2 = 0) are device vectors, cell-interleaved. One pass, one warp
+ * per cell, on the handle's stream; the call synchronises it to report
+ * errors. Errors: INVALID_ARG (sizes, null pointers, a row_ptr entry outside
+ * [0, nnzb]), SINGULAR_BLOCK (a J22 block needs pivoting), OOM, CUDA. */
+int mss_condense(mss_handle* h, const mss_full* J, const double* r1, const double* r2,
+                 double* a, double* b);
+
+/* d2 (device, N * n2) = J22^{-1} (-r2 - J21 d1) per cell, for the primary
+ * solution d1 (device, N * n1). Synchronises the handle's stream. Errors:
+ * as mss_condense, and INVALID_ARG for a col_idx entry outside [0, N) or a
+ * row of more than 64 blocks. */
+int mss_recover(mss_handle* h, const mss_full* J, const double* r2, const double* d1,
+                double* d2);
+
 /* ---- introspection (tests) --------------------------------------------- */
 /* Copy the scaled blocks Abar (device, nnzb*nb*nb, row-major) into `abar`
  * (device, caller-owned). */
@@ -350,7 +390,8 @@ long long mss_kernel_launches(int reset);
  * every Arnoldi orthogonalisation step (4), the set-up phases: scaling
  * (5), the span in which the two AMG hierarchies are built on worker streams
  * while the last stage is ordered and factorised (6), that ordering and
- * factorisation alone (7), and every whole preconditioner application (8).
+ * factorisation alone (7), every whole preconditioner application (8), and
+ * the kernels of mss_condense (9) and mss_recover (10).
  * Solves run with MSS_DRIVER_GRAPH record no events (a graph holds none). */
 int mss_trace_enable(mss_handle* h, int enable);
 

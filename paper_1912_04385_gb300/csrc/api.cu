@@ -636,6 +636,18 @@ int mss_solve_host(mss_handle* hh, const mss_bsr* Jh, int nb, mss_layout layout,
   return st;
 }
 
+int mss_condense(mss_handle* hh, const mss_full* J, const double* r1, const double* r2,
+                 double* a, double* b) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] { condense(&hh->h, J, r1, r2, a, b); });
+}
+
+int mss_recover(mss_handle* hh, const mss_full* J, const double* r2, const double* d1,
+                double* d2) {
+  if (!hh) return MSS_ERR_INVALID_ARG;
+  return guarded(hh, [&] { recover(&hh->h, J, r2, d1, d2); });
+}
+
 int mss_residual_norm(mss_handle* hh, const mss_bsr* J, int nb, const double* b, const double* x,
                       double* norms) {
   if (!hh) return MSS_ERR_INVALID_ARG;

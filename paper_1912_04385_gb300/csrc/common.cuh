@@ -46,6 +46,8 @@ enum TraceKind {
   TR_SETUP_AMG,     // one AMG hierarchy set-up
   TR_SETUP_BILU,    // colouring, ordering and factorisation
   TR_APPLY,         // one whole preconditioner application
+  TR_CONDENSE,      // static condensation kernel
+  TR_RECOVER,       // recovery of the secondary unknowns
   TR_KINDS
 };
 
@@ -384,6 +386,11 @@ void gnn_set_vectors(GnnGraph* g, int K, const double* starts, int nu, double om
 double gnn_loss_grad(GnnGraph* g, const float* params, float* grad);
 void gnn_adam(Handle* h, float* params, float* m1, float* m2, const float* grad, int step,
               float lr, float b1, float b2, float eps);
+
+// condense.cu: static condensation and recovery of the secondary unknowns
+void condense(Handle* h, const mss_full* J, const double* r1, const double* r2, double* a,
+              double* b);
+void recover(Handle* h, const mss_full* J, const double* r2, const double* d1, double* d2);
 
 // residual.cu
 void check_residual_args(const mss_bsr* J, int nb, const double* b, const double* x,

@@ -43,7 +43,8 @@ static cudaEvent_t take_event(Handle* h) {
 // no cost without an attached tool)
 static const char* const kTraceNames[TR_KINDS] = {
     "mss.spmv", "mss.bilu_fwd", "mss.bilu_bwd", "mss.vcycle", "mss.ortho",
-    "mss.setup_scale", "mss.setup_amg", "mss.setup_bilu", "mss.apply"};
+    "mss.setup_scale", "mss.setup_amg", "mss.setup_bilu", "mss.apply", "mss.condense",
+    "mss.recover"};
 
 TraceScope::TraceScope(Handle* hh, int k) : h(hh), kind(k) {
   if (h->capturing) return;   // no event nodes (and no host ranges) inside a solve graph

@@ -28,7 +28,7 @@ FACTOR_FORMS = {"auto": 0, "warp": 1, "lanes": 2}
 # every exported symbol declared in include/mss.h
 EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss_update_values", "mss_scale_rhs",
            "mss_spmv", "mss_apply", "mss_stage_apply", "mss_fgmres_solve", "mss_solve_host",
-           "mss_residual_norm", "mss_residual_norm_noalloc", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
+           "mss_residual_norm", "mss_residual_norm_noalloc", "mss_condense", "mss_recover", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
            "mss_bilu_num_colours", "mss_bilu_ordering", "mss_bilu_factors", "mss_probe_wait_limit", "mss_kernel_launches",
            "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error",
            "mss_batch_create", "mss_batch_destroy", "mss_batch_solve", "mss_batch_tuned",
@@ -37,7 +37,8 @@ EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss
            "mss_gnn_adam", "mss_gnn_last_error"]
 
 TRACE_KINDS = {"spmv": 0, "bilu_fwd": 1, "bilu_bwd": 2, "vcycle": 3, "ortho": 4,
-               "setup_scale": 5, "setup_amg": 6, "setup_bilu": 7, "apply": 8}
+               "setup_scale": 5, "setup_amg": 6, "setup_bilu": 7, "apply": 8,
+               "condense": 9, "recover": 10}
 
 
 class Options(C.Structure):
@@ -66,6 +67,13 @@ class Result(C.Structure):
 class Bsr(C.Structure):
     _fields_ = [("n_rows", C.c_int32), ("nnzb", C.c_int32), ("row_ptr", C.c_void_p),
                 ("col_idx", C.c_void_p), ("vals", C.c_void_p)]
+
+
+class Full(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("nnzb", C.c_int32), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("n1", C.c_int32), ("n2", C.c_int32),
+                ("j11", C.c_void_p), ("j21", C.c_void_p), ("j12", C.c_void_p),
+                ("j22", C.c_void_p)]
 
 
 class Layout(C.Structure):
@@ -116,6 +124,8 @@ def load(path: Path | str | None = None):
     L.mss_solve_host.argtypes = [P, C.POINTER(Bsr), C.c_int, Layout, C.POINTER(Options), P, P,
                                  C.c_double, C.c_int, C.POINTER(Result)]
     L.mss_residual_norm.argtypes = [P, C.POINTER(Bsr), C.c_int, P, P, P]
+    L.mss_condense.argtypes = [P, C.POINTER(Full), P, P, P, P]
+    L.mss_recover.argtypes = [P, C.POINTER(Full), P, P, P]
     L.mss_residual_norm_noalloc.argtypes = [P, C.POINTER(Bsr), C.c_int, P, P, P]
     L.mss_get_scaled.argtypes = [P, P]
     L.mss_amg_num_levels.argtypes = [P, C.c_int]
@@ -390,6 +400,37 @@ class Solver:
                                                _ptr(out)), "mss_residual_norm")
         r = out.cpu()
         return float(r[0]), float(r[1])
+
+    # ---- static condensation (Sec. 3) --------------------------------------
+    @staticmethod
+    def _full(f):
+        """An mss_full over CUDA tensors (row_ptr, col_idx, j11, j21, j12, j22
+        in a dict, n1, n2); the tensors must stay alive during the call."""
+        t = f["tensors"]
+        z = lambda k: _ptr(t[k]) if t.get(k) is not None and t[k].numel() else None
+        return Full(t["row_ptr"].numel() - 1, t["col_idx"].numel(), _ptr(t["row_ptr"]),
+                    _ptr(t["col_idx"]), f["n1"], f["n2"], _ptr(t["j11"]), z("j21"), z("j12"),
+                    z("j22"))
+
+    def condense(self, f, r1, r2):
+        """(A blocks, b) of Eq. reduced for the full system f (see _full)."""
+        torch = self._torch
+        t = f["tensors"]
+        a = torch.empty_like(t["j11"])
+        b = torch.empty(r1.numel(), dtype=torch.float64, device="cuda")
+        J = self._full(f)
+        self._check(self.lib.mss_condense(self.h, C.byref(J), _ptr(r1),
+                                          _ptr(r2) if r2 is not None and r2.numel() else None,
+                                          _ptr(a), _ptr(b)), "mss_condense")
+        return a, b
+
+    def recover(self, f, r2, d1):
+        torch = self._torch
+        d2 = torch.empty(max(r2.numel(), 1), dtype=torch.float64, device="cuda")
+        J = self._full(f)
+        self._check(self.lib.mss_recover(self.h, C.byref(J), _ptr(r2), _ptr(d1), _ptr(d2)),
+                    "mss_recover")
+        return d2[:r2.numel()]
 
     # ---- introspection ----------------------------------------------------
     def scaled(self):

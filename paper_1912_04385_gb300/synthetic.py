@@ -42,8 +42,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["BlockSystem", "make_system", "lognormal_field", "tiny_plain",
-           "plain_at_scale", "poisson_csr"]
+__all__ = ["BlockSystem", "FullSystem", "make_system", "make_full_system", "lognormal_field",
+           "tiny_plain", "plain_at_scale", "poisson_csr"]
 
 
 @dataclass
@@ -237,10 +237,87 @@ def make_system(nx: int, ny: int, nb: int = 4, *, pe: float = 1.0,
     b = rng.standard_normal(N * nb)
     meta = dict(pe=pe, sigma=sigma, corr_len=corr_len, band=band, seed=seed,
                 kappa=kappa, velocity=velocity, family=family,
-                couple_neighbors=couple_neighbors, band_cells=int(band_cells.size))
+                couple_neighbors=couple_neighbors, band_cells=int(band_cells.size),
+                local_diag=local)
     return BlockSystem(row_ptr.astype(np.int32), col_idx.astype(np.int32),
                        np.ascontiguousarray(vals), b, nx, ny, nb, p_idx, t_idx,
                        meta)
+
+
+@dataclass
+class FullSystem:
+    """The global system J delta = -r of Sec. 3 (Eq. global) before static
+    condensation: per cell n1 primary and n2 secondary unknowns, the
+    secondary ones coupled only inside their cell. J11 (primary equations,
+    primary unknowns) and J21 (secondary equations, primary unknowns) have
+    the cell graph's block pattern; J12 and J22 are one block per cell.
+    Blocks row-major; vectors cell-interleaved."""
+    row_ptr: np.ndarray      # int32 [N + 1]
+    col_idx: np.ndarray      # int32 [nnzb]
+    j11: np.ndarray          # float64 [nnzb, n1, n1]
+    j21: np.ndarray          # float64 [nnzb, n2, n1]
+    j12: np.ndarray          # float64 [N, n1, n2]
+    j22: np.ndarray          # float64 [N, n2, n2]
+    r1: np.ndarray           # float64 [N * n1]
+    r2: np.ndarray           # float64 [N * n2]
+    nx: int
+    ny: int
+    n1: int
+    n2: int
+    p_idx: int = 0
+    t_idx: int = 1
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_cells(self) -> int:
+        return self.row_ptr.shape[0] - 1
+
+    @property
+    def nnzb(self) -> int:
+        return int(self.col_idx.shape[0])
+
+
+def make_full_system(nx: int, ny: int, n1: int = 6, n2: int = 4, *, seed: int = 0,
+                     coupling: float = 0.1, j21_neighbors: bool = False,
+                     **kw) -> FullSystem:
+    """A global system with secondary unknowns around a ``make_system``
+    primary block (J11 = its blocks, r1 = minus its right-hand side; ``kw``
+    goes to make_system). The secondary rows stand in for the local
+    constraints of Sec. 2.3 (fugacity, phase constraints), aligned with their
+    unknowns so J22 needs no pivoting (Sec. 3):
+    * J22: diagonal U(1, 2), off-diagonal U(-coupling, coupling) times the
+      row's diagonal (diagonally dominant for n2 <= 10);
+    * J12: U(-coupling, coupling) times the cell-local diagonal term of the
+      primary row (as make_system's intra-cell couplings);
+    * J21: diagonal block U(-0.5, 0.5) times the secondary row's diagonal;
+      with ``j21_neighbors`` the neighbour blocks U(-coupling/5,
+      coupling/5) times it, else zero;
+    * r2: standard normal.
+    Draws come from a second stream PCG64([seed, 1]) in this order, so the
+    primary block is make_system's exactly."""
+    if n1 < 2 or n2 < 0:
+        raise ValueError("n1 >= 2 and n2 >= 0 required")
+    base = make_system(nx, ny, n1, seed=seed, **kw)
+    rng = np.random.Generator(np.random.PCG64([seed, 1]))
+    N, nnzb = base.n_cells, base.nnzb
+    d22 = rng.uniform(1.0, 2.0, size=(N, n2))
+    j22 = rng.uniform(-coupling, coupling, size=(N, n2, n2)) * d22[:, :, None]
+    j22[:, np.arange(n2), np.arange(n2)] = d22
+    local = base.meta["local_diag"]
+    j12 = rng.uniform(-coupling, coupling, size=(N, n1, n2)) * local[:, :, None]
+    rows = np.repeat(np.arange(N), np.diff(base.row_ptr))
+    diag = base.col_idx == rows
+    j21 = np.zeros((nnzb, n2, n1))
+    j21[diag] = rng.uniform(-0.5, 0.5, size=(N, n2, n1)) * d22[:, :, None]
+    if j21_neighbors:
+        off = ~diag
+        j21[off] = (rng.uniform(-coupling / 5, coupling / 5, size=(int(off.sum()), n2, n1))
+                    * d22[rows[off]][:, :, None])
+    r2 = rng.standard_normal(N * n2)
+    meta = dict(base.meta, n2=n2, j21_neighbors=j21_neighbors)
+    return FullSystem(base.row_ptr, base.col_idx, base.vals, np.ascontiguousarray(j21),
+                      np.ascontiguousarray(j12), np.ascontiguousarray(j22), -base.b, r2,
+                      nx, ny, n1, n2, base.p_idx, base.t_idx, meta)
 
 
 def tiny_plain(seed: int = 0, pe: float = 1.0, n: int = 32, nb: int = 4) -> BlockSystem:
