@@ -49,7 +49,8 @@
 /* options                                                                  */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  int scheme;        /* 0 CPTR3 (three stages), 1 CPR (two stages), 2 ILU only */
+  int scheme;        /* 0 CPTR3 (three stages), 1 CPR (two stages), 2 ILU only,
+                        3 CPTR (two stages, system AMG on the 2 x 2 block B_ee) */
   int stage_order;   /* 0: T stage then P stage (Alg. 2 order); 1: P then T */
   int exact_sub;     /* 1: M_TT = C_TT^-1 and M_PP = B_PP^-1 by dense LU */
   int stage3;        /* 0: block ILU(0) of the scaled matrix, 1: block Jacobi */
@@ -327,6 +328,8 @@ static int csr_diag_pos(const csr_t* a, int i) {
  *            entries of the once-scaled block N1^{-1} D (the B blocks).
  *   W = N2^{-1} N1^{-1}.
  * CPR (Eq. CPR): h = all unknowns but P; row P <- row P - D_Ph D_hh^{-1} (rows h).
+ * CPTR (Eq. CPTR1): e = {P, T}; rows e <- rows e - D_es D_ss^{-1} (rows s), which
+ *   is N1 of CPTR3 alone.
  * ILU only: W = I (no decoupling for the single-stage baseline).
  * Parity: pinned (tests check the zero pattern of W D, det W = 1 and the
  * invariance of the solution).
@@ -370,6 +373,10 @@ static int build_scaling(int nb, int p, int t, int scheme, const double* D, doub
       n1[p * nb + s[b]] = -wp;
       n1[t * nb + s[b]] = -wt;
     }
+  }
+  if (scheme == 3) {   /* CPTR (Eq. CPTR1): the lower block factor of [s | e] only */
+    for (int k = 0; k < nb * nb; ++k) W[k] = n1[k];
+    return OR_OK;
   }
   /* once-scaled entries B_PP and B_Tp of N1^{-1} D */
   double bpp = 0.0, btp = 0.0;
@@ -418,6 +425,7 @@ typedef struct {
   int ncolour;             /* multicolour Gauss-Seidel: colours of A's graph */
   int* cstart;             /* colour c holds mcorder[cstart[c] .. cstart[c + 1]) */
   int* mcorder;            /* points in colour-major order, ascending inside a colour */
+  double* dinv2;           /* system AMG: inverse of each point's 2 x 2 diagonal block */
 } level_t;
 
 typedef struct {
@@ -426,6 +434,7 @@ typedef struct {
   double* lu;
   int* piv;
   or_opts o;
+  int bs;                  /* unknowns per point: 1 scalar AMG, 2 system AMG (CPTR) */
 } amg_t;
 
 /* Strength of connection, sign-aware classical rule (reading): j is strong
@@ -664,7 +673,7 @@ static void level_free(level_t* L) {
   csr_free(&L->A); csr_free(&L->P); csr_free(&L->R);
   free(L->strong); free(L->cf); free(L->cidx); free(L->dinv);
   free(L->b); free(L->x); free(L->r); free(L->t1); free(L->t2);
-  free(L->cstart); free(L->mcorder);
+  free(L->cstart); free(L->mcorder); free(L->dinv2);
   memset(L, 0, sizeof(*L));
 }
 
@@ -804,6 +813,208 @@ fail:
 }
 
 /* ------------------------------------------------------------------------ */
+/* system AMG for the 2 x 2 block B_ee of CPTR (Sec. 4.2, Eq. CPTRM1)         */
+/* ------------------------------------------------------------------------ */
+/* The paper names system AMG (SAMG, BoomerAMG) for B_ee without fixing one.
+ * Reading: nodal coarsening with unknown-wise interpolation. A level is a
+ * matrix of 2 x 2 blocks on a point graph (unknowns [P, T] of a point
+ * interleaved in the scalar form). Per level:
+ *   - norm matrix: |B_ij|_F off the diagonal with a negative sign, |B_ii|_F
+ *     on it (Frobenius norms summed in the order b00, b01, b10, b11);
+ *   - strength on it (the scalar rule) and PMIS -> one C/F split of points;
+ *   - for each unknown k, classical interpolation of the scalar matrix of
+ *     the (k, k) entries with its own strength and the common split;
+ *   - P interleaved: P[2i+k][2J+k] = w^k_iJ (no cross-unknown weights);
+ *   - A_c = P^T A P on the scalar interleaved form (coupled P-T entries
+ *     kept), read back as 2 x 2 blocks on the union of each point's columns
+ *     (absent entries zero).
+ * The smoother is damped 2 x 2 block Jacobi, the coarsest level a dense
+ * solve. Parity: pinned (2 x 2 block-diagonal systems reduce to two
+ * decoupled scalar hierarchies; Galerkin products against dense P^T A P). */
+static int bcsr2_to_scalar(int np, const int* rp, const int* ci, const double* bv, csr_t* S) {
+  if (csr_alloc(S, 2 * np, 2 * np, 4 * rp[np]) != OR_OK) return OR_ERR_MEM;
+  int q = 0;
+  S->rp[0] = 0;
+  for (int i = 0; i < np; ++i)
+    for (int k = 0; k < 2; ++k) {
+      for (int e = rp[i]; e < rp[i + 1]; ++e)
+        for (int l = 0; l < 2; ++l) {
+          S->ci[q] = 2 * ci[e] + l;
+          S->v[q] = bv[(size_t)4 * e + 2 * k + l];
+          ++q;
+        }
+      S->rp[2 * i + k + 1] = q;
+    }
+  return OR_OK;
+}
+
+/* 2 x 2 blocks of a scalar interleaved matrix: block row I holds every point
+ * J with an entry in row 2I or 2I+1; absent entries are zero. */
+static int scalar_to_bcsr2(const csr_t* S, int** rp_out, int** ci_out, double** bv_out) {
+  int np = S->n / 2;
+  int* rp = (int*)malloc(sizeof(int) * ((size_t)np + 1));
+  if (!rp) return OR_ERR_MEM;
+  rp[0] = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    int* ci = pass ? *ci_out : NULL;
+    double* bv = pass ? *bv_out : NULL;
+    for (int I = 0; I < np; ++I) {
+      int a = S->rp[2 * I], ae = S->rp[2 * I + 1];
+      int b = S->rp[2 * I + 1], be = S->rp[2 * I + 2];
+      int q = pass ? rp[I] : 0, last = -1;
+      while (a < ae || b < be) {
+        int ja = a < ae ? S->ci[a] / 2 : 0x7fffffff;
+        int jb = b < be ? S->ci[b] / 2 : 0x7fffffff;
+        int j = ja < jb ? ja : jb;
+        if (j != last) {
+          if (pass) {
+            ci[q] = j;
+            for (int t = 0; t < 4; ++t) bv[(size_t)4 * q + t] = 0.0;
+          }
+          ++q;
+          last = j;
+        }
+        if (ja == j) {
+          if (pass) bv[(size_t)4 * (q - 1) + (S->ci[a] & 1)] = S->v[a];
+          ++a;
+        } else {
+          if (pass) bv[(size_t)4 * (q - 1) + 2 + (S->ci[b] & 1)] = S->v[b];
+          ++b;
+        }
+      }
+      if (!pass) rp[I + 1] = rp[I] + q;
+    }
+    if (!pass) {
+      *ci_out = (int*)malloc(sizeof(int) * (size_t)(rp[np] > 0 ? rp[np] : 1));
+      *bv_out = (double*)malloc(sizeof(double) * 4 * (size_t)(rp[np] > 0 ? rp[np] : 1));
+      if (!*ci_out || !*bv_out) return OR_ERR_MEM;
+    }
+  }
+  *rp_out = rp;
+  return OR_OK;
+}
+
+static int amg_build_system(int np0, const int* rp0, const int* ci0, const double* bv0,
+                            const or_opts* o, amg_t** out) {
+  amg_t* h = (amg_t*)calloc(1, sizeof(amg_t));
+  if (!h) return OR_ERR_MEM;
+  h->o = *o;
+  h->bs = 2;
+  int st = OR_OK, np = np0;
+  int* brp = (int*)malloc(sizeof(int) * ((size_t)np + 1));
+  int* bci = (int*)malloc(sizeof(int) * (size_t)(rp0[np] > 0 ? rp0[np] : 1));
+  double* bv = (double*)malloc(sizeof(double) * 4 * (size_t)(rp0[np] > 0 ? rp0[np] : 1));
+  int *cfp = NULL, *cidx = NULL;
+  unsigned char *sn = NULL, *sk = NULL;
+  csr_t Nm = {0}, Ak = {0}, Pk[2] = {{0}, {0}};
+  if (!brp || !bci || !bv) { st = OR_ERR_MEM; goto fail; }
+  memcpy(brp, rp0, sizeof(int) * ((size_t)np + 1));
+  memcpy(bci, ci0, sizeof(int) * (size_t)rp0[np]);
+  memcpy(bv, bv0, sizeof(double) * 4 * (size_t)rp0[np]);
+  h->nlev = 1;
+  for (int l = 0;; ++l) {
+    level_t* L = &h->lev[l];
+    int nnzb = brp[np];
+    if ((st = bcsr2_to_scalar(np, brp, bci, bv, &L->A)) != OR_OK) goto fail;
+    if ((st = level_vectors(L)) != OR_OK) goto fail;
+    L->dinv2 = (double*)malloc(sizeof(double) * 4 * (size_t)(np > 0 ? np : 1));
+    if (!L->dinv2) { st = OR_ERR_MEM; goto fail; }
+    for (int i = 0; i < np; ++i)
+      for (int e = brp[i]; e < brp[i + 1]; ++e)
+        if (bci[e] == i && (st = gj_inverse_nopiv(2, &bv[(size_t)4 * e], &L->dinv2[(size_t)4 * i])) != OR_OK)
+          goto fail;
+    if (np <= o->max_coarse || l + 1 >= o->max_levels || l + 1 >= OR_MAXLEV) break;
+    /* norm matrix, strength, PMIS on points */
+    if (csr_alloc(&Nm, np, np, nnzb) != OR_OK) { st = OR_ERR_MEM; goto fail; }
+    memcpy(Nm.rp, brp, sizeof(int) * ((size_t)np + 1));
+    memcpy(Nm.ci, bci, sizeof(int) * (size_t)nnzb);
+    for (int i = 0; i < np; ++i)
+      for (int e = brp[i]; e < brp[i + 1]; ++e) {
+        const double* q = &bv[(size_t)4 * e];
+        double f = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        Nm.v[e] = bci[e] == i ? f : -f;
+      }
+    sn = (unsigned char*)malloc((size_t)(nnzb > 0 ? nnzb : 1));
+    sk = (unsigned char*)malloc((size_t)(nnzb > 0 ? nnzb : 1));
+    cfp = (int*)malloc(sizeof(int) * (size_t)(np > 0 ? np : 1));
+    cidx = (int*)malloc(sizeof(int) * (size_t)(np > 0 ? np : 1));
+    if (!sn || !sk || !cfp || !cidx) { st = OR_ERR_MEM; goto fail; }
+    amg_strength(&Nm, o->theta, sn);
+    if ((st = amg_pmis(&Nm, sn, o->seed, l, cfp, NULL, NULL)) != OR_OK) goto fail;
+    int ncp = 0;
+    for (int i = 0; i < np; ++i) cidx[i] = cfp[i] ? ncp++ : -1;
+    if (ncp == 0 || ncp == np) break;   /* coarsening stalled: the coarsest level */
+    /* unknown-wise classical interpolation on the common split */
+    for (int k = 0; k < 2; ++k) {
+      if (csr_alloc(&Ak, np, np, nnzb) != OR_OK) { st = OR_ERR_MEM; goto fail; }
+      memcpy(Ak.rp, brp, sizeof(int) * ((size_t)np + 1));
+      memcpy(Ak.ci, bci, sizeof(int) * (size_t)nnzb);
+      for (int e = 0; e < nnzb; ++e) Ak.v[e] = bv[(size_t)4 * e + 3 * k];
+      amg_strength(&Ak, o->theta, sk);
+      if ((st = amg_interp(&Ak, sk, cfp, cidx, ncp, o->interp_max, &Pk[k])) != OR_OK) goto fail;
+      csr_free(&Ak);
+    }
+    /* interleaved P, the split per unknown, and the Galerkin product */
+    if (csr_alloc(&L->P, 2 * np, 2 * ncp, Pk[0].nnz + Pk[1].nnz) != OR_OK) { st = OR_ERR_MEM; goto fail; }
+    L->cf = (int*)malloc(sizeof(int) * (size_t)2 * np);
+    L->cidx = (int*)malloc(sizeof(int) * (size_t)2 * np);
+    if (!L->cf || !L->cidx) { st = OR_ERR_MEM; goto fail; }
+    {
+      int q = 0;
+      L->P.rp[0] = 0;
+      for (int i = 0; i < np; ++i)
+        for (int k = 0; k < 2; ++k) {
+          for (int e = Pk[k].rp[i]; e < Pk[k].rp[i + 1]; ++e) {
+            L->P.ci[q] = 2 * Pk[k].ci[e] + k;
+            L->P.v[q] = Pk[k].v[e];
+            ++q;
+          }
+          L->P.rp[2 * i + k + 1] = q;
+          L->cf[2 * i + k] = cfp[i];
+          L->cidx[2 * i + k] = cfp[i] ? 2 * cidx[i] + k : -1;
+        }
+    }
+    L->nc = 2 * ncp;
+    csr_free(&Pk[0]); csr_free(&Pk[1]); csr_free(&Nm);
+    free(sn); free(sk); free(cfp); free(cidx);
+    sn = sk = NULL; cfp = cidx = NULL;
+    if ((st = csr_transpose(&L->P, &L->R)) != OR_OK) goto fail;
+    csr_t AP, Ac;
+    if ((st = csr_matmul(&L->A, &L->P, &AP)) != OR_OK) goto fail;
+    if ((st = csr_matmul(&L->R, &AP, &Ac)) != OR_OK) goto fail;
+    csr_free(&AP);
+    free(brp); free(bci); free(bv);
+    brp = NULL; bci = NULL; bv = NULL;
+    st = scalar_to_bcsr2(&Ac, &brp, &bci, &bv);
+    csr_free(&Ac);
+    if (st != OR_OK) goto fail;
+    np = ncp;
+    h->nlev = l + 2;
+  }
+  {
+    level_t* C = &h->lev[h->nlev - 1];
+    int nc = C->A.n;
+    if (nc > OR_MAX_DENSE) { st = OR_ERR_AMG; goto fail; }
+    h->lu = (double*)calloc((size_t)nc * nc + 1, sizeof(double));
+    h->piv = (int*)malloc(sizeof(int) * (size_t)(nc + 1));
+    if (!h->lu || !h->piv) { st = OR_ERR_MEM; goto fail; }
+    for (int i = 0; i < nc; ++i)
+      for (int e = C->A.rp[i]; e < C->A.rp[i + 1]; ++e)
+        h->lu[(size_t)i * nc + C->A.ci[e]] = C->A.v[e];
+    if ((st = lu_factor(nc, h->lu, h->piv)) != OR_OK) goto fail;
+  }
+  free(brp); free(bci); free(bv); free(sn); free(sk); free(cfp); free(cidx);
+  csr_free(&Nm); csr_free(&Pk[0]); csr_free(&Pk[1]);
+  *out = h;
+  return OR_OK;
+fail:
+  free(brp); free(bci); free(bv); free(sn); free(sk); free(cfp); free(cidx);
+  csr_free(&Nm); csr_free(&Ak); csr_free(&Pk[0]); csr_free(&Pk[1]);
+  or_amg_free(h);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* V-cycle (Sec. 5.1: one V-cycle, direct coarse solve)                      */
 /* ------------------------------------------------------------------------ */
 static void residual(const level_t* L, const double* b, const double* x, double* r) {
@@ -869,9 +1080,22 @@ static void smooth_mcsgs(level_t* L, const double* b, double* x) {
     }
 }
 
+/* damped block Jacobi for the system AMG: x_i <- x_i + omega D_i^{-1} r_i
+ * with D_i the 2 x 2 diagonal block of point i (unknowns 2i, 2i+1) */
+static void smooth_bjac2(level_t* L, const double* b, double* x, double omega) {
+  residual(L, b, x, L->r);
+  for (int i = 0; i < L->A.n / 2; ++i) {
+    const double* d = &L->dinv2[(size_t)4 * i];
+    double r0 = L->r[2 * i], r1 = L->r[2 * i + 1];
+    x[2 * i] = x[2 * i] + omega * (d[0] * r0 + d[1] * r1);
+    x[2 * i + 1] = x[2 * i + 1] + omega * (d[2] * r0 + d[3] * r1);
+  }
+}
+
 static void smooth(amg_t* h, level_t* L, const double* b, double* x, int nu) {
   for (int k = 0; k < nu; ++k) {
-    if (h->o.smoother == 1) smooth_cheb(L, b, x, &h->o);
+    if (h->bs == 2) smooth_bjac2(L, b, x, h->o.omega);
+    else if (h->o.smoother == 1) smooth_cheb(L, b, x, &h->o);
     else if (h->o.smoother == 2) smooth_sgs(L, b, x);
     else if (h->o.smoother == 3) smooth_mcsgs(L, b, x);
     else smooth_jacobi(L, b, x, h->o.omega);
@@ -1291,6 +1515,37 @@ static or_solver* setup_impl(int N, int nb, const int* rp, const int* ci, const 
     for (int e = rp[i]; e < rp[i + 1]; ++e)
       block_left_mul(nb, Wi, &vals[(size_t)e * nb2], &s->Abar[(size_t)e * nb2]);
   }
+  if (o->scheme == 3) {
+    /* B_ee = Abar[e, e], e = (P, T): one 2 x 2 block per block of Abar */
+    double* be = (double*)malloc(sizeof(double) * 4 * (size_t)(nnzb > 0 ? nnzb : 1));
+    if (!be) { st = OR_ERR_MEM; goto fail; }
+    int ev[2] = {p, t};
+    for (int e = 0; e < nnzb; ++e)
+      for (int k = 0; k < 2; ++k)
+        for (int l = 0; l < 2; ++l)
+          be[(size_t)4 * e + 2 * k + l] = s->Abar[(size_t)e * nb2 + ev[k] * nb + ev[l]];
+    if (o->exact_sub) {
+      /* M_ee = B_ee^{-1} by dense LU (the paper's direct sub-solver study) */
+      csr_t S;
+      st = bcsr2_to_scalar(N, rp, ci, be, &S);
+      if (st == OR_OK && 2 * N > OR_MAX_DENSE) st = OR_ERR_ARG;
+      if (st == OR_OK) {
+        s->luP = (double*)calloc((size_t)4 * N * N, sizeof(double));
+        s->pivP = (int*)malloc(sizeof(int) * (size_t)(2 * N > 0 ? 2 * N : 1));
+        if (!s->luP || !s->pivP) st = OR_ERR_MEM;
+      }
+      if (st == OR_OK) {
+        for (int i = 0; i < 2 * N; ++i)
+          for (int e = S.rp[i]; e < S.rp[i + 1]; ++e) s->luP[(size_t)i * 2 * N + S.ci[e]] = S.v[e];
+        st = lu_factor(2 * N, s->luP, s->pivP);
+      }
+      csr_free(&S);
+    } else {
+      st = amg_build_system(N, rp, ci, be, o, &s->amgP);
+    }
+    free(be);
+    if (st != OR_OK) goto fail;
+  }
   if (o->scheme == 0 || o->scheme == 1) {
     if (o->exact_sub) {
       if ((st = dense_subsystem(s, p, &s->luP, &s->pivP)) != OR_OK) goto fail;
@@ -1351,6 +1606,30 @@ static void scalar_stage(or_solver* s, int var, const double* r, double* y) {
     for (int k = 0; k < nb; ++k) y[(size_t)i * nb + k] = k == var ? s->sy[i] : 0.0;
 }
 
+/* CPTR first stage (Eq. CPTRM1): y_e = M_ee^{-1} r_e on e = (P, T), zero
+ * elsewhere; M_ee is the system AMG V-cycle (or the dense solve). */
+static int system_stage(or_solver* s, const double* r, double* y) {
+  int N = s->N, nb = s->nb;
+  double* b2 = (double*)malloc(sizeof(double) * 2 * (size_t)(N > 0 ? N : 1));
+  double* x2 = (double*)malloc(sizeof(double) * 2 * (size_t)(N > 0 ? N : 1));
+  if (!b2 || !x2) { free(b2); free(x2); return OR_ERR_MEM; }
+  for (int i = 0; i < N; ++i) {
+    b2[2 * i] = r[(size_t)i * nb + s->p];
+    b2[2 * i + 1] = r[(size_t)i * nb + s->t];
+  }
+  if (s->o.exact_sub) {
+    memcpy(x2, b2, sizeof(double) * 2 * (size_t)N);
+    lu_solve(2 * N, s->luP, s->pivP, x2);
+  } else {
+    vcycle(s->amgP, 0, b2, x2);
+  }
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < nb; ++k)
+      y[(size_t)i * nb + k] = k == s->p ? x2[2 * i] : (k == s->t ? x2[2 * i + 1] : 0.0);
+  free(b2); free(x2);
+  return OR_OK;
+}
+
 static int last_stage(or_solver* s, const double* u, double* y) {
   int nb = s->nb, nb2 = nb * nb;
   if (s->o.stage3 == 0) return bilu_solve(s->ilu, u, y, s->work);
@@ -1371,6 +1650,7 @@ int or_stage(or_solver* s, int which, const double* r, double* y) {
   }
   if (which == 1) {
     if (s->o.scheme == 2) return OR_ERR_ARG;
+    if (s->o.scheme == 3) return system_stage(s, r, y);
     scalar_stage(s, s->p, r, y);
     return OR_OK;
   }
@@ -1382,14 +1662,17 @@ int or_stage(or_solver* s, int which, const double* r, double* y) {
  *                      y = x + v + M3 u, with M1 = amg(C_TT) on T and
  *                      M2 = amg(B_PP) on P (swapped by stage_order = 1).
  * CPR (Algorithm 1):   x = M1 r; z = r - Abar x; y = x + M2 z, M1 = amg(B_PP).
+ * CPTR (Sec. 4.2):     the same two stages with M1 = system AMG of B_ee on
+ *                      (P, T) (Eq. CPTRM1) and M2 = ilu(Abar).
  * ILU only:            y = M r. */
 int or_apply(or_solver* s, const double* r, double* y) {
   int n = s->N * s->nb;
   double* x = s->tmp;
   int st;
   if (s->o.scheme == 2) return last_stage(s, r, y);
-  if (s->o.scheme == 1) {
-    scalar_stage(s, s->p, r, x);
+  if (s->o.scheme == 1 || s->o.scheme == 3) {
+    if (s->o.scheme == 1) scalar_stage(s, s->p, r, x);
+    else if ((st = system_stage(s, r, x)) != OR_OK) return st;
     bsr_mv(s, s->Abar, x, s->z);
     for (int i = 0; i < n; ++i) s->z[i] = r[i] - s->z[i];
     if ((st = last_stage(s, s->z, y)) != OR_OK) return st;
@@ -1512,6 +1795,81 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* static condensation (Sec. 3, Eqs. global and reduced)                     */
+/* ------------------------------------------------------------------------ */
+/* The global system [J11 J12; J21 J22] [d1; d2] = -[r1; r2] with the
+ * secondary unknowns coupled only inside their cell: J12 (n1 x n2) and J22
+ * (n2 x n2) are one block per cell, J11 (n1 x n1) and J21 (n2 x n1) have the
+ * cell graph's block pattern (rp, ci). The reduced system A d1 = b has
+ *   A = J11 - J12 J22^{-1} J21,   b = -r1 + J12 J22^{-1} r2,
+ * assembled block by block: with T_i = J12_i J22_i^{-1} (cell i),
+ * A_ij = J11_ij - T_i J21_ij and b_i = -r1_i + T_i r2_i. J22_i is inverted
+ * without pivoting (Sec. 3 aligns the secondary equations so that its
+ * diagonal is nonzero). Parity: pinned against a dense solve of the global
+ * system and the dense Schur complement. */
+int or_condense(int N, const int* rp, const int* ci, int n1, int n2, const double* j11,
+                const double* j21, const double* j12, const double* j22, const double* r1,
+                const double* r2, double* a, double* b) {
+  if (N < 0 || n1 < 1 || n1 > 32 || n2 < 0 || n2 > 32) return OR_ERR_ARG;
+  double inv[32 * 32], T[32 * 32];
+  for (int i = 0; i < N; ++i) {
+    if (n2 > 0) {
+      int st = gj_inverse_nopiv(n2, &j22[(size_t)i * n2 * n2], inv);
+      if (st != OR_OK) return st;
+    }
+    const double* J12 = &j12[(size_t)i * n1 * n2];
+    for (int r = 0; r < n1; ++r)
+      for (int c = 0; c < n2; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < n2; ++k) s += J12[r * n2 + k] * inv[k * n2 + c];
+        T[r * n2 + c] = s;
+      }
+    for (int r = 0; r < n1; ++r) {
+      double s = 0.0;
+      for (int k = 0; k < n2; ++k) s += T[r * n2 + k] * r2[(size_t)i * n2 + k];
+      b[(size_t)i * n1 + r] = -r1[(size_t)i * n1 + r] + s;
+    }
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const double* J11 = &j11[(size_t)e * n1 * n1];
+      const double* J21 = &j21[(size_t)e * n2 * n1];
+      double* A = &a[(size_t)e * n1 * n1];
+      for (int r = 0; r < n1; ++r)
+        for (int c = 0; c < n1; ++c) {
+          double s = 0.0;
+          for (int k = 0; k < n2; ++k) s += T[r * n2 + k] * J21[k * n1 + c];
+          A[r * n1 + c] = J11[r * n1 + c] - s;
+        }
+    }
+  }
+  return OR_OK;
+}
+
+/* Secondary unknowns from the primary ones (the second block row of Eq.
+ * global): J22_i d2_i = -r2_i - sum_j J21_ij d1_j, solved per cell by
+ * Gaussian elimination without pivoting. */
+int or_recover(int N, const int* rp, const int* ci, int n1, int n2, const double* j21,
+               const double* j22, const double* r2, const double* d1, double* d2) {
+  if (N < 0 || n1 < 1 || n1 > 32 || n2 < 0 || n2 > 32) return OR_ERR_ARG;
+  for (int i = 0; i < N; ++i) {
+    double* w = &d2[(size_t)i * n2];
+    for (int k = 0; k < n2; ++k) {
+      double s = 0.0;
+      for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        const double* J21 = &j21[(size_t)e * n2 * n1];
+        const double* x = &d1[(size_t)ci[e] * n1];
+        for (int c = 0; c < n1; ++c) s += J21[k * n1 + c] * x[c];
+      }
+      w[k] = -r2[(size_t)i * n2 + k] - s;
+    }
+    if (n2 > 0) {
+      int st = ge_solve_nopiv(n2, &j22[(size_t)i * n2 * n2], w);
+      if (st != OR_OK) return st;
+    }
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* accessors for the tests                                                  */
 /* ------------------------------------------------------------------------ */
 void or_get_scaled(const or_solver* s, double* abar, double* W) {
@@ -1582,6 +1940,15 @@ amg_t* or_amg_create(int n, const int* rp, const int* ci, const double* v, const
   amg_t* h = NULL;
   *status = amg_build(n, rp, ci, v, o, NULL, &h);
   return h;
+}
+
+/* Stand-alone system AMG on np points of 2 x 2 blocks (bv: 4 per block,
+ * row-major); levels are read back in the scalar interleaved form. */
+amg_t* or_amg_create_system(int np, const int* rp, const int* ci, const double* bv,
+                            const or_opts* o, int* status) {
+  amg_t* h = NULL;
+  *status = amg_build_system(np, rp, ci, bv, o, &h);
+  return *status == OR_OK ? h : NULL;
 }
 
 int or_amg_nlev(const amg_t* h) { return h->nlev; }

@@ -15,7 +15,7 @@ from .build import build_oracle
 
 OK, ERR_ARG, ERR_SINGULAR, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_MEM, ERR_AMG = 0, -1, -2, -3, -4, -5, -6
 
-SCHEME = {"cptr3": 0, "cpr": 1, "ilu0": 2}
+SCHEME = {"cptr3": 0, "cpr": 1, "ilu0": 2, "cptr": 3}
 SMOOTHER = {"jacobi": 0, "chebyshev": 1, "sgs": 2, "mcsgs": 3}
 
 
@@ -65,6 +65,9 @@ def lib():
         L.or_amg_create.restype = _P
         L.or_amg_create.argtypes = [C.c_int, _P, _P, _P, C.POINTER(OrOpts), C.POINTER(C.c_int)]
         L.or_amg_free.argtypes = [_P]
+        L.or_amg_create_system.restype = _P
+        L.or_amg_create_system.argtypes = [C.c_int, _P, _P, _P, C.POINTER(OrOpts),
+                                           C.POINTER(C.c_int)]
         L.or_amg_nlev.argtypes = [_P]
         L.or_amg_sizes.argtypes = [_P, C.c_int, _P]
         L.or_amg_get.argtypes = [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P]
@@ -73,6 +76,9 @@ def lib():
         L.or_interp_only.argtypes = [C.c_int, _P, _P, _P, C.c_double, C.c_int, C.c_uint64,
                                      _P, _P, _P, _P, _P, _P]
         L.or_colour.argtypes = [C.c_int, _P, _P, C.c_uint64, _P]
+        L.or_condense.argtypes = [C.c_int, _P, _P, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P,
+                                  _P, _P]
+        L.or_recover.argtypes = [C.c_int, _P, _P, C.c_int, C.c_int, _P, _P, _P, _P, _P]
         L.or_pmis_rounds.argtypes = [C.c_int, _P, _P, _P, C.c_double, C.c_uint64, C.c_int,
                                      _P, _P, _P, _P]
         L.or_hash.restype = C.c_uint64
@@ -257,6 +263,22 @@ class OracleAMG:
         if not self._h:
             raise OracleError(st.value, "or_amg_create")
 
+    @classmethod
+    def system(cls, row_ptr, col_idx, blocks, opts: OrOpts | None = None, **kw):
+        """System AMG (the CPTR first stage) on 2 x 2 blocks [nnzb, 2, 2];
+        levels and vectors are in the scalar form with the two unknowns of a
+        point interleaved."""
+        new = object.__new__(cls)
+        new._keep = (_i32(row_ptr), _i32(col_idx), _f64(blocks))
+        new.n = 2 * (new._keep[0].shape[0] - 1)
+        new.opts = opts if opts is not None else options(**kw)
+        st = C.c_int(0)
+        new._h = lib().or_amg_create_system(new.n // 2, _ptr(new._keep[0]), _ptr(new._keep[1]),
+                                            _ptr(new._keep[2]), C.byref(new.opts), C.byref(st))
+        if not new._h:
+            raise OracleError(st.value, "or_amg_create_system")
+        return new
+
     def __del__(self):
         if getattr(self, "_h", None):
             lib().or_amg_free(self._h)
@@ -331,6 +353,33 @@ def pmis_rounds(row_ptr, col_idx, vals, theta=0.25, seed=0x5eed, level=0):
     if st:
         raise OracleError(st, "or_pmis_rounds")
     return strong[:ci.shape[0]].astype(bool), pre[:n], rnd[:n], cf[:n]
+
+
+def condense(full):
+    """Static condensation (Sec. 3, Eq. reduced) of a synthetic.FullSystem:
+    (A blocks [nnzb, n1, n1], b [N * n1])."""
+    rp, ci = _i32(full.row_ptr), _i32(full.col_idx)
+    j11, j21, j12, j22 = (_f64(x) for x in (full.j11, full.j21, full.j12, full.j22))
+    r1, r2 = _f64(full.r1), _f64(full.r2)
+    a = np.empty((full.nnzb, full.n1, full.n1))
+    b = np.empty(full.n_cells * full.n1)
+    st = lib().or_condense(full.n_cells, _ptr(rp), _ptr(ci), full.n1, full.n2, _ptr(j11),
+                           _ptr(j21), _ptr(j12), _ptr(j22), _ptr(r1), _ptr(r2), _ptr(a), _ptr(b))
+    if st:
+        raise OracleError(st, "or_condense")
+    return a, b
+
+
+def recover(full, d1):
+    """The secondary unknowns d2 from the primary ones d1 (Eq. global)."""
+    rp, ci = _i32(full.row_ptr), _i32(full.col_idx)
+    j21, j22, r2, x1 = (_f64(x) for x in (full.j21, full.j22, full.r2, d1))
+    d2 = np.empty(full.n_cells * full.n2)
+    st = lib().or_recover(full.n_cells, _ptr(rp), _ptr(ci), full.n1, full.n2, _ptr(j21),
+                          _ptr(j22), _ptr(r2), _ptr(x1), _ptr(d2))
+    if st:
+        raise OracleError(st, "or_recover")
+    return d2
 
 
 def colour(row_ptr, col_idx, seed=0x5eed):
