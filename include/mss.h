@@ -50,7 +50,7 @@ extern "C" {
 #define MSS_ERR_NOT_SETUP (-8)      /* handle has no set-up, or another matrix was passed */
 
 /* ---- option values ------------------------------------------------------ */
-enum { MSS_CPTR3 = 0, MSS_CPR = 1, MSS_ILU0 = 2 };   /* preconditioner scheme */
+enum { MSS_CPTR3 = 0, MSS_CPR = 1, MSS_ILU0 = 2, MSS_CPTR = 3 }; /* preconditioner scheme */
 enum { MSS_STAGE_T_FIRST = 0, MSS_STAGE_P_FIRST = 1 }; /* CPTR3 stage order */
 enum { MSS_BILU0 = 0, MSS_BLOCK_JACOBI = 1 };        /* last stage */
 enum { MSS_MULTICOLOR = 0, MSS_STRIPS = 2 };         /* block ILU(0) ordering */
@@ -80,7 +80,17 @@ typedef struct {
 } mss_layout;
 
 typedef struct {
-  int32_t scheme;           /* MSS_CPTR3 (default) | MSS_CPR | MSS_ILU0 */
+  int32_t scheme;           /* MSS_CPTR3 (default; Sec. 4.3) | MSS_CPR (Sec. 4.1) |
+                               MSS_ILU0 (no scaling, the last stage alone) |
+                               MSS_CPTR (Sec. 4.2, Eqs. CPTRinit, CPTR1, CPTRM1): the
+                               scaling N1 of Eq. CPTR31 alone, then two stages: a
+                               system AMG for the 2 x 2 block B_ee on (P, T) --
+                               nodal coarsening (PMIS on the Frobenius norms of the
+                               blocks), classical interpolation per unknown on the
+                               common split, Galerkin products of the coupled
+                               system, damped 2 x 2 block Jacobi with jacobi_omega,
+                               nu_pre, nu_post (the smoother option is not used) --
+                               and the last stage. */
   int32_t stage_order;      /* MSS_STAGE_T_FIRST (Algorithm 2, default) | P first */
   int32_t stage3;           /* MSS_BILU0 (default) | MSS_BLOCK_JACOBI */
   int32_t ilu_order;        /* MSS_STRIPS (default): strips of ilu_strip consecutive
@@ -230,8 +240,8 @@ int mss_apply(mss_handle* h, const double* r, double* y);
 
 /* One stage operator alone, for testing the composition of Eq.
  * multistageprec: which = 0 temperature AMG stage (Eq. CPTR3M1), 1 pressure
- * AMG stage (Eq. CPTRM2 / CPRM1), 2 last stage (block ILU(0) or block
- * Jacobi of Abar). The result is zero outside the stage's unknowns. Always
+ * AMG stage (Eq. CPTRM2 / CPRM1; for MSS_CPTR the system AMG stage on
+ * (P, T), Eq. CPTRM1), 2 last stage (block ILU(0) or block Jacobi of Abar). The result is zero outside the stage's unknowns. Always
  * float64, whatever mss_options.precision (mss_apply follows precision).
  * Errors: NOT_SETUP, INVALID_ARG (stage absent in the scheme). */
 int mss_stage_apply(mss_handle* h, int which, const double* r, double* y);
@@ -340,7 +350,9 @@ int mss_recover(mss_handle* h, const mss_full* J, const double* r2, const double
  * (device, caller-owned). */
 int mss_get_scaled(mss_handle* h, double* abar);
 
-/* Number of AMG levels of stage `which` (0 = C_TT, 1 = B_PP); 0 if the
+/* Number of AMG levels of stage `which` (0 = C_TT, 1 = B_PP, or B_ee for
+ * MSS_CPTR, whose levels are read in the scalar form with the (P, T) pair of
+ * a point interleaved and the point split repeated per unknown); 0 if the
  * scheme has no such stage. */
 int mss_amg_num_levels(mss_handle* h, int which);
 

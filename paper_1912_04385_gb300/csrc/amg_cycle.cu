@@ -436,6 +436,55 @@ __global__ void k_mcgs(int q0, int q1, const int* __restrict__ order, const int*
   x[i] = s * dinv[i];
 }
 
+// One damped block-Jacobi sweep of the system AMG (2 unknowns per point):
+// r = b - A x_in on the point's two rows, x_out = x_in + omega D_i^{-1} r
+template <class V, class C>
+__global__ void k_bjac2(int np, const int* __restrict__ rp, const int* __restrict__ ci,
+                        const V* __restrict__ v, const C* __restrict__ dinv2,
+                        const C* __restrict__ b, C omega, const C* __restrict__ xin,
+                        C* __restrict__ xout) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  C r[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int row = 2 * i + k;
+    C s = 0;
+    for (int q = rp[row]; q < rp[row + 1]; ++q) s += cvt<C>(v[q]) * xin[ci[q]];
+    r[k] = b[row] - s;
+  }
+  const C* d = dinv2 + (size_t)4 * i;
+  xout[2 * i] = xin[2 * i] + omega * (d[0] * r[0] + d[1] * r[1]);
+  xout[2 * i + 1] = xin[2 * i + 1] + omega * (d[2] * r[0] + d[3] * r[1]);
+}
+
+// CPTR: out[2i] = v[i*nb + p], out[2i+1] = v[i*nb + t]
+template <class C>
+__global__ void k_gather_pair(int N, int nb, const double* __restrict__ v, int p, int t,
+                              C* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  out[2 * i] = (C)v[(size_t)i * nb + p];
+  out[2 * i + 1] = (C)v[(size_t)i * nb + t];
+}
+
+template <class C>
+__global__ void k_split_pair(int N, const C* __restrict__ pair, C* __restrict__ vP,
+                             C* __restrict__ xT) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  vP[i] = pair[2 * i];
+  xT[i] = pair[2 * i + 1];
+}
+
+__global__ void k_scatter_pair_zero(int N, int nb, const double* __restrict__ pair, int p, int t,
+                                    double* __restrict__ out) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)N * nb) return;
+  const int i = (int)(tid / nb), k = (int)(tid % nb);
+  out[tid] = k == p ? pair[2 * i] : (k == t ? pair[2 * i + 1] : 0.0);
+}
+
 template <class V, class C>
 __global__ void k_residual(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                            const V* __restrict__ v, const C* __restrict__ b,
@@ -661,17 +710,18 @@ struct LV {
   double lam;
   const int* mcorder;                 // multicolour Gauss-Seidel order (or null)
   const std::vector<int>* cstart;     // its colour boundaries (host)
+  const C* dinv2;                     // system AMG: inverse 2 x 2 diagonal blocks
 };
 
 LV<double, double> view(Level& L, double*) {
   return {L.n, L.nc, L.rp.p, L.ci.p, L.prp.p, L.pci.p, L.rrp.p, L.rci.p,
           L.v.p, L.pv.p, L.rv.p, L.dinv.p, L.x2.p, L.r.p, L.d.p, L.lam,
-          L.mcorder.p, &L.cstart};
+          L.mcorder.p, &L.cstart, L.dinv2.p};
 }
 LV<__nv_bfloat16, float> view(Level& L, float*) {
   return {L.n, L.nc, L.rp.p, L.ci.p, L.prp.p, L.pci.p, L.rrp.p, L.rci.p,
           L.vh.p, L.pvh.p, L.rvh.p, L.dinvf.p, L.x2f.p, L.rf.p, L.df.p, L.lam,
-          L.mcorder.p, &L.cstart};
+          L.mcorder.p, &L.cstart, L.dinv2f.p};
 }
 double* level_b(Level& L, double*) { return L.b.p; }
 float* level_b(Level& L, float*) { return L.bf.p; }
@@ -691,6 +741,13 @@ struct Sweeper {
     k_jacobi<V, C><<<grid_for(L.n, h->tb), h->tb, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.dinv, b,
                                                             (C)o.jacobi_omega, xin, xout);
     MSS_LAUNCH_CK("k_jacobi");
+  }
+  // one damped 2 x 2 block-Jacobi sweep (system AMG); xin and xout differ
+  void bjac2(const C* b, const C* xin, C* xout) {
+    const int np = L.n / 2;
+    k_bjac2<V, C><<<grid_for(np, h->tb), h->tb, 0, h->stream>>>(np, L.rp, L.ci, L.v, L.dinv2, b,
+                                                               (C)o.jacobi_omega, xin, xout);
+    MSS_LAUNCH_CK("k_bjac2");
   }
   // symmetric multicolour Gauss-Seidel, in place on x: the colours in
   // order, then in reverse. The reverse pass starts with the colour the
@@ -742,7 +799,7 @@ struct Sweeper {
 // Does the V-cycle on level l start with a Jacobi sweep from zero whose
 // result the producer of b can write? (Jacobi smoothing, not the coarsest.)
 bool has_sweep0(const Hierarchy& H, const mss_options& o, int l) {
-  return o.smoother == MSS_JACOBI && l < (int)H.lev.size() - 1;
+  return H.bs == 1 && o.smoother == MSS_JACOBI && l < (int)H.lev.size() - 1;
 }
 
 // V-cycle on level l for right-hand side b; the result goes to out. With
@@ -807,7 +864,15 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out, bool x_has
   // ---- pre-smoothing from zero, then the residual
   C* cur = out;
   C* alt = L.x2;
-  if (o.smoother == MSS_JACOBI && x_has_sweep0) {
+  if (H.bs == 2) {   // system AMG: block Jacobi from zero
+    MSS_CK(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)n, h->stream));
+    for (int s = 0; s < o.nu_pre; ++s) {
+      sw.bjac2(b, cur, alt);
+      std::swap(cur, alt);
+    }
+    k_residual<V, C><<<grid_for(n, h->tb), h->tb, 0, h->stream>>>(n, L.rp, L.ci, L.v, b, cur, L.r);
+    MSS_LAUNCH_CK("k_residual");
+  } else if (o.smoother == MSS_JACOBI && x_has_sweep0) {
     for (int s = 1; s < o.nu_pre; ++s) {
       sw.jacobi(b, cur, alt);
       std::swap(cur, alt);
@@ -853,7 +918,8 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out, bool x_has
   // ---- prolongation into the vector from which the post-smoothing sweeps,
   // alternating between the two vectors, end in out
   // (Gauss-Seidel sweeps work in place)
-  const int writes = o.smoother == MSS_MCSGS
+  const int writes = H.bs == 2 ? o.nu_post
+                   : o.smoother == MSS_MCSGS
                          ? 0
                          : o.nu_post * (o.smoother == MSS_JACOBI ? 1 : o.cheb_degree);
   C* target = writes % 2 == 0 ? out : L.x2;
@@ -864,7 +930,10 @@ void vcycle_level(Handle* h, Hierarchy& H, int l, const C* b, C* out, bool x_has
   alt = target == out ? L.x2 : out;
   // ---- post-smoothing
   for (int s = 0; s < o.nu_post; ++s) {
-    if (o.smoother == MSS_JACOBI) {
+    if (H.bs == 2) {
+      sw.bjac2(b, cur, alt);
+      std::swap(cur, alt);
+    } else if (o.smoother == MSS_JACOBI) {
       sw.jacobi(b, cur, alt);
       std::swap(cur, alt);
     } else if (o.smoother == MSS_MCSGS) {
@@ -1004,6 +1073,10 @@ void pack_hierarchy_mixed(Handle* h, Hierarchy& H) {
     to_bf16(h, L.v.p, L.vh.p, L.nnz);
     L.dinvf.reset(h, L.n);
     to_float(h, L.dinv.p, L.dinvf.p, L.n);
+    if (L.dinv2.p) {
+      L.dinv2f.reset(h, L.dinv2.n);
+      to_float(h, L.dinv2.p, L.dinv2f.p, (long long)L.dinv2.n);
+    }
     if (!last) {
       L.pvh.reset(h, L.nnzP);
       to_bf16(h, L.pv.p, L.pvh.p, L.nnzP);
@@ -1052,7 +1125,7 @@ void prepare_tail(Handle* h, Hierarchy& H) {
   H.tdesc.release();
   H.tdescf.release();
   const int nl = (int)H.lev.size();
-  if (h->opt.smoother != MSS_JACOBI || nl < 3) return;
+  if (h->opt.smoother != MSS_JACOBI || H.bs != 1 || nl < 3) return;
   int t = -1;
   for (int l = 1; l + 1 < nl; ++l)
     if (H.lev[l].n <= kTailRows) {
@@ -1131,6 +1204,33 @@ void csr_block_pattern_spmv_sub(Handle* h, const float* vals, const float* x, co
   k_pattern_sub<float><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(
       h->N, h->nb, h->rp.p, h->ci.p, vals, x, r, var, out, s0.dinv, s0.omega, s0.x);
   MSS_LAUNCH_CK("k_pattern_sub");
+}
+
+void gather_pair(Handle* h, const double* v, double* out) {
+  k_gather_pair<double><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, v, h->p,
+                                                                       h->t, out);
+  MSS_LAUNCH_CK("k_gather_pair");
+}
+
+void gather_pair(Handle* h, const double* v, float* out) {
+  k_gather_pair<float><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, v, h->p,
+                                                                      h->t, out);
+  MSS_LAUNCH_CK("k_gather_pair");
+}
+
+template <class C>
+void split_pair(Handle* h, const C* pair, C* vP, C* xT) {
+  k_split_pair<C><<<grid_for(h->N, h->tb), h->tb, 0, h->stream>>>(h->N, pair, vP, xT);
+  MSS_LAUNCH_CK("k_split_pair");
+}
+template void split_pair<double>(Handle*, const double*, double*, double*);
+template void split_pair<float>(Handle*, const float*, float*, float*);
+
+void scatter_pair_zero(Handle* h, const double* pair, double* out) {
+  const long long tot = (long long)h->N * h->nb;
+  k_scatter_pair_zero<<<grid_for(tot, h->tb), h->tb, 0, h->stream>>>(h->N, h->nb, pair, h->p,
+                                                                     h->t, out);
+  MSS_LAUNCH_CK("k_scatter_pair_zero");
 }
 
 }  // namespace mss

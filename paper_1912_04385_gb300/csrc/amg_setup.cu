@@ -603,6 +603,93 @@ void transpose(Handle* h, int n, int m, const int* rp, const int* ci, const doub
   MSS_LAUNCH_CK("k_sort_rows");
 }
 
+// Strength of connection of a scalar CSR matrix: the flag per nonzero, the
+// strength graph S (strong dependencies by row) and its transpose, as PMIS
+// reads them.
+struct Strength {
+  DBuf<unsigned char> strong;
+  DBuf<int> srp, sci, strp, stci;
+};
+
+void strength_graph(Handle* h, int n, int nnz, const int* rp, const int* ci, const double* v,
+                    double theta, Strength& S) {
+  S.strong.reset(h, nnz > 0 ? nnz : 1);
+  DBuf<int> scount(h, n);
+  S.srp.reset(h, n + 1);
+  k_strength<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, theta, S.strong.p,
+                                                      scount.p);
+  MSS_LAUNCH_CK("k_strength");
+  exclusive_scan(h, scount.p, S.srp.p, n);
+  int ns = read_int(h, S.srp.p + n);
+  S.sci.reset(h, ns > 0 ? ns : 1);
+  k_fill_strong<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, S.strong.p, S.srp.p,
+                                                         S.sci.p);
+  MSS_LAUNCH_CK("k_fill_strong");
+  transpose(h, n, n, S.srp.p, S.sci.p, nullptr, ns, S.strp, S.stci, nullptr);
+}
+
+// PMIS C/F split (1 = C) of AMG level `level`; |S_i^T| are the row lengths
+// of the transposed strength graph
+void pmis_split(Handle* h, int n, const Strength& S, uint64_t seed, int level, DBuf<int>& cf) {
+  DBuf<int> tcount(h, n);
+  k_row_lengths<<<grid_for(n, 256), 256, 0, h->stream>>>(n, S.strp.p, tcount.p);
+  MSS_LAUNCH_CK("k_row_lengths");
+  DBuf<double> lam(h, n);
+  DBuf<int> state(h, n), newc(h, n), und(h, 1);
+  fill_int(h, und.p, 0, 1);
+  k_pmis_init<<<grid_for(n, 256), 256, 0, h->stream>>>(n, tcount.p, seed, level, lam.p, state.p,
+                                                       und.p);
+  MSS_LAUNCH_CK("k_pmis_init");
+  int undecided = read_int(h, und.p);
+  int rounds = 0;
+  while (undecided > 0) {
+    // three synchronous rounds per read-back: a round with nothing
+    // undecided changes nothing, so the split is the one of round-by-round
+    // checking with fewer host synchronisations
+    for (int r = 0; r < 3; ++r) {
+      if (++rounds > n + 3) fail(MSS_ERR_AMG, "PMIS did not terminate");
+      k_pmis_select<<<grid_for(n, 256), 256, 0, h->stream>>>(n, S.srp.p, S.sci.p, S.strp.p,
+                                                             S.stci.p, lam.p, state.p, newc.p);
+      MSS_LAUNCH_CK("k_pmis_select");
+      fill_int(h, und.p, 0, 1);
+      k_pmis_update<<<grid_for(n, 256), 256, 0, h->stream>>>(n, S.srp.p, S.sci.p, state.p,
+                                                             newc.p, und.p);
+      MSS_LAUNCH_CK("k_pmis_update");
+    }
+    undecided = read_int(h, und.p);
+  }
+  cf.reset(h, n);
+  k_pmis_finalize<<<grid_for(n, 256), 256, 0, h->stream>>>(n, S.srp.p, S.sci.p, state.p, cf.p);
+  MSS_LAUNCH_CK("k_pmis_finalize");
+}
+
+// Classical interpolation P (n x nc, CSR) for the split cf with coarse
+// indices cidx; returns nnz(P)
+int classical_interp(Handle* h, int n, int nnz, const int* rp, const int* ci, const double* v,
+                     const unsigned char* strong, const int* cf, const int* cidx, int maxel,
+                     DBuf<int>& prp, DBuf<int>& pci, DBuf<double>& pv) {
+  DBuf<int> scr_ci(h, nnz), scr_k(h, nnz), plen(h, n);
+  DBuf<double> scr_v(h, nnz);
+  if (n <= 65536 && nnz > 8LL * n) {   // few, long rows: one warp per row
+    k_interp_warp<<<grid_for((long long)n * 32, 256), 256, 0, h->stream>>>(
+        n, rp, ci, v, strong, cf, cidx, maxel, scr_ci.p, scr_v.p, scr_k.p, plen.p);
+    MSS_LAUNCH_CK("k_interp_warp");
+  } else {
+    k_interp<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, strong, cf, cidx, maxel,
+                                                      scr_ci.p, scr_v.p, scr_k.p, plen.p);
+    MSS_LAUNCH_CK("k_interp");
+  }
+  prp.reset(h, n + 1);
+  exclusive_scan(h, plen.p, prp.p, n);
+  const int nnzP = read_int(h, prp.p + n);
+  pci.reset(h, nnzP > 0 ? nnzP : 1);
+  pv.reset(h, nnzP > 0 ? nnzP : 1);
+  k_seg_copy<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, scr_ci.p, scr_v.p, prp.p, pci.p,
+                                                      pv.p);
+  MSS_LAUNCH_CK("k_seg_copy");
+  return nnzP;
+}
+
 void level_prepare(Handle* h, Level& L) {
   int n = L.n;
   L.dinv.reset(h, n);
@@ -662,6 +749,148 @@ void level_colours(Handle* h, Level& L) {
   if (base != n) fail(MSS_ERR_CUDA, "AMG level colours do not cover every point");
 }
 
+// ---- system AMG for CPTR: 2 x 2 blocks on a point graph ---------------------
+// Scalar form of a 2 x 2 block CSR with the two unknowns of a point
+// interleaved: row 2i+k holds, for each block of point row i in order, the
+// entries (k, 0) and (k, 1) at columns 2j and 2j+1.
+__global__ void k_b2s(int np, const int* __restrict__ brp, const int* __restrict__ bci,
+                      const double* __restrict__ bv, int* __restrict__ srp,
+                      int* __restrict__ sci, double* __restrict__ sv) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * np) return;
+  const int i = t >> 1, k = t & 1;
+  const int b = brp[i], e = brp[i + 1], len = e - b;
+  const int base = 4 * b + 2 * k * len;
+  srp[t] = base;
+  if (t == 2 * np - 1) srp[2 * np] = 4 * e;
+  for (int q = 0; q < len; ++q)
+    for (int l = 0; l < 2; ++l) {
+      sci[base + 2 * q + l] = 2 * bci[b + q] + l;
+      sv[base + 2 * q + l] = bv[(size_t)4 * (b + q) + 2 * k + l];
+    }
+}
+
+// Norm matrix of the blocks: -|B_ij|_F off the diagonal, |B_ii|_F on it
+// (squares summed in the order b00, b01, b10, b11)
+__global__ void k_block_norm(int np, const int* __restrict__ brp, const int* __restrict__ bci,
+                             const double* __restrict__ bv, double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  for (int e = brp[i]; e < brp[i + 1]; ++e) {
+    const double* q = bv + (size_t)4 * e;
+    const double f = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    out[e] = bci[e] == i ? f : -f;
+  }
+}
+
+__global__ void k_block_entry(int nnzb, const double* __restrict__ bv, int idx,
+                              double* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnzb) out[e] = bv[(size_t)4 * e + idx];
+}
+
+// inverse of each point's 2 x 2 diagonal block: Gauss-Jordan without
+// pivoting, divisions as written (the smoother's D_i^-1)
+__global__ void k_dinv2(int np, const int* __restrict__ brp, const int* __restrict__ bci,
+                        const double* __restrict__ bv, double* __restrict__ dinv2,
+                        int* __restrict__ bad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  int d = -1;
+  for (int e = brp[i]; e < brp[i + 1]; ++e)
+    if (bci[e] == i) d = e;
+  if (d < 0) {
+    atomicMin(bad, i);
+    return;
+  }
+  double a[4], inv[4] = {1.0, 0.0, 0.0, 1.0};
+  for (int t = 0; t < 4; ++t) a[t] = bv[(size_t)4 * d + t];
+  for (int k = 0; k < 2; ++k) {
+    const double piv = a[2 * k + k];
+    if (piv == 0.0 || !isfinite(piv)) {
+      atomicMin(bad, i);
+      return;
+    }
+    for (int j = 0; j < 2; ++j) {
+      a[2 * k + j] = a[2 * k + j] / piv;
+      inv[2 * k + j] = inv[2 * k + j] / piv;
+    }
+    const int r = 1 - k;
+    const double f = a[2 * r + k];
+    for (int j = 0; j < 2; ++j) {
+      a[2 * r + j] = a[2 * r + j] - f * a[2 * k + j];
+      inv[2 * r + j] = inv[2 * r + j] - f * inv[2 * k + j];
+    }
+  }
+  for (int t = 0; t < 4; ++t) dinv2[(size_t)4 * i + t] = inv[t];
+}
+
+// the point split per unknown: cf2[2i+k] = cf[i]
+__global__ void k_dup2(int np, const int* __restrict__ cf, int* __restrict__ cf2) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 2 * np) cf2[t] = cf[t >> 1];
+}
+
+// interleaved P: row 2i+k is row i of P^k with columns 2c+k
+__global__ void k_p2_len(int np, const int* __restrict__ prp0, const int* __restrict__ prp1,
+                         int* __restrict__ len) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * np) return;
+  const int i = t >> 1;
+  const int* rp = (t & 1) ? prp1 : prp0;
+  len[t] = rp[i + 1] - rp[i];
+}
+
+__global__ void k_p2_fill(int np, const int* __restrict__ prp0, const int* __restrict__ pci0,
+                          const double* __restrict__ pv0, const int* __restrict__ prp1,
+                          const int* __restrict__ pci1, const double* __restrict__ pv1,
+                          const int* __restrict__ prp, int* __restrict__ pci,
+                          double* __restrict__ pv) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * np) return;
+  const int i = t >> 1, k = t & 1;
+  const int* rp = k ? prp1 : prp0;
+  const int* ci = k ? pci1 : pci0;
+  const double* v = k ? pv1 : pv0;
+  int q = prp[t];
+  for (int e = rp[i]; e < rp[i + 1]; ++e, ++q) {
+    pci[q] = 2 * ci[e] + k;
+    pv[q] = v[e];
+  }
+}
+
+// 2 x 2 blocks of a scalar interleaved matrix: block row I holds every point
+// with an entry in row 2I or 2I+1 (the merged, ascending point columns);
+// fill == false counts them, fill == true writes columns and values (the
+// values must be zeroed first: absent entries stay zero)
+__global__ void k_s2b(int np, const int* __restrict__ srp, const int* __restrict__ sci,
+                      const double* __restrict__ sv, int* __restrict__ cnt,
+                      const int* __restrict__ brp, int* __restrict__ bci,
+                      double* __restrict__ bv, int fill) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= np) return;
+  int a = srp[2 * I], ae = srp[2 * I + 1], b = srp[2 * I + 1], be = srp[2 * I + 2];
+  int q = fill ? brp[I] : 0, last = -1;
+  while (a < ae || b < be) {
+    const int ja = a < ae ? sci[a] / 2 : 0x7fffffff;
+    const int jb = b < be ? sci[b] / 2 : 0x7fffffff;
+    const int j = ja < jb ? ja : jb;
+    if (j != last) {
+      if (fill) bci[q] = j;
+      ++q;
+      last = j;
+    }
+    if (ja == j) {
+      if (fill) bv[(size_t)4 * (q - 1) + (sci[a] & 1)] = sv[a];
+      ++a;
+    } else {
+      if (fill) bv[(size_t)4 * (q - 1) + 2 + (sci[b] & 1)] = sv[b];
+      ++b;
+    }
+  }
+  if (!fill) cnt[I] = q;
+}
+
 }  // namespace
 
 // Host time per set-up phase, printed when MSS_SETUP_TIMES is set (each mark
@@ -715,19 +944,8 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     const int* rp = H.lev[l].rp.p;
     const int* ci = H.lev[l].ci.p;
     const double* v = H.lev[l].v.p;
-    // strength and its transpose
-    DBuf<unsigned char> strong(h, nnz);
-    DBuf<int> scount(h, n), srp(h, n + 1);
-    k_strength<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, o.amg_theta, strong.p,
-                                                        scount.p);
-    MSS_LAUNCH_CK("k_strength");
-    exclusive_scan(h, scount.p, srp.p, n);
-    int ns = read_int(h, srp.p + n);
-    DBuf<int> sci(h, ns > 0 ? ns : 1);
-    k_fill_strong<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, strong.p, srp.p, sci.p);
-    MSS_LAUNCH_CK("k_fill_strong");
-    DBuf<int> strp, stci;
-    transpose(h, n, n, srp.p, sci.p, nullptr, ns, strp, stci, nullptr);
+    Strength S;
+    strength_graph(h, n, nnz, rp, ci, v, o.amg_theta, S);
     Level& L = H.lev[l];
     // Newton-loop reuse: the level keeps the C/F split of the earlier set-up
     const bool frozen = frozen_cf && l < (int)frozen_cf->size() &&
@@ -735,39 +953,9 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     if (frozen) {
       L.cf = std::move((*frozen_cf)[l]);
     } else {
-    // PMIS; |S_i^T| are the row lengths of the transposed strength graph
-    pc.mark(1);
-    DBuf<int> tcount(h, n);
-    k_row_lengths<<<grid_for(n, 256), 256, 0, h->stream>>>(n, strp.p, tcount.p);
-    MSS_LAUNCH_CK("k_row_lengths");
-    DBuf<double> lam(h, n);
-    DBuf<int> state(h, n), newc(h, n), und(h, 1);
-    fill_int(h, und.p, 0, 1);
-    k_pmis_init<<<grid_for(n, 256), 256, 0, h->stream>>>(n, tcount.p, o.seed, l, lam.p, state.p,
-                                                         und.p);
-    MSS_LAUNCH_CK("k_pmis_init");
-    int undecided = read_int(h, und.p);
-    int rounds = 0;
-    while (undecided > 0) {
-      // three synchronous rounds per read-back: a round with nothing
-      // undecided changes nothing, so the split is the one of round-by-round
-      // checking with fewer host synchronisations
-      for (int r = 0; r < 3; ++r) {
-        if (++rounds > n + 3) fail(MSS_ERR_AMG, "PMIS did not terminate");
-        k_pmis_select<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, strp.p, stci.p,
-                                                               lam.p, state.p, newc.p);
-        MSS_LAUNCH_CK("k_pmis_select");
-        fill_int(h, und.p, 0, 1);
-        k_pmis_update<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, state.p, newc.p,
-                                                               und.p);
-        MSS_LAUNCH_CK("k_pmis_update");
-      }
-      undecided = read_int(h, und.p);
-    }
-    pc.mark(2);
-    L.cf.reset(h, n);
-    k_pmis_finalize<<<grid_for(n, 256), 256, 0, h->stream>>>(n, srp.p, sci.p, state.p, L.cf.p);
-    MSS_LAUNCH_CK("k_pmis_finalize");
+      pc.mark(1);
+      pmis_split(h, n, S, o.seed, l, L.cf);
+      pc.mark(2);
     }
     DBuf<int> cidx(h, n + 1);
     exclusive_scan(h, L.cf.p, cidx.p, n);
@@ -777,28 +965,8 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
       break;
     }
     L.nc = nc;
-    // interpolation
-    DBuf<int> scr_ci(h, nnz), scr_k(h, nnz), plen(h, n);
-    DBuf<double> scr_v(h, nnz);
-    if (n <= 65536 && nnz > 8LL * n) {   // few, long rows: one warp per row
-      k_interp_warp<<<grid_for((long long)n * 32, 256), 256, 0, h->stream>>>(
-          n, rp, ci, v, strong.p, L.cf.p, cidx.p, o.interp_max_elems, scr_ci.p, scr_v.p, scr_k.p,
-          plen.p);
-      MSS_LAUNCH_CK("k_interp_warp");
-    } else {
-      k_interp<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, v, strong.p, L.cf.p, cidx.p,
-                                                        o.interp_max_elems, scr_ci.p, scr_v.p,
-                                                        scr_k.p, plen.p);
-      MSS_LAUNCH_CK("k_interp");
-    }
-    L.prp.reset(h, n + 1);
-    exclusive_scan(h, plen.p, L.prp.p, n);
-    L.nnzP = read_int(h, L.prp.p + n);
-    L.pci.reset(h, L.nnzP > 0 ? L.nnzP : 1);
-    L.pv.reset(h, L.nnzP > 0 ? L.nnzP : 1);
-    k_seg_copy<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, scr_ci.p, scr_v.p, L.prp.p,
-                                                        L.pci.p, L.pv.p);
-    MSS_LAUNCH_CK("k_seg_copy");
+    L.nnzP = classical_interp(h, n, nnz, rp, ci, v, S.strong.p, L.cf.p, cidx.p,
+                              o.interp_max_elems, L.prp, L.pci, L.pv);
     if (learned && l == 0) {
       // learned weights on classical interpolation's pattern (level 0 only)
       std::unique_ptr<GnnGraph, void (*)(GnnGraph*)> g(
@@ -825,6 +993,129 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
   pc.mark(6);
   if (o.smoother == MSS_MCSGS)   // the coarsest level is solved directly, not smoothed
     for (size_t l = 0; l + 1 < H.lev.size(); ++l) level_colours(h, H.lev[l]);
+}
+
+// System AMG of the 2 x 2 block B_ee for CPTR (Sec. 4.2, Eq. CPTRM1): nodal
+// coarsening (PMIS on the Frobenius norms of the blocks), classical
+// interpolation per unknown on the common split, P interleaved without
+// cross-unknown weights, A_c = R (A P) on the scalar interleaved form, read
+// back as 2 x 2 blocks for the next level. Levels are stored in the scalar
+// interleaved form (n = 2 points), with each point's inverse diagonal block
+// for the block Jacobi smoother and the split duplicated per unknown.
+void amg_build_system(Handle* h, Hierarchy& H, int np0, int nnzb0, const int* rp0,
+                      const int* ci0, const double* bv0) {
+  const mss_options& o = h->opt;
+  H.lev.clear();
+  H.lev.reserve(32);
+  H.bs = 2;
+  int np = np0, nnzb = nnzb0;
+  DBuf<int> brp(h, np + 1), bci(h, nnzb);
+  DBuf<double> bv(h, (size_t)4 * nnzb);
+  copy_dev(h, brp.p, rp0, sizeof(int) * ((size_t)np + 1));
+  copy_dev(h, bci.p, ci0, sizeof(int) * (size_t)nnzb);
+  copy_dev(h, bv.p, bv0, sizeof(double) * 4 * (size_t)nnzb);
+  const int max_levels = o.amg_max_levels < 1 ? 1 : (o.amg_max_levels > 25 ? 25 : o.amg_max_levels);
+  for (int l = 0;; ++l) {
+    {
+      Level L;
+      L.n = 2 * np;
+      L.nnz = 4 * nnzb;
+      L.rp.reset(h, 2 * np + 1);
+      L.ci.reset(h, L.nnz);
+      L.v.reset(h, L.nnz);
+      k_b2s<<<grid_for(2 * np, 128), 128, 0, h->stream>>>(np, brp.p, bci.p, bv.p, L.rp.p, L.ci.p,
+                                                          L.v.p);
+      MSS_LAUNCH_CK("k_b2s");
+      L.dinv2.reset(h, (size_t)4 * np);
+      DBuf<int> bad(h, 1);
+      fill_int(h, bad.p, 0x7fffffff, 1);
+      k_dinv2<<<grid_for(np, 256), 256, 0, h->stream>>>(np, brp.p, bci.p, bv.p, L.dinv2.p, bad.p);
+      MSS_LAUNCH_CK("k_dinv2");
+      const int b = read_int(h, bad.p);
+      if (b != 0x7fffffff)
+        fail(MSS_ERR_AMG, "system AMG level of " + std::to_string(np) +
+                              " points: singular 2 x 2 diagonal block at point " +
+                              std::to_string(b));
+      H.lev.push_back(std::move(L));
+    }
+    level_prepare(h, H.lev[l]);
+    if (np <= o.amg_max_coarse || l + 1 >= max_levels) break;
+    // nodal coarsening
+    DBuf<double> nv(h, nnzb);
+    k_block_norm<<<grid_for(np, 128), 128, 0, h->stream>>>(np, brp.p, bci.p, bv.p, nv.p);
+    MSS_LAUNCH_CK("k_block_norm");
+    DBuf<int> cfp;
+    {
+      Strength Sn;
+      strength_graph(h, np, nnzb, brp.p, bci.p, nv.p, o.amg_theta, Sn);
+      pmis_split(h, np, Sn, o.seed, l, cfp);
+    }
+    DBuf<int> cidx(h, np + 1);
+    exclusive_scan(h, cfp.p, cidx.p, np);
+    const int ncp = read_int(h, cidx.p + np);
+    if (ncp == 0 || ncp == np) break;   // coarsening stalled: this level is the coarsest
+    // classical interpolation per unknown on the common split
+    DBuf<int> prpk[2], pcik[2];
+    DBuf<double> pvk[2];
+    for (int k = 0; k < 2; ++k) {
+      DBuf<double> vk(h, nnzb);
+      k_block_entry<<<grid_for(nnzb, 256), 256, 0, h->stream>>>(nnzb, bv.p, 3 * k, vk.p);
+      MSS_LAUNCH_CK("k_block_entry");
+      DBuf<unsigned char> sk(h, nnzb);
+      DBuf<int> scount(h, np);
+      k_strength<<<grid_for(np, 128), 128, 0, h->stream>>>(np, brp.p, bci.p, vk.p, o.amg_theta,
+                                                           sk.p, scount.p);
+      MSS_LAUNCH_CK("k_strength");
+      classical_interp(h, np, nnzb, brp.p, bci.p, vk.p, sk.p, cfp.p, cidx.p, o.interp_max_elems,
+                       prpk[k], pcik[k], pvk[k]);
+    }
+    Level& L = H.lev[l];
+    L.nc = 2 * ncp;
+    L.cf.reset(h, 2 * np);
+    k_dup2<<<grid_for(2 * np, 256), 256, 0, h->stream>>>(np, cfp.p, L.cf.p);
+    MSS_LAUNCH_CK("k_dup2");
+    {
+      DBuf<int> plen(h, 2 * np);
+      k_p2_len<<<grid_for(2 * np, 256), 256, 0, h->stream>>>(np, prpk[0].p, prpk[1].p, plen.p);
+      MSS_LAUNCH_CK("k_p2_len");
+      L.prp.reset(h, 2 * np + 1);
+      exclusive_scan(h, plen.p, L.prp.p, 2 * np);
+      L.nnzP = read_int(h, L.prp.p + 2 * np);
+      L.pci.reset(h, L.nnzP > 0 ? L.nnzP : 1);
+      L.pv.reset(h, L.nnzP > 0 ? L.nnzP : 1);
+      k_p2_fill<<<grid_for(2 * np, 128), 128, 0, h->stream>>>(
+          np, prpk[0].p, pcik[0].p, pvk[0].p, prpk[1].p, pcik[1].p, pvk[1].p, L.prp.p, L.pci.p,
+          L.pv.p);
+      MSS_LAUNCH_CK("k_p2_fill");
+    }
+    transpose(h, 2 * np, 2 * ncp, L.prp.p, L.pci.p, L.pv.p, L.nnzP, L.rrp, L.rci, &L.rv);
+    // Galerkin product on the scalar interleaved form, then its blocks
+    DBuf<int> aprp, apci, acrp, acci;
+    DBuf<double> apv, acv;
+    int apnnz = 0, acnnz = 0;
+    sparse_product(h, 2 * np, L.rp.p, L.ci.p, L.v.p, L.prp.p, L.pci.p, L.pv.p, aprp, apci, apv,
+                   apnnz);
+    sparse_product(h, 2 * ncp, L.rrp.p, L.rci.p, L.rv.p, aprp.p, apci.p, apv.p, acrp, acci, acv,
+                   acnnz);
+    DBuf<int> cnt(h, ncp), nrp(h, ncp + 1);
+    k_s2b<<<grid_for(ncp, 128), 128, 0, h->stream>>>(ncp, acrp.p, acci.p, acv.p, cnt.p, nullptr,
+                                                     nullptr, nullptr, 0);
+    MSS_LAUNCH_CK("k_s2b");
+    exclusive_scan(h, cnt.p, nrp.p, ncp);
+    const int nnzb_c = read_int(h, nrp.p + ncp);
+    DBuf<int> nci(h, nnzb_c > 0 ? nnzb_c : 1);
+    DBuf<double> nbv(h, (size_t)4 * (nnzb_c > 0 ? nnzb_c : 1));
+    fill_double(h, nbv.p, 0.0, (long long)4 * nnzb_c);
+    k_s2b<<<grid_for(ncp, 128), 128, 0, h->stream>>>(ncp, acrp.p, acci.p, acv.p, nullptr, nrp.p,
+                                                     nci.p, nbv.p, 1);
+    MSS_LAUNCH_CK("k_s2b");
+    brp = std::move(nrp);
+    bci = std::move(nci);
+    bv = std::move(nbv);
+    np = ncp;
+    nnzb = nnzb_c;
+  }
+  coarse_inverse(h, H);
 }
 
 }  // namespace mss

@@ -40,7 +40,7 @@ int guarded(mss_handle* hh, F&& f) {
 
 void check_options(const mss_options& o) {
   auto bad = [](const char* what) { fail(MSS_ERR_INVALID_ARG, std::string("option ") + what); };
-  if (o.scheme < MSS_CPTR3 || o.scheme > MSS_ILU0) bad("scheme");
+  if (o.scheme < MSS_CPTR3 || o.scheme > MSS_CPTR) bad("scheme");
   if (o.stage_order != MSS_STAGE_T_FIRST && o.stage_order != MSS_STAGE_P_FIRST)
     bad("stage_order");
   if (o.stage3 != MSS_BILU0 && o.stage3 != MSS_BLOCK_JACOBI) bad("stage3");
@@ -158,6 +158,7 @@ void release_setup(Handle& H) {
   H.fslo.release(); H.fshi.release(); H.cL.release(); H.cG.release(); H.cflag.release();
   H.fv.release(); H.fdinv.release(); H.fcs.release();
   H.rT.release(); H.xT.release(); H.zP.release(); H.vP.release(); H.w.release();
+  H.rE.release(); H.xE.release(); H.rEf.release(); H.xEf.release();
   H.fvh.release(); H.fdinvh.release(); H.cLh.release(); H.cGh.release();
   H.fcsf.release(); H.aptf.release(); H.atpf.release();
   H.rTf.release(); H.xTf.release(); H.zPf.release(); H.vPf.release(); H.wf.release();
@@ -196,10 +197,14 @@ void numeric_setup(Handle& H, const double* vals, bool ordering, std::vector<DBu
   // their own streams while this thread factorises on the handle's stream.
   {
     TraceScope ts(h, TR_SETUP_AMG);
-    DBuf<double> bpp, ctt;
-    if (o.scheme != MSS_ILU0) {
+    DBuf<double> bpp, ctt, bee;
+    if (o.scheme == MSS_CPR || o.scheme == MSS_CPTR3) {
       bpp.reset(h, nnzb);
       extract_subsystem(h, H.p, bpp.p);           // B_PP
+    }
+    if (o.scheme == MSS_CPTR) {
+      bee.reset(h, (size_t)4 * nnzb);
+      extract_pair(h, bee.p);                     // B_ee (Eq. CPTR1)
     }
     if (o.scheme == MSS_CPTR3) {
       ctt.reset(h, nnzb);
@@ -214,7 +219,15 @@ void numeric_setup(Handle& H, const double* vals, bool ordering, std::vector<DBu
     };
     double tp = 0, tt = 0, tb = 0;
     Fork fork(H);
-    if (o.scheme != MSS_ILU0)
+    if (o.scheme == MSS_CPTR)
+      fork.run(0, [&](Handle* a) {
+        amg_build_system(a, H.amgP, N, nnzb, H.rp.p, H.ci.p, bee.p);
+        if (times) {
+          cudaStreamSynchronize(a->stream);
+          tp = since();
+        }
+      });
+    if (o.scheme == MSS_CPR || o.scheme == MSS_CPTR3)
       fork.run(0, [&](Handle* a) {
         amg_build(a, H.amgP, N, nnzb, H.rp.p, H.ci.p, bpp.p, nullptr, cfP);
         if (times) {
@@ -255,6 +268,10 @@ void numeric_setup(Handle& H, const double* vals, bool ordering, std::vector<DBu
     H.vP.reset(h, N);
     H.w.reset(h, (size_t)N * H.nb);
   }
+  if (o.scheme == MSS_CPTR && H.rE.n != (size_t)2 * N) {
+    H.rE.reset(h, (size_t)2 * N);
+    H.xE.reset(h, (size_t)2 * N);
+  }
   if (o.precision == MSS_MIXED) {
     // reduced-precision copies of everything the preconditioner reads
     TraceScope ts(h, TR_SETUP_BILU);
@@ -272,6 +289,10 @@ void numeric_setup(Handle& H, const double* vals, bool ordering, std::vector<DBu
       H.xTf.reset(h, N);
       H.zPf.reset(h, N);
       H.vPf.reset(h, N);
+    }
+    if (o.scheme == MSS_CPTR && H.rEf.n != (size_t)2 * N) {
+      H.rEf.reset(h, (size_t)2 * N);
+      H.xEf.reset(h, (size_t)2 * N);
     }
   }
   if (H.amgT.present()) prepare_tail(h, H.amgT);
@@ -342,6 +363,9 @@ void do_update(Handle& H, const mss_bsr* J, int reuse) {
     fail(MSS_ERR_INVALID_ARG, "reuse must be MSS_REUSE_PATTERN or MSS_REUSE_COARSENING");
   if (J->n_rows != H.N || J->nnzb != H.nnzb)
     fail(MSS_ERR_INVALID_ARG, "the matrix sizes differ from the set-up's");
+  if (reuse == MSS_REUSE_COARSENING && H.opt.scheme == MSS_CPTR)
+    fail(MSS_ERR_INVALID_ARG, "MSS_REUSE_COARSENING keeps scalar AMG splits; CPTR's system "
+                              "AMG is rebuilt (use MSS_REUSE_PATTERN)");
   Handle* h = &H;
   {
     DBuf<int> diff(h, 1);
@@ -563,6 +587,12 @@ int mss_stage_apply(mss_handle* hh, int which, const double* r, double* y) {
       return;
     }
     Hierarchy& A = pick(H, which);
+    if (A.bs == 2) {   // CPTR's first stage (Eq. CPTRM1) on (P, T)
+      gather_pair(&H, r, H.rE.p);
+      vcycle(&H, A, H.rE.p, H.xE.p);
+      scatter_pair_zero(&H, H.xE.p, y);
+      return;
+    }
     int var = which == 0 ? H.t : H.p;
     gather_var(&H, r, var, H.rT.p);
     vcycle(&H, A, H.rT.p, H.xT.p);

@@ -114,10 +114,14 @@ struct Level {
   int ncolour = 0;
   std::vector<int> cstart;
   DBuf<int> mcorder;
+  // system AMG (2 unknowns per point): inverse 2 x 2 diagonal block per point
+  DBuf<double> dinv2;
+  DBuf<float> dinv2f;
 };
 
 struct Hierarchy {
   std::vector<Level> lev;
+  int bs = 1;                 // unknowns per point: 1 scalar AMG, 2 the system AMG of CPTR
   DBuf<double> coarse_inv;    // dense inverse of the coarsest operator, row-major
   DBuf<float> coarse_invf;    // its FP32 copy (mixed precision)
   int nc = 0;                 // size of the coarsest level
@@ -205,6 +209,8 @@ struct Handle {
   DBuf<double> fcs;            // Abar column slices [t | p] per factor block (2 nb)
   // preconditioner work vectors
   DBuf<double> rT, xT, zP, vP, w;
+  DBuf<double> rE, xE;         // CPTR: the (P, T) pair of every cell, interleaved
+  DBuf<float> rEf, xEf;
   // Krylov workspace
   int m = 0;
   DBuf<double> V, Z, bbar, res, hbuf, part;
@@ -312,6 +318,8 @@ void build_scaling(Handle* h, const double* vals, bool col_major);
 void scale_vector(Handle* h, const double* b, double* bbar);
 // var >= 0: Abar[var][var] per block; var = -1: Abar[p][t]; var = -2: Abar[t][p]
 void extract_subsystem(Handle* h, int var, double* out);
+// B_ee of CPTR: the 2 x 2 block Abar[(p, t), (p, t)] of every block (4 per block)
+void extract_pair(Handle* h, double* out);
 
 // amg_setup.cu
 // level 0: the n0-row CSR (rp0, ci0, vals0), read on h's stream. frozen_cf
@@ -320,6 +328,10 @@ void extract_subsystem(Handle* h, int var, double* out);
 void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const int* ci0,
                const double* vals0, const float* learned = nullptr,
                std::vector<DBuf<int>>* frozen_cf = nullptr);
+
+// the system AMG of CPTR on np points of 2 x 2 blocks (bv: 4 per block)
+void amg_build_system(Handle* h, Hierarchy& H, int np, int nnzb, const int* rp, const int* ci,
+                      const double* bv);
 
 // amg_cycle.cu
 // The first Jacobi sweep from zero on level 0 of a hierarchy, x = omega D^-1 b,
@@ -348,6 +360,12 @@ int wait_limit_probe(Handle* h);
 void gather_var(Handle* h, const double* v, int var, double* out, Sweep0<double> s0 = {});
 void gather_var(Handle* h, const double* v, int var, float* out, Sweep0<float> s0 = {});
 void scatter_var_zero(Handle* h, const double* s, int var, double* out);
+// CPTR: the (P, T) pair of every cell to an interleaved vector and back
+void gather_pair(Handle* h, const double* v, double* out);
+void gather_pair(Handle* h, const double* v, float* out);
+template <class C>
+void split_pair(Handle* h, const C* pair, C* vP, C* xT);
+void scatter_pair_zero(Handle* h, const double* pair, double* out);
 void csr_block_pattern_spmv_sub(Handle* h, const double* vals, const double* x,
                                 const double* r, int var, double* out, Sweep0<double> s0 = {});
 void csr_block_pattern_spmv_sub(Handle* h, const float* vals, const float* x, const double* r,

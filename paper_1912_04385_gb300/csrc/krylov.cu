@@ -734,6 +734,13 @@ static void precond_apply_mixed(Handle* h, const double* r, double* y) {
     last_stage_apply(h, r, (const float*)nullptr, h->vPf.p, y);
     return;
   }
+  if (scheme == MSS_CPTR) {
+    gather_pair(h, r, h->rEf.p);
+    vcycle_mixed(h, h->amgP, h->rEf.p, h->xEf.p);
+    split_pair(h, (const float*)h->xEf.p, h->vPf.p, h->xTf.p);
+    last_stage_apply(h, r, h->xTf.p, h->vPf.p, y);
+    return;
+  }
   if (h->opt.stage_order == MSS_STAGE_T_FIRST) {
     gather_var(h, r, h->t, h->rTf.p, sweep0_mixed(h, h->amgT, h->xTf.p));
     vcycle_mixed(h, h->amgT, h->rTf.p, h->xTf.p, true);
@@ -750,7 +757,8 @@ static void precond_apply_mixed(Handle* h, const double* r, double* y) {
   last_stage_apply(h, r, h->xTf.p, h->vPf.p, y);
 }
 
-// y = M^{-1} r: Algorithm 2 (CPTR3), Algorithm 1 (CPR) or the last stage only
+// y = M^{-1} r: Algorithm 2 (CPTR3), Algorithm 1 (CPR), its CPTR form, or the
+// last stage only
 void precond_apply(Handle* h, const double* r, double* y) {
   TraceScope ts(h, TR_APPLY);
   if (h->opt.precision == MSS_MIXED) {
@@ -768,6 +776,15 @@ void precond_apply(Handle* h, const double* r, double* y) {
     gather_var(h, r, h->p, h->rT.p, sweep0(h, h->amgP, h->vP.p));
     vcycle(h, h->amgP, h->rT.p, h->vP.p, true);            // x = M1 r (pressure)
     last_stage_apply(h, r, (const double*)nullptr, h->vP.p, y);          // y = x + M2 (r - Abar x)
+    return;
+  }
+  if (scheme == MSS_CPTR) {
+    // Sec. 4.2: x_e = M_ee^{-1} r_e by the system AMG on (P, T) (Eq. CPTRM1),
+    // then y = x + ilu(Abar)^{-1} (r - Abar x) with x = x_e at (p, t)
+    gather_pair(h, r, h->rE.p);
+    vcycle(h, h->amgP, h->rE.p, h->xE.p);
+    split_pair(h, (const double*)h->xE.p, h->vP.p, h->xT.p);
+    last_stage_apply(h, r, h->xT.p, h->vP.p, y);
     return;
   }
   if (h->opt.stage_order == MSS_STAGE_T_FIRST) {

@@ -89,7 +89,8 @@ __device__ bool gj_inverse(int m, double* a, double* inv) {
 // One thread per cell: W = N^{-1} restricted to the cell, built from the
 // diagonal block D. Only rows p and t of W differ from the identity; they
 // are stored as wrows[i][0][:] (row p) and wrows[i][1][:] (row t).
-// scheme: 0 CPTR3 (Eq. CPTR31 then Eq. CPTR32), 1 CPR (Eq. CPR), 2 none.
+// scheme: 0 CPTR3 (Eq. CPTR31 then Eq. CPTR32), 1 CPR (Eq. CPR), 2 none,
+// 3 CPTR (Eq. CPTR1: the N1 of Eq. CPTR31 alone).
 template <int NB>
 __global__ void k_build_w(const double* __restrict__ vals, const int* __restrict__ diag, int N,
                           int p, int t, int scheme, int col_major, double* __restrict__ wrows,
@@ -127,7 +128,7 @@ __global__ void k_build_w(const double* __restrict__ vals, const int* __restrict
       for (int a = 0; a < nh; ++a) w = w + D[p * NB + h[a]] * inv[a * nh + b];
       wp[h[b]] = -w;
     }
-  } else if (scheme == 0) {
+  } else if (scheme == 0 || scheme == 3) {
     int s[NB];
     int ns = 0;
     for (int k = 0; k < NB; ++k)
@@ -150,6 +151,7 @@ __global__ void k_build_w(const double* __restrict__ vals, const int* __restrict
         wt[s[b]] = -vt;
       }
     }
+    if (scheme == 0) {
     // once-scaled entries B_PP and B_Tp of N1^{-1} D, then the N2 factor
     double bpp = 0.0, btp = 0.0;
     for (int k = 0; k < NB; ++k) {
@@ -162,6 +164,7 @@ __global__ void k_build_w(const double* __restrict__ vals, const int* __restrict
     }
     double c = btp / bpp;
     for (int k = 0; k < NB; ++k) wt[k] = wt[k] - c * wp[k];
+    }
   }
   double* out = wrows + (size_t)i * 2 * NB;
   for (int k = 0; k < NB; ++k) {
@@ -208,7 +211,7 @@ __global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict
 #pragma unroll
   for (int k = 0; k < NB; ++k) acc = acc + w[k] * col[k];
   dst[p * NB] = acc;
-  if (scheme == 0) {
+  if (scheme == 0 || scheme == 3) {
     double acc2 = 0.0;
 #pragma unroll
     for (int k = 0; k < NB; ++k) acc2 = acc2 + w[NB + k] * col[k];
@@ -222,7 +225,7 @@ __global__ void k_scale_vec(const double* __restrict__ b, int N, int p, int t, i
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (long long)N * NB) return;
   int i = (int)(tid / NB), r = (int)(tid % NB);
-  bool scaled_row = scheme != 2 && (r == p || (scheme == 0 && r == t));
+  bool scaled_row = scheme != 2 && (r == p || ((scheme == 0 || scheme == 3) && r == t));
   if (!scaled_row) {
     out[tid] = b[tid];
     return;
@@ -243,6 +246,18 @@ __global__ void k_extract_pt(const double* __restrict__ abar, int nnzb, int nb, 
                              double* __restrict__ out) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < nnzb) out[e] = abar[(size_t)e * nb * nb + p * nb + t];
+}
+
+// B_ee of CPTR: out[4e + 2k + l] = Abar_e[e_k][e_l], e = (p, t)
+__global__ void k_extract_pair(const double* __restrict__ abar, int nnzb, int nb, int p, int t,
+                               double* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnzb) return;
+  const double* a = abar + (size_t)e * nb * nb;
+  out[(size_t)4 * e + 0] = a[p * nb + p];
+  out[(size_t)4 * e + 1] = a[p * nb + t];
+  out[(size_t)4 * e + 2] = a[t * nb + p];
+  out[(size_t)4 * e + 3] = a[t * nb + t];
 }
 
 template <int NB>
@@ -319,6 +334,12 @@ void extract_subsystem(Handle* h, int var, double* out) {
                                                                 col, out);
     MSS_LAUNCH_CK("k_extract_pt");
   }
+}
+
+void extract_pair(Handle* h, double* out) {
+  k_extract_pair<<<grid_for(h->nnzb, 256), 256, 0, h->stream>>>(h->abar.p, h->nnzb, h->nb, h->p,
+                                                                 h->t, out);
+  MSS_LAUNCH_CK("k_extract_pair");
 }
 
 }  // namespace mss

@@ -19,7 +19,7 @@ OK = 0
 ERR_INVALID_ARG, ERR_SINGULAR_BLOCK, ERR_NOT_CONVERGED, ERR_BREAKDOWN = -1, -2, -3, -4
 ERR_CUDA, ERR_OOM, ERR_AMG, ERR_NOT_SETUP = -5, -6, -7, -8
 
-SCHEMES = {"cptr3": 0, "cpr": 1, "ilu0": 2}
+SCHEMES = {"cptr3": 0, "cpr": 1, "ilu0": 2, "cptr": 3}
 SMOOTHERS = {"jacobi": 0, "chebyshev": 1, "mcsgs": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 DRIVERS = {"host": 0, "graph": 1}

@@ -78,7 +78,7 @@ def test_library_and_oracle_defaults_agree(lib_path):
     lo, oo = mss.options(), oracle.options()
     for lk, ok in _SHARED.items():
         assert getattr(lo, lk) == getattr(oo, ok), (lk, getattr(lo, lk), getattr(oo, ok))
-    for name in ("cptr3", "cpr", "ilu0"):
+    for name in ("cptr3", "cpr", "ilu0", "cptr"):
         assert mss.SCHEMES[name] == oracle.oracle.SCHEME[name]
     for name in ("jacobi", "chebyshev", "mcsgs"):
         assert mss.SMOOTHERS[name] == oracle.oracle.SMOOTHER[name]

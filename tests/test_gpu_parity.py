@@ -73,7 +73,7 @@ def _sys(c):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("scheme", ["cptr3", "cpr", "ilu0"])
+@pytest.mark.parametrize("scheme", ["cptr3", "cpr", "ilu0", "cptr"])
 def test_scaled_matrix_bit_exact(mss, case, scheme):
     s = _sys(CASES[case])
     g = _gpu(mss, s, scheme=scheme)
@@ -281,7 +281,8 @@ def test_residual_norm_entry_point(mss, nb):
 @pytest.mark.parametrize("scheme,smoother,precision", [("cptr3", "jacobi", "fp64"),
                                                        ("cptr3", "chebyshev", "fp64"),
                                                        ("cptr3", "mcsgs", "fp64"),
-                                                       ("cpr", "jacobi", "fp64")])
+                                                       ("cpr", "jacobi", "fp64"),
+                                                       ("cptr", "jacobi", "fp64")])
 def test_larger_hierarchy(mss, scheme, smoother, precision):
     # a 6,144-cell system: several AMG levels above 4,096 rows, stage and
     # whole-preconditioner parity, and the FGMRES iteration bar
@@ -366,3 +367,42 @@ def test_multicolour_gauss_seidel(mss, case, nu):
     gg = _gpu(mss, s, driver="graph", **kw)
     xg, ig = gg.solve(_t(s.b), tol=1e-8, maxit=400)
     assert ig["iters"] == ih["iters"] and torch.equal(xg, xh)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_cptr_with_system_amg(mss, case):
+    # Sec. 4.2: the system AMG of B_ee bit for bit (split, P, every Galerkin
+    # operator in the interleaved scalar form), the first stage, the last
+    # stage and the whole two-stage operator within 1e-12, FGMRES within +-1,
+    # graph = host loop
+    s = _sys(CASES[case])
+    kw = dict(scheme="cptr", amg_max_coarse=40, restart=100)
+    g = _gpu(mss, s, **kw)
+    o = _orc(s, scheme="cptr", max_coarse=40, restart=100)
+    lg, lo = g.amg_levels(1), o.amg_levels(1)
+    assert len(lg) == len(lo) and g.lib.mss_amg_num_levels(g.h, 0) == 0
+    for a, b in zip(lg, lo):
+        for k in range(3):
+            assert np.array_equal(_n(a["A"][k]), b.A[k]), k
+        if b.cf is not None:
+            assert np.array_equal(_n(a["cf"]), b.cf)
+            for k in range(3):
+                assert np.array_equal(_n(a["P"][k]), b.P[k])
+    r = np.random.default_rng(case).standard_normal(s.n_cells * s.nb)
+    rt = _t(r)
+    for which in (1, 2):
+        assert _rel(_n(g.stage(which, rt)), o.stage(which, r)) < APPLY_TOL, which
+    assert _rel(_n(g.apply(rt)), o.apply(r)) < APPLY_TOL
+    with pytest.raises(mss.MssError):
+        g.stage(0, rt)                      # CPTR has no temperature stage
+    xo, io = o.fgmres(o.scale_rhs(s.b), tol=1e-8, maxit=400, restart=100)
+    xh, ih = g.solve(_t(s.b), tol=1e-8, maxit=400)
+    assert io["status"] == 0 and ih["status"] == 0
+    assert abs(ih["iters"] - io["iters"]) <= 1, (ih["iters"], io["iters"])
+    gg = _gpu(mss, s, driver="graph", **kw)
+    xg, ig = gg.solve(_t(s.b), tol=1e-8, maxit=400)
+    assert ig["iters"] == ih["iters"] and torch.equal(xg, xh)
+    # the mixed form (BF16 hierarchy, FP32 sweeps) reaches the FP64 tolerance
+    gm = _gpu(mss, s, precision="mixed", **kw)
+    xm, im = gm.solve(_t(s.b), tol=1e-8, maxit=400)
+    assert im["status"] == 0 and im["rel_res_true"] <= 1e-8
