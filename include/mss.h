@@ -49,6 +49,10 @@ extern "C" {
 #define MSS_ERR_AMG (-7)            /* AMG set-up failed (coarsest level too large, ...) */
 #define MSS_ERR_NOT_SETUP (-8)      /* handle has no set-up, or another matrix was passed */
 
+/* Largest cell block size nb the library takes (the paper's primary systems
+ * have 14 unknowns per cell, Sec. 5.1). */
+#define MSS_MAX_NB 16
+
 /* ---- option values ------------------------------------------------------ */
 enum { MSS_CPTR3 = 0, MSS_CPR = 1, MSS_ILU0 = 2, MSS_CPTR = 3 }; /* preconditioner scheme */
 enum { MSS_STAGE_T_FIRST = 0, MSS_STAGE_P_FIRST = 1 }; /* CPTR3 stage order */
@@ -197,7 +201,7 @@ void mss_destroy(mss_handle* h);
  * copied or consumed during the call;
  * the caller may free them afterwards, except that mss_fgmres_solve checks
  * that it receives the same mss_bsr (pointers and sizes). `opt` may be NULL
- * (defaults). nb in [2, 8] (CPTR3 needs nb >= 2). Errors: INVALID_ARG (bad
+ * (defaults). nb in [2, MSS_MAX_NB]. Errors: INVALID_ARG (bad
  * sizes, pattern, layout or option), SINGULAR_BLOCK (a cell block needs
  * pivoting), AMG, OOM, CUDA. */
 int mss_setup(mss_handle* h, const mss_bsr* J, int nb, mss_layout layout,

@@ -304,7 +304,7 @@ void do_setup(Handle& H, const mss_bsr* J, int nb, mss_layout layout, const mss_
   auto t0 = std::chrono::steady_clock::now();
   if (!J || !J->row_ptr || !J->col_idx || !J->vals) fail(MSS_ERR_INVALID_ARG, "null matrix");
   if (J->n_rows < 1 || J->nnzb < J->n_rows) fail(MSS_ERR_INVALID_ARG, "bad matrix sizes");
-  if (nb < 2 || nb > 8) fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 8]");
+  if (nb < 2 || nb > MSS_MAX_NB) fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 16]");
   if (layout.p_idx < 0 || layout.p_idx >= nb || layout.t_idx < 0 || layout.t_idx >= nb ||
       layout.p_idx == layout.t_idx)
     fail(MSS_ERR_INVALID_ARG, "p_idx and t_idx must be distinct indices in [0, nb)");
@@ -624,7 +624,7 @@ int mss_solve_host(mss_handle* hh, const mss_bsr* Jh, int nb, mss_layout layout,
     Handle* h = &H;
     if (!Jh || !Jh->row_ptr || !Jh->col_idx || !Jh->vals || !b_host || !x_host)
       fail(MSS_ERR_INVALID_ARG, "null host pointer");
-    if (Jh->n_rows < 1 || Jh->nnzb < Jh->n_rows || nb < 2 || nb > 8)
+    if (Jh->n_rows < 1 || Jh->nnzb < Jh->n_rows || nb < 2 || nb > MSS_MAX_NB)
       fail(MSS_ERR_INVALID_ARG, "bad sizes");
     const size_t N = (size_t)Jh->n_rows, nnzb = (size_t)Jh->nnzb, nb2 = (size_t)nb * nb;
     if (H.host_rp.n < N + 1) H.host_rp.reset(h, N + 1);

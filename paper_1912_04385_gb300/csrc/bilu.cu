@@ -243,15 +243,20 @@ __device__ __forceinline__ void st_row(double* p, const double (&x)[NB]) {
 // instructions per row than NB lanes per strip, so it is the faster form for
 // colours too small to fill the SMs, where the row-by-row latency of each
 // strip decides the time.
+// warps per CTA of the warp-per-strip factorisation: its shared work blocks
+// (3 nb x nb per warp) stay under the 48 KB static limit
 template <int NB>
-__global__ void __launch_bounds__(256)
+constexpr int factor_warps() { return NB <= 12 ? 8 : 4; }
+
+template <int NB>
+__global__ void __launch_bounds__(32 * factor_warps<NB>())
 k_bilu_factor_warp(int s0, int s1, const int* __restrict__ st_first, const int* __restrict__ st_len,
               const int* __restrict__ frp, const int* __restrict__ fdp,
               const int* __restrict__ fpos, double* __restrict__ fv,
               double* __restrict__ fdinv, int diag_only, int* __restrict__ bad) {
   constexpr int B2 = NB * NB;
   constexpr int W2 = 2 * NB;
-  __shared__ double smem[8][3 * B2];
+  __shared__ double smem[factor_warps<NB>()][3 * B2];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long k = s0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (k >= s1) return;                       // uniform per warp
@@ -989,7 +994,8 @@ void bilu_numeric_nb(Handle* h) {
         form == MSS_FACTOR_WARP ||
         (form == MSS_FACTOR_AUTO && (long long)(s1 - s0) < (long long)kSmallColour * G * h->num_sms);
     if (warp_form) {
-      k_bilu_factor_warp<NB><<<grid_for((long long)(s1 - s0) * 32, 256), 256, 0, h->stream>>>(
+      constexpr int FT = 32 * factor_warps<NB>();
+      k_bilu_factor_warp<NB><<<grid_for((long long)(s1 - s0) * 32, FT), FT, 0, h->stream>>>(
           s0, s1, h->st_first.p, h->st_len.p, h->frp.p, h->fdp.p, h->fpos.p, h->fv.p,
           h->fdinv.p, bjac ? 1 : 0, bad.p);
       MSS_LAUNCH_CK("k_bilu_factor_warp");

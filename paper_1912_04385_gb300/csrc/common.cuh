@@ -278,7 +278,7 @@ template <class C>
 __device__ __forceinline__ C cvt(__nv_bfloat16 x) { return (C)__bfloat162float(x); }
 
 // ---- launch helpers --------------------------------------------------------
-// Dispatch a call templated on the block size NB (2..8).
+// Dispatch a call templated on the block size NB (2..MSS_MAX_NB).
 #define MSS_NB_DISPATCH(NBV, CALL)                                     \
   switch (NBV) {                                                       \
     case 2: { constexpr int NB = 2; CALL; } break;                     \
@@ -288,7 +288,15 @@ __device__ __forceinline__ C cvt(__nv_bfloat16 x) { return (C)__bfloat162float(x
     case 6: { constexpr int NB = 6; CALL; } break;                     \
     case 7: { constexpr int NB = 7; CALL; } break;                     \
     case 8: { constexpr int NB = 8; CALL; } break;                     \
-    default: fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 8]");        \
+    case 9: { constexpr int NB = 9; CALL; } break;                     \
+    case 10: { constexpr int NB = 10; CALL; } break;                   \
+    case 11: { constexpr int NB = 11; CALL; } break;                   \
+    case 12: { constexpr int NB = 12; CALL; } break;                   \
+    case 13: { constexpr int NB = 13; CALL; } break;                   \
+    case 14: { constexpr int NB = 14; CALL; } break;                   \
+    case 15: { constexpr int NB = 15; CALL; } break;                   \
+    case 16: { constexpr int NB = 16; CALL; } break;                   \
+    default: fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 16]");       \
   }
 
 inline unsigned grid_for(long long n, int threads) {

@@ -105,7 +105,7 @@ void check_residual_args(const mss_bsr* J, int nb, const double* b, const double
   if (!J || !J->row_ptr || !J->col_idx || !J->vals || !b || !x || !norms)
     fail(MSS_ERR_INVALID_ARG, "null pointer");
   if (J->n_rows < 1 || J->nnzb < J->n_rows) fail(MSS_ERR_INVALID_ARG, "bad matrix sizes");
-  if (nb < 2 || nb > 8) fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 8]");
+  if (nb < 2 || nb > MSS_MAX_NB) fail(MSS_ERR_INVALID_ARG, "nb must be in [2, 16]");
 }
 
 void residual_norms(cudaStream_t s, const mss_bsr* J, int nb, const double* b, const double* x,

@@ -207,7 +207,7 @@ def test_host_solve_matches_device_solve(mss):
     assert np.array_equal(xh, _n(xd))
 
 
-@pytest.mark.parametrize("nb", [2, 3, 7, 8])
+@pytest.mark.parametrize("nb", [2, 3, 7, 8, 9, 10, 13, 14, 16])
 def test_block_sizes(mss, nb):
     s = sy.make_system(19, 17, nb, pe=1.0, seed=nb)
     g = _gpu(mss, s, amg_max_coarse=30)
@@ -406,3 +406,30 @@ def test_cptr_with_system_amg(mss, case):
     gm = _gpu(mss, s, precision="mixed", **kw)
     xm, im = gm.solve(_t(s.b), tol=1e-8, maxit=400)
     assert im["status"] == 0 and im["rel_res_true"] <= 1e-8
+
+
+@pytest.mark.parametrize("nb,p,t", [(14, 0, 1), (12, 5, 2), (16, 0, 1)])
+@pytest.mark.parametrize("scheme", ["cptr3", "cpr", "cptr"])
+def test_paper_block_size(mss, nb, p, t, scheme):
+    # the paper's primary systems have 14 unknowns per cell (Sec. 5.1): the
+    # scaling bit for bit, both factorisation forms equal, every stage and
+    # the whole operator within 1e-12, FGMRES within +-1
+    s = sy.make_system(23, 19, nb, pe=10.0, sigma=1.0, band=True, seed=nb, p_idx=p, t_idx=t)
+    kw = dict(scheme=scheme, amg_max_coarse=40, restart=100)
+    g = _gpu(mss, s, **kw)
+    o = _orc(s, scheme=scheme, max_coarse=40, restart=100)
+    assert np.array_equal(_n(g.scaled()), o.scaled()[0])
+    gw = _gpu(mss, s, factor_form="warp", **kw)
+    fl, dl = g.bilu_factors()
+    fw, dw = gw.bilu_factors()
+    assert torch.equal(fl, fw) and torch.equal(dl, dw)
+    r = np.random.default_rng(nb).standard_normal(s.n_cells * nb)
+    rt = _t(r)
+    stages = [2, 1] + ([0] if scheme == "cptr3" else [])
+    for which in stages:
+        assert _rel(_n(g.stage(which, rt)), o.stage(which, r)) < APPLY_TOL, which
+    assert _rel(_n(g.apply(rt)), o.apply(r)) < APPLY_TOL
+    xo, io = o.fgmres(o.scale_rhs(s.b), tol=1e-8, maxit=400, restart=100)
+    xg, ig = g.solve(_t(s.b), tol=1e-8, maxit=400)
+    assert io["status"] == 0 and ig["status"] == 0
+    assert abs(ig["iters"] - io["iters"]) <= 1, (ig["iters"], io["iters"])
