@@ -71,6 +71,13 @@ def args_():
     return ap.parse_args()
 
 
+def leg_steps(a, cap):
+    """Timed steps of an auxiliary leg: the run's step count, at most cap (the
+    headline keeps the run's count; the legs around it must not multiply the
+    run's length)."""
+    return max(1, min(a.steps, cap))
+
+
 def workload_config(a):
     return {"workload": f"cptr3-fgmres{a.restart}-{a.n}x{a.n}-nb6", "grid": [a.n, a.n], "nb": 6,
             "cells": a.n * a.n, "pe": list(PES), "sigma": 2.0, "corr_len": 16, "band": True,
@@ -362,11 +369,12 @@ def mixed_leg(a, dev, solver, torch, stream):
                 r, bn = solver.residual_norm(rp, ci, v, 6, b, x)
                 rels.append(r / bn)
 
-    for _ in range(max(1, a.warmup)):
+    steps = leg_steps(a, 5)
+    for _ in range(max(1, min(a.warmup, 2))):
         step(False)
     torch.cuda.synchronize()
     ms = 0.0
-    for _ in range(a.steps):
+    for _ in range(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for rp, ci, v, b in dev:
@@ -388,7 +396,7 @@ def mixed_leg(a, dev, solver, torch, stream):
     tr = solver.trace_read(reset=True)
     solver.trace(False)
     n_apply, apply_ms = tr["apply"]
-    return {"ms_per_system": round(ms / (a.steps * len(dev)), 3),
+    return {"ms_per_system": round(ms / (steps * len(dev)), 3), "steps": steps,
             "iters": [i["iters"] for i in infos],
             "setup_ms_mean": round(float(np.mean([i["setup_ms"] for i in infos])), 3),
             "solve_ms_mean": round(float(np.mean([i["solve_ms"] for i in infos])), 3),
@@ -415,13 +423,14 @@ def variant_leg(a, dev, solver, torch, stream, **kw):
             if infos is not None:
                 infos.append(info)
 
-    for _ in range(max(1, a.warmup)):
+    steps = leg_steps(a, 2)
+    for _ in range(1):
         step(opts)
     torch.cuda.synchronize()
     infos = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(a.steps):
+    for _ in range(steps):
         step(opts, infos)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -434,7 +443,7 @@ def variant_leg(a, dev, solver, torch, stream, **kw):
     solver.trace(False)
     n_apply, apply_ms = tr["apply"]
     n_vc, vc_ms = tr["vcycle"]
-    return {"options": kw, "ms_per_system": round(ms / (a.steps * len(dev)), 3),
+    return {"options": kw, "ms_per_system": round(ms / (steps * len(dev)), 3), "steps": steps,
             "iters": [i["iters"] for i in infos[:len(dev)]],
             "status": [i["status"] for i in infos[:len(dev)]],
             "setup_ms_mean": round(float(np.mean([i["setup_ms"] for i in infos])), 3),
@@ -559,7 +568,7 @@ def mixed_config_leg(a, solver, torch, stream):
             solver.solve(b, tol=a.tol, maxit=a.maxit)
         torch.cuda.synchronize()
         ms, infos = 0.0, []
-        for _ in range(a.steps):
+        for _ in range(leg_steps(a, 3)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             solver.setup(rp, ci, v, 6, 0, 1, opts=opts)
@@ -582,7 +591,7 @@ def mixed_config_leg(a, solver, torch, stream):
         tr = solver.trace_read(reset=True)
         solver.trace(False)
         n_apply, apply_ms = tr["apply"]
-        res[prec] = {"ms": round(ms / a.steps, 3), "iters": infos[-1]["iters"],
+        res[prec] = {"ms": round(ms / leg_steps(a, 3), 3), "iters": infos[-1]["iters"],
                      "setup_ms": round(infos[-1]["setup_ms"], 3),
                      "solve_ms": round(infos[-1]["solve_ms"], 3),
                      "apply_ms_mean": round(apply_ms / max(n_apply, 1), 4),
@@ -699,7 +708,7 @@ def batch_leg(a, torch):
     B = mss.Batch(lanes=a.batch_lanes, autotune=True)
     B.solve(dev, tol=a.tol, maxit=a.maxit, restart=a.restart)
     walls, lat_b, its_b = [], [], []
-    for _ in range(max(1, a.steps)):
+    for _ in range(leg_steps(a, 3)):
         t0 = time.perf_counter()
         xs, res, inf = B.solve(dev, tol=a.tol, maxit=a.maxit, restart=a.restart)
         walls.append((time.perf_counter() - t0) * 1e3)
