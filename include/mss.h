@@ -57,7 +57,7 @@ extern "C" {
 enum { MSS_CPTR3 = 0, MSS_CPR = 1, MSS_ILU0 = 2, MSS_CPTR = 3 }; /* preconditioner scheme */
 enum { MSS_STAGE_T_FIRST = 0, MSS_STAGE_P_FIRST = 1 }; /* CPTR3 stage order */
 enum { MSS_BILU0 = 0, MSS_BLOCK_JACOBI = 1 };        /* last stage */
-enum { MSS_MULTICOLOR = 0, MSS_STRIPS = 2 };         /* block ILU(0) ordering */
+enum { MSS_MULTICOLOR = 0, MSS_STRIPS = 2, MSS_STRIPS_JP = 3 }; /* block ILU(0) ordering */
 enum { MSS_JACOBI = 0, MSS_CHEBYSHEV = 1, MSS_MCSGS = 3 }; /* AMG smoother (2: lexicographic
                                                        symmetric Gauss-Seidel, sequential,
                                                        has no GPU form) */
@@ -98,8 +98,14 @@ typedef struct {
   int32_t stage_order;      /* MSS_STAGE_T_FIRST (Algorithm 2, default) | P first */
   int32_t stage3;           /* MSS_BILU0 (default) | MSS_BLOCK_JACOBI */
   int32_t ilu_order;        /* MSS_STRIPS (default): strips of ilu_strip consecutive
-                               cells, coloured, natural order inside a strip;
-                               MSS_MULTICOLOR: every cell coloured on its own */
+                               cells, coloured first-fit in strip order (each
+                               strip the smallest colour none of its lower-index
+                               adjacent strips has: two colours on a structured
+                               grid), colour-major, natural order inside a strip;
+                               MSS_STRIPS_JP: the same strips coloured by
+                               Jones-Plassmann (SplitMix64 priorities, `seed`);
+                               MSS_MULTICOLOR: every cell coloured on its own
+                               (Jones-Plassmann) */
   int32_t smoother;         /* MSS_JACOBI (default) | MSS_CHEBYSHEV | MSS_MCSGS:
                                symmetric Gauss-Seidel, the smoother of the paper's
                                AMG (Sec. 5.1), in multicolour form: per level the

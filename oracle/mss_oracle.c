@@ -54,7 +54,9 @@ typedef struct {
   int stage_order;   /* 0: T stage then P stage (Alg. 2 order); 1: P then T */
   int exact_sub;     /* 1: M_TT = C_TT^-1 and M_PP = B_PP^-1 by dense LU */
   int stage3;        /* 0: block ILU(0) of the scaled matrix, 1: block Jacobi */
-  int ilu_order;     /* 0: multicolour (Jones-Plassmann), 1: natural, 2: strips */
+  int ilu_order;     /* 0: multicolour (Jones-Plassmann), 1: natural, 2: strips
+                        coloured first-fit in strip order, 3: strips coloured by
+                        Jones-Plassmann */
   int smoother;      /* 0: damped Jacobi, 1: Chebyshev, 2: symmetric Gauss-Seidel,
                         3: multicolour symmetric Gauss-Seidel */
   int nu_pre, nu_post;
@@ -1197,9 +1199,44 @@ static void bilu_free(bilu_t* f) {
   free(f);
 }
 
-/* Strip colouring: cells are grouped into strips of `strip` consecutive
- * indices, and the strips are coloured by Jones-Plassmann on the strip
- * graph (strips a != b adjacent when a block couples a cell of a to a cell
+/* First-fit strip colouring (the default strip order, a reading: the paper
+ * does not fix the block ILU(0) ordering): cells are grouped into strips of
+ * `strip` consecutive indices; in strip order, each strip takes the
+ * smallest colour that none of its lower-index adjacent strips has (strips
+ * a != b adjacent when a block couples a cell of a to a cell of b). Always a
+ * proper colouring; on a structured grid's strip graph (bipartite) it needs
+ * two colours. */
+static int strip_colour_firstfit(int n, const int* rp, const int* ci, int strip, int* colour,
+                                 int* ncol_out) {
+  if (strip < 1) return OR_ERR_ARG;
+  int ns = (n + strip - 1) / strip, ncol = 0;
+  int* sc = (int*)malloc(sizeof(int) * (size_t)(ns > 0 ? ns : 1));
+  if (!sc) return OR_ERR_MEM;
+  for (int a = 0; a < ns; ++a) {
+    int lo = a * strip, hi = lo + strip < n ? lo + strip : n;
+    for (int c = 0;; ++c) {
+      int used = 0;
+      for (int i = lo; i < hi && !used; ++i)
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+          int b = ci[e] / strip;
+          if (b < a && sc[b] == c) { used = 1; break; }
+        }
+      if (!used) {
+        sc[a] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+        break;
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) colour[i] = sc[i / strip];
+  *ncol_out = ncol;
+  free(sc);
+  return OR_OK;
+}
+
+/* Jones-Plassmann strip colouring: cells are grouped into strips of `strip`
+ * consecutive indices, and the strips are coloured by Jones-Plassmann on the
+ * strip graph (strips a != b adjacent when a block couples a cell of a to a cell
  * of b), with SplitMix64 priorities (key 0xFFFE<<32 | strip): per
  * synchronous round every uncoloured strip whose (priority, index) beats all
  * uncoloured adjacent strips takes the smallest colour unused by its
@@ -1279,6 +1316,8 @@ static int bilu_factor(int n, int nb, const int* rp, const int* ci, const double
   if (order == 0) {
     if ((st = jp_colour(n, rp, ci, seed, f->colour, &f->ncol)) != OR_OK) { bilu_free(f); return st; }
   } else if (order == 2) {
+    if ((st = strip_colour_firstfit(n, rp, ci, strip, f->colour, &f->ncol)) != OR_OK) { bilu_free(f); return st; }
+  } else if (order == 3) {
     if ((st = strip_colour(n, rp, ci, strip, seed, f->colour, &f->ncol)) != OR_OK) { bilu_free(f); return st; }
   } else {
     f->ncol = n > 0 ? 1 : 0;

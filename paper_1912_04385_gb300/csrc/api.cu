@@ -44,7 +44,8 @@ void check_options(const mss_options& o) {
   if (o.stage_order != MSS_STAGE_T_FIRST && o.stage_order != MSS_STAGE_P_FIRST)
     bad("stage_order");
   if (o.stage3 != MSS_BILU0 && o.stage3 != MSS_BLOCK_JACOBI) bad("stage3");
-  if (o.ilu_order != MSS_MULTICOLOR && o.ilu_order != MSS_STRIPS) bad("ilu_order");
+  if (o.ilu_order != MSS_MULTICOLOR && o.ilu_order != MSS_STRIPS && o.ilu_order != MSS_STRIPS_JP)
+    bad("ilu_order");
   if (o.ilu_strip < 1 || o.ilu_strip > 1024) bad("ilu_strip (1..1024)");
   if (o.orthog != MSS_CGS1 && o.orthog != MSS_CGS2) bad("orthog");
   if (o.smoother != MSS_JACOBI && o.smoother != MSS_CHEBYSHEV && o.smoother != MSS_MCSGS)

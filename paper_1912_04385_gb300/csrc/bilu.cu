@@ -93,6 +93,34 @@ __global__ void k_jp_commit(int ns, const int* __restrict__ pick, int* __restric
   }
 }
 
+// First-fit colouring of strips needs, per strip, its distinct lower-index
+// adjacent strips; up to kStripNbrs of them are listed (cnt = -1: more)
+constexpr int kStripNbrs = 32;
+
+__global__ void k_strip_lower(int ns, int S, int n, const int* __restrict__ rp,
+                              const int* __restrict__ ci, int* __restrict__ nbr,
+                              int* __restrict__ cnt) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= ns) return;
+  int* out = nbr + (size_t)a * kStripNbrs;
+  int m = 0;
+  const int lo = a * S, hi = min(lo + S, n);
+  for (int i = lo; i < hi && m >= 0; ++i)
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int b = ci[k] / S;
+      if (b >= a) continue;
+      bool seen = false;
+      for (int t = 0; t < m && !seen; ++t) seen = out[t] == b;
+      if (seen) continue;
+      if (m == kStripNbrs) {
+        m = -1;
+        break;
+      }
+      out[m++] = b;
+    }
+  cnt[a] = m;
+}
+
 __global__ void k_cell_colour(int n, int S, const int* __restrict__ scol, int* __restrict__ col) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) col[i] = scol[i / S];
@@ -864,7 +892,7 @@ void bilu_setup_nb(Handle* h) {
   const int N = h->N;
   const int nnzb = h->nnzb;
   const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
-  const bool strips = !bjac && h->opt.ilu_order == MSS_STRIPS;
+  const bool strips = !bjac && (h->opt.ilu_order == MSS_STRIPS || h->opt.ilu_order == MSS_STRIPS_JP);
   const int S = strips ? h->opt.ilu_strip : 1;
   const int ns = (N + S - 1) / S;
   DBuf<int> scol(h, ns);
@@ -875,6 +903,52 @@ void bilu_setup_nb(Handle* h) {
   if (bjac) {
     fill_int(h, scol.p, 0, ns);
     h->ncol = 1;
+  } else if (strips && h->opt.ilu_order == MSS_STRIPS) {
+    // first-fit in strip order: each strip takes the smallest colour none of
+    // its lower-index adjacent strips has (two colours on a structured
+    // grid). The device lists the neighbours; the host walks the strips.
+    DBuf<int> nbr(h, (size_t)ns * kStripNbrs), cnt(h, ns);
+    k_strip_lower<<<grid_for(ns, 128), 128, 0, h->stream>>>(ns, S, N, h->rp.p, h->ci.p, nbr.p,
+                                                            cnt.p);
+    MSS_LAUNCH_CK("k_strip_lower");
+    std::vector<int> hn((size_t)ns * kStripNbrs), hc(ns), sc(ns);
+    MSS_CK(cudaMemcpyAsync(hn.data(), nbr.p, sizeof(int) * hn.size(), cudaMemcpyDeviceToHost,
+                           h->stream));
+    MSS_CK(cudaMemcpyAsync(hc.data(), cnt.p, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost,
+                           h->stream));
+    MSS_CK(cudaStreamSynchronize(h->stream));
+    std::vector<int> hrp, hci;               // the cell pattern, only for long lists
+    std::vector<unsigned char> used;
+    int ncol = 0;
+    for (int a = 0; a < ns; ++a) {
+      used.assign((size_t)ncol + 1, 0);
+      if (hc[a] >= 0) {
+        for (int t = 0; t < hc[a]; ++t) used[sc[hn[(size_t)a * kStripNbrs + t]]] = 1;
+      } else {
+        if (hrp.empty()) {
+          hrp.resize((size_t)N + 1);
+          hci.resize((size_t)nnzb);
+          MSS_CK(cudaMemcpy(hrp.data(), h->rp.p, sizeof(int) * hrp.size(),
+                            cudaMemcpyDeviceToHost));
+          MSS_CK(cudaMemcpy(hci.data(), h->ci.p, sizeof(int) * hci.size(),
+                            cudaMemcpyDeviceToHost));
+        }
+        const int lo = a * S, hi = std::min(lo + S, N);
+        for (int i = lo; i < hi; ++i)
+          for (int k = hrp[i]; k < hrp[i + 1]; ++k) {
+            const int b = hci[k] / S;
+            if (b < a) used[sc[b]] = 1;
+          }
+      }
+      int c = 0;
+      while (c <= ncol && used[c]) ++c;
+      sc[a] = c;
+      if (c + 1 > ncol) ncol = c + 1;
+    }
+    MSS_CK(cudaMemcpyAsync(scol.p, sc.data(), sizeof(int) * ns, cudaMemcpyHostToDevice,
+                           h->stream));
+    MSS_CK(cudaStreamSynchronize(h->stream));   // sc lives on this frame
+    h->ncol = ncol;
   } else {
     fill_int(h, scol.p, -1, ns);
     DBuf<int> pick(h, ns), left(h, 1), maxcol(h, 1);
@@ -971,7 +1045,7 @@ void bilu_numeric_nb(Handle* h) {
   const int N = h->N;
   const int nnzb = h->nnzb;
   const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
-  const bool strips = !bjac && h->opt.ilu_order == MSS_STRIPS;
+  const bool strips = !bjac && (h->opt.ilu_order == MSS_STRIPS || h->opt.ilu_order == MSS_STRIPS_JP);
   const int S = strips ? h->opt.ilu_strip : 1;
   {
     long long tot = (long long)nnzb * NB * NB;
@@ -1049,7 +1123,9 @@ void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, con
   constexpr int RPW = 32 / NB;
   const bool bjac = h->opt.stage3 == MSS_BLOCK_JACOBI;
   // strips longer than one cell carry in-strip couplings (chain passes)
-  const bool chains = !bjac && h->opt.ilu_order == MSS_STRIPS && h->opt.ilu_strip > 1;
+  const bool chains = !bjac &&
+                      (h->opt.ilu_order == MSS_STRIPS || h->opt.ilu_order == MSS_STRIPS_JP) &&
+                      h->opt.ilu_strip > 1;
   const int T = h->tb;   // any multiple of 32: results do not depend on it
   for (int c = 0; c < h->ncol; ++c) {
     const int q0 = h->cstart[c], q1 = h->cstart[c + 1];

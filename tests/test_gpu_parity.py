@@ -106,7 +106,7 @@ def test_amg_hierarchy_bit_exact(mss, case):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("order,strip", [(2, 32), (2, 5), (0, 1)])
+@pytest.mark.parametrize("order,strip", [(2, 32), (2, 5), (3, 32), (3, 5), (0, 1)])
 def test_ordering_bit_exact(mss, case, order, strip):
     s = _sys(CASES[case])
     g = _gpu(mss, s, ilu_order=order, ilu_strip=strip)
@@ -119,7 +119,7 @@ def test_ordering_bit_exact(mss, case, order, strip):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("order,strip", [(2, 32), (2, 5), (0, 1)])
+@pytest.mark.parametrize("order,strip", [(2, 32), (2, 5), (3, 32), (0, 1)])
 def test_factor_forms(mss, case, order, strip):
     # Both factorisation kernels, forced on every colour: the same bits as
     # each other, the oracle's factors element by element, and the last stage
@@ -133,7 +133,7 @@ def test_factor_forms(mss, case, order, strip):
     fl, dl = gl.bilu_factors()
     assert torch.equal(fw, fl) and torch.equal(dw, dl)
     o = _orc(s, **kw)
-    efv, edinv = stored_factor_form(o.bilu(), strip if order == 2 else 1)
+    efv, edinv = stored_factor_form(o.bilu(), strip if order in (2, 3) else 1)
     assert _rel(_n(fl), efv) < FACTOR_TOL
     assert _rel(_n(dl), edinv) < FACTOR_TOL
     r = np.random.default_rng(case).standard_normal(s.n_cells * s.nb)
@@ -145,7 +145,8 @@ def test_factor_forms(mss, case, order, strip):
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("scheme,stage3,smoother,order,ilu", [
     ("cptr3", 0, "jacobi", 0, 2), ("cptr3", 0, "jacobi", 0, 0), ("cptr3", 1, "jacobi", 0, 2),
-    ("cptr3", 0, "chebyshev", 0, 2), ("cptr3", 0, "jacobi", 1, 2), ("cpr", 0, "jacobi", 0, 2),
+    ("cptr3", 0, "chebyshev", 0, 2), ("cptr3", 0, "jacobi", 1, 2), ("cptr3", 0, "jacobi", 0, 3),
+    ("cpr", 0, "jacobi", 0, 2),
     ("ilu0", 0, "jacobi", 0, 2), ("ilu0", 0, "jacobi", 0, 0)])
 def test_stages_and_apply(mss, case, scheme, stage3, smoother, order, ilu):
     s = _sys(CASES[case])

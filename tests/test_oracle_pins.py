@@ -236,9 +236,10 @@ def test_bilu_reproduces_matrix_on_pattern(order, strip):
 
 
 @pytest.mark.parametrize("strip", [3, 8, 32])
-def test_strip_colouring_is_proper_and_keeps_strips_natural(strip):
+@pytest.mark.parametrize("order", [2, 3])
+def test_strip_colouring_is_proper_and_keeps_strips_natural(strip, order):
     s = sy.make_system(23, 19, 4, pe=10.0, seed=21)
-    o = oracle.OracleSolver.from_system(s, ilu_order=2, ilu_strip=strip)
+    o = oracle.OracleSolver.from_system(s, ilu_order=order, ilu_strip=strip)
     f = o.bilu()
     col, perm = f["colour"], f["perm"]
     # a strip has one colour, coupled strips differ
@@ -255,6 +256,31 @@ def test_strip_colouring_is_proper_and_keeps_strips_natural(strip):
     for a in range(0, s.n_cells, strip):
         pos = iperm[a:min(a + strip, s.n_cells)]
         assert np.all(np.diff(pos) == 1)
+
+
+@pytest.mark.parametrize("nx,ny,strip", [(64, 40, 32), (64, 40, 16), (50, 30, 25), (41, 30, 8)])
+def test_first_fit_strip_colouring(nx, ny, strip):
+    # first-fit in strip order: each strip has the smallest colour that none
+    # of its lower-index adjacent strips has; with the strips aligned to the
+    # grid rows the strip graph is bipartite and two colours suffice (the
+    # Jones-Plassmann colouring of the same strips needs more)
+    s = sy.make_system(nx, ny, 4, pe=10.0, seed=21)
+    f = oracle.OracleSolver.from_system(s, ilu_order=2, ilu_strip=strip).bilu()
+    col = f["colour"][::strip]
+    ns = len(col)
+    lower = [set() for _ in range(ns)]
+    for i in range(s.n_cells):
+        for e in range(s.row_ptr[i], s.row_ptr[i + 1]):
+            a, b = i // strip, s.col_idx[e] // strip
+            if b < a:
+                lower[a].add(b)
+    for a in range(ns):
+        taken = {col[b] for b in lower[a]}
+        assert col[a] not in taken and all(c in taken for c in range(col[a]))
+    if nx % strip == 0:
+        assert f["ncolours"] == 2
+    jp = oracle.OracleSolver.from_system(s, ilu_order=3, ilu_strip=strip).bilu()
+    assert jp["ncolours"] >= f["ncolours"]
 
 
 def test_single_strip_is_the_natural_order():
