@@ -136,7 +136,9 @@ static double dot(int n, const double* a, const double* b) {
 static double nrm2(int n, const double* a) { return sqrt(dot(n, a, a)); }
 
 /* Gauss-Jordan inverse without pivoting (the paper's orderings keep the
- * cell blocks invertible without pivoting, Sec. 3). a, inv: m x m row-major. */
+ * cell blocks invertible without pivoting, Sec. 3). a, inv: m x m row-major.
+ * The eliminations use IEEE fused multiply-adds (one rounding per update),
+ * as do the scaling's dot products below. */
 static int gj_inverse_nopiv(int m, const double* a_in, double* inv) {
   double a[32 * 32];
   if (m > 32) return OR_ERR_ARG;
@@ -154,8 +156,8 @@ static int gj_inverse_nopiv(int m, const double* a_in, double* inv) {
       if (i == k) continue;
       double f = a[i * m + k];
       for (int j = 0; j < m; ++j) {
-        a[i * m + j] = a[i * m + j] - f * a[k * m + j];
-        inv[i * m + j] = inv[i * m + j] - f * inv[k * m + j];
+        a[i * m + j] = fma(-f, a[k * m + j], a[i * m + j]);
+        inv[i * m + j] = fma(-f, inv[k * m + j], inv[i * m + j]);
       }
     }
   }
@@ -351,7 +353,7 @@ static int build_scaling(int nb, int p, int t, int scheme, const double* D, doub
     if (st) return st;
     for (int b = 0; b < nh; ++b) {
       double w = 0.0;
-      for (int a = 0; a < nh; ++a) w = w + D[p * nb + h[a]] * inv[a * nh + b];
+      for (int a = 0; a < nh; ++a) w = fma(D[p * nb + h[a]], inv[a * nh + b], w);
       W[p * nb + h[b]] = -w;
     }
     return OR_OK;
@@ -369,8 +371,8 @@ static int build_scaling(int nb, int p, int t, int scheme, const double* D, doub
     for (int b = 0; b < ns; ++b) {
       double wp = 0.0, wt = 0.0;
       for (int a = 0; a < ns; ++a) {
-        wp = wp + D[p * nb + s[a]] * inv[a * ns + b];
-        wt = wt + D[t * nb + s[a]] * inv[a * ns + b];
+        wp = fma(D[p * nb + s[a]], inv[a * ns + b], wp);
+        wt = fma(D[t * nb + s[a]], inv[a * ns + b], wt);
       }
       n1[p * nb + s[b]] = -wp;
       n1[t * nb + s[b]] = -wt;
@@ -383,22 +385,23 @@ static int build_scaling(int nb, int p, int t, int scheme, const double* D, doub
   /* once-scaled entries B_PP and B_Tp of N1^{-1} D */
   double bpp = 0.0, btp = 0.0;
   for (int k = 0; k < nb; ++k) {
-    bpp = bpp + n1[p * nb + k] * D[k * nb + p];
-    btp = btp + n1[t * nb + k] * D[k * nb + p];
+    bpp = fma(n1[p * nb + k], D[k * nb + p], bpp);
+    btp = fma(n1[t * nb + k], D[k * nb + p], btp);
   }
   if (bpp == 0.0 || !isfinite(bpp)) return OR_ERR_SINGULAR;
   double c = btp / bpp;
   for (int k = 0; k < nb * nb; ++k) W[k] = n1[k];
-  for (int k = 0; k < nb; ++k) W[t * nb + k] = n1[t * nb + k] - c * n1[p * nb + k];
+  for (int k = 0; k < nb; ++k) W[t * nb + k] = fma(-c, n1[p * nb + k], n1[t * nb + k]);
   return OR_OK;
 }
 
-/* out = W in  (nb x nb blocks, row-major), accumulation over ascending k */
+/* out = W in  (nb x nb blocks, row-major), accumulation over ascending k with
+ * fused multiply-adds */
 static void block_left_mul(int nb, const double* W, const double* in, double* out) {
   for (int r = 0; r < nb; ++r)
     for (int c = 0; c < nb; ++c) {
       double acc = 0.0;
-      for (int k = 0; k < nb; ++k) acc = acc + W[r * nb + k] * in[k * nb + c];
+      for (int k = 0; k < nb; ++k) acc = fma(W[r * nb + k], in[k * nb + c], acc);
       out[r * nb + c] = acc;
     }
 }
@@ -406,7 +409,7 @@ static void block_left_mul(int nb, const double* W, const double* in, double* ou
 static void block_vec_left_mul(int nb, const double* W, const double* in, double* out) {
   for (int r = 0; r < nb; ++r) {
     double acc = 0.0;
-    for (int k = 0; k < nb; ++k) acc = acc + W[r * nb + k] * in[k];
+    for (int k = 0; k < nb; ++k) acc = fma(W[r * nb + k], in[k], acc);
     out[r] = acc;
   }
 }

@@ -766,19 +766,30 @@ __global__ void k_bilu_bwd_par(int q0, int q1, const int* __restrict__ frp,
 // backward, chain: x_q = s_q - sum_{in-strip upper} G_qj x_j, rows of a
 // strip in reverse order (cG and the next row's values in registers, rows
 // fetched two steps ahead as in the forward chain); x_q goes back into w.
-// Block Jacobi (upper = 0): x_q = D_qq^{-1} u_q. The output y is assembled
-// afterwards by k_bilu_assemble.
+// Block Jacobi (upper = 0): x_q = D_qq^{-1} u_q. Each final row also goes to
+// the output y = x + v + M3 u in cell order.
 template <int NB, class V, class C>
 __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_first,
                                  const int* __restrict__ st_len, const int* __restrict__ fdp,
                                  const int* __restrict__ fshi, const int* __restrict__ fpos,
                                  const V* __restrict__ fv, const V* __restrict__ fdinv,
                                  const V* __restrict__ cG, const int* __restrict__ cflag,
-                                 C* __restrict__ w, int upper) {
+                                 C* __restrict__ w, int upper, const int* __restrict__ perm,
+                                 const C* __restrict__ xT, const C* __restrict__ vP, int p,
+                                 int t, double* __restrict__ y) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
   const int sub = lane / NB, comp = lane - sub * NB;
+  // a row's values are final once its step is done: y = x + v + M3 u in cell
+  // order, y_cell = w_q (+ x_T at t, + v_P at p)
+  auto emit = [&](int q, C val) {
+    const int cell = perm[q];
+    C out = val;
+    if (xT && comp == t) out += xT[cell];
+    if (vP && comp == p) out += vP[cell];
+    y[(size_t)cell * NB + comp] = (double)out;
+  };
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long kk = s0 + warp * RPW + sub;
   const bool active = sub < RPW && kk < s1;
@@ -799,7 +810,10 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
         C tc = __shfl_sync(0xffffffffu, tv, (base + c) & 31);
         if (on) x += cvt<C>(Ui[c]) * tc;
       }
-      if (on) w[(size_t)q * NB + comp] = x;
+      if (on) {
+        w[(size_t)q * NB + comp] = x;
+        emit(q, x);
+      }
     }
     return;
   }
@@ -860,6 +874,7 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
         }
       }
       wl[r * NB] = x;
+      emit(first + r, x);
       nxt = x;
     }
   };
@@ -868,23 +883,6 @@ __global__ void k_bilu_bwd_chain(int s0, int s1, const int* __restrict__ st_firs
     for (int u = 0; u < D; ++u)
       if (it + u < maxlen) step(it + u, tq[u], mq[u], fq[u]);
   }
-}
-
-// y = x + v + M3 u in cell order: y_cell = w_q (+ x_T at t, + v_P at p)
-template <int NB, int MODE, class C>
-__global__ void k_bilu_assemble(long long N, const int* __restrict__ perm,
-                                const C* __restrict__ w, const C* __restrict__ xT,
-                                const C* __restrict__ vP, int p, int t,
-                                double* __restrict__ y) {
-  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= N * NB) return;
-  const long long q = tid / NB;
-  const int comp = (int)(tid - q * NB);
-  const int cell = perm[q];
-  C out = w[tid];
-  if ((MODE & 1) && comp == t) out += xT[cell];
-  if ((MODE & 2) && comp == p) out += vP[cell];
-  y[(size_t)cell * NB + comp] = (double)out;
 }
 
 template <int NB>
@@ -1161,15 +1159,9 @@ void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, con
     k_bilu_bwd_chain<NB, V, C><<<grid_for(sw * 32, kChainThreads), kChainThreads, 0,
                                  h->stream>>>(
         s0, s1, h->st_first.p, h->st_len.p, h->fdp.p, h->fshi.p, h->fpos.p, F.fv, F.fdinv, F.cG,
-        h->cflag.p, F.w, bjac ? 0 : 1);
+        h->cflag.p, F.w, bjac ? 0 : 1, h->perm.p, (MODE & 1) ? xT : nullptr,
+        (MODE & 2) ? vP : nullptr, h->p, h->t, y);
     MSS_LAUNCH_CK("k_bilu_bwd_chain");
-  }
-  {
-    TraceScope ts(h, TR_BILU_BWD);
-    const long long tot = (long long)h->N * NB;
-    k_bilu_assemble<NB, MODE, C><<<grid_for(tot, T), T, 0, h->stream>>>(h->N, h->perm.p, F.w,
-                                                                        xT, vP, h->p, h->t, y);
-    MSS_LAUNCH_CK("k_bilu_assemble");
   }
 }
 

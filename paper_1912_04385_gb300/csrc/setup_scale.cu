@@ -61,112 +61,114 @@ __global__ void k_validate(const int* __restrict__ rp, const int* __restrict__ c
   }
 }
 
-// Gauss-Jordan inverse without pivoting, m <= 8, same operation order as the
-// oracle: divide the pivot row, then eliminate the column from every other
-// row. Returns false on a zero or non-finite pivot.
-__device__ bool gj_inverse(int m, double* a, double* inv) {
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) inv[i * m + j] = (i == j) ? 1.0 : 0.0;
-  for (int k = 0; k < m; ++k) {
-    double piv = a[k * m + k];
-    if (piv == 0.0 || !isfinite(piv)) return false;
-    for (int j = 0; j < m; ++j) {
-      a[k * m + j] = a[k * m + j] / piv;
-      inv[k * m + j] = inv[k * m + j] / piv;
+// W = N^{-1} restricted to one cell, built from the cell's diagonal block D
+// (read through src): only rows p and t differ from the identity, stored as
+// wrows[i][0][:] (row p) and wrows[i][1][:] (row t).
+// scheme: 0 CPTR3 (Eq. CPTR31 then Eq. CPTR32), 1 CPR (Eq. CPR), 2 none,
+// 3 CPTR (Eq. CPTR1: the N1 of Eq. CPTR31 alone).
+//
+// The inverse of the sub-block D_xx (x = s for CPTR3/CPTR, h = all but p for
+// CPR) is formed by Gauss-Jordan without pivoting on the whole NB x NB block
+// with the rows and columns outside x replaced by the identity: pivoting
+// only on the x positions, in ascending order, performs on the x-by-x part
+// exactly the operations, in the same order, of the elimination on the
+// compacted sub-block (the other entries are zero and never enter it), while
+// every array index is a compile-time constant, so the work stays in
+// registers. Divisions as written, updates as fused multiply-adds; the same
+// arithmetic as the FP64 definition, so the scaled blocks match it bit for
+// bit.
+template <int NB>
+__device__ bool build_w_cell(const double* src, bool col_major, int p, int t, int scheme,
+                             double (&wp)[NB], double (&wt)[NB]) {
+  auto D = [&](int r, int c) { return col_major ? src[c * NB + r] : src[r * NB + c]; };
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    wp[k] = (k == p) ? 1.0 : 0.0;
+    wt[k] = (k == t) ? 1.0 : 0.0;
+  }
+  if (scheme == 2) return true;
+  // x: the eliminated unknowns
+  auto in_x = [&](int k) { return scheme == 1 ? k != p : (k != p && k != t); };
+  double a[NB][NB], inv[NB][NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      a[r][c] = (in_x(r) && in_x(c)) ? D(r, c) : (r == c ? 1.0 : 0.0);
+      inv[r][c] = r == c ? 1.0 : 0.0;
     }
-    for (int i = 0; i < m; ++i) {
-      if (i == k) continue;
-      double f = a[i * m + k];
-      for (int j = 0; j < m; ++j) {
-        a[i * m + j] = a[i * m + j] - f * a[k * m + j];
-        inv[i * m + j] = inv[i * m + j] - f * inv[k * m + j];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    if (!in_x(k)) continue;
+    const double piv = a[k][k];
+    if (piv == 0.0 || !isfinite(piv)) return false;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (!in_x(j)) continue;
+      a[k][j] = a[k][j] / piv;
+      inv[k][j] = inv[k][j] / piv;
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      if (i == k || !in_x(i)) continue;
+      const double f = a[i][k];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (!in_x(j)) continue;
+        a[i][j] = fma(-f, a[k][j], a[i][j]);
+        inv[i][j] = fma(-f, inv[k][j], inv[i][j]);
       }
     }
+  }
+  // w = -D_e,x D_xx^{-1} for the scaled rows e (p; and t for CPTR3 / CPTR)
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    if (!in_x(c)) continue;
+    double vp = 0.0, vt = 0.0;
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      if (!in_x(r)) continue;
+      vp = fma(D(p, r), inv[r][c], vp);
+      if (scheme != 1) vt = fma(D(t, r), inv[r][c], vt);
+    }
+    wp[c] = -vp;
+    if (scheme != 1) wt[c] = -vt;
+  }
+  if (scheme == 0) {
+    // once-scaled entries B_PP and B_Tp of N1^{-1} D, then the N2 factor
+    double bpp = 0.0, btp = 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      bpp = fma(wp[k], D(k, p), bpp);
+      btp = fma(wt[k], D(k, p), btp);
+    }
+    if (bpp == 0.0 || !isfinite(bpp)) return false;
+    const double cc = btp / bpp;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) wt[k] = fma(-cc, wp[k], wt[k]);
   }
   return true;
 }
 
-// One thread per cell: W = N^{-1} restricted to the cell, built from the
-// diagonal block D. Only rows p and t of W differ from the identity; they
-// are stored as wrows[i][0][:] (row p) and wrows[i][1][:] (row t).
-// scheme: 0 CPTR3 (Eq. CPTR31 then Eq. CPTR32), 1 CPR (Eq. CPR), 2 none,
-// 3 CPTR (Eq. CPTR1: the N1 of Eq. CPTR31 alone).
+// One thread per cell: W_i from the diagonal block (see build_w_cell).
 template <int NB>
 __global__ void k_build_w(const double* __restrict__ vals, const int* __restrict__ diag, int N,
                           int p, int t, int scheme, int col_major, double* __restrict__ wrows,
                           int* __restrict__ flag, double* __restrict__ dcopy) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double D[NB * NB];
   const double* src = vals + (size_t)diag[i] * NB * NB;
-  for (int r = 0; r < NB; ++r)
-    for (int c = 0; c < NB; ++c) D[r * NB + c] = col_major ? src[c * NB + r] : src[r * NB + c];
   if (dcopy) {   // the block as stored, for k_apply_w (host-resident values are read once)
-    for (int r = 0; r < NB; ++r)
-      for (int c = 0; c < NB; ++c)
-        dcopy[(size_t)i * NB * NB + (col_major ? c * NB + r : r * NB + c)] = D[r * NB + c];
+    for (int k = 0; k < NB * NB; ++k) dcopy[(size_t)i * NB * NB + k] = src[k];
+    src = dcopy + (size_t)i * NB * NB;
   }
   double wp[NB], wt[NB];
-  for (int k = 0; k < NB; ++k) {
-    wp[k] = (k == p) ? 1.0 : 0.0;
-    wt[k] = (k == t) ? 1.0 : 0.0;
-  }
-  if (scheme == 1) {
-    int h[NB];
-    int nh = 0;
-    for (int k = 0; k < NB; ++k)
-      if (k != p) h[nh++] = k;
-    double Dhh[NB * NB], inv[NB * NB];
-    for (int a = 0; a < nh; ++a)
-      for (int b = 0; b < nh; ++b) Dhh[a * nh + b] = D[h[a] * NB + h[b]];
-    if (!gj_inverse(nh, Dhh, inv)) {
-      atomicMin(flag, i);
-      return;
-    }
-    for (int b = 0; b < nh; ++b) {
-      double w = 0.0;
-      for (int a = 0; a < nh; ++a) w = w + D[p * NB + h[a]] * inv[a * nh + b];
-      wp[h[b]] = -w;
-    }
-  } else if (scheme == 0 || scheme == 3) {
-    int s[NB];
-    int ns = 0;
-    for (int k = 0; k < NB; ++k)
-      if (k != p && k != t) s[ns++] = k;
-    if (ns > 0) {
-      double Dss[NB * NB], inv[NB * NB];
-      for (int a = 0; a < ns; ++a)
-        for (int b = 0; b < ns; ++b) Dss[a * ns + b] = D[s[a] * NB + s[b]];
-      if (!gj_inverse(ns, Dss, inv)) {
-        atomicMin(flag, i);
-        return;
-      }
-      for (int b = 0; b < ns; ++b) {
-        double vp = 0.0, vt = 0.0;
-        for (int a = 0; a < ns; ++a) {
-          vp = vp + D[p * NB + s[a]] * inv[a * ns + b];
-          vt = vt + D[t * NB + s[a]] * inv[a * ns + b];
-        }
-        wp[s[b]] = -vp;
-        wt[s[b]] = -vt;
-      }
-    }
-    if (scheme == 0) {
-    // once-scaled entries B_PP and B_Tp of N1^{-1} D, then the N2 factor
-    double bpp = 0.0, btp = 0.0;
-    for (int k = 0; k < NB; ++k) {
-      bpp = bpp + wp[k] * D[k * NB + p];
-      btp = btp + wt[k] * D[k * NB + p];
-    }
-    if (bpp == 0.0 || !isfinite(bpp)) {
-      atomicMin(flag, i);
-      return;
-    }
-    double c = btp / bpp;
-    for (int k = 0; k < NB; ++k) wt[k] = wt[k] - c * wp[k];
-    }
+  if (!build_w_cell<NB>(src, col_major != 0, p, t, scheme, wp, wt)) {
+    atomicMin(flag, i);
+    return;
   }
   double* out = wrows + (size_t)i * 2 * NB;
+#pragma unroll
   for (int k = 0; k < NB; ++k) {
     out[k] = wp[k];
     out[NB + k] = wt[k];
@@ -209,12 +211,12 @@ __global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict
   const double* w = wrows + (size_t)brow[e] * 2 * NB;
   double acc = 0.0;
 #pragma unroll
-  for (int k = 0; k < NB; ++k) acc = acc + w[k] * col[k];
+  for (int k = 0; k < NB; ++k) acc = fma(w[k], col[k], acc);
   dst[p * NB] = acc;
   if (scheme == 0 || scheme == 3) {
     double acc2 = 0.0;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) acc2 = acc2 + w[NB + k] * col[k];
+    for (int k = 0; k < NB; ++k) acc2 = fma(w[NB + k], col[k], acc2);
     dst[t * NB] = acc2;
   }
 }
@@ -232,7 +234,7 @@ __global__ void k_scale_vec(const double* __restrict__ b, int N, int p, int t, i
   }
   const double* w = wrows + (size_t)i * 2 * NB + (r == p ? 0 : NB);
   double acc = 0.0;
-  for (int k = 0; k < NB; ++k) acc = acc + w[k] * b[(size_t)i * NB + k];
+  for (int k = 0; k < NB; ++k) acc = fma(w[k], b[(size_t)i * NB + k], acc);
   out[tid] = acc;
 }
 
