@@ -148,9 +148,10 @@ static int gj_inverse_nopiv(int m, const double* a_in, double* inv) {
   for (int k = 0; k < m; ++k) {
     double piv = a[k * m + k];
     if (piv == 0.0 || !isfinite(piv)) return OR_ERR_SINGULAR;
+    double rpiv = 1.0 / piv;     /* the pivot row is scaled by the reciprocal */
     for (int j = 0; j < m; ++j) {
-      a[k * m + j] = a[k * m + j] / piv;
-      inv[k * m + j] = inv[k * m + j] / piv;
+      a[k * m + j] = a[k * m + j] * rpiv;
+      inv[k * m + j] = inv[k * m + j] * rpiv;
     }
     for (int i = 0; i < m; ++i) {
       if (i == k) continue;

@@ -74,7 +74,8 @@ __global__ void k_validate(const int* __restrict__ rp, const int* __restrict__ c
 // exactly the operations, in the same order, of the elimination on the
 // compacted sub-block (the other entries are zero and never enter it), while
 // every array index is a compile-time constant, so the work stays in
-// registers. Divisions as written, updates as fused multiply-adds; the same
+// registers. One division per pivot (the row is scaled by its reciprocal),
+// updates as fused multiply-adds; the same
 // arithmetic as the FP64 definition, so the scaled blocks match it bit for
 // bit.
 template <int NB>
@@ -102,11 +103,12 @@ __device__ bool build_w_cell(const double* src, bool col_major, int p, int t, in
     if (!in_x(k)) continue;
     const double piv = a[k][k];
     if (piv == 0.0 || !isfinite(piv)) return false;
+    const double rpiv = 1.0 / piv;     // the pivot row scaled by the reciprocal
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       if (!in_x(j)) continue;
-      a[k][j] = a[k][j] / piv;
-      inv[k][j] = inv[k][j] / piv;
+      a[k][j] = a[k][j] * rpiv;
+      inv[k][j] = inv[k][j] * rpiv;
     }
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
