@@ -437,7 +437,26 @@ int mss_trace_read(mss_handle* h, int kind, int64_t* launches, double* ms, int r
  * does not depend on it) and one solve with each driver (host loop, or the
  * CUDA graph including its capture); the fastest choice is cached in the
  * batch object for later systems of the bucket. With autotune == 0 every
- * system uses 256 threads and the driver in the options. */
+ * system uses 256 threads and the driver in the options.
+ *
+ * Fused schedule (mss_batch_set_schedule(b, MSS_SCHEDULE_FUSED)): the lanes
+ * set the systems up, each on a handle of its own; then the systems of each
+ * block size are solved in lock step as one group: every kernel launch of the
+ * restarted FGMRES and of the preconditioner serves all systems of the group.
+ * A launch walks a list of tiles (runs of blocks of one system's own launch of
+ * that kernel) with CTAs that stay resident and take tile after tile, and the
+ * whole group solve is one CUDA graph whose loops run while any system takes
+ * another step. Each system still computes exactly the values of its own
+ * solve (same kernels' bodies, same launch shapes per system), so solutions
+ * and iteration counts equal the lanes schedule's bit for bit. The tile shape
+ * (blocks per tile, resident CTAs per SM) is tuned on the group's first
+ * preconditioner application and product and cached per (floor(log2 of the
+ * group's rows), nb) (fixed at 1 block and 4 CTAs with autotune == 0). It
+ * covers FP64 solves with Jacobi smoothing (CPTR3, CPR, ILU0) and nb <= 8;
+ * other systems take the lanes schedule. Every system of a group finishes with
+ * the group: latency is traded for throughput. */
+enum { MSS_SCHEDULE_LANES = 0, MSS_SCHEDULE_FUSED = 1 };
+
 typedef struct {
   mss_bsr J;                /* device arrays, as for mss_setup */
   int32_t nb;
@@ -450,9 +469,13 @@ typedef struct {
   int32_t bucket;           /* floor(log2(n_rows)) */
   int32_t threads;          /* threads per CTA used */
   int32_t driver;           /* MSS_DRIVER_* used */
-  int32_t lane;             /* worker that solved it */
+  int32_t lane;             /* worker that solved it (fused: the worker that set it up) */
   double latency_ms;        /* host clock: start of its set-up to end of its solve */
   double finish_ms;         /* host clock: start of the batch call to end of its solve */
+  int32_t schedule;         /* MSS_SCHEDULE_* that solved it */
+  int32_t group;            /* fused: its group (systems of one nb); lanes: -1 */
+  int32_t tile_blocks;      /* fused: blocks of a system's launch per tile */
+  int32_t per_sm;           /* fused: resident CTAs per SM of each launch */
 } mss_batch_info;
 
 typedef struct mss_batch mss_batch;
@@ -461,6 +484,10 @@ typedef struct mss_batch mss_batch;
  * Errors: INVALID_ARG, CUDA, OOM. */
 int mss_batch_create(mss_batch** b, int lanes, int autotune);
 void mss_batch_destroy(mss_batch* b);
+
+/* MSS_SCHEDULE_LANES (default) or MSS_SCHEDULE_FUSED for later
+ * mss_batch_solve calls. Errors: INVALID_ARG. */
+int mss_batch_set_schedule(mss_batch* b, int schedule);
 
 /* Sets up and solves the n systems (tol, maxit as for mss_fgmres_solve; opt
  * NULL = defaults). The device is synchronised first, so inputs written on

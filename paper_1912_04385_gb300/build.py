@@ -26,7 +26,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 NO_FMA = {"setup_scale.cu", "amg_setup.cu"}
 SOURCES = ["util.cu", "setup_scale.cu", "amg_setup.cu", "amg_cycle.cu", "bilu.cu", "spmv.cu", "krylov.cu",
-           "residual.cu", "noalloc.cu", "condense.cu", "api.cu", "batch.cu", "gnn.cu"]
+           "residual.cu", "noalloc.cu", "condense.cu", "api.cu", "batch.cu", "fused.cu", "gnn.cu"]
 
 
 def _nvcc() -> str:

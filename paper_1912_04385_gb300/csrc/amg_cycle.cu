@@ -20,11 +20,14 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "vcycle_rows.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace mss {
 namespace {
+
+using namespace dev;
 
 // ---- coarse inverse: Gauss-Jordan with partial pivoting ------------------
 // M is the n x 2n augmented matrix [A | I] (row-major). Every block finds
@@ -321,78 +324,6 @@ __global__ void k_jacobi0_twice(int n, const int* __restrict__ rp, const int* __
   x[i] = x1 + omega * (dinv[i] * (b[i] - s));
 }
 
-// Row operations of the V-cycle, shared by the per-level kernels and the
-// fused coarse-level kernel (so both give the same values). LD reads the
-// vectors: plain loads in the per-level kernels; in the fused kernel, whose
-// blocks read what other blocks wrote before a grid barrier, loads that
-// bypass the non-coherent L1.
-struct LdPlain {
-  template <class T>
-  __device__ __forceinline__ static T ld(const T* p) { return *p; }
-};
-struct LdL2 {
-  template <class T>
-  __device__ __forceinline__ static T ld(const T* p) { return __ldcg(p); }
-};
-
-// x_out = x_in + omega D^-1 (b - A x_in)
-template <class V, class C, class LD>
-__device__ __forceinline__ void jacobi_row(int i, const int* __restrict__ rp,
-                                           const int* __restrict__ ci, const V* __restrict__ v,
-                                           const C* __restrict__ dinv, const C* b, C omega,
-                                           const C* xin, C* xout) {
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * LD::ld(xin + ci[k]);
-  xout[i] = LD::ld(xin + i) + omega * (dinv[i] * (LD::ld(b + i) - s));
-}
-
-// r = b - A x
-template <class V, class C, class LD>
-__device__ __forceinline__ void residual_row(int i, const int* __restrict__ rp,
-                                             const int* __restrict__ ci,
-                                             const V* __restrict__ v, const C* b, const C* x,
-                                             C* r) {
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * LD::ld(x + ci[k]);
-  r[i] = LD::ld(b + i) - s;
-}
-
-// b = R r on the next level and, with x1, that level's first Jacobi sweep
-// from zero x1 = omega D^-1 b (the expression the sweep kernels use)
-template <class V, class C, class LD>
-__device__ __forceinline__ void restrict_row(int i, const int* __restrict__ rp,
-                                             const int* __restrict__ ci,
-                                             const V* __restrict__ v, const C* r, C* b,
-                                             const C* __restrict__ dinv, C omega, C* x1) {
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * LD::ld(r + ci[k]);
-  b[i] = s;
-  if (x1) x1[i] = omega * dinv[i] * s;
-}
-
-// xout = x + P xc (x and xout may be the same vector: each entry is read
-// and written by its own thread only)
-template <class V, class C, class LD>
-__device__ __forceinline__ void prolong_row(int i, const int* __restrict__ rp,
-                                            const int* __restrict__ ci,
-                                            const V* __restrict__ v, const C* xc, const C* x,
-                                            C* xout) {
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += cvt<C>(v[k]) * LD::ld(xc + ci[k]);
-  xout[i] = LD::ld(x + i) + s;
-}
-
-// x_row = (Ainv b)_row by one warp: lanes over the row, then a tree
-template <class C, class LD>
-__device__ __forceinline__ C gemv_row(int row, int lane, int n, const C* __restrict__ A,
-                                      const C* b) {
-  const C* a = A + (size_t)row * n;
-  C s = 0;
-  for (int j = lane; j < n; j += 32) s += a[j] * LD::ld(b + j);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  return s;
-}
-
 template <class V, class C>
 __global__ void k_jacobi(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                          const V* __restrict__ v, const C* __restrict__ dinv,
@@ -653,11 +584,7 @@ template <class C>
 __global__ void k_gather_var(int N, int nb, const double* __restrict__ v, int var,
                              C* __restrict__ out, const C* __restrict__ dinv, C omega,
                              C* __restrict__ x1) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const C bi = (C)v[(size_t)i * nb + var];
-  out[i] = bi;
-  if (x1) x1[i] = omega * dinv[i] * bi;
+  gather_var_row(blockIdx.x * blockDim.x + threadIdx.x, N, nb, v, var, out, dinv, omega, x1);
 }
 
 __global__ void k_scatter_var_zero(int N, int nb, const double* __restrict__ s, int var,
@@ -668,20 +595,14 @@ __global__ void k_scatter_var_zero(int N, int nb, const double* __restrict__ s, 
   out[tid] = k == var ? s[i] : 0.0;
 }
 
-// out_i = r[i*nb + var] - sum_j vals_ij x_j over the block pattern
 template <class C>
 __global__ void k_pattern_sub(int N, int nb, const int* __restrict__ rp,
                               const int* __restrict__ ci, const C* __restrict__ vals,
                               const C* __restrict__ x, const double* __restrict__ r, int var,
                               C* __restrict__ out, const C* __restrict__ dinv, C omega,
                               C* __restrict__ x1) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  C s = 0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += vals[k] * x[ci[k]];
-  const C bi = (C)r[(size_t)i * nb + var] - s;
-  out[i] = bi;
-  if (x1) x1[i] = omega * dinv[i] * bi;
+  pattern_sub_row(blockIdx.x * blockDim.x + threadIdx.x, N, nb, rp, ci, vals, x, r, var, out, dinv,
+                  omega, x1);
 }
 
 __global__ void k_to_float(long long n, const double* __restrict__ in, float* __restrict__ out) {

@@ -12,6 +12,10 @@
 // preconditioner application and the matrix-vector product at 64..512
 // threads per CTA, then one solve per driver (host loop; CUDA graph with its
 // capture), and caches the fastest. None of these choices changes a result.
+//
+// Fused schedule: the lanes only set the systems up (each on a handle of its
+// own); the solves of each block size then run in lock step as one group
+// through multi-system launches (fused.cu).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -71,6 +75,8 @@ struct mss_batch {
   int device = 0;
   int lanes = 1;
   int autotune = 1;
+  int schedule = MSS_SCHEDULE_LANES;
+  FusedTuneCache fcache;        // tile shapes of the fused schedule
   std::vector<std::unique_ptr<Handle>> lane;
   std::mutex mu;
   std::map<long long, Choice> cache;   // key: bucket * 16 + nb
@@ -125,6 +131,19 @@ Choice tune(Handle& H, const mss_system& s, double tol, int maxit, mss_result* r
   return c;
 }
 
+// status code of the exception being handled (inside a catch block)
+int error_code() {
+  try {
+    throw;
+  } catch (const Error& e) {
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    return MSS_ERR_OOM;
+  } catch (...) {
+  }
+  return MSS_ERR_CUDA;
+}
+
 void run_one(mss_batch* B, Handle& H, int lane, const mss_system& s, const mss_options& base,
              double tol, int maxit, mss_result* res, mss_batch_info* inf,
              Clock::time_point tbatch) {
@@ -158,15 +177,7 @@ void run_one(mss_batch* B, Handle& H, int lane, const mss_system& s, const mss_o
       solve_handle(H, &s.J, s.b, s.x, tol, maxit, res);
     }
   } catch (...) {
-    int code = MSS_ERR_CUDA;
-    try {
-      throw;
-    } catch (const Error& e) {
-      code = e.code;
-    } catch (const std::bad_alloc&) {
-      code = MSS_ERR_OOM;
-    } catch (...) {
-    }
+    const int code = error_code();
     if (tuner) {   // let the next system of the bucket tune it
       std::lock_guard<std::mutex> lk(B->mu);
       B->cache.erase(key);
@@ -181,7 +192,110 @@ void run_one(mss_batch* B, Handle& H, int lane, const mss_system& s, const mss_o
     inf->lane = lane;
     inf->latency_ms = ms_since(t0);
     inf->finish_ms = ms_since(tbatch);
+    inf->schedule = MSS_SCHEDULE_LANES;
+    inf->group = -1;
+    inf->tile_blocks = 0;
+    inf->per_sm = 0;
   }
+}
+
+// The fused schedule: every system set up on a handle of its own by the lanes
+// (largest first), then one lock-step group solve per block size, the groups
+// on their own streams and threads. The systems in `idx` are the ones it
+// takes (order: largest first).
+void batch_fused(mss_batch* B, const std::vector<int>& idx, const mss_system* sys,
+                 const mss_options& base, double tol, int maxit, mss_result* results,
+                 mss_batch_info* info, Clock::time_point tbatch) {
+  const int n = (int)idx.size();
+  std::vector<std::unique_ptr<Handle>> hs((size_t)n);
+  std::vector<double> t0((size_t)n, 0.0);
+  std::vector<int> lane_of((size_t)n, 0);
+  std::vector<char> ok((size_t)n, 0);
+  std::atomic<int> next{0};
+  auto work = [&](int l) {
+    cudaSetDevice(B->device);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n) break;
+      const int i = idx[k];
+      t0[k] = ms_since(tbatch);
+      lane_of[k] = l;
+      try {
+        hs[k].reset(make_lane(B->device));
+        setup_handle(*hs[k], &sys[i].J, sys[i].nb, sys[i].layout, &base);
+        MSS_CK(cudaStreamSynchronize(hs[k]->stream));
+        ok[k] = 1;
+      } catch (...) {
+        results[i] = mss_result{};
+        results[i].status = error_code();
+      }
+    }
+  };
+  {
+    const int nl = std::min(B->lanes, n);
+    std::vector<std::thread> th;
+    for (int l = 1; l < nl; ++l) th.emplace_back(work, l);
+    work(0);
+    for (auto& t : th) t.join();
+  }
+  std::map<int, std::vector<int>> groups;   // nb -> positions in idx
+  for (int k = 0; k < n; ++k)
+    if (ok[k]) groups[sys[idx[k]].nb].push_back(k);
+  std::vector<std::thread> gt;
+  int gno = 0;
+  for (auto& g : groups) {
+    gt.emplace_back([&, ks = g.second, gi = gno] {
+      cudaSetDevice(B->device);
+      std::vector<Handle*> hv;
+      std::vector<const double*> bv;
+      std::vector<double*> xv;
+      for (int k : ks) {
+        hv.push_back(hs[k].get());
+        bv.push_back(sys[idx[k]].b);
+        xv.push_back(sys[idx[k]].x);
+      }
+      std::vector<mss_result> res;
+      FusedInfo fi;
+      int code = MSS_OK;
+      const auto ts = Clock::now();
+      try {
+        std::unique_ptr<Handle> gh(make_lane(B->device));
+        fused_solve(gh.get(), hv, bv, xv, tol, maxit, base.driver,
+                    B->autotune ? &B->fcache : nullptr, res, &fi);
+        MSS_CK(cudaStreamSynchronize(gh->stream));
+      } catch (...) {
+        code = error_code();
+      }
+      const double solve_ms = ms_since(ts), tend = ms_since(tbatch);
+      for (size_t q = 0; q < ks.size(); ++q) {
+        const int k = ks[q], i = idx[k];
+        if (code == MSS_OK) {
+          results[i] = res[q];
+          results[i].solve_ms = solve_ms;
+        } else {
+          results[i] = mss_result{};
+          results[i].status = code;
+        }
+        if (info) {
+          mss_batch_info& f = info[i];
+          f.bucket = bucket_of(sys[i].J.n_rows);
+          f.threads = 256;
+          f.driver = base.driver;
+          f.lane = lane_of[k];
+          f.latency_ms = tend - t0[k];
+          f.finish_ms = tend;
+          f.schedule = MSS_SCHEDULE_FUSED;
+          f.group = gi;
+          f.tile_blocks = fi.tile_blocks;
+          f.per_sm = fi.per_sm;
+        }
+      }
+    });
+    ++gno;
+  }
+  for (auto& t : gt) t.join();
+  for (auto& h : hs)
+    if (h) cudaStreamSynchronize(h->stream);
 }
 
 }  // namespace
@@ -241,28 +355,45 @@ int mss_batch_solve(mss_batch* B, int n, const mss_system* sys, const mss_option
     const double wb = (double)sys[b].J.nnzb * sys[b].nb * sys[b].nb;
     return wa > wb;
   });
-  std::atomic<int> next{0};
   const auto tbatch = Clock::now();
+  if (B->schedule == MSS_SCHEDULE_FUSED && fused_supported(base, kFusedMaxNB)) {
+    // systems of nb <= kFusedMaxNB take the fused schedule, the others the lanes
+    std::vector<int> fused, rest;
+    for (int i : order) (sys[i].nb <= kFusedMaxNB ? fused : rest).push_back(i);
+    batch_fused(B, fused, sys, base, tol, maxit, results, info, tbatch);
+    order = rest;
+  }
+  std::atomic<int> next{0};
+  const int nrest = (int)order.size();
   auto work = [&](int l) {
     cudaSetDevice(B->device);
     Handle& H = *B->lane[l];
     for (;;) {
       const int k = next.fetch_add(1);
-      if (k >= n) break;
+      if (k >= nrest) break;
       const int i = order[k];
       run_one(B, H, l, sys[i], base, tol, maxit, &results[i], info ? &info[i] : nullptr,
               tbatch);
     }
   };
-  const int nl = std::min(B->lanes, n);
-  std::vector<std::thread> th;
-  for (int l = 1; l < nl; ++l) th.emplace_back(work, l);
-  work(0);
-  for (auto& t : th) t.join();
+  if (nrest > 0) {
+    const int nl = std::min(B->lanes, nrest);
+    std::vector<std::thread> th;
+    for (int l = 1; l < nl; ++l) th.emplace_back(work, l);
+    work(0);
+    for (auto& t : th) t.join();
+  }
   int st = MSS_OK;
   for (int i = 0; i < n && st == MSS_OK; ++i) st = results[i].status;
   B->last_error = st == MSS_OK ? "" : "a system did not converge or failed; see its result";
   return st;
+}
+
+int mss_batch_set_schedule(mss_batch* B, int schedule) {
+  if (!B || (schedule != MSS_SCHEDULE_LANES && schedule != MSS_SCHEDULE_FUSED))
+    return MSS_ERR_INVALID_ARG;
+  B->schedule = schedule;
+  return MSS_OK;
 }
 
 int mss_batch_tuned(mss_batch* B, int cap, int32_t* out) {

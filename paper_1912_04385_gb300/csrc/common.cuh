@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <memory>
@@ -412,6 +414,27 @@ void gnn_set_vectors(GnnGraph* g, int K, const double* starts, int nu, double om
 double gnn_loss_grad(GnnGraph* g, const float* params, float* grad);
 void gnn_adam(Handle* h, float* params, float* m1, float* m2, const float* grad, int step,
               float lr, float b1, float b2, float eps);
+
+// fused.cu: lock-step solves of a group of set-up systems (one block size,
+// one set of options) through multi-system launches; the tile shape of the
+// launches is tuned once per (size bucket, nb) and cached (cache == null: a
+// fixed shape); driver MSS_DRIVER_GRAPH runs the group solve as one graph
+struct FusedTuneCache {
+  std::mutex mu;
+  std::map<long long, std::pair<int, int>> choice;   // key -> (blocks per tile, CTAs per SM)
+};
+struct FusedInfo {
+  int tile_blocks = 0, per_sm = 0;
+  long long sites = 0;   // multi-system launches in the init, head, step and tail sequences
+  int steps = 0;         // Arnoldi steps of the group (the longest system's count)
+};
+// the fused schedule covers FP64 solves with Jacobi-smoothed V-cycles (CPTR3,
+// CPR or the last stage alone) and block sizes up to kFusedMaxNB
+constexpr int kFusedMaxNB = 8;
+bool fused_supported(const mss_options& o, int nb);
+void fused_solve(Handle* gh, const std::vector<Handle*>& hs, const std::vector<const double*>& b,
+                 const std::vector<double*>& x, double tol, int maxit, int driver,
+                 FusedTuneCache* cache, std::vector<mss_result>& res, FusedInfo* info);
 
 // condense.cu: static condensation and recovery of the secondary unknowns
 void condense(Handle* h, const mss_full* J, const double* r1, const double* r2, double* a,

@@ -6,6 +6,7 @@
 // AMG set-up (whose strength tests turn floating point into index decisions)
 // with values that do not depend on instruction selection.
 #include "common.cuh"
+#include "vec_rows.cuh"
 
 namespace mss {
 namespace {
@@ -91,6 +92,9 @@ __device__ bool build_w_cell(const double* src, bool col_major, int p, int t, in
   // x: the eliminated unknowns
   auto in_x = [&](int k) { return scheme == 1 ? k != p : (k != p && k != t); };
   double a[NB][NB], inv[NB][NB];
+  // the elimination fully unrolled (register arrays) up to 8 unknowns; larger
+  // blocks run the same operations in loops (fast compilation, same values)
+  constexpr int U = NB <= 8 ? NB : 1;
 #pragma unroll
   for (int r = 0; r < NB; ++r)
 #pragma unroll
@@ -98,23 +102,23 @@ __device__ bool build_w_cell(const double* src, bool col_major, int p, int t, in
       a[r][c] = (in_x(r) && in_x(c)) ? D(r, c) : (r == c ? 1.0 : 0.0);
       inv[r][c] = r == c ? 1.0 : 0.0;
     }
-#pragma unroll
+#pragma unroll U
   for (int k = 0; k < NB; ++k) {
     if (!in_x(k)) continue;
     const double piv = a[k][k];
     if (piv == 0.0 || !isfinite(piv)) return false;
     const double rpiv = 1.0 / piv;     // the pivot row scaled by the reciprocal
-#pragma unroll
+#pragma unroll U
     for (int j = 0; j < NB; ++j) {
       if (!in_x(j)) continue;
       a[k][j] = a[k][j] * rpiv;
       inv[k][j] = inv[k][j] * rpiv;
     }
-#pragma unroll
+#pragma unroll U
     for (int i = 0; i < NB; ++i) {
       if (i == k || !in_x(i)) continue;
       const double f = a[i][k];
-#pragma unroll
+#pragma unroll U
       for (int j = 0; j < NB; ++j) {
         if (!in_x(j)) continue;
         a[i][j] = fma(-f, a[k][j], a[i][j]);
@@ -123,11 +127,11 @@ __device__ bool build_w_cell(const double* src, bool col_major, int p, int t, in
     }
   }
   // w = -D_e,x D_xx^{-1} for the scaled rows e (p; and t for CPTR3 / CPTR)
-#pragma unroll
+#pragma unroll U
   for (int c = 0; c < NB; ++c) {
     if (!in_x(c)) continue;
     double vp = 0.0, vt = 0.0;
-#pragma unroll
+#pragma unroll U
     for (int r = 0; r < NB; ++r) {
       if (!in_x(r)) continue;
       vp = fma(D(p, r), inv[r][c], vp);
@@ -226,18 +230,8 @@ __global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict
 template <int NB>
 __global__ void k_scale_vec(const double* __restrict__ b, int N, int p, int t, int scheme,
                             const double* __restrict__ wrows, double* __restrict__ out) {
-  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (long long)N * NB) return;
-  int i = (int)(tid / NB), r = (int)(tid % NB);
-  bool scaled_row = scheme != 2 && (r == p || ((scheme == 0 || scheme == 3) && r == t));
-  if (!scaled_row) {
-    out[tid] = b[tid];
-    return;
-  }
-  const double* w = wrows + (size_t)i * 2 * NB + (r == p ? 0 : NB);
-  double acc = 0.0;
-  for (int k = 0; k < NB; ++k) acc = fma(w[k], b[(size_t)i * NB + k], acc);
-  out[tid] = acc;
+  dev::scale_vec_entry<NB>((long long)blockIdx.x * blockDim.x + threadIdx.x, b, N, p, t, scheme,
+                           wrows, out);
 }
 
 __global__ void k_extract(const double* __restrict__ abar, int nnzb, int nb, int var,

@@ -2,6 +2,7 @@
 // FGMRES iterates with (Sec. 4, Eq. splitPrec1; Sec. 5.1). Kept in a file of
 // its own: the kernel's ncu counters are tied to this source.
 #include "common.cuh"
+#include "vec_rows.cuh"
 
 namespace mss {
 namespace {
@@ -11,22 +12,8 @@ template <int NB>
 __global__ void k_bsr_spmv(int N, const int* __restrict__ rp, const int* __restrict__ ci,
                            const double* __restrict__ vals, const double* __restrict__ x,
                            double* __restrict__ y) {
-  constexpr int RPW = 32 / NB;
-  constexpr int B2 = NB * NB;
-  const int lane = threadIdx.x & 31;
-  const int sub = lane / NB, comp = lane - sub * NB;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long ii = warp * RPW + sub;
-  if (sub >= RPW || ii >= N) return;
-  const int i = (int)ii;
-  double acc = 0.0;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) {
-    const double* a = vals + (size_t)e * B2 + comp * NB;
-    const double* xj = x + (size_t)ci[e] * NB;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) acc += a[c] * xj[c];
-  }
-  y[(size_t)i * NB + comp] = acc;
+  dev::bsr_spmv_rows<NB>(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, N, rp, ci, vals,
+                         x, y);
 }
 
 template <int NB>

@@ -31,7 +31,8 @@ EXPORTS = ["mss_options_default", "mss_create", "mss_destroy", "mss_setup", "mss
            "mss_residual_norm", "mss_residual_norm_noalloc", "mss_condense", "mss_recover", "mss_get_scaled", "mss_amg_num_levels", "mss_amg_level_sizes", "mss_amg_level_copy",
            "mss_bilu_num_colours", "mss_bilu_ordering", "mss_bilu_factors", "mss_probe_wait_limit", "mss_kernel_launches",
            "mss_trace_enable", "mss_trace_read", "mss_status_string", "mss_last_error",
-           "mss_batch_create", "mss_batch_destroy", "mss_batch_solve", "mss_batch_tuned",
+           "mss_batch_create", "mss_batch_destroy", "mss_batch_set_schedule", "mss_batch_solve",
+           "mss_batch_tuned",
            "mss_batch_last_error", "mss_gnn_num_params", "mss_gnn_create", "mss_gnn_destroy",
            "mss_gnn_info", "mss_gnn_set_vectors", "mss_gnn_weights", "mss_gnn_loss_grad",
            "mss_gnn_adam", "mss_gnn_last_error"]
@@ -87,7 +88,9 @@ class System(C.Structure):
 
 class BatchInfo(C.Structure):
     _fields_ = [("bucket", C.c_int32), ("threads", C.c_int32), ("driver", C.c_int32),
-                ("lane", C.c_int32), ("latency_ms", C.c_double), ("finish_ms", C.c_double)]
+                ("lane", C.c_int32), ("latency_ms", C.c_double), ("finish_ms", C.c_double),
+                ("schedule", C.c_int32), ("group", C.c_int32), ("tile_blocks", C.c_int32),
+                ("per_sm", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -148,6 +151,7 @@ def load(path: Path | str | None = None):
     L.mss_batch_destroy.restype = None
     L.mss_batch_solve.argtypes = [P, C.c_int, C.POINTER(System), C.POINTER(Options), C.c_double,
                                   C.c_int, C.POINTER(Result), C.POINTER(BatchInfo)]
+    L.mss_batch_set_schedule.argtypes = [P, C.c_int]
     L.mss_batch_tuned.argtypes = [P, C.c_int, P]
     L.mss_batch_last_error.restype = C.c_char_p
     L.mss_batch_last_error.argtypes = [P]
@@ -483,12 +487,17 @@ class Solver:
         return fv.view(self.nnzb, self.nb, self.nb), fd.view(self.N, self.nb, self.nb)
 
 
+SCHEDULES = {"lanes": 0, "fused": 1}
+
+
 class Batch:
     """Batched set-up and solve of independent systems (mss_batch_*): `lanes`
     worker threads, each with its own handle and stream; the autotuner picks
-    threads per CTA and the solve driver per size bucket."""
+    threads per CTA and the solve driver per size bucket. schedule="fused"
+    solves the systems of each block size in lock step through multi-system
+    launches (one graph per group; the autotuner picks their tile shape)."""
 
-    def __init__(self, lanes: int = 8, autotune: bool = True):
+    def __init__(self, lanes: int = 8, autotune: bool = True, schedule: str = "lanes"):
         import torch
         self._torch = torch
         self.lib = load()
@@ -496,6 +505,12 @@ class Batch:
         st = self.lib.mss_batch_create(C.byref(self.b), int(lanes), int(autotune))
         if st != OK:
             raise MssError(st, "mss_batch_create -> " + self.lib.mss_status_string(st).decode())
+        self.set_schedule(schedule)
+
+    def set_schedule(self, schedule: str):
+        st = self.lib.mss_batch_set_schedule(self.b, SCHEDULES[schedule])
+        if st != OK:
+            raise MssError(st, "mss_batch_set_schedule -> " + self.lib.mss_status_string(st).decode())
 
     def __del__(self):
         if sys.is_finalizing():
