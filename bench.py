@@ -716,8 +716,35 @@ def batch_leg(a, torch):
             raise RuntimeError("batched solve failed")
         lat_b = [f["latency_ms"] for f in inf]
         its_b = [r["iters"] for r in res]
+        setup_sum_b = sum(r["setup_ms"] for r in res)
+        solve_sum_b = sum(r["solve_ms"] for r in res)
     wall_b = float(np.median(walls))
     assert its_b == its_s, "batched and sequential iteration counts differ"
+    xs_lanes = [x.clone() for x in xs]
+    # fused schedule: set-ups on the lanes, then one lock-step group solve per
+    # block size through multi-system launches (tile shape tuned on the
+    # warm-up run)
+    F = mss.Batch(lanes=a.batch_lanes, autotune=True, schedule="fused")
+    F.solve(dev, tol=a.tol, maxit=a.maxit, restart=a.restart)
+    walls_f, lat_f, its_f, solve_f, setup_f = [], [], [], [], []
+    for _ in range(leg_steps(a, 3)):
+        t0 = time.perf_counter()
+        xs, res, inf_f = F.solve(dev, tol=a.tol, maxit=a.maxit, restart=a.restart)
+        walls_f.append((time.perf_counter() - t0) * 1e3)
+        if any(r["status"] != 0 for r in res):
+            raise RuntimeError("fused batched solve failed")
+        lat_f = [f["latency_ms"] for f in inf_f]
+        its_f = [r["iters"] for r in res]
+        solve_f.append(max(r["solve_ms"] for r in res))
+        setup_f.append(max(f["finish_ms"] - r["solve_ms"] for f, r in zip(inf_f, res)))
+    wall_f = float(np.median(walls_f))
+    assert its_f == its_s, "fused and sequential iteration counts differ"
+    same_bits = all(bool(torch.equal(x, y)) for x, y in zip(xs, xs_lanes))
+    groups = {}
+    for f, d in zip(inf_f, dev):
+        groups.setdefault(f["group"], {"nb": d["nb"], "systems": 0,
+                                       "tile_blocks": f["tile_blocks"], "per_sm": f["per_sm"]})
+        groups[f["group"]]["systems"] += 1
     n = len(dev)
     return {"workload": f"{n} systems, sides U[64,512], nb in {{4,6}}, Pe log-U[0.1,1000], "
                         f"sigma 2, fgmres{a.restart} to {a.tol:g}",
@@ -731,6 +758,18 @@ def batch_leg(a, torch):
                            "latency_p50_ms": round(float(np.percentile(lat_s, 50)), 3),
                            "latency_p99_ms": round(float(np.percentile(lat_s, 99)), 3)},
             "speedup_solves_per_s": round(wall_s / wall_b, 3),
+            "lanes_setup_ms_sum": round(setup_sum_b, 1),
+            "lanes_solve_ms_sum": round(solve_sum_b, 1),
+            "fused": {"solves_per_s": round(n / (wall_f * 1e-3), 2),
+                      "wall_ms": round(wall_f, 2),
+                      "group_solve_ms": round(float(np.median(solve_f)), 2),
+                      "setup_phase_ms": round(float(np.median(setup_f)), 2),
+                      "latency_p50_ms": round(float(np.percentile(lat_f, 50)), 3),
+                      "latency_p99_ms": round(float(np.percentile(lat_f, 99)), 3),
+                      "speedup_solves_per_s_over_sequential": round(wall_s / wall_f, 3),
+                      "speedup_solves_per_s_over_lanes": round(wall_b / wall_f, 3),
+                      "solutions_equal_lanes_bitwise": same_bits,
+                      "groups": [groups[k] for k in sorted(groups)]},
             "iters_total": int(sum(its_b)),
             "tuned": [list(t) for t in B.tuned()],
             "timing": "host clock around each call (every solution complete on return); "

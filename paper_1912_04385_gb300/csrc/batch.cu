@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cmath>
 #include <map>
 #include <memory>
@@ -77,6 +78,10 @@ struct mss_batch {
   int autotune = 1;
   int schedule = MSS_SCHEDULE_LANES;
   FusedTuneCache fcache;        // tile shapes of the fused schedule
+  // the fused schedule's per-system handles, kept between calls (the k-th
+  // largest system of a call takes handle k; a set-up replaces its contents)
+  std::vector<std::unique_ptr<Handle>> sysh;
+  std::vector<std::unique_ptr<Handle>> grouph;   // the group solves' streams and buffers
   std::vector<std::unique_ptr<Handle>> lane;
   std::mutex mu;
   std::map<long long, Choice> cache;   // key: bucket * 16 + nb
@@ -199,18 +204,112 @@ void run_one(mss_batch* B, Handle& H, int lane, const mss_system& s, const mss_o
   }
 }
 
-// The fused schedule: every system set up on a handle of its own by the lanes
-// (largest first), then one lock-step group solve per block size, the groups
-// on their own streams and threads. The systems in `idx` are the ones it
+// The fused schedule. The systems of each block size are split, in
+// largest-first order, into kWaves groups of about equal cell counts; the
+// lanes set every system up on a handle of its own (largest first), and each
+// group is solved in lock step (fused_solve) on its own thread and stream as
+// soon as its last set-up is done, so the group solves of the first waves
+// overlap the set-ups of the later ones. The systems in `idx` are the ones it
 // takes (order: largest first).
+constexpr int kWaves = 3;
+
 void batch_fused(mss_batch* B, const std::vector<int>& idx, const mss_system* sys,
                  const mss_options& base, double tol, int maxit, mss_result* results,
                  mss_batch_info* info, Clock::time_point tbatch) {
   const int n = (int)idx.size();
-  std::vector<std::unique_ptr<Handle>> hs((size_t)n);
+  if ((int)B->sysh.size() < n) B->sysh.resize((size_t)n);
+  auto& hs = B->sysh;
+  // groups: per nb, consecutive systems (largest first) up to 1/kWaves of the
+  // nb's cells each
+  std::map<int, long long> cells_of_nb;
+  for (int k = 0; k < n; ++k) cells_of_nb[sys[idx[k]].nb] += sys[idx[k]].J.n_rows;
+  std::vector<std::vector<int>> members;
+  std::vector<int> gid((size_t)n);
+  {
+    std::map<int, std::pair<int, long long>> open;   // nb -> (group, cells so far)
+    for (int k = 0; k < n; ++k) {
+      const int nb = sys[idx[k]].nb;
+      auto it = open.find(nb);
+      if (it == open.end()) {
+        members.emplace_back();
+        it = open.emplace(nb, std::make_pair((int)members.size() - 1, 0LL)).first;
+      }
+      const int g = it->second.first;
+      members[g].push_back(k);
+      gid[k] = g;
+      it->second.second += sys[idx[k]].J.n_rows;
+      if (it->second.second * kWaves >= cells_of_nb[nb]) open.erase(it);   // the group is full
+    }
+  }
+  const int ng = (int)members.size();
+  if ((int)B->grouph.size() < ng) B->grouph.resize((size_t)ng);
   std::vector<double> t0((size_t)n, 0.0);
   std::vector<int> lane_of((size_t)n, 0);
   std::vector<char> ok((size_t)n, 0);
+  std::vector<int> pending((size_t)ng);
+  for (int g = 0; g < ng; ++g) pending[g] = (int)members[g].size();
+  std::mutex mu;
+  std::condition_variable cv;
+  // ---- group solves: each waits for its set-ups, then runs
+  auto solve_group = [&](int g) {
+    cudaSetDevice(B->device);
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [&] { return pending[g] == 0; });
+    }
+    std::vector<int> ks;
+    for (int k : members[g])
+      if (ok[k]) ks.push_back(k);
+    if (ks.empty()) return;
+    std::vector<Handle*> hv;
+    std::vector<const double*> bv;
+    std::vector<double*> xv;
+    for (int k : ks) {
+      hv.push_back(hs[k].get());
+      bv.push_back(sys[idx[k]].b);
+      xv.push_back(sys[idx[k]].x);
+    }
+    std::vector<mss_result> res;
+    FusedInfo fi;
+    int code = MSS_OK;
+    const auto ts = Clock::now();
+    try {
+      if (!B->grouph[g]) B->grouph[g].reset(make_lane(B->device));
+      Handle* gh = B->grouph[g].get();
+      fused_solve(gh, hv, bv, xv, tol, maxit, base.driver, B->autotune ? &B->fcache : nullptr,
+                  res, &fi);
+      MSS_CK(cudaStreamSynchronize(gh->stream));
+    } catch (...) {
+      code = error_code();
+    }
+    const double solve_ms = ms_since(ts), tend = ms_since(tbatch);
+    for (size_t q = 0; q < ks.size(); ++q) {
+      const int k = ks[q], i = idx[k];
+      if (code == MSS_OK) {
+        results[i] = res[q];
+        results[i].solve_ms = solve_ms;
+      } else {
+        results[i] = mss_result{};
+        results[i].status = code;
+      }
+      if (info) {
+        mss_batch_info& f = info[i];
+        f.bucket = bucket_of(sys[i].J.n_rows);
+        f.threads = 256;
+        f.driver = base.driver;
+        f.lane = lane_of[k];
+        f.latency_ms = tend - t0[k];
+        f.finish_ms = tend;
+        f.schedule = MSS_SCHEDULE_FUSED;
+        f.group = g;
+        f.tile_blocks = fi.tile_blocks;
+        f.per_sm = fi.per_sm;
+      }
+    }
+  };
+  std::vector<std::thread> gt;
+  for (int g = 0; g < ng; ++g) gt.emplace_back(solve_group, g);
+  // ---- set-ups on the lanes, largest first
   std::atomic<int> next{0};
   auto work = [&](int l) {
     cudaSetDevice(B->device);
@@ -221,7 +320,7 @@ void batch_fused(mss_batch* B, const std::vector<int>& idx, const mss_system* sy
       t0[k] = ms_since(tbatch);
       lane_of[k] = l;
       try {
-        hs[k].reset(make_lane(B->device));
+        if (!hs[k]) hs[k].reset(make_lane(B->device));
         setup_handle(*hs[k], &sys[i].J, sys[i].nb, sys[i].layout, &base);
         MSS_CK(cudaStreamSynchronize(hs[k]->stream));
         ok[k] = 1;
@@ -229,6 +328,11 @@ void batch_fused(mss_batch* B, const std::vector<int>& idx, const mss_system* sy
         results[i] = mss_result{};
         results[i].status = error_code();
       }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        --pending[gid[k]];
+      }
+      cv.notify_all();
     }
   };
   {
@@ -238,64 +342,9 @@ void batch_fused(mss_batch* B, const std::vector<int>& idx, const mss_system* sy
     work(0);
     for (auto& t : th) t.join();
   }
-  std::map<int, std::vector<int>> groups;   // nb -> positions in idx
-  for (int k = 0; k < n; ++k)
-    if (ok[k]) groups[sys[idx[k]].nb].push_back(k);
-  std::vector<std::thread> gt;
-  int gno = 0;
-  for (auto& g : groups) {
-    gt.emplace_back([&, ks = g.second, gi = gno] {
-      cudaSetDevice(B->device);
-      std::vector<Handle*> hv;
-      std::vector<const double*> bv;
-      std::vector<double*> xv;
-      for (int k : ks) {
-        hv.push_back(hs[k].get());
-        bv.push_back(sys[idx[k]].b);
-        xv.push_back(sys[idx[k]].x);
-      }
-      std::vector<mss_result> res;
-      FusedInfo fi;
-      int code = MSS_OK;
-      const auto ts = Clock::now();
-      try {
-        std::unique_ptr<Handle> gh(make_lane(B->device));
-        fused_solve(gh.get(), hv, bv, xv, tol, maxit, base.driver,
-                    B->autotune ? &B->fcache : nullptr, res, &fi);
-        MSS_CK(cudaStreamSynchronize(gh->stream));
-      } catch (...) {
-        code = error_code();
-      }
-      const double solve_ms = ms_since(ts), tend = ms_since(tbatch);
-      for (size_t q = 0; q < ks.size(); ++q) {
-        const int k = ks[q], i = idx[k];
-        if (code == MSS_OK) {
-          results[i] = res[q];
-          results[i].solve_ms = solve_ms;
-        } else {
-          results[i] = mss_result{};
-          results[i].status = code;
-        }
-        if (info) {
-          mss_batch_info& f = info[i];
-          f.bucket = bucket_of(sys[i].J.n_rows);
-          f.threads = 256;
-          f.driver = base.driver;
-          f.lane = lane_of[k];
-          f.latency_ms = tend - t0[k];
-          f.finish_ms = tend;
-          f.schedule = MSS_SCHEDULE_FUSED;
-          f.group = gi;
-          f.tile_blocks = fi.tile_blocks;
-          f.per_sm = fi.per_sm;
-        }
-      }
-    });
-    ++gno;
-  }
   for (auto& t : gt) t.join();
-  for (auto& h : hs)
-    if (h) cudaStreamSynchronize(h->stream);
+  for (int k = 0; k < n; ++k)
+    if (hs[k]) cudaStreamSynchronize(hs[k]->stream);
 }
 
 }  // namespace
@@ -326,6 +375,10 @@ int mss_batch_create(mss_batch** out, int lanes, int autotune) {
 void mss_batch_destroy(mss_batch* B) {
   if (!B) return;
   for (auto& h : B->lane)
+    if (h) cudaStreamSynchronize(h->stream);
+  for (auto& h : B->sysh)
+    if (h) cudaStreamSynchronize(h->stream);
+  for (auto& h : B->grouph)
     if (h) cudaStreamSynchronize(h->stream);
   delete B;
   trim_pools();
