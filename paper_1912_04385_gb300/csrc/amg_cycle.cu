@@ -331,7 +331,7 @@ __global__ void k_jacobi(int n, const int* __restrict__ rp, const int* __restric
                          C* __restrict__ xout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  jacobi_row<V, C, LdPlain>(i, rp, ci, v, dinv, b, omega, xin, xout);
+  jacobi_row<V, C, LdPlain>(i, i, rp, ci, v, dinv, b, omega, xin, xout);
 }
 
 // Chebyshev step: r = b - A x_in; d = c1 d + c2 D^-1 r; x_out = x_in + d
@@ -422,7 +422,7 @@ __global__ void k_residual(int n, const int* __restrict__ rp, const int* __restr
                            const C* __restrict__ x, C* __restrict__ r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  residual_row<V, C, LdPlain>(i, rp, ci, v, b, x, r);
+  residual_row<V, C, LdPlain>(i, i, rp, ci, v, b, x, r);
 }
 
 template <class V, class C>
@@ -432,7 +432,7 @@ __global__ void k_restrict(int n, const int* __restrict__ rp, const int* __restr
                            C* __restrict__ x1) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  restrict_row<V, C, LdPlain>(i, rp, ci, v, r, b, dinv, omega, x1);
+  restrict_row<V, C, LdPlain>(i, i, rp, ci, v, r, b, dinv, omega, x1);
 }
 
 template <class V, class C>
@@ -441,7 +441,7 @@ __global__ void k_prolong(int n, const int* __restrict__ rp, const int* __restri
                           const C* x, C* xout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  prolong_row<V, C, LdPlain>(i, rp, ci, v, xc, x, xout);
+  prolong_row<V, C, LdPlain>(i, i, rp, ci, v, xc, x, xout);
 }
 
 // x = Ainv b, one warp per row
@@ -451,20 +451,27 @@ __global__ void k_dense_gemv(int n, const C* __restrict__ A, const C* __restrict
   int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (row >= n) return;
-  const C s = gemv_row<C, LdPlain>(row, lane, n, A, b);
+  const C s = gemv_row<C, LdPlain>(A + (size_t)row * n, lane, n, b);
   if (lane == 0) x[row] = s;
 }
 
 // ---- fused coarse levels -------------------------------------------------
-// With the host-driven solve, the levels from the first one with at most
-// kTailRows rows down to the coarsest run in one cooperative launch: the
-// per-level steps of the V-cycle (Jacobi sweeps, residual, restriction with
-// the next level's first sweep, the coarse product, prolongation,
-// post-sweeps) as grid-stride loops over rows, separated by grid barriers.
-// Each barrier's wait is bounded: past the limit it sets *err, every block
-// leaves the kernel, and the solve reports the error.
-constexpr int kTailRows = 32768;
+// The levels from the first one whose rows fit the blocks' shared memory down
+// to the coarsest run in one cooperative launch of one block per SM. Block b
+// owns a contiguous slice of the rows of every level (rows [b R_l, (b+1) R_l),
+// R_l = ceil(n_l / blocks)); at the start it copies its rows of A, of P, of R
+// for its rows of the next level, of D^-1 and of the coarse inverse into
+// shared memory. Then it runs the per-level steps of the V-cycle (Jacobi
+// sweeps, residual, restriction with the next level's first sweep, the
+// coarse product, prolongation, post-sweeps) over its rows, with a grid
+// barrier between steps, so a step waits on the gathers of other blocks'
+// vector entries (from L2) and no longer on its matrix rows. Each barrier's
+// wait is bounded: past the limit it sets *err, every block leaves the
+// kernel, and the solve reports the error.
 constexpr unsigned kBarrierSpins = 1u << 20;   // polls of L2: well under a second
+constexpr int kMaxTail = 16;                    // levels of the fused launch
+constexpr int kTailThreads = 512;
+constexpr size_t kTailSmemCap = 200 * 1024;     // shared memory of one block, at most
 
 template <class V, class C>
 struct TailLevel {
@@ -480,6 +487,36 @@ struct TailCoarse {
   int n;
   const C* ainv;
   C *b, *x;
+};
+
+// rows [r0, r1) of n owned by block b of G
+__host__ __device__ __forceinline__ void tail_rows(int n, int G, int b, int& r0, int& r1) {
+  const int R = (n + G - 1) / G;
+  const long long a = (long long)b * R;
+  r0 = (int)(a < n ? a : n);
+  r1 = r0 + R < n ? r0 + R : n;
+}
+
+// Bytes of one level's shared-memory copy: rows nr (next level nc), entries
+// na of A, np of P, nq of R; every array starts on an 8-byte boundary.
+__host__ __device__ __forceinline__ size_t al8(size_t x) { return (x + 7) & ~(size_t)7; }
+template <class V, class C>
+__host__ __device__ __forceinline__ size_t tail_level_bytes(int nr, int nc, int na, int np,
+                                                            int nq) {
+  return al8(sizeof(C) * nr) + al8(sizeof(V) * na) + al8(sizeof(V) * np) +
+         al8(sizeof(V) * nq) + al8(sizeof(int) * (nr + 1)) + al8(sizeof(int) * na) +
+         al8(sizeof(int) * (nr + 1)) + al8(sizeof(int) * np) + al8(sizeof(int) * (nc + 1)) +
+         al8(sizeof(int) * nq);
+}
+
+// One block's copy of one level: its rows [r0, r1) and the next level's [c0,
+// c1); row pointers rebased to the copy
+template <class V, class C>
+struct TailSlice {
+  int r0, r1, c0, c1;
+  C* dinv;
+  V *v, *pv, *rv;
+  int *rp, *ci, *prp, *pci, *rrp, *rci;
 };
 
 // One word per barrier sequence: every block adds 1, block 0 adds 2^31 minus
@@ -521,58 +558,153 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned n
 // runs out, sets *err and returns (the bounded-wait path, exercised by a test).
 __global__ void k_wait_probe(unsigned* bar, int* err) { grid_barrier(bar, err, 2u); }
 
+// dst[k] = src[k] (minus sub: row pointers rebased) for k < n by the block,
+// eight loads in flight per thread (otherwise the copies are a chain of
+// dependent round trips)
+template <class T, bool REBASE = false>
+__device__ __forceinline__ void copy_in(T* dst, const T* __restrict__ src, int n, int sub = 0) {
+  constexpr int U = 8;
+  const int nt = blockDim.x;
+  for (int k0 = threadIdx.x; k0 < n; k0 += U * nt) {
+    T t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u * nt < n) t[u] = src[k0 + u * nt];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u * nt < n) {
+        if constexpr (REBASE) dst[k0 + u * nt] = t[u] - sub;
+        else dst[k0 + u * nt] = t[u];
+      }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T* carve(unsigned char* base, size_t& off, size_t count) {
+  T* p = reinterpret_cast<T*>(base + off);
+  off += al8(sizeof(T) * count);
+  return p;
+}
+
 template <class V, class C>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kTailThreads, 1)
 k_vcycle_tail(const TailLevel<V, C>* __restrict__ lev, int nlev, TailCoarse<C> co, int nu_pre,
               int nu_post, C omega, unsigned* bar, int* err) {
-  constexpr int kMaxTail = 32;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nthr = gridDim.x * blockDim.x;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TailSlice<V, C> S[kMaxTail];
+  __shared__ int bnd[kMaxTail][6];
+  __shared__ C* ainv_s;
+  __shared__ int cr0, cr1;
+  const int G = gridDim.x, blk = blockIdx.x, nt = blockDim.x;
+  // ---- the block's rows and the extents of its copies
+  for (int q = threadIdx.x; q < nlev * 6; q += nt) {
+    const int l = q / 6, k = q - 6 * (q / 6);
+    const TailLevel<V, C>& L = lev[l];
+    int r0, r1, c0, c1;
+    tail_rows(L.n, G, blk, r0, r1);
+    tail_rows(L.nc, G, blk, c0, c1);
+    const int* src[6] = {L.rp + r0, L.rp + r1, L.prp + r0, L.prp + r1, L.rrp + c0, L.rrp + c1};
+    bnd[l][k] = *src[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    size_t off = 0;
+    for (int l = 0; l < nlev; ++l) {
+      TailSlice<V, C>& T = S[l];
+      tail_rows(lev[l].n, G, blk, T.r0, T.r1);
+      tail_rows(lev[l].nc, G, blk, T.c0, T.c1);
+      const int nr = T.r1 - T.r0, nc = T.c1 - T.c0;
+      const int na = bnd[l][1] - bnd[l][0], np = bnd[l][3] - bnd[l][2], nq = bnd[l][5] - bnd[l][4];
+      T.dinv = carve<C>(smem, off, nr);
+      T.v = carve<V>(smem, off, na);
+      T.pv = carve<V>(smem, off, np);
+      T.rv = carve<V>(smem, off, nq);
+      T.rp = carve<int>(smem, off, nr + 1);
+      T.ci = carve<int>(smem, off, na);
+      T.prp = carve<int>(smem, off, nr + 1);
+      T.pci = carve<int>(smem, off, np);
+      T.rrp = carve<int>(smem, off, nc + 1);
+      T.rci = carve<int>(smem, off, nq);
+    }
+    int c0, c1;
+    tail_rows(co.n, G, blk, c0, c1);
+    cr0 = c0;
+    cr1 = c1;
+    ainv_s = carve<C>(smem, off, (size_t)(c1 - c0) * co.n);
+  }
+  __syncthreads();
+  // ---- copies (row pointers rebased to the block's first entry)
+  for (int l = 0; l < nlev; ++l) {
+    const TailLevel<V, C>& L = lev[l];
+    const TailSlice<V, C>& T = S[l];
+    const int nr = T.r1 - T.r0, nc = T.c1 - T.c0;
+    const int a0 = bnd[l][0], p0 = bnd[l][2], q0 = bnd[l][4];
+    const int na = bnd[l][1] - a0, np = bnd[l][3] - p0, nq = bnd[l][5] - q0;
+    copy_in(T.dinv, L.dinv + T.r0, nr);
+    copy_in<int, true>(T.rp, L.rp + T.r0, nr + 1, a0);
+    copy_in<int, true>(T.prp, L.prp + T.r0, nr + 1, p0);
+    copy_in<int, true>(T.rrp, L.rrp + T.c0, nc + 1, q0);
+    copy_in(T.v, L.v + a0, na);
+    copy_in(T.ci, L.ci + a0, na);
+    copy_in(T.pv, L.pv + p0, np);
+    copy_in(T.pci, L.pci + p0, np);
+    copy_in(T.rv, L.rv + q0, nq);
+    copy_in(T.rci, L.rci + q0, nq);
+  }
+  copy_in(ainv_s, co.ainv + (size_t)cr0 * co.n, (cr1 - cr0) * co.n);
+  __syncthreads();
+  // ---- the V-cycle on the block's rows
   bool cur_alt[kMaxTail];            // the level's current vector: x (false) or x2 (true)
   for (int l = 0; l < nlev; ++l) {
-    const TailLevel<V, C> L = lev[l];
+    const TailLevel<V, C>& L = lev[l];
+    const TailSlice<V, C>& T = S[l];
+    const int nr = T.r1 - T.r0, nc = T.c1 - T.c0;
     C* cur = L.x;                    // holds the first sweep from zero
     C* alt = L.x2;
-    for (int s = 1; s < nu_pre; ++s) {
-      for (int i = tid; i < L.n; i += nthr)
-        jacobi_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.dinv, L.b, omega, cur, alt);
-      if (!grid_barrier(bar, err, gridDim.x)) return;
+    for (int q = 1; q < nu_pre; ++q) {
+      for (int m = threadIdx.x; m < nr; m += nt)
+        jacobi_row<V, C, LdL2>(m, T.r0 + m, T.rp, T.ci, T.v, T.dinv, L.b, omega, cur, alt);
+      if (!grid_barrier(bar, err, G)) return;
       C* t = cur;
       cur = alt;
       alt = t;
     }
-    for (int i = tid; i < L.n; i += nthr) residual_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.b, cur, L.r);
-    if (!grid_barrier(bar, err, gridDim.x)) return;
-    C* nb = l + 1 < nlev ? lev[l + 1].b : co.b;
-    C* nx = l + 1 < nlev ? lev[l + 1].x : nullptr;
-    const C* nd = l + 1 < nlev ? lev[l + 1].dinv : nullptr;
-    for (int i = tid; i < L.nc; i += nthr)
-      restrict_row<V, C, LdL2>(i, L.rrp, L.rci, L.rv, L.r, nb, nd, omega, nx);
-    if (!grid_barrier(bar, err, gridDim.x)) return;
+    for (int m = threadIdx.x; m < nr; m += nt)
+      residual_row<V, C, LdL2>(m, T.r0 + m, T.rp, T.ci, T.v, L.b, cur, L.r);
+    if (!grid_barrier(bar, err, G)) return;
+    const bool last = l + 1 == nlev;
+    C* nb = last ? co.b : lev[l + 1].b;
+    C* nx = last ? nullptr : lev[l + 1].x;
+    const C* nd = last ? nullptr : S[l + 1].dinv;
+    for (int m = threadIdx.x; m < nc; m += nt)
+      restrict_row<V, C, LdL2>(m, T.c0 + m, T.rrp, T.rci, T.rv, L.r, nb, nd, omega, nx);
+    if (!grid_barrier(bar, err, G)) return;
     cur_alt[l] = cur != L.x;
   }
   {
     const int lane = threadIdx.x & 31;
-    for (int row = tid >> 5; row < co.n; row += nthr >> 5) {
-      const C s = gemv_row<C, LdL2>(row, lane, co.n, co.ainv, co.b);
+    for (int row = cr0 + (threadIdx.x >> 5); row < cr1; row += nt >> 5) {
+      const C s = gemv_row<C, LdL2>(ainv_s + (size_t)(row - cr0) * co.n, lane, co.n, co.b);
       if (lane == 0) co.x[row] = s;
     }
-    if (!grid_barrier(bar, err, gridDim.x)) return;
+    if (!grid_barrier(bar, err, G)) return;
   }
   for (int l = nlev - 1; l >= 0; --l) {
-    const TailLevel<V, C> L = lev[l];
+    const TailLevel<V, C>& L = lev[l];
+    const TailSlice<V, C>& T = S[l];
+    const int nr = T.r1 - T.r0;
     const C* xc = l + 1 < nlev ? lev[l + 1].x : co.x;
     C* cur = cur_alt[l] ? L.x2 : L.x;
     C* target = nu_post % 2 == 0 ? L.x : L.x2;
-    for (int i = tid; i < L.n; i += nthr)
-      prolong_row<V, C, LdL2>(i, L.prp, L.pci, L.pv, xc, cur, target);
-    if (!grid_barrier(bar, err, gridDim.x)) return;
+    for (int m = threadIdx.x; m < nr; m += nt)
+      prolong_row<V, C, LdL2>(m, T.r0 + m, T.prp, T.pci, T.pv, xc, cur, target);
+    if (!grid_barrier(bar, err, G)) return;
     cur = target;
     C* alt = target == L.x ? L.x2 : L.x;
-    for (int s = 0; s < nu_post; ++s) {
-      for (int i = tid; i < L.n; i += nthr)
-        jacobi_row<V, C, LdL2>(i, L.rp, L.ci, L.v, L.dinv, L.b, omega, cur, alt);
-      if (!grid_barrier(bar, err, gridDim.x)) return;
+    for (int q = 0; q < nu_post; ++q) {
+      for (int m = threadIdx.x; m < nr; m += nt)
+        jacobi_row<V, C, LdL2>(m, T.r0 + m, T.rp, T.ci, T.v, T.dinv, L.b, omega, cur, alt);
+      if (!grid_barrier(bar, err, G)) return;
       C* t = cur;
       cur = alt;
       alt = t;
@@ -745,7 +877,8 @@ void launch_tail(Handle* h, Hierarchy& H) {
   int* err = H.terr.p;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)H.tail_grid);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = H.tail_smem;
   cfg.stream = h->stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
@@ -1041,25 +1174,73 @@ void upload_tail(Handle* h, Hierarchy& H, DBuf<unsigned char>& dst) {
   MSS_CK(cudaStreamSynchronize(h->stream));   // hv lives on this frame
 }
 
+// Per-block bytes of the fused launch's shared-memory copies of levels
+// l..(coarsest) over G blocks (FP64 storage, the larger of the two forms);
+// the row pointers are read back for the levels that can fit at all.
+static std::vector<size_t> tail_level_block_bytes(Handle* h, Level& L, int G) {
+  std::vector<int> rp((size_t)L.n + 1), prp((size_t)L.n + 1), rrp((size_t)L.nc + 1);
+  MSS_CK(cudaMemcpyAsync(rp.data(), L.rp.p, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost,
+                         h->stream));
+  MSS_CK(cudaMemcpyAsync(prp.data(), L.prp.p, sizeof(int) * prp.size(), cudaMemcpyDeviceToHost,
+                         h->stream));
+  MSS_CK(cudaMemcpyAsync(rrp.data(), L.rrp.p, sizeof(int) * rrp.size(), cudaMemcpyDeviceToHost,
+                         h->stream));
+  MSS_CK(cudaStreamSynchronize(h->stream));
+  std::vector<size_t> out((size_t)G);
+  for (int b = 0; b < G; ++b) {
+    int r0, r1, c0, c1;
+    tail_rows(L.n, G, b, r0, r1);
+    tail_rows(L.nc, G, b, c0, c1);
+    out[b] = tail_level_bytes<double, double>(r1 - r0, c1 - c0, rp[r1] - rp[r0], prp[r1] - prp[r0],
+                                              rrp[c1] - rrp[c0]);
+  }
+  return out;
+}
+
 void prepare_tail(Handle* h, Hierarchy& H) {
   H.tail = -1;
   H.tdesc.release();
   H.tdescf.release();
   const int nl = (int)H.lev.size();
   if (h->opt.smoother != MSS_JACOBI || H.bs != 1 || nl < 3) return;
-  int t = -1;
-  for (int l = 1; l + 1 < nl; ++l)
-    if (H.lev[l].n <= kTailRows) {
-      t = l;
-      break;
+  // one block per SM; the first level from which every block's copies fit
+  const int G = h->num_sms;
+  std::vector<size_t> tot((size_t)G, 0);
+  {
+    const int nc = H.lev.back().n;
+    for (int b = 0; b < G; ++b) {
+      int c0, c1;
+      tail_rows(nc, G, b, c0, c1);
+      tot[b] = al8(sizeof(double) * (size_t)(c1 - c0) * nc);
     }
+  }
+  int t = -1;
+  size_t smem = 0;
+  for (int l = nl - 2; l >= 1; --l) {
+    Level& L = H.lev[l];
+    // a level whose average share is already too large cannot fit
+    if ((size_t)L.nnz * 12 / G > kTailSmemCap) break;
+    const std::vector<size_t> lb = tail_level_block_bytes(h, L, G);
+    size_t mx = 0;
+    for (int b = 0; b < G; ++b) mx = std::max(mx, tot[b] + lb[b]);
+    if (mx > kTailSmemCap || nl - 1 - l > kMaxTail) break;
+    for (int b = 0; b < G; ++b) tot[b] += lb[b];
+    t = l;
+    smem = mx;
+  }
   if (t < 0) return;
+  // the kernels' shared-memory limit is process-wide: every handle sets the
+  // same cap (never its own size, which would shrink another handle's)
+  MSS_CK(cudaFuncSetAttribute(k_vcycle_tail<double, double>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemCap));
+  MSS_CK(cudaFuncSetAttribute(k_vcycle_tail<__nv_bfloat16, float>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemCap));
   int per_sm = 0;
   MSS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vcycle_tail<double, double>,
-                                                       256, 0));
+                                                       kTailThreads, smem));
   if (per_sm < 1) return;
-  int want = (H.lev[t].n + 255) / 256;
-  H.tail_grid = std::max(1, std::min(want, h->num_sms));
+  H.tail_grid = G;
+  H.tail_smem = smem;
   H.tail = t;
   H.tbar.reset(h, 1);
   H.terr.reset(h, 1);

@@ -128,10 +128,11 @@ struct Hierarchy {
   DBuf<float> coarse_invf;    // its FP32 copy (mixed precision)
   int nc = 0;                 // size of the coarsest level
   // fused coarse levels: the first level of the tail (-1: none), its launch
-  // width, device descriptors of the tail levels (FP64 and mixed), the grid
+  // width and shared memory, device descriptors of the tail levels (FP64 and mixed), the grid
   // barrier's words and its error flag
   int tail = -1;
   int tail_grid = 0;
+  size_t tail_smem = 0;       // dynamic shared memory of the fused launch's blocks
   DBuf<unsigned char> tdesc, tdescf;
   DBuf<unsigned> tbar;
   DBuf<int> terr;

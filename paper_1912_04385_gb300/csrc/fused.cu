@@ -83,26 +83,27 @@ struct BVOp {
     switch (p.kind) {
       case V_JACOBI:
         if (i < p.n)
-          dev::jacobi_row<double, double, dev::LdPlain>(i, p.rp, p.ci, p.v, p.dinv, p.b, p.omega,
+          dev::jacobi_row<double, double, dev::LdPlain>(i, i, p.rp, p.ci, p.v, p.dinv, p.b, p.omega,
                                                         p.xin, p.xout);
         break;
       case V_RESIDUAL:
-        if (i < p.n) dev::residual_row<double, double, dev::LdPlain>(i, p.rp, p.ci, p.v, p.b,
+        if (i < p.n) dev::residual_row<double, double, dev::LdPlain>(i, i, p.rp, p.ci, p.v, p.b,
                                                                      p.xin, p.xout);
         break;
       case V_RESTRICT:
         if (i < p.n)
-          dev::restrict_row<double, double, dev::LdPlain>(i, p.rp, p.ci, p.v, p.xin, p.xout,
+          dev::restrict_row<double, double, dev::LdPlain>(i, i, p.rp, p.ci, p.v, p.xin, p.xout,
                                                           p.dinv, p.omega, p.x1);
         break;
       case V_PROLONG:
-        if (i < p.n) dev::prolong_row<double, double, dev::LdPlain>(i, p.rp, p.ci, p.v, p.xc,
+        if (i < p.n) dev::prolong_row<double, double, dev::LdPlain>(i, i, p.rp, p.ci, p.v, p.xc,
                                                                     p.xin, p.xout);
         break;
       case V_GEMV: {
         const int row = i >> 5, lane = threadIdx.x & 31;
         if (row < p.n) {
-          const double s = dev::gemv_row<double, dev::LdPlain>(row, lane, p.n, p.v, p.b);
+          const double s = dev::gemv_row<double, dev::LdPlain>(p.v + (size_t)row * p.n, lane,
+                                                               p.n, p.b);
           if (lane == 0) p.xout[row] = s;
         }
         break;
