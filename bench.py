@@ -26,6 +26,12 @@ import sys
 import time
 from pathlib import Path
 
+# More hardware work queues than CUDA's default of 8: the batch legs run many
+# streams at once (lanes, their set-up workers, the fused groups), and streams
+# that share a queue wait on each other's work. Read when CUDA starts, so set
+# before torch touches the device.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import numpy as np
 
 ROOT = Path(__file__).resolve().parent

@@ -454,7 +454,12 @@ int mss_trace_read(mss_handle* h, int kind, int64_t* launches, double* ms, int r
  * group's rows), nb) (fixed at 1 block and 4 CTAs with autotune == 0). It
  * covers FP64 solves with Jacobi smoothing (CPTR3, CPR, ILU0) and nb <= 8;
  * other systems take the lanes schedule. Every system of a group finishes with
- * the group: latency is traded for throughput. */
+ * the group: latency is traded for throughput.
+ *
+ * Both schedules keep many streams busy at once; a process that sets
+ * CUDA_DEVICE_MAX_CONNECTIONS (e.g. 32) before CUDA starts gives them more
+ * hardware work queues than the default 8 (streams sharing a queue wait on
+ * each other's work). */
 enum { MSS_SCHEDULE_LANES = 0, MSS_SCHEDULE_FUSED = 1 };
 
 typedef struct {
