@@ -56,6 +56,8 @@ def args_():
     ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--driver", default="graph", choices=["host", "graph"],
                     help="FGMRES driver: host loop, or the whole solve as one CUDA graph")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="preconditioner precision of the main leg (the bench line is fp64)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--mixed-n", type=int, default=2048,
@@ -219,7 +221,7 @@ def run_ours(a, rank, world, dist):
                     torch.from_numpy(s.vals.reshape(-1)).cuda(), torch.from_numpy(s.b).cuda()))
     torch.cuda.synchronize()
     solver = mss.Solver()
-    opts = mss.options(restart=a.restart, driver=a.driver)
+    opts = mss.options(restart=a.restart, driver=a.driver, precision=a.precision)
     stream = torch.cuda.current_stream()
 
     def step(trace=False, info_out=None, o=None):
@@ -260,7 +262,7 @@ def run_ours(a, rank, world, dist):
     if a.driver == "graph":
         # a solve graph holds no events: kernel-class times come from one
         # host-driven step after the timed region (same kernels, same order)
-        step(o=mss.options(restart=a.restart, driver="host"))
+        step(o=mss.options(restart=a.restart, driver="host", precision=a.precision))
         torch.cuda.synchronize()
         tr = solver.trace_read(reset=True)
         trace_from = "one host-driven step after the timed region"
@@ -303,7 +305,8 @@ def run_ours(a, rank, world, dist):
     n_apply, apply_ms = tr["apply"]
     out = {"metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 3),
-           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if a.precision == "fp64" else "bf16/f32 (FGMRES f64)",
            "data": DATA,
            "config": {**workload_config(a), "parallelism": f"replicas x{world}"},
            "iters": iters, "iters_mean": float(np.mean(iters)),
