@@ -755,34 +755,38 @@ def batch_leg(a, torch):
                                        "tile_blocks": f["tile_blocks"], "per_sm": f["per_sm"]})
         groups[f["group"]]["systems"] += 1
     n = len(dev)
+    # the headline numbers are the fused schedule's (persistent multi-system
+    # launches in one graph per group, tile shape from the autotuner); the
+    # lanes and the one-by-one runs are the comparisons
     return {"workload": f"{n} systems, sides U[64,512], nb in {{4,6}}, Pe log-U[0.1,1000], "
                         f"sigma 2, fgmres{a.restart} to {a.tol:g}",
-            "systems": n, "cells_total": cells, "lanes": a.batch_lanes,
-            "solves_per_s": round(n / (wall_b * 1e-3), 2),
-            "wall_ms": round(wall_b, 2),
-            "latency_p50_ms": round(float(np.percentile(lat_b, 50)), 3),
-            "latency_p99_ms": round(float(np.percentile(lat_b, 99)), 3),
+            "systems": n, "cells_total": cells, "schedule": "fused",
+            "solves_per_s": round(n / (wall_f * 1e-3), 2),
+            "wall_ms": round(wall_f, 2),
+            "latency_p50_ms": round(float(np.percentile(lat_f, 50)), 3),
+            "latency_p99_ms": round(float(np.percentile(lat_f, 99)), 3),
+            "group_solve_ms": round(float(np.median(solve_f)), 2),
+            "setup_phase_ms": round(float(np.median(setup_f)), 2),
+            "groups": [groups[k] for k in sorted(groups)],
+            "solutions_equal_lanes_bitwise": same_bits,
+            "speedup_solves_per_s_over_sequential": round(wall_s / wall_f, 3),
+            "speedup_solves_per_s_over_lanes": round(wall_b / wall_f, 3),
+            "lanes": {"lanes": a.batch_lanes,
+                      "solves_per_s": round(n / (wall_b * 1e-3), 2),
+                      "wall_ms": round(wall_b, 2),
+                      "latency_p50_ms": round(float(np.percentile(lat_b, 50)), 3),
+                      "latency_p99_ms": round(float(np.percentile(lat_b, 99)), 3),
+                      "setup_ms_sum": round(setup_sum_b, 1),
+                      "solve_ms_sum": round(solve_sum_b, 1),
+                      "tuned": [list(t) for t in B.tuned()]},
             "sequential": {"solves_per_s": round(n / (wall_s * 1e-3), 2),
                            "wall_ms": round(wall_s, 2),
                            "latency_p50_ms": round(float(np.percentile(lat_s, 50)), 3),
                            "latency_p99_ms": round(float(np.percentile(lat_s, 99)), 3)},
-            "speedup_solves_per_s": round(wall_s / wall_b, 3),
-            "lanes_setup_ms_sum": round(setup_sum_b, 1),
-            "lanes_solve_ms_sum": round(solve_sum_b, 1),
-            "fused": {"solves_per_s": round(n / (wall_f * 1e-3), 2),
-                      "wall_ms": round(wall_f, 2),
-                      "group_solve_ms": round(float(np.median(solve_f)), 2),
-                      "setup_phase_ms": round(float(np.median(setup_f)), 2),
-                      "latency_p50_ms": round(float(np.percentile(lat_f, 50)), 3),
-                      "latency_p99_ms": round(float(np.percentile(lat_f, 99)), 3),
-                      "speedup_solves_per_s_over_sequential": round(wall_s / wall_f, 3),
-                      "speedup_solves_per_s_over_lanes": round(wall_b / wall_f, 3),
-                      "solutions_equal_lanes_bitwise": same_bits,
-                      "groups": [groups[k] for k in sorted(groups)]},
-            "iters_total": int(sum(its_b)),
-            "tuned": [list(t) for t in B.tuned()],
+            "iters_total": int(sum(its_f)),
+            "set_up_lanes": a.batch_lanes,
             "timing": "host clock around each call (every solution complete on return); "
-                      "batch wall = median over the timed runs after one tuning run"}
+                      "wall = median over the timed runs after one tuning run"}
 
 
 def apply_alg_bytes(N, nnzb, nb, solver, opts):
