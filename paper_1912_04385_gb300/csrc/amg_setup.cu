@@ -131,11 +131,14 @@ __device__ __forceinline__ bool beats(const double* lam, int a, int b) {
 
 // an undecided point becomes C when its (measure, index) beats every
 // undecided strong neighbour in either direction
+// (also zeroes the round's undecided count, which the update kernel after it
+// accumulates)
 __global__ void k_pmis_select(int n, const int* __restrict__ srp, const int* __restrict__ sci,
                               const int* __restrict__ strp, const int* __restrict__ stci,
                               const double* __restrict__ lam, const int* __restrict__ state,
-                              int* __restrict__ newc) {
+                              int* __restrict__ newc, int* __restrict__ undecided) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *undecided = 0;
   if (i >= n) return;
   int pick = 0;
   if (state[i] == ST_U) {
@@ -649,9 +652,9 @@ void pmis_split(Handle* h, int n, const Strength& S, uint64_t seed, int level, D
     for (int r = 0; r < 3; ++r) {
       if (++rounds > n + 3) fail(MSS_ERR_AMG, "PMIS did not terminate");
       k_pmis_select<<<grid_for(n, 256), 256, 0, h->stream>>>(n, S.srp.p, S.sci.p, S.strp.p,
-                                                             S.stci.p, lam.p, state.p, newc.p);
+                                                             S.stci.p, lam.p, state.p, newc.p,
+                                                             und.p);
       MSS_LAUNCH_CK("k_pmis_select");
-      fill_int(h, und.p, 0, 1);
       k_pmis_update<<<grid_for(n, 256), 256, 0, h->stream>>>(n, S.srp.p, S.sci.p, state.p,
                                                              newc.p, und.p);
       MSS_LAUNCH_CK("k_pmis_update");

@@ -39,7 +39,9 @@ constexpr uint64_t KEY_STRIP = 0xFFFEULL << 32;   // priorities of strips
 // no neighbour strip has.
 __global__ void k_jp_pick(int ns, int S, int n, const int* __restrict__ rp,
                           const int* __restrict__ ci, uint64_t seed, uint64_t key,
-                          const int* __restrict__ scol, int* __restrict__ pick) {
+                          const int* __restrict__ scol, int* __restrict__ pick,
+                          int* __restrict__ left) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *left = 0;   // the round's count (k_jp_commit)
   const int lane = threadIdx.x & 31;
   const long long a = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (a >= ns) return;                     // uniform per warp
@@ -701,9 +703,8 @@ void bilu_setup_nb(Handle* h) {
       for (int r = 0; r < 3; ++r) {
         if (++rounds > ns + 3) fail(MSS_ERR_CUDA, "colouring did not terminate");
         k_jp_pick<<<grid_for((long long)ns * 32, 128), 128, 0, h->stream>>>(
-            ns, S, N, h->rp.p, h->ci.p, h->opt.seed, key, scol.p, pick.p);
+            ns, S, N, h->rp.p, h->ci.p, h->opt.seed, key, scol.p, pick.p, left.p);
         MSS_LAUNCH_CK("k_jp_pick");
-        fill_int(h, left.p, 0, 1);
         k_jp_commit<<<grid_for(ns, 256), 256, 0, h->stream>>>(ns, pick.p, scol.p, left.p,
                                                               maxcol.p);
         MSS_LAUNCH_CK("k_jp_commit");
@@ -929,10 +930,9 @@ int colour_points(Handle* h, int n, const int* rp, const int* ci, uint64_t seed,
   while (remaining > 0) {
     for (int r = 0; r < 3; ++r) {   // three rounds per read-back, as for the strips
       if (++rounds > n + 3) fail(MSS_ERR_CUDA, "colouring did not terminate");
-      k_jp_pick<<<grid_for((long long)n * 32, 128), 128, 0, h->stream>>>(n, 1, n, rp, ci, seed,
-                                                                          KEY_CELL, colour, pick.p);
+      k_jp_pick<<<grid_for((long long)n * 32, 128), 128, 0, h->stream>>>(
+          n, 1, n, rp, ci, seed, KEY_CELL, colour, pick.p, left.p);
       MSS_LAUNCH_CK("k_jp_pick");
-      fill_int(h, left.p, 0, 1);
       k_jp_commit<<<grid_for(n, 256), 256, 0, h->stream>>>(n, pick.p, colour, left.p, maxcol.p);
       MSS_LAUNCH_CK("k_jp_commit");
     }

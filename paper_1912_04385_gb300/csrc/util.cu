@@ -227,6 +227,32 @@ __global__ void k_scan_apply(const int* __restrict__ in, int* __restrict__ out, 
   }
 }
 
+// one block: the whole scan tile by tile with a running carry (arrays of at
+// most kScanOneBlock entries: one launch instead of three)
+constexpr int kScanOneBlock = 16 * SCAN_TILE;
+__global__ void k_scan_one_block(const int* __restrict__ in, int* __restrict__ out, int n) {
+  int carry = 0;
+  for (int t0 = 0; t0 < n; t0 += SCAN_TILE) {
+    const int base = t0 + threadIdx.x * SCAN_IPT;
+    int vals[SCAN_IPT];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; ++k) {
+      vals[k] = base + k < n ? in[base + k] : 0;
+      s += vals[k];
+    }
+    int tot;
+    int ex = block_exclusive_scan(s, &tot) + carry;
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; ++k) {
+      if (base + k < n) out[base + k] = ex;
+      if (base + k == n - 1) out[n] = ex + vals[k];
+      ex += vals[k];
+    }
+    carry += tot;
+  }
+}
+
 __global__ void k_fill_int(int* p, int v, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long stride = (long long)gridDim.x * blockDim.x;
@@ -243,6 +269,11 @@ __global__ void k_fill_double(double* p, double v, long long n) {
 void exclusive_scan(Handle* h, const int* in, int* out, int n) {
   if (n <= 0) {
     fill_int(h, out, 0, 1);
+    return;
+  }
+  if (n <= kScanOneBlock) {
+    k_scan_one_block<<<1, SCAN_T, 0, h->stream>>>(in, out, n);
+    MSS_LAUNCH_CK("k_scan_one_block");
     return;
   }
   int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
