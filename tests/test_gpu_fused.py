@@ -112,3 +112,13 @@ def test_fused_unsupported_options_use_the_lanes(mss):
     systems = _systems(seed=5, count=4)
     dev = [_dev(s) for s in systems]
     _check(mss, systems, dev, 1e-8, 500, dict(smoother="chebyshev"), fused_nbs=())
+
+
+def test_fused_degenerate_systems(mss):
+    # a single cell, a few cells (the coarsest level is level 0: the V-cycle
+    # is the dense coarse solve), and ordinary systems in one group
+    shapes = [(1, 1), (2, 3), (5, 4), (24, 17), (31, 30)]
+    systems = [sy.make_system(nx, ny, 4, pe=10.0, sigma=1.0, band=True, seed=400 + k)
+               for k, (nx, ny) in enumerate(shapes)]
+    dev = [_dev(s) for s in systems]
+    _check(mss, systems, dev, 1e-9, 300, dict(amg_max_coarse=20))
