@@ -55,7 +55,7 @@ enum TraceKind {
 
 struct Handle;
 void* dev_alloc(Handle* h, size_t bytes);   // the handle's hooks, else the device pool
-void dev_free(Handle* h, void* p);
+void dev_free(Handle* h, void* p, size_t bytes);   // bytes: as passed to dev_alloc
 cudaMemPool_t device_pool(int device);      // library-owned stream-ordered pool
 void trim_pools();                          // return unused pool memory
 
@@ -74,7 +74,7 @@ struct DBuf {
     p = nn ? static_cast<T*>(dev_alloc(hh, nn * sizeof(T))) : nullptr;
   }
   void release() {
-    if (p) dev_free(h, p);
+    if (p) dev_free(h, p, n * sizeof(T));
     p = nullptr;
     n = 0;
   }
@@ -160,9 +160,24 @@ struct PinnedHost {
 };
 constexpr size_t kPinnedBytes = 256;
 
+// Device blocks a handle without allocation hooks has freed, kept for its
+// next allocations of the same size class on the same stream (reuse on the
+// stream that freed them is ordered after every earlier use there, so it needs
+// no driver call; a set-up allocates and frees a few hundred buffers). Bounded
+// in block size and in total; the rest goes back to the pool. Declared after
+// the stream and before every buffer of the handle: the buffers' frees land
+// here, and the destructor returns the blocks while the stream still exists.
+struct BlockCache {
+  cudaStream_t s = nullptr;                           // the stream the blocks were freed on
+  std::map<size_t, std::vector<void*>> blocks;        // size class -> free blocks
+  size_t bytes = 0;
+  ~BlockCache();
+};
+
 struct Handle {
   OwnedStream owned;
   PinnedHost pin;
+  BlockCache cache;
   // binding
   cudaStream_t stream = nullptr;
   // Worker handles of the concurrent set-up (T and P hierarchies built on

@@ -94,6 +94,24 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
   fail(e == cudaErrorMemoryAllocation ? MSS_ERR_OOM : MSS_ERR_CUDA, buf);
 }
 
+// Size classes of the pool allocations: eight per octave (at most 12.5 %
+// rounding), 256 bytes at least, so that freed blocks fit later requests of
+// nearby sizes.
+static size_t size_class(size_t b) {
+  if (b <= 256) return 256;
+  int e = 0;
+  while (((size_t)1 << (e + 1)) < b) ++e;          // 2^e < b <= 2^(e+1)
+  const size_t step = (size_t)1 << (e >= 3 ? e - 3 : 0);
+  return (b + step - 1) / step * step;
+}
+constexpr size_t kCacheBlockMax = (size_t)64 << 20;   // larger blocks go back to the pool
+constexpr size_t kCacheMax = (size_t)256 << 20;       // per handle
+
+BlockCache::~BlockCache() {
+  for (auto& kv : blocks)
+    for (void* p : kv.second) cudaFreeAsync(p, s);
+}
+
 void* dev_alloc(Handle* h, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) return nullptr;
@@ -104,7 +122,18 @@ void* dev_alloc(Handle* h, size_t bytes) {
       fail(MSS_ERR_INVALID_ARG, "allocator returned memory not aligned to 256 bytes");
     return p;
   }
-  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, device_pool(h->device), h->stream);
+  const size_t cls = size_class(bytes);
+  BlockCache& C = h->cache;
+  if (!h->capturing && C.s == h->stream) {
+    auto it = C.blocks.find(cls);
+    if (it != C.blocks.end() && !it->second.empty()) {
+      p = it->second.back();
+      it->second.pop_back();
+      C.bytes -= cls;
+      return p;
+    }
+  }
+  cudaError_t e = cudaMallocFromPoolAsync(&p, cls, device_pool(h->device), h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     fail(MSS_ERR_OOM, "pool allocation of " + std::to_string(bytes) + " bytes failed");
@@ -112,10 +141,21 @@ void* dev_alloc(Handle* h, size_t bytes) {
   return p;
 }
 
-void dev_free(Handle* h, void* p) {
+void dev_free(Handle* h, void* p, size_t bytes) {
   if (!p) return;
-  if (h->free_fn) h->free_fn(p, h->ctx);
-  else cudaFreeAsync(p, h->stream);
+  if (h->free_fn) {
+    h->free_fn(p, h->ctx);
+    return;
+  }
+  const size_t cls = size_class(bytes);
+  BlockCache& C = h->cache;
+  if (!C.s && C.blocks.empty()) C.s = h->stream;
+  if (!h->capturing && C.s == h->stream && cls <= kCacheBlockMax && C.bytes + cls <= kCacheMax) {
+    C.blocks[cls].push_back(p);
+    C.bytes += cls;
+    return;
+  }
+  cudaFreeAsync(p, h->stream);
 }
 
 // One stream-ordered memory pool per device for handles without hooks (and
