@@ -863,6 +863,13 @@ bool has_sweep0(const Hierarchy& H, const mss_options& o, int l) {
 const unsigned char* tail_desc(Hierarchy& H, double*) { return H.tdesc.p; }
 const unsigned char* tail_desc(Hierarchy& H, float*) { return H.tdescf.p; }
 
+// The fused launches of different handles run one after the other on the
+// device: a grid with one block per SM cannot share the device with another
+// such grid, so each launch waits (on its stream, no host wait) for the
+// completion event of the previous one, whichever stream ran it.
+std::mutex g_tail_mu;
+cudaEvent_t g_tail_done[64] = {};   // per device
+
 template <class V, class C>
 void launch_tail(Handle* h, Hierarchy& H) {
   const int nlev = (int)H.lev.size() - 1 - H.tail;
@@ -885,9 +892,15 @@ void launch_tail(Handle* h, Hierarchy& H) {
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  std::lock_guard<std::mutex> lk(g_tail_mu);
+  if (h->device < 0 || h->device >= 64) fail(MSS_ERR_CUDA, "device index out of range");
+  cudaEvent_t& done = g_tail_done[h->device];
+  if (!done) MSS_CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+  MSS_CK(cudaStreamWaitEvent(h->stream, done, 0));
   MSS_CK(cudaLaunchKernelEx(&cfg, k_vcycle_tail<V, C>, lev, nlev, co, nu_pre, nu_post, omega, bar,
                             err));
   MSS_LAUNCH_CK("k_vcycle_tail");
+  MSS_CK(cudaEventRecord(done, h->stream));
 }
 
 template <class V, class C>

@@ -204,12 +204,19 @@ __global__ void k_interp(int n, const int* __restrict__ rp, const int* __restric
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int b = rp[i], e = rp[i + 1];
-  int* cset = scr_ci + b;
-  double* num = scr_v + b;
-  int* keep = scr_k + b;
+  // the row's work lists in thread-local arrays when the row is short enough
+  // (the common case), else in its scratch segment; the result goes to the
+  // scratch segment either way
+  constexpr int kLocal = 16;
+  int lci[kLocal], lkeep[kLocal];
+  double lnum[kLocal];
+  const bool loc = e - b <= kLocal;
+  int* cset = loc ? lci : scr_ci + b;
+  double* num = loc ? lnum : scr_v + b;
+  int* keep = loc ? lkeep : scr_k + b;
   if (cf[i]) {
-    cset[0] = cidx[i];
-    num[0] = 1.0;
+    scr_ci[b] = cidx[i];
+    scr_v[b] = 1.0;
     plen[i] = 1;
     return;
   }
@@ -289,6 +296,11 @@ __global__ void k_interp(int n, const int* __restrict__ rp, const int* __restric
       cset[len] = cidx[cset[q]];
       num[len] = num[q];
       ++len;
+    }
+  if (loc)
+    for (int q = 0; q < len; ++q) {
+      scr_ci[b + q] = cset[q];
+      scr_v[b + q] = num[q];
     }
   plen[i] = len;
 }
