@@ -195,7 +195,7 @@ struct Handle {
   int N = 0, nb = 0, nnzb = 0, p = 0, t = 1;
   bool col_major = false;      // layout of the set-up's blocks
   mss_options opt{};
-  int tb = 256;                // threads per CTA of the apply-path kernels (a multiple
+  int tb = 128;                // threads per CTA of the apply-path kernels (a multiple
                                // of 32; no result depends on it); set by the autotuner
   mss_bsr J{};                 // the caller's matrix (identity check in solve)
   double setup_ms = 0.0;
