@@ -513,10 +513,11 @@ __global__ void k_bilu_fwd_par(int q0, int q1, const int* __restrict__ perm,
                                const int* __restrict__ fpos, const int* __restrict__ fcell,
                                const V* __restrict__ fv, const C* __restrict__ fcs,
                                const double* __restrict__ r, const C* __restrict__ xT,
-                               const C* __restrict__ vP, C* __restrict__ w, int lower) {
+                               const C* __restrict__ vP, C* __restrict__ w, int lower,
+                               int wait_first) {
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   fwd_par<NB, MODE, V, C>(warp, q0, q1, perm, frp, fslo, fpos, fcell, fv, fcs, r, xT, vP, w,
-                          lower);
+                          lower, wait_first);
 }
 
 template <int NB, class V, class C>
@@ -858,6 +859,27 @@ Factors<__nv_bfloat16, float> factors(Handle* h, const float*) {
   return {h->fvh.p, h->fdinvh.p, h->cLh.p, h->cGh.p, h->fcsf.p, h->wf.p};
 }
 
+// The sweep kernels follow one another on the handle's stream with
+// programmatic serialization: each may be scheduled once its predecessor has
+// passed its own wait, loads what does not depend on that predecessor (factor
+// data, chain blocks, the stage terms of later colours) and then waits for it
+// (bilu_sweeps.cuh), so one launch's ramp overlaps the drain of the one
+// before. The first sweep kernel is launched without the attribute.
+template <class... P, class... A>
+void launch_sweep(void (*k)(P...), unsigned grid, unsigned block, cudaStream_t s, bool pdl,
+                  A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  MSS_CK(cudaLaunchKernelEx(&cfg, k, ((P)args)...));
+}
+
 template <int NB, int MODE, class V, class C>
 void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, const C* vP,
             double* y) {
@@ -868,22 +890,26 @@ void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, con
                       (h->opt.ilu_order == MSS_STRIPS || h->opt.ilu_order == MSS_STRIPS_JP) &&
                       h->opt.ilu_strip > 1;
   const int T = h->tb;   // any multiple of 32: results do not depend on it
+  // with the event trace on, the events between launches would stand between
+  // the kernels, so the attribute is not asked for
+  const bool pdl = !h->trace;
+  bool first = true;
   for (int c = 0; c < h->ncol; ++c) {
     const int q0 = h->cstart[c], q1 = h->cstart[c + 1];
     const int s0 = h->sc_start[c], s1 = h->sc_start[c + 1];
     if (q1 <= q0) continue;
     TraceScope ts(h, TR_BILU_FWD);
     const long long rw = (q1 - q0 + RPW - 1) / RPW;
-    k_bilu_fwd_par<NB, MODE, V, C><<<grid_for(rw * 32, T), T, 0, h->stream>>>(
-        q0, q1, h->perm.p, h->frp.p, h->fslo.p, h->fpos.p, h->fcell.p, F.fv, F.fcs, r, xT, vP,
-        F.w, bjac ? 0 : 1);
+    launch_sweep(k_bilu_fwd_par<NB, MODE, V, C>, grid_for(rw * 32, T), T, h->stream,
+                 pdl && !first, q0, q1, h->perm.p, h->frp.p, h->fslo.p, h->fpos.p, h->fcell.p,
+                 F.fv, F.fcs, r, xT, vP, F.w, bjac ? 0 : 1, first ? 1 : 0);
     MSS_LAUNCH_CK("k_bilu_fwd_par");
+    first = false;
     if (chains) {
       const long long sw = (s1 - s0 + RPW - 1) / RPW;
-      k_bilu_fwd_chain<NB, V, C><<<grid_for(sw * 32, kChainThreads), kChainThreads, 0,
-                                   h->stream>>>(
-          s0, s1, h->st_first.p, h->st_len.p, h->fslo.p, h->fdp.p, h->fpos.p, F.fv, F.cL,
-          h->cflag.p, F.w);
+      launch_sweep(k_bilu_fwd_chain<NB, V, C>, grid_for(sw * 32, kChainThreads), kChainThreads,
+                   h->stream, pdl, s0, s1, h->st_first.p, h->st_len.p, h->fslo.p, h->fdp.p,
+                   h->fpos.p, F.fv, F.cL, h->cflag.p, F.w);
       MSS_LAUNCH_CK("k_bilu_fwd_chain");
     }
   }
@@ -894,16 +920,15 @@ void sweeps(Handle* h, const Factors<V, C>& F, const double* r, const C* xT, con
     TraceScope ts(h, TR_BILU_BWD);
     if (!bjac) {
       const long long rw = (q1 - q0 + RPW - 1) / RPW;
-      k_bilu_bwd_par<NB, V, C><<<grid_for(rw * 32, T), T, 0, h->stream>>>(
-          q0, q1, h->frp.p, h->fshi.p, h->fpos.p, F.fv, F.fdinv, F.w);
+      launch_sweep(k_bilu_bwd_par<NB, V, C>, grid_for(rw * 32, T), T, h->stream, pdl, q0, q1,
+                   h->frp.p, h->fshi.p, h->fpos.p, F.fv, F.fdinv, F.w);
       MSS_LAUNCH_CK("k_bilu_bwd_par");
     }
     const long long sw = (s1 - s0 + RPW - 1) / RPW;
-    k_bilu_bwd_chain<NB, V, C><<<grid_for(sw * 32, kChainThreads), kChainThreads, 0,
-                                 h->stream>>>(
-        s0, s1, h->st_first.p, h->st_len.p, h->fdp.p, h->fshi.p, h->fpos.p, F.fv, F.fdinv, F.cG,
-        h->cflag.p, F.w, bjac ? 0 : 1, h->perm.p, (MODE & 1) ? xT : nullptr,
-        (MODE & 2) ? vP : nullptr, h->p, h->t, y);
+    launch_sweep(k_bilu_bwd_chain<NB, V, C>, grid_for(sw * 32, kChainThreads), kChainThreads,
+                 h->stream, pdl, s0, s1, h->st_first.p, h->st_len.p, h->fdp.p, h->fshi.p,
+                 h->fpos.p, F.fv, F.fdinv, F.cG, h->cflag.p, F.w, bjac ? 0 : 1, h->perm.p,
+                 (MODE & 1) ? xT : nullptr, (MODE & 2) ? vP : nullptr, h->p, h->t, y);
     MSS_LAUNCH_CK("k_bilu_bwd_chain");
   }
 }

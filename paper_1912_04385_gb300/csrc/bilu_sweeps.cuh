@@ -11,6 +11,18 @@
 namespace mss {
 namespace dev {
 
+// Programmatic dependent launch: a sweep kernel launched with the
+// programmatic-serialization attribute may start while the previous kernel of
+// its stream still runs. pdl_wait() blocks until that kernel has completed and
+// its writes are visible (it returns at once in a kernel launched without
+// the attribute); pdl_trigger(), issued only after the wait, lets the next
+// such kernel start, so that what a kernel reads before its own wait is never
+// newer than its predecessor's predecessor.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ int warp_max(int v) {
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
@@ -33,7 +45,7 @@ __device__ __forceinline__ void fwd_par(long long warp, int q0, int q1,
                                         const int* __restrict__ fcell, const V* __restrict__ fv,
                                         const C* __restrict__ fcs, const double* __restrict__ r,
                                         const C* __restrict__ xT, const C* __restrict__ vP,
-                                        C* __restrict__ w, int lower) {
+                                        C* __restrict__ w, int lower, int wait_first) {
   constexpr int RPW = 32 / NB;
   constexpr int B2 = NB * NB;
   const int lane = threadIdx.x & 31;
@@ -42,6 +54,9 @@ __device__ __forceinline__ void fwd_par(long long warp, int q0, int q1,
   if (sub >= RPW || qq >= q1) return;
   const int q = (int)qq;
   const int cell = perm[q];
+  // the u terms read r and the earlier stages' results, which only the
+  // first colour's predecessor may still be writing (wait_first)
+  if (wait_first) pdl_wait();
   C acc = (C)r[(size_t)cell * NB + comp];
   const int b = frp[q], e = frp[q + 1];
   if (MODE) {
@@ -52,6 +67,8 @@ __device__ __forceinline__ void fwd_par(long long warp, int q0, int q1,
       if (MODE & 2) acc -= cs[NB + comp] * vP[j];
     }
   }
+  if (!wait_first) pdl_wait();
+  pdl_trigger();
   if (lower) {
     const int d = fslo[q];
     for (int f = b; f < d; ++f) {
@@ -115,12 +132,17 @@ __device__ __forceinline__ void fwd_chain(long long warp, int s0, int s1,
 #pragma unroll
     for (int c = 0; c < NB; ++c) mq[u][c] = 0;
     if (u < len) {
-      tq[u] = wl[u * NB];
       fq[u] = fl[u];
 #pragma unroll
       for (int c = 0; c < NB; ++c) mq[u][c] = cvt<C>(ml[u * B2 + c]);
     }
   }
+  // the factor data above; w only after the previous sweep kernel
+  pdl_wait();
+#pragma unroll
+  for (int u = 0; u < D; ++u)
+    if (u < len) tq[u] = wl[u * NB];
+  pdl_trigger();
   C prev = 0;                               // component comp of w_{q-1}
   auto step = [&](int it, C& t, C (&m)[NB], int& f) {
     // this row's values, then the refill two rows ahead is issued before the
@@ -179,6 +201,8 @@ __device__ __forceinline__ void bwd_par(long long warp, int q0, int q1,
   const long long qq = q0 + warp * RPW + sub;
   const bool on = sub < RPW && qq < q1;
   const int q = on ? (int)qq : q0;
+  pdl_wait();
+  pdl_trigger();
   C acc = 0;
   if (on) {
     acc = w[(size_t)q * NB + comp];
@@ -237,6 +261,8 @@ __device__ __forceinline__ void bwd_chain(long long warp, int s0, int s1,
   const int base = sub * NB;
   const unsigned gmask = ((1u << NB) - 1u) << base;   // the strip's lanes
   if (!upper) {
+    pdl_wait();
+    pdl_trigger();
     for (int it = 0; it < maxlen; ++it) {
       const bool on = it < len;
       const int q = on ? first + it : 0;
@@ -272,12 +298,16 @@ __device__ __forceinline__ void bwd_chain(long long warp, int s0, int s1,
     for (int c = 0; c < NB; ++c) mq[u][c] = 0;
     if (u < len) {
       const int r = len - 1 - u;
-      tq[u] = wl[r * NB];
       fq[u] = fl[r];
 #pragma unroll
       for (int c = 0; c < NB; ++c) mq[u][c] = cvt<C>(gl[r * B2 + c]);
     }
   }
+  pdl_wait();
+#pragma unroll
+  for (int u = 0; u < D; ++u)
+    if (u < len) tq[u] = wl[(len - 1 - u) * NB];
+  pdl_trigger();
   C nxt = 0;                                // component comp of x_{q+1}
   auto step = [&](int it, C& t, C (&m)[NB], int& f) {
     const int r = len - 1 - it;

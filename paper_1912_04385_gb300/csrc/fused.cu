@@ -139,7 +139,7 @@ struct BLast {
       case B_FWD_PAR:
         dev::fwd_par<NB, MODE, double, double>(warp, p.q0, p.q1, p.perm, p.frp, p.fslo, p.fpos,
                                                p.fcell, p.fv, p.fcs, p.r, p.xT, p.vP, p.w,
-                                               p.lower);
+                                               p.lower, 1);
         break;
       case B_FWD_CHAIN:
         dev::fwd_chain<NB, double, double>(warp, p.s0, p.s1, p.st_first, p.st_len, p.fslo, p.fdp,
