@@ -189,8 +189,57 @@ __global__ void k_pmis_finalize(int n, const int* __restrict__ srp, const int* _
   cf[i] = c;
 }
 
-__device__ __forceinline__ bool opposite_sign(double akk, double akm) {
-  return akk < 0.0 ? akm > 0.0 : akm < 0.0;
+// The interpolation kernels are bound by the FP64 pipe, which executes a
+// warp's instruction whatever the number of its active lanes (a thread per row
+// leaves few lanes active in the inner loops). So their inner loops test
+// signs on the bits (integer pipe) and share one reciprocal among the
+// quotients of one divisor; both give the bits of the plain expressions.
+//
+// sign_of(x): -1 when x < 0.0, +1 when x > 0.0, 0 for zeros and NaN (the
+// values both comparisons reject). opposite(sign_of(akk), akm) is the test
+// "akm has the sign opposite to akk's", akk < 0.0 ? akm > 0.0 : akm < 0.0.
+__device__ __forceinline__ int sign_of(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = u & 0x7fffffffffffffffULL;
+  if (mag == 0ULL || mag > 0x7ff0000000000000ULL) return 0;
+  return (u >> 63) ? -1 : 1;
+}
+__device__ __forceinline__ bool opposite(int sk, double akm) {
+  return sign_of(akm) == (sk < 0 ? 1 : -1);
+}
+
+// a / b, correctly rounded, from y = RN(1/b) computed once per divisor:
+// q0 = RN(a y) is within 1.5 ulp of a/b; one correction with the remainder,
+// q1 = RN(q0 + RN(a - b q0) y), is within one ulp; then r = a - b q1 is exact
+// and RN(q1 + r y) = RN(a/b) (Markstein's theorem: P. W. Markstein,
+// "Computation of elementary functions on the IBM RISC System/6000
+// processor", IBM J. Res. Develop. 34(1), 1990; the FMA division sequences of
+// Cornea, Harrison and Tang). The theorem needs every quantity normal: an
+// operand with a binary exponent outside [-400, 400] (zeros, subnormals,
+// infinities and NaN included) takes the division itself. The products are
+// explicit FMAs, so -fmad=false leaves them as written.
+struct Recip {
+  double b, y;
+  bool fast;
+};
+__device__ __forceinline__ bool mid_exponent(double x) {
+  const unsigned e = (unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffu;
+  return e >= 1023u - 400u && e <= 1023u + 400u;
+}
+__device__ __forceinline__ Recip recip(double b) {
+  Recip d;
+  d.b = b;
+  d.fast = mid_exponent(b);
+  d.y = d.fast ? 1.0 / b : 0.0;
+  return d;
+}
+__device__ __forceinline__ double quot(double a, const Recip& d) {
+  if (!d.fast || !mid_exponent(a)) return a / d.b;
+  double q = __dmul_rn(a, d.y);
+  double r = __fma_rn(-q, d.b, a);
+  q = __fma_rn(r, d.y, q);
+  r = __fma_rn(-q, d.b, a);
+  return __fma_rn(r, d.y, q);
 }
 
 // Direct classical interpolation with distribution of strong F couplings
@@ -238,6 +287,7 @@ __global__ void k_interp(int n, const int* __restrict__ rp, const int* __restric
       double akk = 0.0;
       for (int f = rp[j]; f < rp[j + 1]; ++f)
         if (ci[f] == j) akk = v[f];
+      const int sk = sign_of(akk);
       double sigma = 0.0;
       for (int f = rp[j]; f < rp[j + 1]; ++f) {
         int m = ci[f];
@@ -245,20 +295,21 @@ __global__ void k_interp(int n, const int* __restrict__ rp, const int* __restric
         double akm = v[f];
         bool inC = false;
         for (int q = 0; q < nC; ++q) if (cset[q] == m) { inC = true; break; }
-        if (inC && opposite_sign(akk, akm)) sigma = sigma + akm;
+        if (inC && opposite(sk, akm)) sigma = sigma + akm;
       }
       if (sigma == 0.0) {
         d = d + aik;
       } else {
+        const Recip rs = recip(sigma);
         for (int f = rp[j]; f < rp[j + 1]; ++f) {
           int m = ci[f];
           if (m == j) continue;
           double akm = v[f];
-          if (!opposite_sign(akk, akm)) continue;
+          if (!opposite(sk, akm)) continue;
           for (int q = 0; q < nC; ++q)
             if (cset[q] == m) {
               double tq = aik * akm;
-              tq = tq / sigma;
+              tq = quot(tq, rs);
               num[q] = num[q] + tq;
               break;
             }
@@ -269,7 +320,11 @@ __global__ void k_interp(int n, const int* __restrict__ rp, const int* __restric
     }
   }
   if (d == 0.0 || !isfinite(d)) { plen[i] = 0; return; }
-  for (int q = 0; q < nC; ++q) num[q] = -num[q] / d;
+  {
+    // -(num / d): RN(-x) = -RN(x)
+    const Recip rd = recip(d);
+    for (int q = 0; q < nC; ++q) num[q] = -quot(num[q], rd);
+  }
   for (int q = 0; q < nC; ++q) keep[q] = 1;
   if (maxel > 0 && nC > maxel) {
     double total = 0.0;
@@ -405,6 +460,7 @@ k_interp_warp(int n, const int* __restrict__ rp, const int* __restrict__ ci,
         const double vf = isd ? v[f] : 0.0;
         if (m) akk = __shfl_sync(FULL, vf, 31 - __clz(m));
       }
+      const int sk = sign_of(akk);
       double sigma = 0.0;
       for (int f0 = fb; f0 < fe; f0 += 32) {
         const int f = f0 + lane;
@@ -413,7 +469,7 @@ k_interp_warp(int n, const int* __restrict__ rp, const int* __restrict__ ci,
         if (f < fe) {
           const int mm = ci[f];
           akm = v[f];
-          add = mm != jj && find_c(cset, nC, mm) >= 0 && opposite_sign(akk, akm);
+          add = mm != jj && find_c(cset, nC, mm) >= 0 && opposite(sk, akm);
         }
         unsigned am = __ballot_sync(FULL, add);
         while (am) {
@@ -425,16 +481,17 @@ k_interp_warp(int n, const int* __restrict__ rp, const int* __restrict__ ci,
       if (sigma == 0.0) {
         d = d + aik;
       } else {
+        const Recip rs = recip(sigma);
         for (int f0 = fb; f0 < fe; f0 += 32) {
           const int f = f0 + lane;
           if (f < fe) {
             const int mm = ci[f];
             const double akm = v[f];
-            if (mm != jj && opposite_sign(akk, akm)) {
+            if (mm != jj && opposite(sk, akm)) {
               const int q = find_c(cset, nC, mm);
               if (q >= 0) {
                 double tq = aik * akm;
-                tq = tq / sigma;
+                tq = quot(tq, rs);
                 num[q] = num[q] + tq;
               }
             }
@@ -450,7 +507,10 @@ k_interp_warp(int n, const int* __restrict__ rp, const int* __restrict__ ci,
     plen[i] = 0;
     return;
   }
-  for (int q = 0; q < nC; ++q) num[q] = -num[q] / d;
+  {
+    const Recip rd = recip(d);
+    for (int q = 0; q < nC; ++q) num[q] = -quot(num[q], rd);
+  }
   for (int q = 0; q < nC; ++q) keep[q] = 1;
   if (maxel > 0 && nC > maxel) {
     double total = 0.0;
@@ -508,40 +568,91 @@ __global__ void k_spgemm_count(int n, const int* __restrict__ xrp, const int* __
 
 // contributions x_ik y_kj accumulate in ascending k, then ascending j in row
 // k; the row is kept sorted by column in its scratch segment
-__global__ void k_spgemm_accum(int n, const int* __restrict__ xrp, const int* __restrict__ xci,
-                               const double* __restrict__ xv, const int* __restrict__ yrp,
-                               const int* __restrict__ yci, const double* __restrict__ yv,
-                               const int* __restrict__ off, int* __restrict__ sc_ci,
-                               double* __restrict__ sc_v, int* __restrict__ ulen) {
+// Row i of C = X Y: the products x_ik y_kj in order (k ascending, then the
+// entries of row k), each added to its column's entry, the row's columns kept
+// sorted by insertion. With SHARED the row's list lives in shared memory
+// (kAccumS entries per thread, entry q of thread t at q * kAccumT + t) until
+// it outgrows it, then moves to the row's scratch segment [off[i], off[i+1])
+// and continues there; without it, the list is in the scratch segment from
+// the start (rows of few products: the shared copy costs occupancy and saves
+// little). Either way every entry is the same sum in the same order; the
+// result ends in the scratch segment.
+constexpr int kAccumT = 128;   // threads per block (the shared layout's stride)
+constexpr int kAccumS = 24;    // entries per thread in shared memory
+
+template <bool SHARED>
+__global__ void __launch_bounds__(kAccumT)
+k_spgemm_accum(int n, const int* __restrict__ xrp, const int* __restrict__ xci,
+               const double* __restrict__ xv, const int* __restrict__ yrp,
+               const int* __restrict__ yci, const double* __restrict__ yv,
+               const int* __restrict__ off, int* __restrict__ sc_ci, double* __restrict__ sc_v,
+               int* __restrict__ ulen) {
+  __shared__ int s_ci[SHARED ? kAccumS * kAccumT : 1];
+  __shared__ double s_v[SHARED ? kAccumS * kAccumT : 1];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int* cc = sc_ci + off[i];
-  double* cv = sc_v + off[i];
+  int* gc = sc_ci + off[i];
+  double* gv = sc_v + off[i];
+  int* lc = s_ci + threadIdx.x;
+  double* lv = s_v + threadIdx.x;
   int cnt = 0;
+  bool spilled = !SHARED;
   for (int k = xrp[i]; k < xrp[i + 1]; ++k) {
     int r = xci[k];
     double x = xv[k];
     for (int f = yrp[r]; f < yrp[r + 1]; ++f) {
       int j = yci[f];
       double prod = x * yv[f];
+      if (!spilled) {
+        int lo = 0, hi = cnt;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (lc[mid * kAccumT] < j) lo = mid + 1; else hi = mid;
+        }
+        if (lo < cnt && lc[lo * kAccumT] == j) {
+          lv[lo * kAccumT] = lv[lo * kAccumT] + prod;
+          continue;
+        }
+        if (cnt < kAccumS) {
+          for (int q = cnt; q > lo; --q) {
+            lc[q * kAccumT] = lc[(q - 1) * kAccumT];
+            lv[q * kAccumT] = lv[(q - 1) * kAccumT];
+          }
+          lc[lo * kAccumT] = j;
+          lv[lo * kAccumT] = 0.0 + prod;
+          ++cnt;
+          continue;
+        }
+        // the list outgrows its shared slots: on in the scratch segment
+        for (int q = 0; q < cnt; ++q) {
+          gc[q] = lc[q * kAccumT];
+          gv[q] = lv[q * kAccumT];
+        }
+        spilled = true;
+      }
       int lo = 0, hi = cnt;
       while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if (cc[mid] < j) lo = mid + 1; else hi = mid;
+        if (gc[mid] < j) lo = mid + 1; else hi = mid;
       }
-      if (lo < cnt && cc[lo] == j) {
-        cv[lo] = cv[lo] + prod;
+      if (lo < cnt && gc[lo] == j) {
+        gv[lo] = gv[lo] + prod;
       } else {
         for (int q = cnt; q > lo; --q) {
-          cc[q] = cc[q - 1];
-          cv[q] = cv[q - 1];
+          gc[q] = gc[q - 1];
+          gv[q] = gv[q - 1];
         }
-        cc[lo] = j;
-        cv[lo] = 0.0 + prod;
+        gc[lo] = j;
+        gv[lo] = 0.0 + prod;
         ++cnt;
       }
     }
   }
+  if (!spilled)
+    for (int q = 0; q < cnt; ++q) {
+      gc[q] = lc[q * kAccumT];
+      gv[q] = lv[q * kAccumT];
+    }
   ulen[i] = cnt;
 }
 
@@ -585,8 +696,15 @@ void sparse_product(Handle* h, int n, const int* xrp, const int* xci, const doub
   int tot = read_int(h, off.p + n);
   DBuf<int> sc_ci(h, tot > 0 ? tot : 1);
   DBuf<double> sc_v(h, tot > 0 ? tot : 1);
-  k_spgemm_accum<<<grid_for(n, 128), 128, 0, h->stream>>>(n, xrp, xci, xv, yrp, yci, yv, off.p,
-                                                          sc_ci.p, sc_v.p, ulen.p);
+  // the shared-memory lists for rows of many products on average (measured
+  // at 1024^2: R (A P) 270 -> 157 us on level 0; A P with about 12 products
+  // a row 142 -> 180 us, so such products keep the scratch lists)
+  if (tot > 16LL * n)
+    k_spgemm_accum<true><<<grid_for(n, kAccumT), kAccumT, 0, h->stream>>>(
+        n, xrp, xci, xv, yrp, yci, yv, off.p, sc_ci.p, sc_v.p, ulen.p);
+  else
+    k_spgemm_accum<false><<<grid_for(n, kAccumT), kAccumT, 0, h->stream>>>(
+        n, xrp, xci, xv, yrp, yci, yv, off.p, sc_ci.p, sc_v.p, ulen.p);
   MSS_LAUNCH_CK("k_spgemm_accum");
   crp.reset(h, n + 1);
   exclusive_scan(h, ulen.p, crp.p, n);
@@ -708,16 +826,21 @@ int classical_interp(Handle* h, int n, int nnz, const int* rp, const int* ci, co
 void level_prepare(Handle* h, Level& L) {
   int n = L.n;
   L.dinv.reset(h, n);
-  DBuf<unsigned long long> bound(h, 1);
-  DBuf<int> bad(h, 1);
-  MSS_CK(cudaMemsetAsync(bound.p, 0, sizeof(unsigned long long), h->stream));
-  fill_int(h, bad.p, 0x7fffffff, 1);
+  // the bound's bits and the first row with a zero diagonal in one word pair,
+  // read back together (one host synchronisation per level)
+  DBuf<unsigned long long> res(h, 2);
+  unsigned long long* bound = res.p;
+  int* bad = reinterpret_cast<int*>(res.p + 1);
+  MSS_CK(cudaMemsetAsync(res.p, 0, 2 * sizeof(unsigned long long), h->stream));
+  fill_int(h, bad, 0x7fffffff, 1);
   k_dinv_bound<<<grid_for(n, 256), 256, 0, h->stream>>>(n, L.rp.p, L.ci.p, L.v.p, L.dinv.p,
-                                                        bound.p, bad.p);
+                                                        bound, bad);
   MSS_LAUNCH_CK("k_dinv_bound");
-  unsigned long long bits = 0;
-  read_back(h, &bits, bound.p, sizeof(bits));
-  int badrow = read_int(h, bad.p);
+  unsigned long long both[2] = {0, 0};
+  read_back(h, both, res.p, sizeof(both));
+  const unsigned long long bits = both[0];
+  int badrow = 0;
+  std::memcpy(&badrow, &both[1], sizeof(int));
   if (badrow != 0x7fffffff)
     fail(MSS_ERR_AMG, "AMG level of size " + std::to_string(n) + ": zero diagonal in row " +
                           std::to_string(badrow));
