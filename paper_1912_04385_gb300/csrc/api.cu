@@ -182,34 +182,35 @@ void numeric_setup(Handle& H, const double* vals, bool ordering, std::vector<DBu
   const mss_options& o = H.opt;
   const int N = H.N, nnzb = H.nnzb;
   Handle* h = &H;
+  // B_PP and C_TT (the hierarchies' level 0) and the P-T couplings of CPTR3
+  // are written by the scaling kernel beside Abar
+  DBuf<double> bpp, ctt, bee;
   {
     TraceScope ts(h, TR_SETUP_SCALE);
-    // left scaling (Eq. splitPrec1 with Eq. CPR or Eqs. CPTR31/CPTR32)
-    build_scaling(h, vals, H.col_major);
+    Extract ex;
+    if (o.scheme == MSS_CPR || o.scheme == MSS_CPTR3) {
+      bpp.reset(h, nnzb);
+      ex.pp = bpp.p;
+    }
     if (o.scheme == MSS_CPTR3) {
       if (H.apt.n != (size_t)nnzb) H.apt.reset(h, nnzb);
       if (H.atp.n != (size_t)nnzb) H.atp.reset(h, nnzb);
-      extract_subsystem(h, -1, H.apt.p);
-      extract_subsystem(h, -2, H.atp.p);
+      ctt.reset(h, nnzb);
+      ex.tt = ctt.p;
+      ex.pt = H.apt.p;
+      ex.tp = H.atp.p;
     }
+    // left scaling (Eq. splitPrec1 with Eq. CPR or Eqs. CPTR31/CPTR32)
+    build_scaling(h, vals, H.col_major, ex);
   }
   // The scalar subsystems' AMG hierarchies and the last-stage factorisation
   // depend only on Abar: the hierarchies are built by worker threads on
   // their own streams while this thread factorises on the handle's stream.
   {
     TraceScope ts(h, TR_SETUP_AMG);
-    DBuf<double> bpp, ctt, bee;
-    if (o.scheme == MSS_CPR || o.scheme == MSS_CPTR3) {
-      bpp.reset(h, nnzb);
-      extract_subsystem(h, H.p, bpp.p);           // B_PP
-    }
     if (o.scheme == MSS_CPTR) {
       bee.reset(h, (size_t)4 * nnzb);
       extract_pair(h, bee.p);                     // B_ee (Eq. CPTR1)
-    }
-    if (o.scheme == MSS_CPTR3) {
-      ctt.reset(h, nnzb);
-      extract_subsystem(h, H.t, ctt.p);           // C_TT
     }
     // MSS_SETUP_TIMES=1 prints the phases' host times (diagnostics)
     static const bool times = std::getenv("MSS_SETUP_TIMES") != nullptr;

@@ -340,10 +340,17 @@ void copy_dev(Handle* h, void* dst, const void* src, size_t bytes);
 
 // setup_scale.cu
 void validate_pattern(Handle* h, const int* rp, const int* ci, int N, int nnzb, int* diag);
-void build_scaling(Handle* h, const double* vals, bool col_major);
+// entries of the scaled blocks written beside Abar, one per block (any
+// pointer may be null): pp = Abar[p][p] (B_PP), tt = Abar[t][t] (C_TT),
+// pt = Abar[p][t], tp = Abar[t][p]
+struct Extract {
+  double* pp = nullptr;
+  double* tt = nullptr;
+  double* pt = nullptr;
+  double* tp = nullptr;
+};
+void build_scaling(Handle* h, const double* vals, bool col_major, const Extract& ex = Extract{});
 void scale_vector(Handle* h, const double* b, double* bbar);
-// var >= 0: Abar[var][var] per block; var = -1: Abar[p][t]; var = -2: Abar[t][p]
-void extract_subsystem(Handle* h, int var, double* out);
 // B_ee of CPTR: the 2 x 2 block Abar[(p, t), (p, t)] of every block (4 per block)
 void extract_pair(Handle* h, double* out);
 

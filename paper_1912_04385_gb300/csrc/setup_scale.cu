@@ -192,11 +192,14 @@ __global__ void k_block_rows(int N, const int* __restrict__ rp, int* __restrict_
 // not unit vectors (p, and t for CPTR3) give Abar_ij[r][c] = sum_k W_i[r][k]
 // J_ij[k][c] (ascending k); the other rows are copied. Every lane of a warp
 // does the same FP64 work (FP64 issue is the bound of this kernel on GB300).
+// The threads of columns p and t also write the entries of the scalar
+// subsystems (Extract), so no later pass reads one entry per 8 nb^2 bytes.
 template <int NB>
 __global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict__ brow,
                           long long nnzb, int p, int t, int scheme, int col_major,
                           const double* __restrict__ wrows, double* __restrict__ abar,
-                          const int* __restrict__ diag, const double* __restrict__ dcopy) {
+                          const int* __restrict__ diag, const double* __restrict__ dcopy,
+                          Extract ex) {
   constexpr int B2 = NB * NB;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= nnzb * NB) return;
@@ -213,17 +216,29 @@ __global__ void k_apply_w(const double* __restrict__ vals, const int* __restrict
   double* dst = abar + (size_t)e * B2 + c;
 #pragma unroll
   for (int r = 0; r < NB; ++r) dst[r * NB] = col[r];
-  if (scheme == 2) return;
-  const double* w = wrows + (size_t)brow[e] * 2 * NB;
-  double acc = 0.0;
+  double rowp = col[p], rowt = col[t];   // the final entries (p, c) and (t, c)
+  if (scheme != 2) {
+    const double* w = wrows + (size_t)brow[e] * 2 * NB;
+    double acc = 0.0;
 #pragma unroll
-  for (int k = 0; k < NB; ++k) acc = fma(w[k], col[k], acc);
-  dst[p * NB] = acc;
-  if (scheme == 0 || scheme == 3) {
-    double acc2 = 0.0;
+    for (int k = 0; k < NB; ++k) acc = fma(w[k], col[k], acc);
+    dst[p * NB] = acc;
+    rowp = acc;
+    if (scheme == 0 || scheme == 3) {
+      double acc2 = 0.0;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) acc2 = fma(w[NB + k], col[k], acc2);
-    dst[t * NB] = acc2;
+      for (int k = 0; k < NB; ++k) acc2 = fma(w[NB + k], col[k], acc2);
+      dst[t * NB] = acc2;
+      rowt = acc2;
+    }
+  }
+  if (c == p) {
+    if (ex.pp) ex.pp[e] = rowp;
+    if (ex.tp) ex.tp[e] = rowt;
+  }
+  if (c == t) {
+    if (ex.tt) ex.tt[e] = rowt;
+    if (ex.pt) ex.pt[e] = rowp;
   }
 }
 
@@ -234,17 +249,6 @@ __global__ void k_scale_vec(const double* __restrict__ b, int N, int p, int t, i
                            wrows, out);
 }
 
-__global__ void k_extract(const double* __restrict__ abar, int nnzb, int nb, int var,
-                          double* __restrict__ out) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nnzb) out[e] = abar[(size_t)e * nb * nb + var * nb + var];
-}
-
-__global__ void k_extract_pt(const double* __restrict__ abar, int nnzb, int nb, int p, int t,
-                             double* __restrict__ out) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nnzb) out[e] = abar[(size_t)e * nb * nb + p * nb + t];
-}
 
 // B_ee of CPTR: out[4e + 2k + l] = Abar_e[e_k][e_l], e = (p, t)
 __global__ void k_extract_pair(const double* __restrict__ abar, int nnzb, int nb, int p, int t,
@@ -259,7 +263,7 @@ __global__ void k_extract_pair(const double* __restrict__ abar, int nnzb, int nb
 }
 
 template <int NB>
-void build_scaling_nb(Handle* h, const double* vals, bool col_major) {
+void build_scaling_nb(Handle* h, const double* vals, bool col_major, const Extract& ex) {
   int N = h->N;
   int scheme = h->opt.scheme;
   DBuf<int> flag(h, 1);
@@ -285,7 +289,7 @@ void build_scaling_nb(Handle* h, const double* vals, bool col_major) {
   long long tot = (long long)h->nnzb * NB;
   k_apply_w<NB><<<grid_for(tot, 256), 256, 0, h->stream>>>(vals, brow.p, h->nnzb, h->p, h->t,
                                                            scheme, col_major, h->wrows.p,
-                                                           h->abar.p, h->diag.p, dcopy.p);
+                                                           h->abar.p, h->diag.p, dcopy.p, ex);
   MSS_LAUNCH_CK("k_apply_w");
 }
 
@@ -314,24 +318,12 @@ void validate_pattern(Handle* h, const int* rp, const int* ci, int N, int nnzb, 
   }
 }
 
-void build_scaling(Handle* h, const double* vals, bool col_major) {
-  MSS_NB_DISPATCH(h->nb, build_scaling_nb<NB>(h, vals, col_major));
+void build_scaling(Handle* h, const double* vals, bool col_major, const Extract& ex) {
+  MSS_NB_DISPATCH(h->nb, build_scaling_nb<NB>(h, vals, col_major, ex));
 }
 
 void scale_vector(Handle* h, const double* b, double* bbar) {
   MSS_NB_DISPATCH(h->nb, scale_vector_nb<NB>(h, b, bbar));
-}
-
-void extract_subsystem(Handle* h, int var, double* out) {
-  if (var >= 0) {
-    k_extract<<<grid_for(h->nnzb, 256), 256, 0, h->stream>>>(h->abar.p, h->nnzb, h->nb, var, out);
-    MSS_LAUNCH_CK("k_extract");
-  } else {
-    int row = var == -1 ? h->p : h->t, col = var == -1 ? h->t : h->p;
-    k_extract_pt<<<grid_for(h->nnzb, 256), 256, 0, h->stream>>>(h->abar.p, h->nnzb, h->nb, row,
-                                                                col, out);
-    MSS_LAUNCH_CK("k_extract_pt");
-  }
 }
 
 void extract_pair(Handle* h, double* out) {
