@@ -69,9 +69,13 @@ __global__ void k_fill_strong(int n, const int* __restrict__ rp, const int* __re
     if (strong[k]) sci[q++] = ci[k];
 }
 
-__global__ void k_count_cols(int nnz, const int* __restrict__ ci, int* __restrict__ cnt) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nnz) atomicAdd(&cnt[ci[e]], 1);
+// entries per column of an n-row CSR pattern (rows' ranges only: entries past
+// rp[n] in an over-sized array are never read)
+__global__ void k_count_cols(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                             int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) atomicAdd(&cnt[ci[k]], 1);
 }
 
 // scatter of a CSR pattern (and optional values) into its transpose; the
@@ -716,12 +720,14 @@ void sparse_product(Handle* h, int n, const int* xrp, const int* xci, const doub
   MSS_LAUNCH_CK("k_seg_copy");
 }
 
+// the transpose (m rows) of an n-row CSR pattern with at most nnz entries
+// (nnz sizes the output; the entries are those of the rows' ranges)
 void transpose(Handle* h, int n, int m, const int* rp, const int* ci, const double* v, int nnz,
                DBuf<int>& trp, DBuf<int>& tci, DBuf<double>* tv) {
   DBuf<int> cnt(h, m > 0 ? m : 1), fill(h, m > 0 ? m : 1);
   fill_int(h, cnt.p, 0, m);
-  if (nnz > 0) {
-    k_count_cols<<<grid_for(nnz, 256), 256, 0, h->stream>>>(nnz, ci, cnt.p);
+  if (nnz > 0 && n > 0) {
+    k_count_cols<<<grid_for(n, 256), 256, 0, h->stream>>>(n, rp, ci, cnt.p);
     MSS_LAUNCH_CK("k_count_cols");
   }
   trp.reset(h, m + 1);
@@ -753,12 +759,13 @@ void strength_graph(Handle* h, int n, int nnz, const int* rp, const int* ci, con
                                                       scount.p);
   MSS_LAUNCH_CK("k_strength");
   exclusive_scan(h, scount.p, S.srp.p, n);
-  int ns = read_int(h, S.srp.p + n);
-  S.sci.reset(h, ns > 0 ? ns : 1);
+  // S has at most nnz entries: sized by that bound, no read-back (every
+  // kernel on S reads the rows' ranges only)
+  S.sci.reset(h, nnz > 0 ? nnz : 1);
   k_fill_strong<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, ci, S.strong.p, S.srp.p,
                                                          S.sci.p);
   MSS_LAUNCH_CK("k_fill_strong");
-  transpose(h, n, n, S.srp.p, S.sci.p, nullptr, ns, S.strp, S.stci, nullptr);
+  transpose(h, n, n, S.srp.p, S.sci.p, nullptr, nnz, S.strp, S.stci, nullptr);
 }
 
 // PMIS C/F split (1 = C) of AMG level `level`; |S_i^T| are the row lengths
@@ -773,7 +780,9 @@ void pmis_split(Handle* h, int n, const Strength& S, uint64_t seed, int level, D
   k_pmis_init<<<grid_for(n, 256), 256, 0, h->stream>>>(n, tcount.p, seed, level, lam.p, state.p,
                                                        und.p);
   MSS_LAUNCH_CK("k_pmis_init");
-  int undecided = read_int(h, und.p);
+  // the first three rounds run without a read-back (rounds with nothing
+  // undecided change nothing)
+  int undecided = 1;
   int rounds = 0;
   while (undecided > 0) {
     // three synchronous rounds per read-back: a round with nothing
@@ -798,9 +807,11 @@ void pmis_split(Handle* h, int n, const Strength& S, uint64_t seed, int level, D
 
 // Classical interpolation P (n x nc, CSR) for the split cf with coarse
 // indices cidx; returns nnz(P)
+// (with nc_dev, *nc_out receives *nc_dev in the same read-back as nnz(P))
 int classical_interp(Handle* h, int n, int nnz, const int* rp, const int* ci, const double* v,
                      const unsigned char* strong, const int* cf, const int* cidx, int maxel,
-                     DBuf<int>& prp, DBuf<int>& pci, DBuf<double>& pv) {
+                     DBuf<int>& prp, DBuf<int>& pci, DBuf<double>& pv,
+                     const int* nc_dev = nullptr, int* nc_out = nullptr) {
   DBuf<int> scr_ci(h, nnz), scr_k(h, nnz), plen(h, n);
   DBuf<double> scr_v(h, nnz);
   if (n <= 65536 && nnz > 8LL * n) {   // few, long rows: one warp per row
@@ -814,7 +825,16 @@ int classical_interp(Handle* h, int n, int nnz, const int* rp, const int* ci, co
   }
   prp.reset(h, n + 1);
   exclusive_scan(h, plen.p, prp.p, n);
-  const int nnzP = read_int(h, prp.p + n);
+  int nnzP = 0;
+  if (nc_dev) {
+    const int* src[2] = {prp.p + n, nc_dev};
+    int got[2];
+    read_ints(h, src, got, 2);
+    nnzP = got[0];
+    *nc_out = got[1];
+  } else {
+    nnzP = read_int(h, prp.p + n);
+  }
   pci.reset(h, nnzP > 0 ? nnzP : 1);
   pv.reset(h, nnzP > 0 ? nnzP : 1);
   k_seg_copy<<<grid_for(n, 128), 128, 0, h->stream>>>(n, rp, scr_ci.p, scr_v.p, prp.p, pci.p,
@@ -1097,14 +1117,21 @@ void amg_build(Handle* h, Hierarchy& H, int n0, int nnz0, const int* rp0, const 
     }
     DBuf<int> cidx(h, n + 1);
     exclusive_scan(h, L.cf.p, cidx.p, n);
-    int nc = read_int(h, cidx.p + n);
+    // the interpolation is formed before the coarse size is known (one
+    // read-back for both); a split with no C point or no F point makes no
+    // level, and its P is dropped
+    int nc = 0;
+    L.nnzP = classical_interp(h, n, nnz, rp, ci, v, S.strong.p, L.cf.p, cidx.p,
+                              o.interp_max_elems, L.prp, L.pci, L.pv, cidx.p + n, &nc);
     if (nc == 0 || nc == n) {     // coarsening stalled: this level is the coarsest
       L.cf.release();
+      L.prp.release();
+      L.pci.release();
+      L.pv.release();
+      L.nnzP = 0;
       break;
     }
     L.nc = nc;
-    L.nnzP = classical_interp(h, n, nnz, rp, ci, v, S.strong.p, L.cf.p, cidx.p,
-                              o.interp_max_elems, L.prp, L.pci, L.pv);
     if (learned && l == 0) {
       // learned weights on classical interpolation's pattern (level 0 only)
       std::unique_ptr<GnnGraph, void (*)(GnnGraph*)> g(

@@ -333,6 +333,8 @@ void read_back(Handle* h, void* dst, const void* dptr, size_t bytes);
 // synchronises the handle's stream
 void write_to_device(Handle* h, void* dptr, const void* src, size_t bytes);
 int read_int(Handle* h, const int* dptr);                         // synchronises
+// count ints from device addresses dptrs[k] into out[k], one synchronisation
+void read_ints(Handle* h, const int* const* dptrs, int* out, int count);
 double read_double(Handle* h, const double* dptr);
 void fill_int(Handle* h, int* p, int value, long long n);
 void fill_double(Handle* h, double* p, double value, long long n);

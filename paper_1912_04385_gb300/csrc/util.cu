@@ -348,6 +348,14 @@ void write_to_device(Handle* h, void* dptr, const void* src, size_t bytes) {
   MSS_CK(cudaStreamSynchronize(h->stream));   // the staging word is reused
 }
 
+void read_ints(Handle* h, const int* const* dptrs, int* out, int count) {
+  int* s = static_cast<int*>(staging(h, sizeof(int) * (size_t)count));
+  for (int k = 0; k < count; ++k)
+    MSS_CK(cudaMemcpyAsync(s + k, dptrs[k], sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  MSS_CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(out, s, sizeof(int) * (size_t)count);
+}
+
 int read_int(Handle* h, const int* dptr) {
   int v = 0;
   read_back(h, &v, dptr, sizeof(int));
